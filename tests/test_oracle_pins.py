@@ -1,0 +1,418 @@
+"""Pins of the CPU oracle against facts fixed outside it (no GPU needed).
+
+Each test checks an oracle function against mathematics or published data
+that the oracle itself does not compute: sympy's primality test, the O(N^2)
+definition of the negacyclic transform, pure-Python schoolbook products over
+the integers, Philox known-answer vectors, a sympy evaluation of the Gaussian
+CDT, Python big-integer rounding of q*m/t, and brute-force integer matrix
+products.  A dropped term, a wrong sign, index or transposition anywhere in
+the oracle fails at least one of them.
+"""
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+import sympy
+
+import oracle as O
+from oracle.core import lib, p32, p64, pi64
+from paper_2305_18396_gb300 import synthetic as S
+
+GOLDEN = Path(__file__).with_name("golden")
+Q0, Q1, Q2 = O.DEFAULT_PRIMES
+
+
+# ------------------------------------------------------------------ primes, roots
+
+
+def test_miller_rabin_matches_sympy():
+    rng = np.random.default_rng(11)
+    cands = [int(x) | 1 for x in rng.integers(1 << 40, 1 << 62, size=300, dtype=np.uint64)]
+    cands += list(O.DEFAULT_PRIMES) + [2, 3, 4, 561, 1105, 1729, 2465, 3215031751, 2**61 - 1, 2**62 - 57]
+    cands += [q + 2 for q in O.DEFAULT_PRIMES]
+    for n in cands:
+        assert bool(lib.or_is_prime(n)) == sympy.isprime(n), n
+
+
+def test_default_primes_are_ntt_friendly():
+    for q in O.DEFAULT_PRIMES:
+        assert sympy.isprime(q)
+        assert q < 2**50
+        assert (q - 1) % (1 << 37) == 0  # q = 1 mod t, hence mod 2N for N <= 2^14
+
+
+@pytest.mark.parametrize("N", [16, 4096, 8192])
+def test_primitive_2n_root(N):
+    for q in O.DEFAULT_PRIMES:
+        psi = lib.or_primitive_2n_root(q, N)
+        assert pow(psi, N, q) == q - 1
+        assert pow(psi, 2 * N, q) == 1
+
+
+# ------------------------------------------------------------------ NTT
+
+
+def _ntt_definition(a, q, psi):
+    N = len(a)
+    return [sum(int(a[i]) * pow(psi, (2 * k + 1) * i, q) for i in range(N)) % q for k in range(N)]
+
+
+def _negacyclic_python(a, b, q=None):
+    N = len(a)
+    c = [0] * N
+    for i in range(N):
+        for j in range(N):
+            v = int(a[i]) * int(b[j])
+            if i + j < N:
+                c[i + j] += v
+            else:
+                c[i + j - N] -= v
+    return [x % q for x in c] if q else c
+
+
+@pytest.mark.parametrize("N", [2, 4, 16, 64])
+def test_ntt_matches_definition(N):
+    rng = np.random.default_rng(N)
+    for q in (Q0, Q2):
+        psi = lib.or_primitive_2n_root(q, N)
+        a = rng.integers(0, q, size=N, dtype=np.uint64)
+        f = a.copy()
+        lib.or_ntt_forward(p64(f), N, q, psi, 1)
+        assert list(map(int, f)) == _ntt_definition(a, q, psi)
+
+
+def test_ntt_of_monomial_closed_form():
+    N, q = 256, Q1
+    psi = lib.or_primitive_2n_root(q, N)
+    a = np.zeros(N, dtype=np.uint64)
+    a[1] = 1
+    lib.or_ntt_forward(p64(a), N, q, psi, 1)
+    assert list(map(int, a)) == [pow(psi, 2 * k + 1, q) for k in range(N)]
+
+
+@pytest.mark.parametrize("N", [4096, 8192])
+def test_ntt_roundtrip(N):
+    rng = np.random.default_rng(5)
+    a = rng.integers(0, Q0, size=(3, N), dtype=np.uint64)
+    f = a.copy()
+    psi = lib.or_primitive_2n_root(Q0, N)
+    lib.or_ntt_forward(p64(f), N, Q0, psi, 3)
+    assert not np.array_equal(f, a)
+    lib.or_ntt_inverse(p64(f), N, Q0, psi, 3)
+    assert np.array_equal(f, a)
+
+
+@pytest.mark.parametrize("N", [8, 32, 64])
+def test_ntt_product_is_negacyclic_product(N):
+    rng = np.random.default_rng(N + 1)
+    q = Q0
+    psi = lib.or_primitive_2n_root(q, N)
+    a = rng.integers(0, q, size=N, dtype=np.uint64)
+    b = rng.integers(0, q, size=N, dtype=np.uint64)
+    want = _negacyclic_python(a, b, q)
+    fa, fb = a.copy(), b.copy()
+    lib.or_ntt_forward(p64(fa), N, q, psi, 1)
+    lib.or_ntt_forward(p64(fb), N, q, psi, 1)
+    prod = np.array([(int(x) * int(y)) % q for x, y in zip(fa, fb)], dtype=np.uint64)
+    lib.or_ntt_inverse(p64(prod), N, q, psi, 1)
+    assert list(map(int, prod)) == want
+    c = np.zeros(N, dtype=np.uint64)
+    lib.or_negacyclic_mul_schoolbook(p64(a), p64(b), p64(c), N, q)
+    assert list(map(int, c)) == want
+
+
+# ------------------------------------------------------------------ randomness
+
+
+def _read_kat():
+    rows = []
+    for line in (GOLDEN / "philox4x32_10_kat.txt").read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            rows.append([int(x, 16) for x in line.split()])
+    return rows
+
+
+def test_philox_known_answers():
+    rows = _read_kat()
+    assert len(rows) == 3
+    for w in rows:
+        ctr = np.array(w[:4], dtype=np.uint32)
+        key = np.array(w[4:6], dtype=np.uint32)
+        out = np.zeros(4, dtype=np.uint32)
+        lib.or_philox4x32_10(p32(ctr), p32(key), p32(out))
+        assert list(map(int, out)) == w[6:]
+
+
+def test_gauss_cdt_matches_sympy():
+    B = lib.or_gauss_bound()
+    assert B == 19
+    table = np.zeros(2 * B, dtype=np.uint64)
+    lib.or_gauss_cdt(p64(table))
+    sigma = sympy.Rational(16, 5)
+    rho = [sympy.exp(-sympy.Rational(k * k) / (2 * sigma**2)) for k in range(-B, B + 1)]
+    total = sum(rho)
+    acc = 0
+    for j in range(2 * B):
+        acc += rho[j]
+        v = sympy.N(acc / total * sympy.Integer(2) ** 64, 60)
+        assert int(sympy.floor(v)) == int(table[j]), j
+
+
+def test_gauss_sampler_moments():
+    e = np.zeros(1 << 18, dtype=np.int64)
+    lib.or_sample_gauss(7, 0, e.size, pi64(e))
+    assert e.min() >= -19 and e.max() <= 19
+    assert abs(e.mean()) < 0.03
+    assert abs(e.std() - 3.2) < 0.03
+
+
+def test_ternary_and_mask_and_uniform_samplers():
+    N = 1 << 16
+    s = np.zeros(N, dtype=np.int64)
+    lib.or_sample_ternary(3, N, pi64(s))
+    counts = [(s == v).sum() for v in (-1, 0, 1)]
+    assert set(np.unique(s)) <= {-1, 0, 1}
+    assert all(abs(c - N / 3) < 0.02 * N for c in counts)
+    m = np.zeros(N, dtype=np.uint64)
+    lib.or_sample_mask(5, 9, N, 37, p64(m))
+    assert int(m.max()) < 2**37 and int(m.max()) > 2**36
+    a = np.zeros(N, dtype=np.uint64)
+    lib.or_sample_uniform(4, 2, 1, Q1, N, p64(a))
+    assert int(a.max()) < Q1 and int(a.max()) > Q1 // 2
+    # the mask draw is the low 37 bits of the first two Philox words of counter (i, obj, 4, 0)
+    ctr = np.array([17, 9, 4, 0], dtype=np.uint32)
+    key = np.array([5, 0], dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.or_philox4x32_10(p32(ctr), p32(key), p32(out))
+    assert int(m[17]) == (int(out[0]) | (int(out[1]) << 32)) & (2**37 - 1)
+
+
+# ------------------------------------------------------------------ BFV scaling
+
+
+def _find_generic_prime(N, t):
+    c = (1 << 49) // (2 * N)
+    while True:
+        q = c * 2 * N + 1
+        if sympy.isprime(q) and q % t != 1:
+            return q
+        c += 1
+
+
+@pytest.mark.parametrize("generic", [False, True])
+def test_delta_residues_match_bigint_rounding(generic):
+    t = 1 << 37
+    primes = (Q0, Q1, Q2) if not generic else (Q0, _find_generic_prime(4096, t))
+    Q = math.prod(primes)
+    rng = np.random.default_rng(2)
+    ms = [0, 1, t // 2 - 1, t // 2, t // 2 + 1, t - 1] + [int(x) for x in rng.integers(0, t, 200, dtype=np.uint64)]
+    qa = np.array(primes, dtype=np.uint64)
+    out = np.zeros(len(primes), dtype=np.uint64)
+    for m in ms:
+        lib.or_delta_residues(p64(qa), len(primes), 37, m, p64(out))
+        want = (2 * Q * m + t) // (2 * t)  # round half up of Q m / t
+        assert [int(x) for x in out] == [want % q for q in primes], m
+
+
+# ------------------------------------------------------------------ encodings (Algorithm 1)
+
+
+def _all_blockings(N):
+    out = []
+    for mb in range(1, N + 1):
+        for kb in range(1, N // mb + 1):
+            for nb in range(1, N // (mb * kb) + 1):
+                out.append((mb, kb, nb))
+    return out
+
+
+def test_encoding_index_map_brute_force():
+    """For every blocking with m_b k_b n_b <= N = 64: the integer negacyclic product
+    pi_A(W^T-block) * pi_B(X^T-block), summed over J and decoded with pi_C^{-1},
+    equals X W exactly (no reduction anywhere)."""
+    N = 64
+    rng = np.random.default_rng(3)
+    blks = _all_blockings(N)
+    assert len(blks) > 500
+    for bi, blk in enumerate(blks):
+        if bi % 7:  # every 7th blocking keeps the runtime small; all shapes of each kind appear
+            continue
+        m_b, k_b, n_b = blk
+        m, k, n = m_b + 1, 2 * k_b - 1 if k_b > 1 else 2, n_b + 2
+        X = rng.integers(0, 50, size=(m, k), dtype=np.uint64)
+        W = rng.integers(0, 50, size=(k, n), dtype=np.uint64)
+        nI, nJ, nLb = O.blocks(m, k, n, blk)
+        A = O.encode_weights_coeff(W, blk, N)
+        B = O.pack_input(X, blk, N).reshape(nLb, nJ, N)
+        dec = np.zeros((nLb * nI, N), dtype=object)
+        for Lb in range(nLb):
+            for I in range(nI):
+                acc = [0] * N
+                for J in range(nJ):
+                    p = _negacyclic_python(A[I, J], B[Lb, J])
+                    acc = [u + v for u, v in zip(acc, p)]
+                dec[Lb * nI + I] = acc
+        ct, coef = O.decode_positions(m, n, blk)
+        got = np.array([[dec[ct[r, c]][coef[r, c]] for c in range(n)] for r in range(m)], dtype=object)
+        assert (got == X.astype(object).dot(W.astype(object))).all(), blk
+
+
+def test_full_blocking_matches_algorithm_1_verbatim():
+    """One block covering the whole product (mrn <= N): the blocked encoders coincide with
+    Algorithm 1's pi_A(A), pi_B(B) for A = W^T, B = X^T, (m, r, n) := (n, k, m)."""
+    N = 64
+    m, k, n = 2, 4, 8
+    rng = np.random.default_rng(4)
+    X = rng.integers(0, 1000, size=(m, k), dtype=np.uint64)
+    W = rng.integers(0, 1000, size=(k, n), dtype=np.uint64)
+    A, B = W.T, X.T
+    am, ar, an = A.shape[0], A.shape[1], B.shape[1]
+    a = np.zeros(N, dtype=np.uint64)
+    b = np.zeros(N, dtype=np.uint64)
+    for i in range(am):
+        for j in range(ar):
+            a[i * ar + ar - 1 - j] = A[i, j]
+    for j in range(ar):
+        for kk in range(an):
+            b[kk * am * ar + j] = B[j, kk]
+    blk = (m, k, n)
+    assert np.array_equal(O.encode_weights_coeff(W, blk, N)[0, 0], a)
+    assert np.array_equal(O.pack_input(X, blk, N)[0], b)
+
+
+# ------------------------------------------------------------------ BFV round trip
+
+
+@pytest.mark.parametrize("N,L", [(64, 2), (4096, 2), (8192, 3)])
+def test_encrypt_decrypt_roundtrip(N, L):
+    P = O.Params(N, L)
+    s = O.keygen(P, S.SEED_KEY)
+    m = S.uniform_plaintexts(2, N, 9)
+    ct = O.encrypt(P, s, m, S.SEED_ENC)
+    assert ct.shape == (2, 2, L, N)
+    for li, q in enumerate(P.q):
+        assert int(ct[:, :, li].max()) < q
+    dec, budget = O.decrypt(P, s, ct)
+    assert np.array_equal(dec, m)
+    assert (budget > 40).all()
+
+
+def test_encryption_structure_small_n():
+    """c0 + c1 s - Delta(m) is the same small integer e (|e| <= 19) modulo every prime."""
+    N, L = 64, 3
+    P = O.Params(N, L)
+    s = O.keygen(P, 1)
+    m = S.uniform_plaintexts(1, N, 2)
+    ct = O.encrypt(P, s, m, 3)
+    e_ref = np.zeros(N, dtype=np.int64)
+    lib.or_sample_gauss(3, 0, N, pi64(e_ref))
+    for li, q in enumerate(P.q):
+        c0 = ct[0, 0, li].astype(object)
+        c1 = ct[0, 1, li].astype(object)
+        c1s = _negacyclic_python(c1, [int(x) % q for x in s], q)
+        for i in range(N):
+            delta = (2 * P.Q * int(m[0, i]) + P.t) // (2 * P.t)
+            e = (int(c0[i]) + c1s[i] - delta) % q
+            e = e - q if e > q // 2 else e
+            assert e == int(e_ref[i])
+            assert abs(e) <= 19
+
+
+# ------------------------------------------------------------------ Algorithm 1 end to end
+
+
+def _schoolbook_matmul_ct(P, ct_in, W, m, k, n, blk, mask_seed):
+    """Independent restatement at small N: pure-Python negacyclic products over Z_q."""
+    nI, nJ, nLb = O.blocks(m, k, n, blk)
+    pt = O.encode_weights_coeff(W, blk, P.N)
+    out = np.zeros((nLb * nI, 2, P.L, P.N), dtype=np.uint64)
+    for Lb in range(nLb):
+        for I in range(nI):
+            o = Lb * nI + I
+            s_mask = O.mask_poly(P, mask_seed, o)
+            for li, q in enumerate(P.q):
+                for c in range(2):
+                    acc = [0] * P.N
+                    for J in range(nJ):
+                        a = [(int(v) - P.t if int(v) >= P.t // 2 else int(v)) for v in pt[I, J]]
+                        p = _negacyclic_python(a, ct_in[Lb * nJ + J, c, li])
+                        acc = [(x + y) % q for x, y in zip(acc, p)]
+                    if c == 0:
+                        acc = [(x - (2 * P.Q * int(sv) + P.t) // (2 * P.t)) % q for x, sv in zip(acc, s_mask)]
+                    out[o, c, li] = acc
+    return out
+
+
+def test_matmul_matches_schoolbook_restatement():
+    N, L = 64, 2
+    P = O.Params(N, L)
+    m, k, n, blk = 5, 6, 7, (2, 4, 8)
+    X = S.uniform_share((m, k), 1)
+    W = S.fixed_point_weights((k, n), 2)
+    s = O.keygen(P, 3)
+    nI, nJ, nLb = O.blocks(m, k, n, blk)
+    ct_in = O.encrypt(P, s, O.pack_input(X, blk, N), 4)
+    got = O.matmul(P, ct_in, W, m, k, n, blk, 5)
+    want = _schoolbook_matmul_ct(P, ct_in, W, m, k, n, blk, 5)
+    assert np.array_equal(got, want)
+
+
+def _end_to_end(P, X, W, blk, seeds=(3, 4, 5)):
+    m, k = X.shape
+    n = W.shape[1]
+    s = O.keygen(P, seeds[0])
+    ct_in = O.encrypt(P, s, O.pack_input(X, blk, P.N), seeds[1])
+    out = O.matmul(P, ct_in, W, m, k, n, blk, seeds[2])
+    dec, budget = O.decrypt(P, s, out)
+    client = O.unpack_output(dec, m, n, blk)
+    server = O.unmask(P, seeds[2], m, n, blk)
+    return (client + server) % np.uint64(P.t), budget, out
+
+
+def test_matmul_end_to_end_single_config():
+    """Config 'single': N=4096, L=2, X 16x64 (uniform share), W 64x64 (fixed point)."""
+    P = O.Params(4096, 2)
+    X = S.uniform_share((16, 64), S.SEED_X)
+    W = S.fixed_point_weights((64, 64), S.SEED_W)
+    got, budget, _ = _end_to_end(P, X, W, (8, 32, 16))
+    assert np.array_equal(got, O.plain_matmul_mod_t(X, W, P.t))
+    assert (budget > 20).all()
+
+
+@pytest.mark.parametrize("blk", [(4, 16, 64), (16, 16, 16), (1, 64, 64)])
+def test_matmul_end_to_end_share_by_share(blk):
+    """Attention cross term: both operands uniform in Z_t (noise grows with |W| ~ 2^36)."""
+    P = O.Params(4096, 2)
+    X = S.uniform_share((12, 40), 21)
+    W = S.uniform_share((40, 24), 22)
+    got, budget, _ = _end_to_end(P, X, W, blk)
+    assert np.array_equal(got, O.plain_matmul_mod_t(X, W, P.t))
+    assert (budget > 0).all()
+
+
+def test_mask_is_needed_for_correct_shares():
+    """The client's decrypted share alone is not X W (the mask hides it), the sum is."""
+    P = O.Params(1024, 2)
+    X = S.uniform_share((4, 8), 31)
+    W = S.fixed_point_weights((8, 4), 32)
+    blk = (4, 8, 4)
+    s = O.keygen(P, 1)
+    ct_in = O.encrypt(P, s, O.pack_input(X, blk, P.N), 2)
+    out = O.matmul(P, ct_in, W, 4, 8, 4, blk, 3)
+    dec, _ = O.decrypt(P, s, out)
+    client = O.unpack_output(dec, 4, 4, blk)
+    assert not np.array_equal(client, O.plain_matmul_mod_t(X, W, P.t))
+
+
+def test_matmul_sampled_outputs_equal_full():
+    P = O.Params(1024, 2)
+    m, k, n, blk = 9, 20, 11, (4, 8, 4)
+    X = S.uniform_share((m, k), 1)
+    W = S.fixed_point_weights((k, n), 2)
+    s = O.keygen(P, 3)
+    ct_in = O.encrypt(P, s, O.pack_input(X, blk, P.N), 4)
+    full = O.matmul(P, ct_in, W, m, k, n, blk, 5)
+    sel = [0, 4, 7, full.shape[0] - 1]
+    part = O.matmul(P, ct_in, W, m, k, n, blk, 5, sel=sel)
+    assert np.array_equal(part, full[sel])
