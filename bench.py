@@ -1,0 +1,434 @@
+"""Benchmark: homomorphic matrix products (Algorithm 1) of one BERT-base layer.
+
+One step = every linear product of one BERT-base encoder layer at sequence
+length 128 (Sec. 3.1.1): the four fully connected layers against resident
+NTT-form weights and, for each of the 12 heads, the two cross terms of Q K^T
+and of P V against the server's shares (encoded per step).  BFV N = 4096, two
+~50-bit primes, t = 2^37.  52 server-side Pi_MatMul calls, 956,301,312 plain
+multiply-accumulates per step.  Input ciphertexts are encrypted (GPU test
+client) before timing and stay resident; every call re-masks with a fresh seed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  value = plain MACs/s over all ranks (each rank
+runs its own layer: independent requests, weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "HE-MatMul plaintext MACs/s"
+UNIT = "MAC/s"
+N_POLY, L_PRIMES = 4096, 2
+WORKLOAD = "bert-base layer linear products, seq 128 (QKV, attn-out, FFN1, FFN2 + 12 heads x 2 cross terms x {QK^T, PV})"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "gb300" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.dev = device_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ the layer
+
+
+class Layer:
+    """Device state of one layer's products: resident weights, input ciphertexts, outputs."""
+
+    def __init__(self, B, ctx, prods, rank, want_host):
+        import numpy as np
+        import torch
+
+        from paper_2305_18396_gb300 import synthetic as S
+
+        self.B, self.ctx = B, ctx
+        self.calls = []
+        dev = ctx.device
+        self.sk = B.he_keygen(ctx, S.SEED_KEY + 1000 * rank)
+        max_ws = max_pt = max_hostws = 0
+        idx = 0
+        for p in prods:
+            blk = ctx.default_blocking(p.m, p.k, p.n)
+            si = ctx.sizes(p.m, p.k, p.n, blk)
+            max_ws = max(max_ws, si["workspace_bytes"])
+            max_hostws = max(max_hostws, B.matmul_host_workspace_words(ctx, p.m, p.k, p.n, blk))
+            for h in range(p.count):
+                seed = 10_000 * (rank + 1) + idx
+                X = S.uniform_share((p.m, p.k), seed)
+                if p.share_weights:
+                    W = S.uniform_share((p.k, p.n), seed + 500_000)
+                else:
+                    W = S.fixed_point_weights((p.k, p.n), seed + 500_000)
+                Xd = torch.from_numpy(X.view(np.int64).reshape(-1)).to(dev)
+                Wd = torch.from_numpy(W.view(np.int64).reshape(-1)).to(dev)
+                polys = B.he_pack_input(ctx, Xd, p.m, p.k, blk)
+                ct_in = B.he_encrypt(ctx, self.sk, polys, seed + 900_000)
+                call = dict(p=p, blk=blk, si=si, ct_in=ct_in, out=ctx.empty(si["out_words"]), idx=idx)
+                if p.share_weights:
+                    call["W"] = Wd  # the server's share, encoded on every step
+                    max_pt = max(max_pt, si["pt_words"])
+                else:
+                    call["pt"] = B.he_encode_weights(ctx, Wd, p.k, p.n, blk)  # resident NTT-form weights
+                if want_host:
+                    call["in_host"] = ct_in.cpu().pin_memory()
+                    call["out_host"] = torch.empty(si["out_words"], dtype=torch.int64).pin_memory()
+                self.calls.append(call)
+                idx += 1
+        self.ws = ctx.empty(max((max_ws + 7) // 8, 1))
+        self.pt_tmp = ctx.empty(max(max_pt, 1))
+        self.host_ws = ctx.empty(max_hostws) if want_host else None
+        self.macs = sum(c["p"].m * c["p"].k * c["p"].n for c in self.calls)
+        torch.cuda.synchronize()
+
+    def step(self, step_idx, host=False):
+        B, ctx = self.B, self.ctx
+        for c in self.calls:
+            p, blk = c["p"], c["blk"]
+            pt = c.get("pt")
+            if pt is None:
+                pt = B.he_encode_weights(ctx, c["W"], p.k, p.n, blk, pt=self.pt_tmp)
+            seed = (step_idx << 20) | c["idx"]
+            if host:
+                B.he_matmul_host(ctx, c["in_host"], pt, p.m, p.k, p.n, blk, seed, c["out_host"], self.host_ws)
+            else:
+                B.he_matmul(ctx, c["ct_in"], pt, p.m, p.k, p.n, blk, seed, c["out"], self.ws)
+
+    def algorithmic_bytes(self):
+        """Per kernel family: algorithmic HBM bytes of one step (reads + writes, 8-byte words)."""
+        L, N = self.ctx.L, self.ctx.N
+        tot = {"mac": 0, "ntt_forward": 0, "intt_mask": 0, "encode_weights": 0}
+        for c in self.calls:
+            si, p = c["si"], c["p"]
+            pt_b, in_b, out_b = 8 * si["pt_words"], 8 * si["in_words"], 8 * si["out_words"]
+            tot["mac"] += pt_b + in_b + out_b
+            tot["ntt_forward"] += 2 * in_b
+            tot["intt_mask"] += 2 * out_b
+            if p.share_weights:
+                tot["encode_weights"] += 8 * p.k * p.n + pt_b
+        return tot
+
+    def slot_macs(self):
+        """Slot-wise modular multiply-accumulates of one step (2 L per plain MAC at full packing)."""
+        return sum(c["si"]["nI"] * c["si"]["nJ"] * c["si"]["nLb"] * 2 * self.ctx.L * self.ctx.N for c in self.calls)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted((ROOT / "paper_2305_18396_gb300" / "csrc").glob("*")):
+        if f.suffix in (".cu", ".cuh", ".h", ".inc"):
+            h.update(f.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM traffic per launch from the committed ncu summary, if it was taken on this source."""
+    for f in (ROOT / "profiles").glob("*.md"):
+        txt = f.read_text()
+        m = re.search(r"^traffic_kernel:\s*(\S+)\s*$", txt, re.M)
+        if not m or m.group(1) != kernel:
+            continue
+        src = re.search(r"^source_hash:\s*(\S+)\s*$", txt, re.M)
+        val = re.search(r"^traffic_bytes_per_launch_full_step_avg:\s*([0-9.eE+]+)\s*$", txt, re.M)
+        if src and val and src.group(1) == kernel_source_hash():
+            return float(val.group(1))
+    return None
+
+
+def peaks():
+    try:
+        return json.loads((ROOT / "MEASURED_PEAKS.json").read_text()), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle legs
+
+
+def oracle_sample(kind="baseline"):
+    """The oracle as it stands on a bounded sample of the layer: one head's four
+    attention cross products (+ the whole attention-output product for the baseline)."""
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    import numpy as np  # noqa: F401
+
+    import oracle as O
+    from paper_2305_18396_gb300 import synthetic as S
+    from paper_2305_18396_gb300 import workloads
+    from paper_2305_18396_gb300.binding import he_choose_blocking
+
+    prods = [p for p in workloads.bert_layer_products(distinct_heads=1, **workloads.BERT_BASE)]
+    heads = [p for p in prods if p.share_weights]
+    heads = heads + [heads[0]]  # qk_x1 has the shape of qk_x0
+    if kind == "baseline":
+        heads = heads + [p for p in prods if p.name == "attn_out"]
+    P = O.Params(N_POLY, L_PRIMES)
+    s = O.keygen(P, S.SEED_KEY)
+    jobs = []
+    for i, p in enumerate(heads):
+        blk = he_choose_blocking(N_POLY, L_PRIMES, p.m, p.k, p.n)
+        X = S.uniform_share((p.m, p.k), 100 + i)
+        W = S.uniform_share((p.k, p.n), 200 + i) if p.share_weights else S.fixed_point_weights((p.k, p.n), 200 + i)
+        ct = O.encrypt(P, s, O.pack_input(X, blk, N_POLY), 300 + i)
+        jobs.append((p, blk, ct, W))
+    return P, jobs, O
+
+
+def run_oracle(P, jobs, O, seed):
+    macs = 0
+    t0 = time.perf_counter()
+    for p, blk, ct, W in jobs:
+        O.matmul(P, ct, W, p.m, p.k, p.n, blk, seed)
+        macs += p.m * p.k * p.n
+    return macs, time.perf_counter() - t0
+
+
+def cpu_baseline():
+    P, jobs, O = oracle_sample("baseline")
+    macs, dt = run_oracle(P, jobs, O, 12345)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": macs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one head's 4 attention cross products + the attn-out product ({macs} plain MACs, "
+                      f"{dt:.1f} s), full Pi_MatMul (encode, NTT, MAC, INTT, mask) on the host cores"}
+
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return
+    P, jobs, O = oracle_sample("reference")
+    for w in range(args.warmup):
+        run_oracle(P, jobs, O, w)
+    tot_macs, tot_t, per = 0, 0.0, []
+    for k in range(args.steps):
+        macs, dt = run_oracle(P, jobs, O, 1000 + k)
+        tot_macs += macs
+        tot_t += dt
+        per.append(dt * 1e3)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    v = tot_macs / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " -- CPU oracle sample", "N": N_POLY, "L": L_PRIMES, "log2_t": 37},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per step: one head's 4 attention cross products ({tot_macs // args.steps} "
+                                       "plain MACs), full Pi_MatMul on the host cores"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "latency_ms": {"p50": statistics.median(per), "p99": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))]}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+
+def gpu_arm(args, world, rank, local):
+    import torch
+
+    from paper_2305_18396_gb300 import binding as B
+    from paper_2305_18396_gb300 import workloads
+
+    torch.cuda.set_device(local)
+    ctx = B.Context(N_POLY, L_PRIMES, device=local)
+    prods = workloads.bert_layer_products(**workloads.BERT_BASE)
+    want_host = not args.no_e2e
+    layer = Layer(B, ctx, prods, rank, want_host)
+    stream = torch.cuda.current_stream()
+
+    for w in range(max(args.warmup, 3) if args.warmup else 0):
+        layer.step(w)
+    torch.cuda.synchronize()
+
+    # headline: K steps, device-resident inputs, CUDA events per step on the launching stream
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = B.he_launch_count(ctx)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(args.steps):
+            evs[k][0].record(stream)
+            layer.step(1000 + k)
+            evs[k][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = B.he_launch_count(ctx) - l0
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), world, device=f"cuda:{local}")
+    per = [a.elapsed_time(b) for a, b in evs]
+    ms_per_step = total_ms / args.steps
+    value = world * layer.macs * args.steps / (total_ms / 1e3)
+
+    # roofline: per-kernel event timing (separate pass, same steps)
+    B.he_profile_enable(ctx, True)
+    for k in range(max(3, min(args.steps, 10))):
+        layer.step(5000 + k)
+    stats = B.he_profile_read(ctx)
+    B.he_profile_enable(ctx, False)
+    alg = layer.algorithmic_bytes()
+    pk, pk_src = peaks()
+    dom = max(stats, key=lambda k: stats[k]["total_ms"])
+    steps_prof = max(3, min(args.steps, 10))
+    total_prof_ms = sum(v["total_ms"] for v in stats.values())
+    kern = {}
+    for name, v in stats.items():
+        b = alg.get(name, 0) * steps_prof
+        kern[name] = {"launches": v["launches"], "ms": round(v["total_ms"], 3),
+                      "share": round(v["total_ms"] / total_prof_ms, 4),
+                      "gbs": round(b / (v["total_ms"] / 1e3) / 1e9, 1) if b else None}
+    achieved = alg.get(dom, 0) * steps_prof / stats[dom]["launches"] / (stats[dom]["total_ms"] / stats[dom]["launches"] / 1e3) / 1e9
+    launches_per_step = stats[dom]["launches"] / steps_prof
+    traffic = recorded_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / pk["hbm_gbs"], 4), "peak_source": pk_src,
+                "algorithmic_bytes_per_launch": alg.get(dom, 0) / launches_per_step,
+                "traffic": traffic, "kernels": kern,
+                "slot_macs_per_s": layer.slot_macs() * steps_prof / (stats["mac"]["total_ms"] / 1e3) if "mac" in stats else None}
+
+    # end to end: host buffers through he_matmul_host (H2D + compute + D2H inside the region)
+    e2e = None
+    if want_host:
+        h2d = sum(8 * c["si"]["in_words"] for c in layer.calls)
+        d2h = sum(8 * c["si"]["out_words"] for c in layer.calls)
+        layer.step(9000, host=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ksteps = max(1, min(args.steps, 5))
+        for k in range(ksteps):
+            layer.step(9100 + k, host=True)
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, world, device=f"cuda:{local}")
+        e2e = {"value": world * layer.macs * ksteps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": ksteps, "ms_per_step": dt * 1e3 / ksteps}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+    blks = {}
+    for c in layer.calls:
+        blks.setdefault(c["p"].name, list(c["blk"]))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N_POLY, "L": L_PRIMES, "log2_t": 37,
+                   "products_per_step": len(layer.calls), "plain_macs_per_step": layer.macs,
+                   "blockings_mkn": blks, "parallelism": f"replicas x{world} (independent layers, no collective)",
+                   "l2": "inputs larger than L2: one step reads/writes ~3 GB of ciphertexts/weights"},
+        "latency_ms": {"p50": statistics.median(per), "p99": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))]},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+    else:
+        gpu_arm(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * he_gb300.h -- C ABI of the GB300 library for the server-side homomorphic
+ * matrix product of Algorithm 1 (Sec. 3.1.1, "Linear Operators") over RNS
+ * BFV (Sec. 2.2, "Homomorphic Encryption").
+ *
+ * Roles (footnote of Sec. 3.1.1, "Attention"): the client holds X (m x k, an
+ * additive share in Z_t) and encrypts it; the server holds W (k x n, weights
+ * or its own share).  In Algorithm 1's notation A = W^T and B = X^T, so the
+ * protocol produces additive shares of C = (X W)^T; both parties transpose at
+ * decode and every share returned here is laid out as X W (m x n).
+ *
+ * Block split (Sec. 3.1.1: larger matrices "split into smaller blocks"): a
+ * blocking {m_b, k_b, n_b} with m_b * k_b * n_b <= N plays the role of
+ * Algorithm 1's (n, r, m).  Block counts: nI = ceil(n/n_b), nJ = ceil(k/k_b),
+ * nLb = ceil(m/m_b).  The blocking is part of the wire format: the same one
+ * must be passed to pack, encode, matmul, unmask and unpack.
+ *
+ * Memory: every data pointer is caller-owned DEVICE memory (e.g. a torch
+ * tensor on the context's device) unless a function says otherwise; the
+ * library owns only the context and its tables.  All u64 values are
+ * little-endian machine words.  Nothing here throws; every function returns
+ * an int status and he_last_error() describes the last failure of the
+ * calling thread.  A context may be used by one host thread at a time.
+ * `stream` is a cudaStream_t (NULL = legacy default stream); all GPU work is
+ * enqueued asynchronously on it unless stated otherwise.
+ *
+ * Layouts (row-major, u64 words):
+ *   plaintext polys  [cnt][N]            coefficients in Z_t
+ *   ciphertexts      [cnt][2][L][N]      (c0, c1), residues in [0, q_l), coefficient form
+ *   input ciphertext  index Lb * nJ + J   (encrypts pi_B of block (J, Lb) of X^T)
+ *   output ciphertext index Lb * nI + I   (share of block (Lb, I) of X W)
+ *   encoded weights  opaque, he_sizes().pt_words words (NTT form, resident)
+ *   secret key       opaque, L * N words (NTT form)
+ *   X, W, shares     [rows][cols] values in Z_t (only the low log2_t bits are read)
+ */
+#ifndef HE_GB300_H
+#define HE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HE_API __attribute__((visibility("default")))
+#else
+#define HE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define HE_OK 0       /* success                                              */
+#define HE_EINVAL 1   /* bad argument: shape, parameters, blocking, NULL ptr  */
+#define HE_ENOMEM 2   /* device allocation failed, or workspace too small     */
+#define HE_ECUDA 3    /* a CUDA runtime call or kernel launch failed          */
+#define HE_ETIMEOUT 4 /* a bounded device wait expired                         */
+#define HE_ENOISE 5   /* decryption found the noise budget exhausted           */
+
+/* ---- flags for he_matmul ------------------------------------------------ */
+#define HE_FLAGS_NONE 0u
+
+typedef struct he_ctx he_ctx;
+
+typedef struct {
+  uint32_t m_b, k_b, n_b;
+} he_blocking;
+
+typedef struct {
+  uint32_t nI, nJ, nLb;     /* block counts                                  */
+  uint64_t in_cts;          /* nLb * nJ input ciphertexts                    */
+  uint64_t out_cts;         /* nLb * nI output ciphertexts                   */
+  uint64_t pts;             /* nI * nJ encoded weight plaintexts             */
+  uint64_t in_words;        /* in_cts * 2 * L * N                            */
+  uint64_t out_words;       /* out_cts * 2 * L * N                           */
+  uint64_t pt_words;        /* words of the opaque encoded-weight buffer     */
+  uint64_t packed_words;    /* in_cts * N: he_pack_input output              */
+  uint64_t workspace_bytes; /* device workspace he_matmul needs              */
+} he_size_info;
+
+/* Most recent error message of the calling thread ("" if none). */
+HE_API const char* he_last_error(void);
+
+/* Parameters {N, t, q} of Sec. 2.2 with q = q_0 ... q_{L-1} (RNS), t = 2^log2_t.
+ * N: power of two in [32, 8192].  L in [1, 3] (L * N <= 3 * 8192).
+ * q: L distinct primes, each = 1 mod 2N and 2^log2_t < q_l < 2^50 (host array).
+ * log2_t in [2, 48].  device: CUDA ordinal the context (and all buffers passed
+ * with it) lives on.  Allocates the NTT twiddle tables on that device.
+ * Returns HE_EINVAL on any invalid parameter (no GPU call made), HE_ECUDA or
+ * HE_ENOMEM on device failures; *ctx is NULL on error. */
+HE_API int he_params_init(he_ctx** ctx, uint32_t N, uint32_t L, const uint64_t* q, uint32_t log2_t, int device);
+
+/* Frees the context and its device tables (NULL is a no-op). */
+HE_API int he_ctx_free(he_ctx* ctx);
+
+/* Host-side query: N, L, log2_t, the primes and the 2N-th roots psi_l the
+ * library chose (psi_l^N = -1 mod q_l).  Arrays hold L entries; any pointer
+ * may be NULL. */
+HE_API int he_get_params(const he_ctx* ctx, uint32_t* N, uint32_t* L, uint32_t* log2_t, uint64_t* q, uint64_t* psi);
+
+/* Host-side: buffer sizes for an (m x k) . (k x n) product under `blk`.
+ * m, k or n == 0 is valid (an empty product: zero-size buffers). */
+HE_API int he_sizes(const he_ctx* ctx, uint32_t m, uint32_t k, uint32_t n, const he_blocking* blk, he_size_info* out);
+
+/* Host-side: the blocking this library picks for a shape: powers of two with
+ * m_b k_b n_b <= N minimising the algorithmic HBM bytes of he_matmul (weights
+ * read once, input ciphertexts read and their NTT written and read back once,
+ * output ciphertexts written once); ties go to the larger m_b, then k_b. */
+HE_API int he_default_blocking(const he_ctx* ctx, uint32_t m, uint32_t k, uint32_t n, he_blocking* out);
+
+/* The same choice without a context (no GPU needed): N a power of two, L >= 1. */
+HE_API int he_choose_blocking(uint32_t N, uint32_t L, uint32_t m, uint32_t k, uint32_t n, he_blocking* out);
+
+/* ---- test client (Sec. 2.2 BFV; encrypt/decrypt are the client's side) -- */
+
+/* Secret key s with ternary coefficients, coefficient i = (u mod 3) - 1 for the
+ * 64-bit Philox4x32-10 draw u at counter (i, 0, 1, 0), key = seed.
+ * sk: device, L * N words (written in the library's NTT form). */
+HE_API int he_keygen(he_ctx* ctx, uint64_t seed, uint64_t* sk, void* stream);
+
+/* Symmetric BFV encryption of cnt plaintext polys: c1 = a, c0 = -a s + e +
+ * round(q m / t) mod q_l.  a_l uniform (128-bit Philox draw at counter
+ * (i, j, 2, l) reduced mod q_l); e discrete Gaussian sigma 3.2, |e| <= 19
+ * (CDT inversion of the 64-bit draw at counter (i, j, 3, 0)); j = index of
+ * the plaintext in the batch; key = seed.  Use a fresh seed per batch.
+ * plain: device [cnt][N]; ct: device [cnt][2][L][N]. */
+HE_API int he_encrypt(he_ctx* ctx, const uint64_t* sk, const uint64_t* plain, uint32_t cnt, uint64_t seed, uint64_t* ct,
+               void* stream);
+
+/* Decryption m = round(t [c0 + c1 s]_q / q) mod t (Sec. 3.1.3, "Reducing the
+ * communication cost": decryption is c0 + c1 s).  plain: device [cnt][N].
+ * noise_budget: optional device int32[cnt], per ciphertext
+ * floor(log2(q/2) - log2 max_i |t x_i - q round(t x_i / q)|) (capped at 63).
+ * min_budget_host: optional host int32; if given, the call synchronizes the
+ * stream, stores the minimum budget there and returns HE_ENOISE if it is <= 0. */
+HE_API int he_decrypt(he_ctx* ctx, const uint64_t* sk, const uint64_t* ct, uint32_t cnt, uint64_t* plain,
+               int32_t* noise_budget, int32_t* min_budget_host, void* stream);
+
+/* Client packing pi_B of Algorithm 1 on B = X^T, per block (J, Lb):
+ * b = sum_{j<k_b, l<m_b} X[Lb m_b + l][J k_b + j] x^{l n_b k_b + j}.
+ * X: device [m][k]; polys: device [nLb * nJ][N] (he_sizes().packed_words). */
+HE_API int he_pack_input(he_ctx* ctx, const uint64_t* X, uint32_t m, uint32_t k, const he_blocking* blk, uint64_t* polys,
+                  void* stream);
+
+/* Client decoding pi_C^{-1} of Algorithm 1 (transposed): its share of X W,
+ * share[Lb m_b + l][I n_b + i] = dec[Lb nI + I][l n_b k_b + i k_b + k_b - 1].
+ * dec: device [nLb * nI][N] decrypted outputs; client_share: device [m][n]. */
+HE_API int he_unpack_output(he_ctx* ctx, const uint64_t* dec, uint32_t m, uint32_t n, const he_blocking* blk,
+                     uint64_t* client_share, void* stream);
+
+/* ---- server (the hot path) ---------------------------------------------- */
+
+/* Server encoding pi_A of Algorithm 1 on A = W^T, per block (I, J):
+ * a = sum_{i<n_b, j<k_b} W[J k_b + j][I n_b + i] x^{i k_b + k_b - 1 - j},
+ * coefficients lifted to the centred range [-t/2, t/2), reduced mod each q_l
+ * and transformed to the NTT domain (footnote of Sec. 3.1.3).
+ * W: device [k][n]; pt: device, he_sizes().pt_words words (opaque). */
+HE_API int he_encode_weights(he_ctx* ctx, const uint64_t* W, uint32_t k, uint32_t n, const he_blocking* blk, uint64_t* pt,
+                      void* stream);
+
+/* Step 3 of Algorithm 1 for every output block: [[c_{Lb,I}]] = sum_J
+ * a_{I,J} * [[b_{Lb,J}]] (NTT, slot-wise multiply-accumulate, inverse NTT),
+ * then the re-mask c0 <- c0 - round(q s / t) with the server's share s of
+ * output o = Lb nI + I: s_i = low log2_t bits of the 64-bit Philox draw at
+ * counter (i, o, 4, 0), key = mask_seed.  Use a fresh mask_seed per call.
+ * ct_in: device [in_cts][2][L][N]; pt: from he_encode_weights with the same
+ * k, n and blk; ct_out: device [out_cts][2][L][N]; workspace: device,
+ * >= he_sizes().workspace_bytes (HE_ENOMEM if smaller).  flags: HE_FLAGS_NONE.
+ * ct_out must not overlap ct_in, pt or workspace. */
+HE_API int he_matmul(he_ctx* ctx, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
+              const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out, void* workspace,
+              size_t workspace_bytes, void* stream);
+
+/* The same product with the ciphertexts in HOST memory (pinned memory gives
+ * asynchronous copies): ct_in_host is copied to the device workspace, the
+ * product is computed as by he_matmul, and the output is copied back to
+ * ct_out_host; the call returns once ct_out_host holds the result.
+ * workspace: device, >= he_sizes().workspace_bytes + 8 * (in_words + out_words). */
+HE_API int he_matmul_host(he_ctx* ctx, const uint64_t* ct_in_host, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
+                   const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out_host, void* workspace,
+                   size_t workspace_bytes, void* stream);
+
+/* Server's share pi_C^{-1}(s) of X W for the masks of he_matmul(mask_seed):
+ * share[Lb m_b + l][I n_b + i] = s_{Lb nI + I}[l n_b k_b + i k_b + k_b - 1].
+ * server_share: device [m][n] (requires k only through blk->k_b). */
+HE_API int he_unmask(he_ctx* ctx, uint64_t mask_seed, uint32_t m, uint32_t n, const he_blocking* blk, uint64_t* server_share,
+              void* stream);
+
+/* ---- test hooks --------------------------------------------------------- */
+
+/* In-place negacyclic NTT of cnt polys laid out [cnt][L][N] (prime l for row l),
+ * residues in [0, q_l).  Forward output is in the library's slot order:
+ * slot j holds a(psi_l^{2 brev(j) + 1}) (brev = log2(N)-bit reversal). */
+HE_API int he_ntt_forward(he_ctx* ctx, uint64_t* polys, uint32_t cnt, void* stream);
+HE_API int he_ntt_inverse(he_ctx* ctx, uint64_t* polys, uint32_t cnt, void* stream);
+
+/* c = a * b in Z_{q_l}[x]/(x^N + 1) for cnt polys laid out [cnt][L][N]
+ * (NTT, slot-wise product, inverse NTT; footnote of Sec. 3.1.3).  c may alias a. */
+HE_API int he_poly_mul(he_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t* c, uint32_t cnt, void* stream);
+
+/* Host-side copy of the library's Gaussian inversion table (2 * 19 words). */
+HE_API int he_gauss_cdt(uint64_t* out, uint32_t cap);
+
+/* ---- profiling (CUDA events recorded on the launching stream) ----------- */
+
+typedef struct {
+  char name[32];     /* kernel family                          */
+  uint64_t launches; /* launches timed since the last reset    */
+  double total_ms;   /* sum of event-measured durations        */
+} he_kernel_stat;
+
+/* Enable (1) / disable (0) per-launch event timing; enabling resets stats. */
+HE_API int he_profile_enable(he_ctx* ctx, int on);
+/* Synchronizes the recorded events and returns up to cap stats in *n. */
+HE_API int he_profile_read(he_ctx* ctx, he_kernel_stat* out, uint32_t cap, uint32_t* n);
+/* Number of kernels this context has launched since creation. */
+HE_API int he_launch_count(const he_ctx* ctx, uint64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HE_GB300_H */

@@ -1,0 +1,312 @@
+"""Thin Python binding of the C ABI in include/he_gb300.h (ctypes).
+
+Argument marshalling only: every function checks that tensors live on the
+context's device with the right size, passes their device pointers and the
+current CUDA stream, and raises HEError on a non-zero status.  All arithmetic
+runs in the CUDA kernels of libhe_gb300.so; there is no CPU fallback -- if the
+library is missing, importing this module raises.
+
+Tensors hold u64 words in torch.int64 storage (bit-identical to uint64;
+numpy views with ``.view(np.uint64)``).
+"""
+import ctypes
+from pathlib import Path
+
+import torch
+
+from . import build as _build
+
+HE_OK, HE_EINVAL, HE_ENOMEM, HE_ECUDA, HE_ETIMEOUT, HE_ENOISE = range(6)
+HE_FLAGS_NONE = 0
+_NAMES = {1: "HE_EINVAL", 2: "HE_ENOMEM", 3: "HE_ECUDA", 4: "HE_ETIMEOUT", 5: "HE_ENOISE"}
+
+
+class HEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Blocking(ctypes.Structure):
+    _fields_ = [("m_b", ctypes.c_uint32), ("k_b", ctypes.c_uint32), ("n_b", ctypes.c_uint32)]
+
+    def as_tuple(self):
+        return (self.m_b, self.k_b, self.n_b)
+
+
+class SizeInfo(ctypes.Structure):
+    _fields_ = [("nI", ctypes.c_uint32), ("nJ", ctypes.c_uint32), ("nLb", ctypes.c_uint32),
+                ("in_cts", ctypes.c_uint64), ("out_cts", ctypes.c_uint64), ("pts", ctypes.c_uint64),
+                ("in_words", ctypes.c_uint64), ("out_words", ctypes.c_uint64), ("pt_words", ctypes.c_uint64),
+                ("packed_words", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
+LIB_PATH = _build.LIB
+
+
+def _load():
+    if not Path(LIB_PATH).exists():
+        raise ImportError(f"CUDA library {LIB_PATH} is not built; run `python -m paper_2305_18396_gb300.build` "
+                          "(or __graft_entry__.build()) -- there is no CPU fallback")
+    so = ctypes.CDLL(str(LIB_PATH))
+    P, u32, u64, i32, sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_size_t
+    pB, pS = ctypes.POINTER(Blocking), ctypes.POINTER(SizeInfo)
+    pu64, pu32, pi32 = ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int32)
+    sig = {
+        "he_last_error": (ctypes.c_char_p, []),
+        "he_params_init": (ctypes.c_int, [ctypes.POINTER(P), u32, u32, pu64, u32, ctypes.c_int]),
+        "he_ctx_free": (ctypes.c_int, [P]),
+        "he_get_params": (ctypes.c_int, [P, pu32, pu32, pu32, pu64, pu64]),
+        "he_sizes": (ctypes.c_int, [P, u32, u32, u32, pB, pS]),
+        "he_default_blocking": (ctypes.c_int, [P, u32, u32, u32, pB]),
+        "he_choose_blocking": (ctypes.c_int, [u32, u32, u32, u32, u32, pB]),
+        "he_keygen": (ctypes.c_int, [P, u64, P, P]),
+        "he_encrypt": (ctypes.c_int, [P, P, P, u32, u64, P, P]),
+        "he_decrypt": (ctypes.c_int, [P, P, P, u32, P, P, pi32, P]),
+        "he_pack_input": (ctypes.c_int, [P, P, u32, u32, pB, P, P]),
+        "he_unpack_output": (ctypes.c_int, [P, P, u32, u32, pB, P, P]),
+        "he_encode_weights": (ctypes.c_int, [P, P, u32, u32, pB, P, P]),
+        "he_matmul": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u64, u32, P, P, sz, P]),
+        "he_matmul_host": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u64, u32, P, P, sz, P]),
+        "he_unmask": (ctypes.c_int, [P, u64, u32, u32, pB, P, P]),
+        "he_ntt_forward": (ctypes.c_int, [P, P, u32, P]),
+        "he_ntt_inverse": (ctypes.c_int, [P, P, u32, P]),
+        "he_poly_mul": (ctypes.c_int, [P, P, P, P, u32, P]),
+        "he_gauss_cdt": (ctypes.c_int, [pu64, u32]),
+        "he_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
+        "he_profile_read": (ctypes.c_int, [P, ctypes.POINTER(KernelStat), u32, pu32]),
+        "he_launch_count": (ctypes.c_int, [P, pu64]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(so, name)
+        fn.restype = res
+        fn.argtypes = args
+    return so
+
+
+lib = _load()
+
+
+def _check(code):
+    if code != HE_OK:
+        raise HEError(code, lib.he_last_error().decode())
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _blk(blk):
+    return ctypes.byref(Blocking(*blk))
+
+
+class Context:
+    """Owns an he_ctx (parameters {N, t, q} of Sec. 2.2 and the NTT tables on `device`)."""
+
+    def __init__(self, N=4096, L=2, primes=None, log2t=37, device=0):
+        if primes is None:
+            from .params import DEFAULT_PRIMES
+            primes = DEFAULT_PRIMES[:L]
+        arr = (ctypes.c_uint64 * L)(*primes)
+        h = ctypes.c_void_p()
+        _check(lib.he_params_init(ctypes.byref(h), N, L, arr, log2t, device))
+        self.h = h
+        self.N, self.L, self.log2t, self.device = N, L, log2t, torch.device("cuda", device)
+        self.primes = tuple(primes)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.he_ctx_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- host-side queries
+    def params(self):
+        N, L, lt = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        q, psi = (ctypes.c_uint64 * 3)(), (ctypes.c_uint64 * 3)()
+        _check(lib.he_get_params(self.h, ctypes.byref(N), ctypes.byref(L), ctypes.byref(lt), q, psi))
+        return {"N": N.value, "L": L.value, "log2t": lt.value, "q": list(q)[: L.value], "psi": list(psi)[: L.value]}
+
+    def sizes(self, m, k, n, blk):
+        si = SizeInfo()
+        _check(lib.he_sizes(self.h, m, k, n, _blk(blk), ctypes.byref(si)))
+        return si.as_dict()
+
+    def default_blocking(self, m, k, n):
+        b = Blocking()
+        _check(lib.he_default_blocking(self.h, m, k, n, ctypes.byref(b)))
+        return b.as_tuple()
+
+    # ---- allocation helpers (device memory comes from torch)
+    def empty(self, words):
+        return torch.empty(int(words), dtype=torch.int64, device=self.device)
+
+    def _dev(self, t, words, name):
+        if t.device != self.device or not t.is_contiguous() or t.dtype not in (torch.int64, torch.uint64):
+            raise ValueError(f"{name} must be a contiguous int64/uint64 tensor on {self.device}")
+        if t.numel() < words:
+            raise ValueError(f"{name} needs at least {words} words, has {t.numel()}")
+        return t
+
+
+def he_choose_blocking(N, L, m, k, n):
+    """Host-only: the blocking the library picks for an (m x k) . (k x n) product."""
+    b = Blocking()
+    _check(lib.he_choose_blocking(N, L, m, k, n, ctypes.byref(b)))
+    return b.as_tuple()
+
+
+def he_params_init(N=4096, L=2, primes=None, log2_t=37, device=0):
+    return Context(N, L, primes, log2_t, device)
+
+
+def he_keygen(ctx, seed, sk=None, stream=None):
+    sk = ctx.empty(ctx.L * ctx.N) if sk is None else ctx._dev(sk, ctx.L * ctx.N, "sk")
+    _check(lib.he_keygen(ctx.h, seed, _ptr(sk), _stream(stream)))
+    return sk
+
+
+def he_encrypt(ctx, sk, plain, seed, ct=None, stream=None):
+    cnt = plain.numel() // ctx.N
+    ctx._dev(plain, cnt * ctx.N, "plain")
+    ct = ctx.empty(cnt * 2 * ctx.L * ctx.N) if ct is None else ctx._dev(ct, cnt * 2 * ctx.L * ctx.N, "ct")
+    _check(lib.he_encrypt(ctx.h, _ptr(ctx._dev(sk, ctx.L * ctx.N, "sk")), _ptr(plain), cnt, seed, _ptr(ct),
+                          _stream(stream)))
+    return ct
+
+
+def he_decrypt(ctx, sk, ct, plain=None, noise_budget=None, check_noise=False, stream=None):
+    """Returns (plain, noise_budget); with check_noise the call synchronizes and raises HE_ENOISE."""
+    cnt = ct.numel() // (2 * ctx.L * ctx.N)
+    ctx._dev(ct, cnt * 2 * ctx.L * ctx.N, "ct")
+    plain = ctx.empty(cnt * ctx.N) if plain is None else ctx._dev(plain, cnt * ctx.N, "plain")
+    if noise_budget is None:
+        noise_budget = torch.empty(max(cnt, 1), dtype=torch.int32, device=ctx.device)
+    mn = ctypes.c_int32()
+    _check(lib.he_decrypt(ctx.h, _ptr(ctx._dev(sk, ctx.L * ctx.N, "sk")), _ptr(ct), cnt, _ptr(plain),
+                          _ptr(noise_budget), ctypes.byref(mn) if check_noise else None, _stream(stream)))
+    return plain, noise_budget[:cnt]
+
+
+def he_pack_input(ctx, X, m, k, blk, polys=None, stream=None):
+    si = ctx.sizes(m, k, 1, blk)
+    ctx._dev(X, m * k, "X")
+    polys = ctx.empty(si["packed_words"]) if polys is None else ctx._dev(polys, si["packed_words"], "polys")
+    _check(lib.he_pack_input(ctx.h, _ptr(X), m, k, _blk(blk), _ptr(polys), _stream(stream)))
+    return polys
+
+
+def he_unpack_output(ctx, dec, m, n, blk, share=None, stream=None):
+    si = ctx.sizes(m, 1, n, blk)
+    ctx._dev(dec, si["out_cts"] * ctx.N, "dec")
+    share = ctx.empty(m * n) if share is None else ctx._dev(share, m * n, "share")
+    _check(lib.he_unpack_output(ctx.h, _ptr(dec), m, n, _blk(blk), _ptr(share), _stream(stream)))
+    return share
+
+
+def he_encode_weights(ctx, W, k, n, blk, pt=None, stream=None):
+    si = ctx.sizes(1, k, n, blk)
+    ctx._dev(W, k * n, "W")
+    pt = ctx.empty(si["pt_words"]) if pt is None else ctx._dev(pt, si["pt_words"], "pt")
+    _check(lib.he_encode_weights(ctx.h, _ptr(W), k, n, _blk(blk), _ptr(pt), _stream(stream)))
+    return pt
+
+
+def he_matmul(ctx, ct_in, pt, m, k, n, blk, mask_seed, ct_out=None, workspace=None, flags=HE_FLAGS_NONE,
+              stream=None):
+    si = ctx.sizes(m, k, n, blk)
+    ctx._dev(ct_in, si["in_words"], "ct_in")
+    ctx._dev(pt, si["pt_words"], "pt")
+    ct_out = ctx.empty(si["out_words"]) if ct_out is None else ctx._dev(ct_out, si["out_words"], "ct_out")
+    ws_words = (si["workspace_bytes"] + 7) // 8
+    workspace = ctx.empty(max(ws_words, 1)) if workspace is None else ctx._dev(workspace, ws_words, "workspace")
+    _check(lib.he_matmul(ctx.h, _ptr(ct_in), _ptr(pt), m, k, n, _blk(blk), mask_seed, flags, _ptr(ct_out),
+                         _ptr(workspace), workspace.numel() * 8, _stream(stream)))
+    return ct_out
+
+
+def matmul_host_workspace_words(ctx, m, k, n, blk):
+    si = ctx.sizes(m, k, n, blk)
+    return (si["workspace_bytes"] + 7) // 8 + si["in_words"] + si["out_words"]
+
+
+def he_matmul_host(ctx, ct_in_host, pt, m, k, n, blk, mask_seed, ct_out_host, workspace, flags=HE_FLAGS_NONE,
+                   stream=None):
+    """ct_in_host / ct_out_host: CPU tensors (pinned for asynchronous copies)."""
+    si = ctx.sizes(m, k, n, blk)
+    for t, w, name in ((ct_in_host, si["in_words"], "ct_in_host"), (ct_out_host, si["out_words"], "ct_out_host")):
+        if t.device.type != "cpu" or not t.is_contiguous() or t.numel() < w:
+            raise ValueError(f"{name} must be a contiguous CPU tensor of >= {w} words")
+    ctx._dev(workspace, matmul_host_workspace_words(ctx, m, k, n, blk), "workspace")
+    _check(lib.he_matmul_host(ctx.h, _ptr(ct_in_host), _ptr(ctx._dev(pt, si["pt_words"], "pt")), m, k, n, _blk(blk),
+                              mask_seed, flags, _ptr(ct_out_host), _ptr(workspace), workspace.numel() * 8,
+                              _stream(stream)))
+    return ct_out_host
+
+
+def he_unmask(ctx, mask_seed, m, n, blk, share=None, stream=None):
+    share = ctx.empty(m * n) if share is None else ctx._dev(share, m * n, "share")
+    _check(lib.he_unmask(ctx.h, mask_seed, m, n, _blk(blk), _ptr(share), _stream(stream)))
+    return share
+
+
+def he_ntt_forward(ctx, polys, stream=None):
+    cnt = polys.numel() // (ctx.L * ctx.N)
+    _check(lib.he_ntt_forward(ctx.h, _ptr(ctx._dev(polys, cnt * ctx.L * ctx.N, "polys")), cnt, _stream(stream)))
+    return polys
+
+
+def he_ntt_inverse(ctx, polys, stream=None):
+    cnt = polys.numel() // (ctx.L * ctx.N)
+    _check(lib.he_ntt_inverse(ctx.h, _ptr(ctx._dev(polys, cnt * ctx.L * ctx.N, "polys")), cnt, _stream(stream)))
+    return polys
+
+
+def he_poly_mul(ctx, a, b, c=None, stream=None):
+    cnt = a.numel() // (ctx.L * ctx.N)
+    words = cnt * ctx.L * ctx.N
+    c = ctx.empty(words) if c is None else ctx._dev(c, words, "c")
+    _check(lib.he_poly_mul(ctx.h, _ptr(ctx._dev(a, words, "a")), _ptr(ctx._dev(b, words, "b")), _ptr(c), cnt,
+                           _stream(stream)))
+    return c
+
+
+def he_gauss_cdt():
+    out = (ctypes.c_uint64 * 38)()
+    _check(lib.he_gauss_cdt(out, 38))
+    return list(out)
+
+
+def he_profile_enable(ctx, on=True):
+    _check(lib.he_profile_enable(ctx.h, 1 if on else 0))
+
+
+def he_profile_read(ctx):
+    buf = (KernelStat * 32)()
+    n = ctypes.c_uint32()
+    _check(lib.he_profile_read(ctx.h, buf, 32, ctypes.byref(n)))
+    return {buf[i].name.decode(): {"launches": buf[i].launches, "total_ms": buf[i].total_ms} for i in range(n.value)}
+
+
+def he_launch_count(ctx):
+    v = ctypes.c_uint64()
+    _check(lib.he_launch_count(ctx.h, ctypes.byref(v)))
+    return v.value

@@ -1,0 +1,614 @@
+// capi.cu -- the extern "C" boundary declared in include/he_gb300.h: argument
+// checking, context set-up (primes, roots, twiddle tables, constants), buffer
+// sizing, the default blocking, launch bookkeeping and event profiling.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/he_gb300.h"
+#include "kernels.h"
+
+using he::u32;
+using he::u64;
+typedef unsigned __int128 u128;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(HE_ECUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+// ---------------------------------------------------------------- host modular arithmetic
+
+u64 mulm(u64 a, u64 b, u64 q) { return (u64)((u128)a * b % q); }
+
+u64 powm(u64 b, u64 e, u64 q) {
+  u64 r = 1 % q;
+  b %= q;
+  for (; e; e >>= 1) {
+    if (e & 1) r = mulm(r, b, q);
+    b = mulm(b, b, q);
+  }
+  return r;
+}
+
+u64 invm(u64 a, u64 q) { return powm(a, q - 2, q); }  // q prime
+
+bool prime64(u64 n) {
+  if (n < 2) return false;
+  const u64 small[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  for (u64 p : small)
+    if (n % p == 0) return n == p;
+  u64 d = n - 1;
+  int r = 0;
+  while (!(d & 1)) d >>= 1, ++r;
+  for (u64 a : small) {
+    u64 x = powm(a, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int i = 1; i < r && comp; ++i) {
+      x = mulm(x, x, n);
+      if (x == n - 1) comp = false;
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+
+// The smallest primitive 2N-th root of unity mod q (all of them are the odd powers of one).
+u64 min_root_2n(u64 q, u32 N) {
+  u64 base = 0;
+  for (u64 g = 2; g < 1000 && !base; ++g) {
+    u64 c = powm(g, (q - 1) / (2 * (u64)N), q);
+    if (powm(c, N, q) == q - 1) base = c;
+  }
+  if (!base) return 0;
+  u64 best = base, sq = mulm(base, base, q), cur = base;
+  for (u32 e = 1; e < N; ++e) {  // odd powers base^(2e+1)
+    cur = mulm(cur, sq, q);
+    if (cur < best) best = cur;
+  }
+  return best;
+}
+
+u64 shoup(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+u32 brev(u32 x, u32 bits) {
+  u32 r = 0;
+  for (u32 i = 0; i < bits; ++i) r |= ((x >> i) & 1u) << (bits - 1 - i);
+  return r;
+}
+
+// floor(2^e / q) for 64 < e < 192 with q < 2^63, as a 128-bit value (caller ensures it fits).
+u128 pow2_div(u32 e, u64 q) {
+  u128 quo = 0, rem = 0;
+  for (int bit = (int)e; bit >= 0; --bit) {
+    rem = (rem << 1) | (bit == (int)e ? 1 : 0);
+    quo <<= 1;
+    if (rem >= q) {
+      rem -= q;
+      quo |= 1;
+    }
+  }
+  return quo;
+}
+
+bool pow2(u64 x) { return x && !(x & (x - 1)); }
+
+u32 ceil_div(u32 a, u32 b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- context
+
+struct ProfRec {
+  int kind;
+  cudaEvent_t e0, e1;
+};
+
+enum Kind { KNttFwd, KNttInv, KPolyMul, KKeygen, KEncrypt, KDecrypt, KPack, KUnpack, KUnmask, KEncode, KMac, KInttMask, KCount };
+static const char* kKindNames[KCount] = {"ntt_forward", "ntt_inverse", "poly_mul", "keygen", "encrypt", "decrypt",
+                                         "pack", "unpack", "unmask", "encode_weights", "mac", "intt_mask"};
+
+struct he_ctx {
+  int device = 0;
+  he::Consts C{};
+  u64 psi[he::kMaxPrimes] = {};
+  u64* d_tables = nullptr;
+  std::atomic<uint64_t> launches{0};
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  uint64_t stat_launches[KCount] = {};
+  double stat_ms[KCount] = {};
+};
+
+namespace {
+
+cudaEvent_t get_event(he_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Runs one launcher under the context's bookkeeping (launch count, optional events).
+template <typename F>
+int launch(he_ctx* c, int kind, cudaStream_t st, const char* where, F&& f) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->prof) {
+    e0 = get_event(c);
+    e1 = get_event(c);
+    cudaEventRecord(e0, st);
+  }
+  cudaError_t e = f();
+  if (c->prof) {
+    cudaEventRecord(e1, st);
+    c->recs.push_back({kind, e0, e1});
+  }
+  c->launches.fetch_add(1, std::memory_order_relaxed);
+  if (e != cudaSuccess) return cuda_fail(e, where);
+  return HE_OK;
+}
+
+int set_device(const he_ctx* c) {
+  cudaError_t e = cudaSetDevice(c->device);
+  return e == cudaSuccess ? HE_OK : cuda_fail(e, "cudaSetDevice");
+}
+
+int check_blk(const he_ctx* c, const he_blocking* b) {
+  if (!b) return fail(HE_EINVAL, "blocking is NULL");
+  if (!b->m_b || !b->k_b || !b->n_b) return fail(HE_EINVAL, "blocking entries must be >= 1");
+  if ((u64)b->m_b * b->k_b * b->n_b > c->C.N) return fail(HE_EINVAL, "blocking needs m_b * k_b * n_b <= N");
+  return HE_OK;
+}
+
+struct Shape {
+  u32 nI, nJ, nLb;
+};
+
+Shape shape_of(u32 m, u32 k, u32 n, const he_blocking* b) {
+  return {ceil_div(n, b->n_b), ceil_div(k, b->k_b), ceil_div(m, b->m_b)};
+}
+
+he::Blk to_blk(const he_blocking* b) { return {b->m_b, b->k_b, b->n_b}; }
+
+}  // namespace
+
+extern "C" {
+
+const char* he_last_error(void) { return g_last_error.c_str(); }
+
+int he_params_init(he_ctx** out, uint32_t N, uint32_t L, const uint64_t* q, uint32_t log2_t, int device) {
+  if (!out) return fail(HE_EINVAL, "ctx out-pointer is NULL");
+  *out = nullptr;
+  if (!pow2(N) || N < 32 || N > 8192) return fail(HE_EINVAL, "N must be a power of two in [32, 8192]");
+  if (L < 1 || L > (u32)he::kMaxPrimes || (u64)L * N > 3ull * 8192)
+    return fail(HE_EINVAL, "L must be in [1, 3] with L * N <= 3 * 8192");
+  if (!q) return fail(HE_EINVAL, "prime array is NULL");
+  if (log2_t < 2 || log2_t > 48) return fail(HE_EINVAL, "log2_t must be in [2, 48]");
+  for (u32 l = 0; l < L; ++l) {
+    if (q[l] >= (1ull << 50) || q[l] <= (1ull << log2_t)) return fail(HE_EINVAL, "need 2^log2_t < q_l < 2^50");
+    if ((q[l] - 1) % (2ull * N)) return fail(HE_EINVAL, "q_l must be 1 mod 2N");
+    if (!prime64(q[l])) return fail(HE_EINVAL, "q_l must be prime");
+    for (u32 j = 0; j < l; ++j)
+      if (q[j] == q[l]) return fail(HE_EINVAL, "primes must be distinct");
+  }
+  if (device < 0) return fail(HE_EINVAL, "device must be >= 0");
+
+  he_ctx* c = new he_ctx();
+  c->device = device;
+  he::Consts& C = c->C;
+  C.N = N;
+  C.logN = 0;
+  while ((1u << C.logN) < N) ++C.logN;
+  C.L = L;
+  C.log2t = log2_t;
+  C.tmask = (1ull << log2_t) - 1;
+  u64 qmt = 1;
+  for (u32 l = 0; l < L; ++l) qmt = (u64)(((u128)qmt * (q[l] & C.tmask)) & C.tmask);
+  C.q_mod_t = qmt;
+
+  std::vector<u64> host((size_t)4 * L * N);
+  for (u32 l = 0; l < L; ++l) {
+    const u64 ql = q[l];
+    he::PrimeConsts& P = C.p[l];
+    u64 psi = min_root_2n(ql, N);
+    if (!psi) {
+      delete c;
+      return fail(HE_EINVAL, "no primitive 2N-th root found");
+    }
+    c->psi[l] = psi;
+    u64 ipsi = invm(psi, ql);
+    u64* tw = host.data() + (size_t)4 * l * N;
+    for (u32 kk = 0; kk < N; ++kk) {
+      u32 e = brev(kk, C.logN);
+      tw[kk] = powm(psi, e, ql);
+      tw[N + kk] = shoup(tw[kk], ql);
+      tw[2 * N + kk] = powm(ipsi, e, ql);
+      tw[3 * N + kk] = shoup(tw[2 * N + kk], ql);
+    }
+    P.q = ql;
+    P.two_q = 2 * ql;
+    P.mu = shoup(1, ql);
+    P.ninv = invm(N % ql, ql);
+    P.ninv_sh = shoup(P.ninv, ql);
+    P.tinv = invm((1ull << log2_t) % ql, ql);
+    P.tinv_sh = shoup(P.tinv, ql);
+    P.r26 = (1ull << 26) % ql;
+    P.r26_sh = shoup(P.r26, ql);
+    P.r52 = (1ull << 52) % ql;
+    P.r52_sh = shoup(P.r52, ql);
+    P.r64 = (u64)(((u128)1 << 64) % ql);
+    P.r64_sh = shoup(P.r64, ql);
+    u64 Ml = 1;
+    for (u32 j = 0; j < L; ++j)
+      if (j != l) Ml = mulm(Ml, q[j] % ql, ql);
+    P.crt = invm(Ml, ql);
+    P.crt_sh = shoup(P.crt, ql);
+    u128 theta = pow2_div(128 + log2_t, ql);
+    P.theta_hi = (u64)(theta >> 64);
+    P.theta_lo = (u64)theta;
+  }
+
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaSetDevice");
+  }
+  e = cudaMalloc(&c->d_tables, host.size() * sizeof(u64));
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(HE_ENOMEM, "cudaMalloc of twiddle tables failed");
+  }
+  e = cudaMemcpy(c->d_tables, host.data(), host.size() * sizeof(u64), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = he::configure_kernels(C);
+  if (e != cudaSuccess) {
+    cudaFree(c->d_tables);
+    delete c;
+    return cuda_fail(e, "table upload / kernel configuration");
+  }
+  for (u32 l = 0; l < L; ++l) {
+    u64* tw = c->d_tables + (size_t)4 * l * N;
+    C.p[l].psi = tw;
+    C.p[l].psi_sh = tw + N;
+    C.p[l].ipsi = tw + 2 * N;
+    C.p[l].ipsi_sh = tw + 3 * N;
+  }
+  *out = c;
+  return HE_OK;
+}
+
+int he_ctx_free(he_ctx* c) {
+  if (!c) return HE_OK;
+  cudaSetDevice(c->device);
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  if (c->d_tables) cudaFree(c->d_tables);
+  delete c;
+  return HE_OK;
+}
+
+int he_get_params(const he_ctx* c, uint32_t* N, uint32_t* L, uint32_t* log2_t, uint64_t* q, uint64_t* psi) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (N) *N = c->C.N;
+  if (L) *L = c->C.L;
+  if (log2_t) *log2_t = c->C.log2t;
+  for (u32 l = 0; l < c->C.L; ++l) {
+    if (q) q[l] = c->C.p[l].q;
+    if (psi) psi[l] = c->psi[l];
+  }
+  return HE_OK;
+}
+
+int he_sizes(const he_ctx* c, uint32_t m, uint32_t k, uint32_t n, const he_blocking* blk, he_size_info* out) {
+  if (!c || !out) return fail(HE_EINVAL, "NULL argument");
+  int r = check_blk(c, blk);
+  if (r) return r;
+  Shape s = shape_of(m, k, n, blk);
+  const u64 N = c->C.N, L = c->C.L;
+  out->nI = s.nI;
+  out->nJ = s.nJ;
+  out->nLb = s.nLb;
+  out->in_cts = (u64)s.nLb * s.nJ;
+  out->out_cts = (u64)s.nLb * s.nI;
+  out->pts = (u64)s.nI * s.nJ;
+  out->in_words = out->in_cts * 2 * L * N;
+  out->out_words = out->out_cts * 2 * L * N;
+  out->pt_words = out->pts * L * N;
+  out->packed_words = out->in_cts * N;
+  out->workspace_bytes = out->in_words * sizeof(u64);  // NTT of the input ciphertexts
+  return HE_OK;
+}
+
+int he_choose_blocking(uint32_t Nw, uint32_t Lw, uint32_t m, uint32_t k, uint32_t n, he_blocking* out) {
+  if (!out) return fail(HE_EINVAL, "NULL argument");
+  if (!pow2(Nw) || Lw < 1) return fail(HE_EINVAL, "N must be a power of two and L >= 1");
+  const u64 N = Nw, L = Lw;
+  auto cap = [&](u32 d) {
+    u64 p = 1;
+    while (p < d && p < N) p <<= 1;
+    return p;
+  };
+  const u64 cm = cap(m ? m : 1), ck = cap(k ? k : 1), cn = cap(n ? n : 1);
+  double best = -1;
+  he_blocking bb{1, 1, 1};
+  for (u64 mb = 1; mb <= cm; mb <<= 1)
+    for (u64 kb = 1; kb <= ck && mb * kb <= N; kb <<= 1)
+      for (u64 nb = 1; nb <= cn && mb * kb * nb <= N; nb <<= 1) {
+        u64 nI = (n + nb - 1) / nb, nJ = (k + kb - 1) / kb, nLb = (m + mb - 1) / mb;
+        // pt read + input ct read + NTT'd inputs written and read + outputs written
+        double bytes = 8.0 * N * L * ((double)nI * nJ + 2.0 * nLb * nJ * 3 + 2.0 * nLb * nI);
+        bool better = best < 0 || bytes < best ||
+                      (bytes == best && (mb > bb.m_b || (mb == bb.m_b && kb > bb.k_b)));
+        if (better) {
+          best = bytes;
+          bb = {(u32)mb, (u32)kb, (u32)nb};
+        }
+      }
+  *out = bb;
+  return HE_OK;
+}
+
+int he_default_blocking(const he_ctx* c, uint32_t m, uint32_t k, uint32_t n, he_blocking* out) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  return he_choose_blocking(c->C.N, c->C.L, m, k, n, out);
+}
+
+int he_keygen(he_ctx* c, uint64_t seed, uint64_t* sk, void* stream) {
+  if (!c || !sk) return fail(HE_EINVAL, "NULL argument");
+  if (int r = set_device(c)) return r;
+  return launch(c, KKeygen, (cudaStream_t)stream, "keygen",
+                [&] { return he::launch_keygen(c->C, seed, sk, (cudaStream_t)stream); });
+}
+
+int he_encrypt(he_ctx* c, const uint64_t* sk, const uint64_t* plain, uint32_t cnt, uint64_t seed, uint64_t* ct,
+               void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (!cnt) return HE_OK;
+  if (!sk || !plain || !ct) return fail(HE_EINVAL, "NULL buffer");
+  if (int r = set_device(c)) return r;
+  return launch(c, KEncrypt, (cudaStream_t)stream, "encrypt",
+                [&] { return he::launch_encrypt(c->C, sk, plain, cnt, seed, ct, (cudaStream_t)stream); });
+}
+
+int he_decrypt(he_ctx* c, const uint64_t* sk, const uint64_t* ct, uint32_t cnt, uint64_t* plain,
+               int32_t* noise_budget, int32_t* min_budget_host, void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (min_budget_host) *min_budget_host = 63;
+  if (!cnt) return HE_OK;
+  if (!sk || !ct || !plain) return fail(HE_EINVAL, "NULL buffer");
+  if (min_budget_host && !noise_budget) return fail(HE_EINVAL, "min_budget_host needs the noise_budget buffer");
+  if (int r = set_device(c)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  int r = launch(c, KDecrypt, st, "decrypt",
+                 [&] { return he::launch_decrypt(c->C, sk, ct, cnt, plain, (int*)noise_budget, st); });
+  if (r || !min_budget_host) return r;
+  std::vector<int32_t> b(cnt);
+  cudaError_t e = cudaMemcpyAsync(b.data(), noise_budget, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "decrypt budget readback");
+  int32_t mn = 63;
+  for (auto v : b) mn = v < mn ? v : mn;
+  *min_budget_host = mn;
+  return mn <= 0 ? fail(HE_ENOISE, "noise budget exhausted") : HE_OK;
+}
+
+int he_pack_input(he_ctx* c, const uint64_t* X, uint32_t m, uint32_t k, const he_blocking* blk, uint64_t* polys,
+                  void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (int r = check_blk(c, blk)) return r;
+  if (!m || !k) return HE_OK;
+  if (!X || !polys) return fail(HE_EINVAL, "NULL buffer");
+  if (int r = set_device(c)) return r;
+  Shape s = shape_of(m, k, 1, blk);
+  return launch(c, KPack, (cudaStream_t)stream, "pack", [&] {
+    return he::launch_pack(c->C, X, m, k, to_blk(blk), s.nJ, s.nLb, polys, (cudaStream_t)stream);
+  });
+}
+
+int he_unpack_output(he_ctx* c, const uint64_t* dec, uint32_t m, uint32_t n, const he_blocking* blk,
+                     uint64_t* client_share, void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (int r = check_blk(c, blk)) return r;
+  if (!m || !n) return HE_OK;
+  if (!dec || !client_share) return fail(HE_EINVAL, "NULL buffer");
+  if (int r = set_device(c)) return r;
+  Shape s = shape_of(m, 1, n, blk);
+  return launch(c, KUnpack, (cudaStream_t)stream, "unpack", [&] {
+    return he::launch_unpack(c->C, dec, m, n, to_blk(blk), s.nI, client_share, (cudaStream_t)stream);
+  });
+}
+
+int he_unmask(he_ctx* c, uint64_t mask_seed, uint32_t m, uint32_t n, const he_blocking* blk, uint64_t* server_share,
+              void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (int r = check_blk(c, blk)) return r;
+  if (!m || !n) return HE_OK;
+  if (!server_share) return fail(HE_EINVAL, "NULL buffer");
+  if (int r = set_device(c)) return r;
+  Shape s = shape_of(m, 1, n, blk);
+  return launch(c, KUnmask, (cudaStream_t)stream, "unmask", [&] {
+    return he::launch_unmask(c->C, mask_seed, m, n, to_blk(blk), s.nI, server_share, (cudaStream_t)stream);
+  });
+}
+
+int he_encode_weights(he_ctx* c, const uint64_t* W, uint32_t k, uint32_t n, const he_blocking* blk, uint64_t* pt,
+                      void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (int r = check_blk(c, blk)) return r;
+  if (!k || !n) return HE_OK;
+  if (!W || !pt) return fail(HE_EINVAL, "NULL buffer");
+  if (int r = set_device(c)) return r;
+  Shape s = shape_of(1, k, n, blk);
+  return launch(c, KEncode, (cudaStream_t)stream, "encode_weights", [&] {
+    return he::launch_encode_weights(c->C, W, k, n, to_blk(blk), s.nI, s.nJ, pt, (cudaStream_t)stream);
+  });
+}
+
+static int matmul_device(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
+                         const he_blocking* blk, uint64_t mask_seed, uint64_t* ct_out, void* ws, cudaStream_t st) {
+  Shape s = shape_of(m, k, n, blk);
+  const u64 in_polys = (u64)s.nLb * s.nJ * 2 * c->C.L;
+  u64* ctN = (u64*)ws;
+  int r = launch(c, KNttFwd, st, "matmul: forward NTT",
+                 [&] { return he::launch_ntt_forward(c->C, ct_in, ctN, in_polys, st); });
+  if (r) return r;
+  r = launch(c, KMac, st, "matmul: multiply-accumulate",
+             [&] { return he::launch_mac(c->C, ctN, pt, ct_out, s.nI, s.nJ, s.nLb, st); });
+  if (r) return r;
+  return launch(c, KInttMask, st, "matmul: inverse NTT + mask",
+                [&] { return he::launch_intt_mask(c->C, ct_out, (u64)s.nLb * s.nI, mask_seed, st); });
+}
+
+static int matmul_checks(he_ctx* c, uint32_t m, uint32_t k, uint32_t n, const he_blocking* blk, uint32_t flags,
+                         he_size_info* si) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (int r = check_blk(c, blk)) return r;
+  if (flags != HE_FLAGS_NONE) return fail(HE_EINVAL, "unknown flags");
+  he_sizes(c, m, k, n, blk, si);
+  if (si->nJ > 4096) return fail(HE_EINVAL, "at most 4096 k-blocks (k / k_b) per product");
+  return HE_OK;
+}
+
+int he_matmul(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
+              const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out, void* workspace,
+              size_t workspace_bytes, void* stream) {
+  he_size_info si;
+  if (int r = matmul_checks(c, m, k, n, blk, flags, &si)) return r;
+  if (!m || !k || !n) return HE_OK;
+  if (!ct_in || !pt || !ct_out || !workspace) return fail(HE_EINVAL, "NULL buffer");
+  if (workspace_bytes < si.workspace_bytes) return fail(HE_ENOMEM, "workspace smaller than he_sizes().workspace_bytes");
+  if (int r = set_device(c)) return r;
+  return matmul_device(c, ct_in, pt, m, k, n, blk, mask_seed, ct_out, workspace, (cudaStream_t)stream);
+}
+
+int he_matmul_host(he_ctx* c, const uint64_t* ct_in_host, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
+                   const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out_host,
+                   void* workspace, size_t workspace_bytes, void* stream) {
+  he_size_info si;
+  if (int r = matmul_checks(c, m, k, n, blk, flags, &si)) return r;
+  if (!m || !k || !n) return HE_OK;
+  if (!ct_in_host || !pt || !ct_out_host || !workspace) return fail(HE_EINVAL, "NULL buffer");
+  const u64 need = si.workspace_bytes + 8 * (si.in_words + si.out_words);
+  if (workspace_bytes < need) return fail(HE_ENOMEM, "workspace smaller than he_matmul_host needs");
+  if (int r = set_device(c)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  u64* d_in = (u64*)((char*)workspace + si.workspace_bytes);
+  u64* d_out = d_in + si.in_words;
+  cudaError_t e = cudaMemcpyAsync(d_in, ct_in_host, si.in_words * 8, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "matmul_host: upload");
+  if (int r = matmul_device(c, d_in, pt, m, k, n, blk, mask_seed, d_out, workspace, st)) return r;
+  e = cudaMemcpyAsync(ct_out_host, d_out, si.out_words * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "matmul_host: download");
+  return HE_OK;
+}
+
+int he_ntt_forward(he_ctx* c, uint64_t* polys, uint32_t cnt, void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (!cnt) return HE_OK;
+  if (!polys) return fail(HE_EINVAL, "NULL buffer");
+  if (int r = set_device(c)) return r;
+  return launch(c, KNttFwd, (cudaStream_t)stream, "ntt_forward", [&] {
+    return he::launch_ntt_forward(c->C, polys, polys, (u64)cnt * c->C.L, (cudaStream_t)stream);
+  });
+}
+
+int he_ntt_inverse(he_ctx* c, uint64_t* polys, uint32_t cnt, void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (!cnt) return HE_OK;
+  if (!polys) return fail(HE_EINVAL, "NULL buffer");
+  if (int r = set_device(c)) return r;
+  return launch(c, KNttInv, (cudaStream_t)stream, "ntt_inverse", [&] {
+    return he::launch_ntt_inverse(c->C, polys, polys, (u64)cnt * c->C.L, (cudaStream_t)stream);
+  });
+}
+
+int he_poly_mul(he_ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, uint32_t cnt, void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (!cnt) return HE_OK;
+  if (!a || !b || !out) return fail(HE_EINVAL, "NULL buffer");
+  if (int r = set_device(c)) return r;
+  return launch(c, KPolyMul, (cudaStream_t)stream, "poly_mul", [&] {
+    return he::launch_poly_mul(c->C, a, b, out, (u64)cnt * c->C.L, (cudaStream_t)stream);
+  });
+}
+
+int he_gauss_cdt(uint64_t* out, uint32_t cap) {
+  static const uint64_t table[2 * he::kGaussBound] = {
+#include "gauss_cdt.inc"
+  };
+  if (!out || cap < 2 * he::kGaussBound) return fail(HE_EINVAL, "need room for 38 words");
+  memcpy(out, table, sizeof(table));
+  return HE_OK;
+}
+
+int he_profile_enable(he_ctx* c, int on) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  c->prof = on != 0;
+  for (auto& r : c->recs) {
+    c->pool.push_back(r.e0);
+    c->pool.push_back(r.e1);
+  }
+  c->recs.clear();
+  for (int i = 0; i < KCount; ++i) {
+    c->stat_launches[i] = 0;
+    c->stat_ms[i] = 0;
+  }
+  return HE_OK;
+}
+
+int he_profile_read(he_ctx* c, he_kernel_stat* out, uint32_t cap, uint32_t* n) {
+  if (!c || !n) return fail(HE_EINVAL, "NULL argument");
+  if (int r = set_device(c)) return r;
+  for (auto& r : c->recs) {
+    cudaError_t e = cudaEventSynchronize(r.e1);
+    if (e != cudaSuccess) return cuda_fail(e, "profile: event sync");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, r.e0, r.e1);
+    c->stat_launches[r.kind] += 1;
+    c->stat_ms[r.kind] += ms;
+    c->pool.push_back(r.e0);
+    c->pool.push_back(r.e1);
+  }
+  c->recs.clear();
+  u32 cnt = 0;
+  for (int i = 0; i < KCount; ++i) {
+    if (!c->stat_launches[i]) continue;
+    if (out && cnt < cap) {
+      memset(&out[cnt], 0, sizeof(he_kernel_stat));
+      strncpy(out[cnt].name, kKindNames[i], sizeof(out[cnt].name) - 1);
+      out[cnt].launches = c->stat_launches[i];
+      out[cnt].total_ms = c->stat_ms[i];
+    }
+    ++cnt;
+  }
+  *n = cnt;
+  return HE_OK;
+}
+
+int he_launch_count(const he_ctx* c, uint64_t* out) {
+  if (!c || !out) return fail(HE_EINVAL, "NULL argument");
+  *out = c->launches.load();
+  return HE_OK;
+}
+
+}  // extern "C"

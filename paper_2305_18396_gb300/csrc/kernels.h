@@ -1,0 +1,39 @@
+// kernels.h -- host-side launchers of the library's CUDA kernels (internal).
+#pragma once
+
+#include "he_common.cuh"
+
+namespace he {
+
+struct Blk {
+  u32 m_b, k_b, n_b;
+};
+
+// Each launcher enqueues one kernel on `st` and returns cudaGetLastError().
+// Shared-memory attributes are set once per device by configure_kernels().
+cudaError_t configure_kernels(const Consts& C);
+
+cudaError_t launch_ntt_forward(const Consts& C, const u64* src, u64* dst, u64 npolys, cudaStream_t st);
+cudaError_t launch_ntt_inverse(const Consts& C, const u64* src, u64* dst, u64 npolys, cudaStream_t st);
+cudaError_t launch_poly_mul(const Consts& C, const u64* a, const u64* b, u64* c, u64 npolys, cudaStream_t st);
+
+cudaError_t launch_keygen(const Consts& C, u64 seed, u64* sk, cudaStream_t st);
+cudaError_t launch_encrypt(const Consts& C, const u64* sk, const u64* plain, u32 cnt, u64 seed, u64* ct,
+                           cudaStream_t st);
+cudaError_t launch_decrypt(const Consts& C, const u64* sk, const u64* ct, u32 cnt, u64* plain, int* budget,
+                           cudaStream_t st);
+cudaError_t launch_pack(const Consts& C, const u64* X, u32 m, u32 k, Blk b, u32 nJ, u32 nLb, u64* polys,
+                        cudaStream_t st);
+cudaError_t launch_unpack(const Consts& C, const u64* dec, u32 m, u32 n, Blk b, u32 nI, u64* share,
+                          cudaStream_t st);
+cudaError_t launch_unmask(const Consts& C, u64 seed, u32 m, u32 n, Blk b, u32 nI, u64* share, cudaStream_t st);
+
+cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u64* pt,
+                                  cudaStream_t st);
+// Slot-wise sum_J pt[I][J] * ctN[Lb][J] for every output (Lb, I), both components, all primes.
+cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out, u32 nI, u32 nJ, u32 nLb,
+                       cudaStream_t st);
+// Inverse NTT of every output polynomial, then c0 -= round(q s / t) for the mask of output o.
+cudaError_t launch_intt_mask(const Consts& C, u64* out, u64 out_cts, u64 seed, cudaStream_t st);
+
+}  // namespace he

@@ -1,0 +1,279 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Everything here is exact integer work, so the bar is bit-exactness: every
+ciphertext word, key word, packed coefficient and share must equal the
+oracle's on the same seeded inputs.  Inputs come from the seeded generators
+and the oracle's own encryption; nothing the GPU computes is fed to the
+oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_util import need_gpu, to_dev, to_np
+from paper_2305_18396_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = [(64, 2), (4096, 2), (8192, 3)]
+_CTX = {}
+
+
+@pytest.fixture(scope="module")
+def B():
+    need_gpu()
+    from paper_2305_18396_gb300 import binding
+
+    return binding
+
+
+def ctx_for(B, N, L):
+    if (N, L) not in _CTX:
+        _CTX[(N, L)] = (B.Context(N, L), O.Params(N, L))
+    return _CTX[(N, L)]
+
+
+def _rand_residues(P, cnt, seed):
+    rng = np.random.default_rng(seed)
+    a = np.zeros((cnt, P.L, P.N), dtype=np.uint64)
+    for li, q in enumerate(P.q):
+        a[:, li] = rng.integers(0, q, size=(cnt, P.N), dtype=np.uint64)
+    return a
+
+
+def _pointwise(P, fa, fb):
+    out = np.zeros_like(fa)
+    for li, q in enumerate(P.q):
+        out[:, li] = ((fa[:, li].astype(object) * fb[:, li].astype(object)) % q).astype(np.uint64)
+    return out
+
+
+# ------------------------------------------------------------------ NTT
+
+
+@pytest.mark.parametrize("N,L", PARAMS)
+def test_ntt_roundtrip_and_negacyclic_product(B, N, L):
+    ctx, P = ctx_for(B, N, L)
+    a = _rand_residues(P, 3, 1)
+    b = _rand_residues(P, 3, 2)
+    t = to_dev(a)
+    B.he_ntt_forward(ctx, t)
+    assert not np.array_equal(to_np(t, a.shape), a)
+    B.he_ntt_inverse(ctx, t)
+    assert np.array_equal(to_np(t, a.shape), a)
+    c = B.he_poly_mul(ctx, to_dev(a), to_dev(b))
+    want = O.ntt_inverse(P, _pointwise(P, O.ntt_forward(P, a), O.ntt_forward(P, b)))
+    assert np.array_equal(to_np(c, a.shape), want)
+
+
+def test_ntt_slot_order(B):
+    """Slot j of the forward transform holds a(psi^{2 brev(j) + 1}) for the library's psi."""
+    N, L = 4096, 2
+    ctx, P = ctx_for(B, N, L)
+    psi_gpu = ctx.params()["psi"]
+    a = _rand_residues(P, 1, 3)
+    t = to_dev(a)
+    B.he_ntt_forward(ctx, t)
+    got = to_np(t, a.shape)
+    ref = O.ntt_forward(P, a)  # ref[k] = a(psi_oracle^{2k+1})
+    logN = N.bit_length() - 1
+    brev = np.array([int(format(j, f"0{logN}b")[::-1], 2) for j in range(N)])
+    for li, q in enumerate(P.q):
+        u = next(e for e in range(1, 2 * N, 2) if pow(P.psi[li], e, q) == psi_gpu[li])
+        k = ((u * (2 * brev + 1)) % (2 * N) - 1) // 2
+        assert np.array_equal(got[0, li], ref[0, li][k])
+
+
+# ------------------------------------------------------------------ test client
+
+
+@pytest.mark.parametrize("N,L", PARAMS)
+def test_keygen_encrypt_decrypt_bit_exact(B, N, L):
+    ctx, P = ctx_for(B, N, L)
+    sk = B.he_keygen(ctx, S.SEED_KEY)
+    s = O.keygen(P, S.SEED_KEY)
+    coeff = sk.clone()
+    B.he_ntt_inverse(ctx, coeff)
+    want = np.stack([np.array([int(v) % q for v in s], dtype=np.uint64) for q in P.q])
+    assert np.array_equal(to_np(coeff, (L, N)), want)
+
+    plain = S.uniform_plaintexts(3, N, 17)
+    ct = B.he_encrypt(ctx, sk, to_dev(plain), S.SEED_ENC)
+    ct_or = O.encrypt(P, s, plain, S.SEED_ENC)
+    assert np.array_equal(to_np(ct, ct_or.shape), ct_or)
+
+    dec, budget = B.he_decrypt(ctx, sk, to_dev(ct_or), check_noise=True)
+    dec_or, budget_or = O.decrypt(P, s, ct_or)
+    assert np.array_equal(to_np(dec, (3, N)), plain)
+    assert np.array_equal(dec_or, plain)
+    assert np.all(np.abs(budget.cpu().numpy() - budget_or) <= 1)
+
+
+def test_decrypt_reports_exhausted_noise(B):
+    """A ciphertext with random c0 has no noise budget left: HE_ENOISE, host-side."""
+    ctx, P = ctx_for(B, 4096, 2)
+    sk = B.he_keygen(ctx, 1)
+    junk = _rand_residues(P, 2, 9).reshape(1, 2, P.L, P.N)
+    with pytest.raises(B.HEError) as e:
+        B.he_decrypt(ctx, sk, to_dev(junk), check_noise=True)
+    assert e.value.code == B.HE_ENOISE
+
+
+def test_pack_unpack_unmask(B):
+    ctx, P = ctx_for(B, 4096, 2)
+    m, k, n, blk = 37, 70, 45, (8, 16, 32)
+    X = S.uniform_share((m, k), 5)
+    polys = B.he_pack_input(ctx, to_dev(X), m, k, blk)
+    want = O.pack_input(X, blk, P.N)
+    assert np.array_equal(to_np(polys, want.shape), want)
+    nI, nJ, nLb = O.blocks(m, k, n, blk)
+    dec = S.uniform_plaintexts(nLb * nI, P.N, 6)
+    share = B.he_unpack_output(ctx, to_dev(dec), m, n, blk)
+    assert np.array_equal(to_np(share, (m, n)), O.unpack_output(dec, m, n, blk))
+    srv = B.he_unmask(ctx, 77, m, n, blk)
+    assert np.array_equal(to_np(srv, (m, n)), O.unmask(P, 77, m, n, blk))
+
+
+# ------------------------------------------------------------------ Algorithm 1 (server)
+
+
+def _run_case(B, N, L, m, k, n, blk, W, X, mask_seed=5, host=False):
+    ctx, P = ctx_for(B, N, L)
+    s = O.keygen(P, S.SEED_KEY)
+    ct_in = O.encrypt(P, s, O.pack_input(X, blk, N), S.SEED_ENC)
+    pt = B.he_encode_weights(ctx, to_dev(W), k, n, blk)
+    if host:
+        ws = ctx.empty(B.matmul_host_workspace_words(ctx, m, k, n, blk))
+        si = ctx.sizes(m, k, n, blk)
+        out_host = torch.empty(si["out_words"], dtype=torch.int64).pin_memory()
+        B.he_matmul_host(ctx, torch.from_numpy(ct_in.reshape(-1).view(np.int64)).pin_memory(), pt, m, k, n, blk,
+                         mask_seed, out_host, ws)
+        got = out_host.numpy().view(np.uint64)
+    else:
+        out = B.he_matmul(ctx, to_dev(ct_in), pt, m, k, n, blk, mask_seed)
+        got = to_np(out)
+    want = O.matmul(P, ct_in, W, m, k, n, blk, mask_seed)
+    assert np.array_equal(got.reshape(want.shape), want)
+    # end to end: client decrypts + server unmasks = X W mod t
+    dec, budget = O.decrypt(P, s, want)
+    client = O.unpack_output(dec, m, n, blk)
+    server = to_np(B.he_unmask(ctx, mask_seed, m, n, blk), (m, n))
+    assert np.array_equal((client + server) % np.uint64(P.t), O.plain_matmul_mod_t(X, W, P.t))
+    assert (budget > 0).all()
+
+
+MATMUL_CASES = [
+    # (N, L, m, k, n, blocking, weights kind)
+    (4096, 2, 16, 64, 64, (8, 32, 16), "fixed"),       # the single-product configuration
+    (4096, 2, 9, 70, 37, (4, 32, 32), "fixed"),        # ragged in every dimension
+    (4096, 2, 12, 40, 24, (4, 16, 64), "uniform"),     # share x share
+    (8192, 3, 7, 33, 20, (8, 32, 32), "uniform"),
+    (64, 2, 5, 6, 7, (2, 4, 8), "fixed"),              # N below one MAC thread block
+    (4096, 2, 1, 1, 1, (1, 1, 1), "uniform"),          # degenerate 1 x 1 x 1
+    (1024, 2, 1, 4096, 4, (1, 1, 4), "uniform"),       # 4096 k-blocks: accumulator headroom limit
+]
+
+
+@pytest.mark.parametrize("N,L,m,k,n,blk,kind", MATMUL_CASES)
+def test_matmul_bit_exact(B, N, L, m, k, n, blk, kind):
+    X = S.uniform_share((m, k), S.SEED_X)
+    W = S.fixed_point_weights((k, n), S.SEED_W) if kind == "fixed" else S.uniform_share((k, n), S.SEED_W)
+    _run_case(B, N, L, m, k, n, blk, W, X)
+
+
+def test_matmul_host_buffers(B):
+    X = S.uniform_share((16, 64), S.SEED_X)
+    W = S.fixed_point_weights((64, 64), S.SEED_W)
+    _run_case(B, 4096, 2, 16, 64, 64, (8, 32, 16), W, X, host=True)
+
+
+def test_matmul_default_blocking_single_config(B):
+    ctx, _ = ctx_for(B, 4096, 2)
+    blk = ctx.default_blocking(16, 64, 64)
+    X = S.uniform_share((16, 64), S.SEED_X)
+    W = S.fixed_point_weights((64, 64), S.SEED_W)
+    _run_case(B, 4096, 2, 16, 64, 64, blk, W, X)
+
+
+def test_matmul_argument_errors(B):
+    ctx, _ = ctx_for(B, 4096, 2)
+    blk = (8, 32, 16)
+    si = ctx.sizes(16, 64, 64, blk)
+    ct = ctx.empty(si["in_words"])
+    pt = ctx.empty(si["pt_words"])
+    out = ctx.empty(si["out_words"])
+    small = ctx.empty(si["workspace_bytes"] // 8 - 1)
+    with pytest.raises(B.HEError) as e:
+        B.he_matmul(ctx, ct, pt, 16, 64, 64, blk, 1, out, small)
+    assert e.value.code == B.HE_ENOMEM
+    with pytest.raises(B.HEError) as e:
+        B.he_matmul(ctx, ct, pt, 16, 64, 64, (16, 32, 16), 1, out)
+    assert e.value.code == B.HE_EINVAL
+    with pytest.raises(B.HEError) as e:
+        B.he_matmul(ctx, ct, pt, 16, 64, 64, blk, 1, out, flags=7)
+    assert e.value.code == B.HE_EINVAL
+    # empty product: valid no-op
+    assert B.lib.he_matmul(ctx.h, None, None, 0, 64, 64, B._blk(blk), 1, 0, None, None, 0, None) == B.HE_OK
+
+
+def test_launch_count_and_profile(B):
+    ctx, _ = ctx_for(B, 4096, 2)
+    X = S.uniform_share((16, 64), 1)
+    W = S.fixed_point_weights((64, 64), 2)
+    blk = (8, 32, 16)
+    pt = B.he_encode_weights(ctx, to_dev(W), 64, 64, blk)
+    polys = B.he_pack_input(ctx, to_dev(X), 16, 64, blk)
+    sk = B.he_keygen(ctx, 3)
+    ct = B.he_encrypt(ctx, sk, polys, 4)
+    before = B.he_launch_count(ctx)
+    B.he_profile_enable(ctx, True)
+    B.he_matmul(ctx, ct, pt, 16, 64, 64, blk, 5)
+    stats = B.he_profile_read(ctx)
+    B.he_profile_enable(ctx, False)
+    assert B.he_launch_count(ctx) - before == 3
+    assert set(stats) == {"ntt_forward", "mac", "intt_mask"}
+    assert all(v["launches"] == 1 and v["total_ms"] > 0 for v in stats.values())
+
+
+# ------------------------------------------------------------------ full-size layer products, sampled
+
+
+def bert_layer_cases():
+    from paper_2305_18396_gb300 import workloads
+
+    return workloads.bert_layer_products(seq=128, hidden=768, ffn=3072, heads=12, distinct_heads=1)
+
+
+@pytest.mark.parametrize("prod", bert_layer_cases(), ids=lambda p: p.name)
+def test_bert_base_layer_products_sampled(B, prod):
+    """Every distinct product shape of one BERT-base layer at seq 128 (N=4096, L=2), run at
+    full size with the blocking the benchmark uses; sampled output ciphertexts must match the
+    oracle bit for bit and decrypt (with the server's unmask) to X W mod t."""
+    N, L = 4096, 2
+    ctx, P = ctx_for(B, N, L)
+    m, k, n = prod.m, prod.k, prod.n
+    blk = ctx.default_blocking(m, k, n)
+    X = S.uniform_share((m, k), S.SEED_X)
+    W = S.uniform_share((k, n), S.SEED_W) if prod.share_weights else S.fixed_point_weights((k, n), S.SEED_W)
+    s = O.keygen(P, S.SEED_KEY)
+    ct_in = O.encrypt(P, s, O.pack_input(X, blk, N), S.SEED_ENC)
+    pt = B.he_encode_weights(ctx, to_dev(W), k, n, blk)
+    out = to_np(B.he_matmul(ctx, to_dev(ct_in), pt, m, k, n, blk, S.SEED_MASK))
+    nI, nJ, nLb = O.blocks(m, k, n, blk)
+    total = nI * nLb
+    rng = np.random.default_rng(11)
+    sel = sorted({0, total - 1, *map(int, rng.integers(0, total, 2))})
+    want = O.matmul(P, ct_in, W, m, k, n, blk, S.SEED_MASK, sel=sel)
+    got = out.reshape(total, 2, L, N)[sel]
+    assert np.array_equal(got, want)
+    dec, _ = O.decrypt(P, s, want)
+    m_b, k_b, n_b = blk
+    ref = O.plain_matmul_mod_t(X, W, P.t)
+    for row, o in enumerate(sel):
+        Lb, I = divmod(o, nI)
+        mask = O.mask_poly(P, S.SEED_MASK, o)
+        for l in range(min(m_b, m - Lb * m_b)):
+            for i in range(min(n_b, n - I * n_b)):
+                pos = l * n_b * k_b + i * k_b + k_b - 1
+                assert (int(dec[row][pos]) + int(mask[pos])) % P.t == int(ref[Lb * m_b + l, I * n_b + i])
