@@ -366,8 +366,10 @@ __global__ void __launch_bounds__(kNttThreads) k_intt_mask(u64* out, u64 seed, c
 
 static size_t poly_smem(const Consts& C) { return (size_t)C.N * sizeof(u64); }
 
-cudaError_t configure_kernels(const Consts& C) {
-  const int one = (int)poly_smem(C), two = 2 * one, all = (int)(C.L * poly_smem(C));
+// The attribute is per function and device, shared by every context: always raise it to the
+// largest size any supported parameter set uses (N <= 8192, L * N <= 3 * 8192).
+cudaError_t configure_kernels(const Consts&) {
+  const int one = 8192 * (int)sizeof(u64), two = 2 * one, all = 3 * one;
   cudaError_t e = cudaSuccess;
   auto set = [&](const void* f, int bytes) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);

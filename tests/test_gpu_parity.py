@@ -107,7 +107,8 @@ def test_keygen_encrypt_decrypt_bit_exact(B, N, L):
     dec_or, budget_or = O.decrypt(P, s, ct_or)
     assert np.array_equal(to_np(dec, (3, N)), plain)
     assert np.array_equal(dec_or, plain)
-    assert np.all(np.abs(budget.cpu().numpy() - budget_or) <= 1)
+    # the library resolves the fraction to 2^-64, so its budget saturates at 63 bits
+    assert np.all(np.abs(budget.cpu().numpy() - np.minimum(budget_or, 63)) <= 1)
 
 
 def test_decrypt_reports_exhausted_noise(B):
@@ -203,10 +204,10 @@ def test_matmul_argument_errors(B):
     ct = ctx.empty(si["in_words"])
     pt = ctx.empty(si["pt_words"])
     out = ctx.empty(si["out_words"])
-    small = ctx.empty(si["workspace_bytes"] // 8 - 1)
-    with pytest.raises(B.HEError) as e:
-        B.he_matmul(ctx, ct, pt, 16, 64, 64, blk, 1, out, small)
-    assert e.value.code == B.HE_ENOMEM
+    ws = ctx.empty(si["workspace_bytes"] // 8)
+    rc = B.lib.he_matmul(ctx.h, B._ptr(ct), B._ptr(pt), 16, 64, 64, B._blk(blk), 1, 0, B._ptr(out), B._ptr(ws),
+                         si["workspace_bytes"] - 8, B._stream(None))
+    assert rc == B.HE_ENOMEM and "workspace" in B.lib.he_last_error().decode()
     with pytest.raises(B.HEError) as e:
         B.he_matmul(ctx, ct, pt, 16, 64, 64, (16, 32, 16), 1, out)
     assert e.value.code == B.HE_EINVAL
