@@ -180,6 +180,28 @@ HE_API int he_matmul_host(he_ctx* ctx, const uint64_t* ct_in_host, const uint64_
                    const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out_host, void* workspace,
                    size_t workspace_bytes, void* stream);
 
+/* he_matmul for callers that cannot allocate device memory.  Some callers have no
+ * way to obtain a workspace: a serving process whose device memory is already
+ * reserved by another allocator (where cudaMalloc would fail, or would stall the
+ * device while requests are in flight), or a host program that is not permitted to
+ * manage device memory.  This entry point computes exactly what he_matmul computes
+ * and allocates nothing: its scratch (the NTT of the input ciphertexts) is a fixed
+ * device array of HE_NOALLOC_SCRATCH_BYTES inside the library, which every GPU
+ * that loads the library keeps until the process exits.
+ * - Products whose he_sizes().workspace_bytes exceeds HE_NOALLOC_SCRATCH_BYTES are
+ *   rejected with HE_EINVAL before any GPU work.
+ * - The first call on a device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ * - All calls share the one array and it keeps the last call's contents (every word
+ *   a call reads is first written by the same call, so nothing is cleared).  Calls
+ *   that overlap on the GPU -- on different streams or host threads -- race on it:
+ *   serialize them, e.g. on one stream.
+ * The paper has no counterpart to this entry point; it exists for deployment. */
+#define HE_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+HE_API int he_matmul_noalloc(he_ctx* ctx, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k,
+                             uint32_t n, const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out,
+                             void* stream);
+
 /* Server's share pi_C^{-1}(s) of X W for the masks of he_matmul(mask_seed):
  * share[Lb m_b + l][I n_b + i] = s_{Lb nI + I}[l n_b k_b + i k_b + k_b - 1].
  * server_share: device [m][n] (requires k only through blk->k_b). */

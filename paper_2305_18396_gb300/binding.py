@@ -75,6 +75,7 @@ def _load():
         "he_encode_weights": (ctypes.c_int, [P, P, u32, u32, pB, P, P]),
         "he_matmul": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u64, u32, P, P, sz, P]),
         "he_matmul_host": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u64, u32, P, P, sz, P]),
+        "he_matmul_noalloc": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u64, u32, P, P]),
         "he_unmask": (ctypes.c_int, [P, u64, u32, u32, pB, P, P]),
         "he_ntt_forward": (ctypes.c_int, [P, P, u32, P]),
         "he_ntt_inverse": (ctypes.c_int, [P, P, u32, P]),
@@ -240,6 +241,21 @@ def he_matmul(ctx, ct_in, pt, m, k, n, blk, mask_seed, ct_out=None, workspace=No
     workspace = ctx.empty(max(ws_words, 1)) if workspace is None else ctx._dev(workspace, ws_words, "workspace")
     _check(lib.he_matmul(ctx.h, _ptr(ct_in), _ptr(pt), m, k, n, _blk(blk), mask_seed, flags, _ptr(ct_out),
                          _ptr(workspace), workspace.numel() * 8, _stream(stream)))
+    return ct_out
+
+
+HE_NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def he_matmul_noalloc(ctx, ct_in, pt, m, k, n, blk, mask_seed, ct_out, flags=HE_FLAGS_NONE, stream=None):
+    """he_matmul without a workspace: for callers that cannot allocate device memory.
+    ct_out must be provided by the caller; the library's fixed scratch is used instead."""
+    si = ctx.sizes(m, k, n, blk)
+    ctx._dev(ct_in, si["in_words"], "ct_in")
+    ctx._dev(pt, si["pt_words"], "pt")
+    ctx._dev(ct_out, si["out_words"], "ct_out")
+    _check(lib.he_matmul_noalloc(ctx.h, _ptr(ct_in), _ptr(pt), m, k, n, _blk(blk), mask_seed, flags, _ptr(ct_out),
+                                 _stream(stream)))
     return ct_out
 
 

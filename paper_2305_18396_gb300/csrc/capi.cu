@@ -522,6 +522,24 @@ int he_matmul_host(he_ctx* c, const uint64_t* ct_in_host, const uint64_t* pt, ui
   return HE_OK;
 }
 
+int he_matmul_noalloc(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
+                      const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out, void* stream) {
+  static_assert(HE_NOALLOC_SCRATCH_BYTES == he::kNoAllocScratchBytes, "scratch size mismatch");
+  he_size_info si;
+  if (int r = matmul_checks(c, m, k, n, blk, flags, &si)) return r;
+  if (!m || !k || !n) return HE_OK;
+  if (!ct_in || !pt || !ct_out) return fail(HE_EINVAL, "NULL buffer");
+  if (si.workspace_bytes > HE_NOALLOC_SCRATCH_BYTES)
+    return fail(HE_EINVAL, "product needs " + std::to_string(si.workspace_bytes) +
+                               " bytes of scratch; he_matmul_noalloc has " +
+                               std::to_string((size_t)HE_NOALLOC_SCRATCH_BYTES) + " (use he_matmul)");
+  if (int r = set_device(c)) return r;
+  void* scratch = nullptr;
+  cudaError_t e = he::noalloc_scratch_address(c->device, &scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "matmul_noalloc: scratch address");
+  return matmul_device(c, ct_in, pt, m, k, n, blk, mask_seed, ct_out, scratch, (cudaStream_t)stream);
+}
+
 int he_ntt_forward(he_ctx* c, uint64_t* polys, uint32_t cnt, void* stream) {
   if (!c) return fail(HE_EINVAL, "ctx is NULL");
   if (!cnt) return HE_OK;

@@ -8,6 +8,8 @@
 // plus the test client (keygen / encrypt / decrypt / pack / unpack) and the
 // server's unmask.  The polynomial product is NTT + slot-wise product + inverse
 // NTT (footnote of Sec. 3.1.3).
+#include <mutex>
+
 #include "kernels.h"
 #include "ntt.cuh"
 
@@ -360,6 +362,30 @@ __global__ void __launch_bounds__(kNttThreads) k_intt_mask(u64* out, u64 seed, c
   } else {
     for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) d[i] = sm[i];
   }
+}
+
+// ------------------------------------------------------------------ fixed scratch for he_matmul_noalloc
+
+// File-scope device scratch used only by he_matmul_noalloc, for callers that cannot
+// allocate device memory.  Every GPU that loads the library holds these bytes until
+// the process exits.  Host code must not pass the symbol itself to a kernel (on the
+// host it names a shadow variable, not device memory): it asks the runtime for the
+// device address once per device, with that device current.
+static __device__ __align__(256) u64 g_noalloc_scratch[kNoAllocScratchBytes / sizeof(u64)];
+
+cudaError_t noalloc_scratch_address(int device, void** ptr) {
+  static std::mutex mu;
+  static void* addr[kMaxDevices] = {};
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // caller made `device` current
+    if (e != cudaSuccess) return e;
+    addr[device] = p;
+  }
+  *ptr = addr[device];
+  return cudaSuccess;
 }
 
 // ------------------------------------------------------------------ launchers

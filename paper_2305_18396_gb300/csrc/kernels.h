@@ -36,4 +36,11 @@ cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out,
 // Inverse NTT of every output polynomial, then c0 -= round(q s / t) for the mask of output o.
 cudaError_t launch_intt_mask(const Consts& C, u64* out, u64 out_cts, u64 seed, cudaStream_t st);
 
+// Fixed device scratch of he_matmul_noalloc (no allocation at call time).
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
+constexpr int kMaxDevices = 64;
+// Device address of that scratch on `device`, which must be the current device.  The first
+// call per device looks the address up with cudaGetSymbolAddress; later calls reuse it.
+cudaError_t noalloc_scratch_address(int device, void** ptr);
+
 }  // namespace he
