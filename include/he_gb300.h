@@ -235,6 +235,12 @@ typedef struct {
 HE_API int he_profile_enable(he_ctx* ctx, int on);
 /* Synchronizes the recorded events and returns up to cap stats in *n. */
 HE_API int he_profile_read(he_ctx* ctx, he_kernel_stat* out, uint32_t cap, uint32_t* n);
+/* Synchronizes `stream` and reports whether any kernel of this context gave up a
+ * bounded wait (a data copy that never completed) since the last call:
+ * HE_ETIMEOUT if so (the flag is then cleared; the affected outputs are invalid),
+ * HE_OK otherwise. */
+HE_API int he_device_status(he_ctx* ctx, void* stream);
+
 /* Number of kernels this context has launched since creation. */
 HE_API int he_launch_count(const he_ctx* ctx, uint64_t* out);
 

@@ -84,6 +84,7 @@ def _load():
         "he_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "he_profile_read": (ctypes.c_int, [P, ctypes.POINTER(KernelStat), u32, pu32]),
         "he_launch_count": (ctypes.c_int, [P, pu64]),
+        "he_device_status": (ctypes.c_int, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(so, name)
@@ -320,6 +321,11 @@ def he_profile_read(ctx):
     n = ctypes.c_uint32()
     _check(lib.he_profile_read(ctx.h, buf, 32, ctypes.byref(n)))
     return {buf[i].name.decode(): {"launches": buf[i].launches, "total_ms": buf[i].total_ms} for i in range(n.value)}
+
+
+def he_device_status(ctx, stream=None):
+    """Raises HEError(HE_ETIMEOUT) if a kernel's bounded wait expired since the last check."""
+    _check(lib.he_device_status(ctx.h, _stream(stream)))
 
 
 def he_launch_count(ctx):

@@ -125,6 +125,7 @@ struct he_ctx {
   he::Consts C{};
   u64 psi[he::kMaxPrimes] = {};
   u64* d_tables = nullptr;
+  int* d_err = nullptr;  // set by kernels whose bounded waits expired
   std::atomic<uint64_t> launches{0};
   bool prof = false;
   std::vector<ProfRec> recs;
@@ -249,10 +250,10 @@ int he_params_init(he_ctx** out, uint32_t N, uint32_t L, const uint64_t* q, uint
     P.ninv_sh = shoup(P.ninv, ql);
     P.tinv = invm((1ull << log2_t) % ql, ql);
     P.tinv_sh = shoup(P.tinv, ql);
-    P.r26 = (1ull << 26) % ql;
-    P.r26_sh = shoup(P.r26, ql);
-    P.r52 = (1ull << 52) % ql;
-    P.r52_sh = shoup(P.r52, ql);
+    P.r25 = (1ull << 25) % ql;
+    P.r25_sh = shoup(P.r25, ql);
+    P.r50 = (1ull << 50) % ql;
+    P.r50_sh = shoup(P.r50, ql);
     P.r64 = (u64)(((u128)1 << 64) % ql);
     P.r64_sh = shoup(P.r64, ql);
     u64 Ml = 1;
@@ -271,14 +272,18 @@ int he_params_init(he_ctx** out, uint32_t N, uint32_t L, const uint64_t* q, uint
     return cuda_fail(e, "cudaSetDevice");
   }
   e = cudaMalloc(&c->d_tables, host.size() * sizeof(u64));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
   if (e != cudaSuccess) {
+    if (c->d_tables) cudaFree(c->d_tables);
     delete c;
-    return fail(HE_ENOMEM, "cudaMalloc of twiddle tables failed");
+    return fail(HE_ENOMEM, "cudaMalloc of context tables failed");
   }
-  e = cudaMemcpy(c->d_tables, host.data(), host.size() * sizeof(u64), cudaMemcpyHostToDevice);
+  e = cudaMemset(c->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_tables, host.data(), host.size() * sizeof(u64), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = he::configure_kernels(C);
   if (e != cudaSuccess) {
     cudaFree(c->d_tables);
+    cudaFree(c->d_err);
     delete c;
     return cuda_fail(e, "table upload / kernel configuration");
   }
@@ -302,6 +307,7 @@ int he_ctx_free(he_ctx* c) {
   }
   for (auto e : c->pool) cudaEventDestroy(e);
   if (c->d_tables) cudaFree(c->d_tables);
+  if (c->d_err) cudaFree(c->d_err);
   delete c;
   return HE_OK;
 }
@@ -466,13 +472,12 @@ int he_encode_weights(he_ctx* c, const uint64_t* W, uint32_t k, uint32_t n, cons
 static int matmul_device(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
                          const he_blocking* blk, uint64_t mask_seed, uint64_t* ct_out, void* ws, cudaStream_t st) {
   Shape s = shape_of(m, k, n, blk);
-  const u64 in_polys = (u64)s.nLb * s.nJ * 2 * c->C.L;
   u64* ctN = (u64*)ws;
   int r = launch(c, KNttFwd, st, "matmul: forward NTT",
-                 [&] { return he::launch_ntt_forward(c->C, ct_in, ctN, in_polys, st); });
+                 [&] { return he::launch_ntt_forward_mm(c->C, ct_in, ctN, s.nJ, s.nLb, st); });
   if (r) return r;
   r = launch(c, KMac, st, "matmul: multiply-accumulate",
-             [&] { return he::launch_mac(c->C, ctN, pt, ct_out, s.nI, s.nJ, s.nLb, st); });
+             [&] { return he::launch_mac(c->C, ctN, pt, ct_out, s.nI, s.nJ, s.nLb, c->d_err, st); });
   if (r) return r;
   return launch(c, KInttMask, st, "matmul: inverse NTT + mask",
                 [&] { return he::launch_intt_mask(c->C, ct_out, (u64)s.nLb * s.nI, mask_seed, st); });
@@ -621,6 +626,20 @@ int he_profile_read(he_ctx* c, he_kernel_stat* out, uint32_t cap, uint32_t* n) {
   }
   *n = cnt;
   return HE_OK;
+}
+
+int he_device_status(he_ctx* c, void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (int r = set_device(c)) return r;
+  int flag = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && flag) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "device status readback");
+  return flag ? fail(HE_ETIMEOUT, "a kernel's bounded wait for its data expired; results of that call are invalid")
+              : HE_OK;
 }
 
 int he_launch_count(const he_ctx* c, uint64_t* out) {

@@ -27,8 +27,8 @@ struct PrimeConsts {
   u64 mu;          // floor(2^64 / q): Shoup companion of 1 (Barrett-style reduction of a word)
   u64 ninv, ninv_sh;   // N^{-1} mod q
   u64 tinv, tinv_sh;   // t^{-1} mod q
-  u64 r26, r26_sh;     // 2^26 mod q
-  u64 r52, r52_sh;     // 2^52 mod q
+  u64 r25, r25_sh;     // 2^25 mod q
+  u64 r50, r50_sh;     // 2^50 mod q
   u64 r64, r64_sh;     // 2^64 mod q
   u64 crt, crt_sh;     // ((Q / q)^{-1} mod q), for decryption
   u64 theta_hi, theta_lo;  // floor(t 2^128 / q) as two words (decryption)

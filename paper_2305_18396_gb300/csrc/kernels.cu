@@ -3,13 +3,14 @@
 // Server hot path of Algorithm 1 (Sec. 3.1.1) on RNS BFV (Sec. 2.2):
 //   k_encode_weights  pi_A of W^T blocks -> centred lift -> mod q_l -> NTT (resident)
 //   k_ntt_forward     NTT of every input ciphertext polynomial (to workspace)
-//   k_mac             slot-wise sum_J pt[I][J] * ct[Lb][J], lazy 3-column accumulation
+//   k_mac             slot-wise sum_J pt[I][J] * ct[Lb][J]: bulk-copy pipeline, Karatsuba lazy accumulation
 //   k_intt_mask       inverse NTT of each output polynomial + re-mask of c0
 // plus the test client (keygen / encrypt / decrypt / pack / unpack) and the
 // server's unmask.  The polynomial product is NTT + slot-wise product + inverse
 // NTT (footnote of Sec. 3.1.3).
 #include <mutex>
 
+#include "async.cuh"
 #include "kernels.h"
 #include "ntt.cuh"
 
@@ -20,9 +21,6 @@ __constant__ u64 c_gauss_cdt[2 * kGaussBound] = {
 };
 
 constexpr int kNttThreads = 256;
-constexpr int kMacThreads = 128;
-constexpr int kMacTI = 4;  // output blocks I per thread
-constexpr int kMacTB = 2;  // output blocks Lb per thread (x 2 ciphertext components)
 
 // a * b mod q for a, b < q < 2^50 (128-bit product folded with 2^64 mod q).
 __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeConsts& P) {
@@ -80,6 +78,49 @@ __global__ void __launch_bounds__(kNttThreads) k_poly_mul(const u64* a, const u6
   __syncthreads();
   ntt_inverse_smem(sa, C.logN, P);
   for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) c[poly * C.N + i] = sa[i];
+}
+
+// Forward NTT of matmul inputs for N < 512 into the slot-chunked layout (see k_mac_t).
+__host__ __device__ constexpr u64 chunked_index(u64 row, u32 J, u32 l, u32 s, u32 nJ, u32 L, u32 N);
+__global__ void __launch_bounds__(kNttThreads) k_ntt_forward_mm_small(const u64* src, u64* ctN, u32 nJ,
+                                                                      const __grid_constant__ Consts C) {
+  extern __shared__ u64 sm[];
+  const u64 poly = blockIdx.x;
+  const u32 l = poly % C.L;
+  const u32 c = (poly / C.L) % 2;
+  const u32 LbJ = (u32)(poly / (2 * C.L));
+  const u32 Lb = LbJ / nJ, J = LbJ % nJ;
+  const PrimeConsts& P = C.p[l];
+  for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) sm[i] = src[poly * C.N + i];
+  __syncthreads();
+  ntt_forward_smem(sm, C.logN, P);
+  for (u32 i = threadIdx.x; i < C.N; i += blockDim.x)
+    ctN[chunked_index((u64)Lb * 2 + c, J, l, i, nJ, C.L, C.N)] = sm[i];
+}
+
+// Register-blocked versions for N >= 512 (blockDim = NttShape<LOGN>::T).
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_forward_t(const u64* src, u64* dst,
+                                                                     const __grid_constant__ Consts C) {
+  using S = NttShape<LOGN>;
+  extern __shared__ u64 sm[];
+  const u64 poly = blockIdx.x;
+  const PrimeConsts& P = C.p[poly % C.L];
+  const u64* s = src + poly * S::N;
+  u64* d = dst + poly * S::N;
+  ntt_forward_block<S>(sm, P, [&](u32 e) { return s[e]; }, [&](u32 e, u64 v) { d[e] = v; });
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_inverse_t(const u64* src, u64* dst,
+                                                                     const __grid_constant__ Consts C) {
+  using S = NttShape<LOGN>;
+  extern __shared__ u64 sm[];
+  const u64 poly = blockIdx.x;
+  const PrimeConsts& P = C.p[poly % C.L];
+  const u64* s = src + poly * S::N;
+  u64* d = dst + poly * S::N;
+  ntt_inverse_block<S>(sm, P, [&](u32 e) { return s[e]; }, [&](u32 e, u64 v) { d[e] = v; });
 }
 
 // ------------------------------------------------------------------ test client
@@ -261,84 +302,221 @@ __global__ void __launch_bounds__(kNttThreads) k_encode_weights(const u64* W, u3
   }
   __syncthreads();
   ntt_forward_smem(sm, C.logN, P);
-  u64* d = pt + poly * C.N;
-  for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) d[i] = sm[i];
+  for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) pt[chunked_index(I, J, l, i, nJ, C.L, C.N)] = sm[i];
 }
 
-// Slot-wise multiply-accumulate.  Each thread owns one slot s of prime l and a
-// kMacTI x kMacTB tile of output blocks (both components).  Operands < 2^50
-// are split as x = x0 + 2^26 x1 (x0 < 2^26, x1 < 2^24) and the products summed
-// in three 64-bit columns (one mad.wide.u32 per partial product; no carries
-// for nJ <= 4096), reduced once per output.
-__global__ void __launch_bounds__(kMacThreads) k_mac(const u64* __restrict__ ctN, const u64* __restrict__ pt,
-                                                     u64* __restrict__ out, u32 nI, u32 nJ, u32 nLb, u32 tilesI,
-                                                     const __grid_constant__ Consts C) {
-  const u32 chunks = (C.N + kMacThreads - 1) / kMacThreads;
-  const u32 s = (blockIdx.x % chunks) * kMacThreads + threadIdx.x;
-  if (s >= C.N) return;
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_encode_weights_t(const u64* W, u32 k, u32 n, Blk b, u32 nJ,
+                                                                        u64* pt, const __grid_constant__ Consts C) {
+  using S = NttShape<LOGN>;
+  extern __shared__ u64 sm[];
+  const u64 poly = blockIdx.x;
+  const u32 l = poly % C.L;
+  const u32 IJ = (u32)(poly / C.L);
+  const u32 I = IJ / nJ, J = IJ % nJ;
+  const PrimeConsts& P = C.p[l];
+  const u32 nk = b.n_b * b.k_b;
+  const u64 half_t = (C.tmask >> 1) + 1;
+  auto load = [&](u32 p) -> u64 {
+    if (p >= nk) return 0;
+    u32 i = p / b.k_b, j = b.k_b - 1 - p % b.k_b;
+    u32 row = J * b.k_b + j, col = I * b.n_b + i;
+    if (row >= k || col >= n) return 0;
+    u64 w = W[(u64)row * n + col] & C.tmask;
+    return w >= half_t ? P.q - (C.tmask + 1 - w) : w;  // centred lift [-t/2, t/2)
+  };
+  ntt_forward_block<S>(sm, P, load, [&](u32 e, u64 v) { pt[chunked_index(I, J, l, e, nJ, C.L, S::N)] = v; });
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_intt_mask_t(u64* out, u64 seed,
+                                                                   const __grid_constant__ Consts C) {
+  using S = NttShape<LOGN>;
+  extern __shared__ u64 sm[];
+  const u64 poly = blockIdx.x;
+  const u32 l = poly % C.L;
+  const u32 c = (poly / C.L) % 2;
+  const u32 o = (u32)(poly / (2 * C.L));
+  const PrimeConsts& P = C.p[l];
+  u64* d = out + poly * S::N;
+  ntt_inverse_block<S>(sm, P, [&](u32 e) { return d[e]; }, [&](u32 e, u64 v) {
+    if (c == 0) {
+      u64 sv = lo64(draw(seed, e, o, kDomainMask, 0)) & C.tmask;
+      v = sub_mod(v, delta_residue(sv, C, P), P.q);
+    }
+    d[e] = v;
+  });
+}
+
+// Slot-wise multiply-accumulate (Algorithm 1 step 3 in the NTT domain).  For each
+// prime l and slot s the outputs form a small matrix product over the k-blocks J:
+//   out[r][I] = sum_J ct[r][J] * pt[I][J],   r = (Lb, component c) rows, I columns.
+//
+// Operand layout ("slot-chunked"): both the NTT of the input ciphertexts and the
+// encoded weights store, for every row (resp. column), prime and chunk of 32 slots, the
+// 32-slot vectors of all nJ k-blocks contiguously:
+//   word ((row * L + l) * (N / 32) + s / 32) * nJ * 32 + J * 32 + s % 32.
+// A block owns one 32-slot chunk of one prime and a (kRows x kCols) output tile.  Per
+// stage, warp 0 streams JB consecutive k-blocks of every operand row of the tile into
+// shared memory -- one 1-D bulk copy (TMA) of JB * 256 contiguous bytes per row --
+// completing on the stage's mbarrier; STAGES stages are in flight.  Each thread owns one
+// slot and a TM x TN register tile.  Operands < 2^50 are split x = x0 + 2^25 x1 and
+// multiplied Karatsuba-style: three mad.wide.u32 per slot product into lo / mid / hi
+// 64-bit columns (no carries for nJ <= 4096), reduced once per output at the end.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: a copy that never lands is an error
+
+__device__ __forceinline__ void split25(u64 v, u32& a0, u32& a1, u32& as) {
+  a0 = (u32)v & ((1u << 25) - 1);
+  a1 = (u32)(v >> 25);
+  as = a0 + a1;
+}
+
+__host__ __device__ constexpr u64 chunked_index(u64 row, u32 J, u32 l, u32 s, u32 nJ, u32 L, u32 N) {
+  return ((row * L + l) * (N >> 5) + (s >> 5)) * (u64)nJ * 32 + (u64)J * 32 + (s & 31);
+}
+
+template <int TM, int TN, int WR, int WC, int JB, int STAGES>
+struct MacCfg {
+  static constexpr int kTM = TM, kTN = TN, kWR = WR, kWC = WC, kJB = JB, kStages = STAGES;
+  static constexpr int kRows = TM * WR, kCols = TN * WC;
+  static constexpr int kThreads = 32 * WR * WC;
+  static constexpr int kStageWords = (kRows + kCols) * JB * 32;
+  static constexpr size_t kSmemBytes = (size_t)STAGES * kStageWords * sizeof(u64);
+};
+
+template <class M, int MINB>
+__global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restrict__ ctN, const u64* __restrict__ pt,
+                                                             u64* __restrict__ out, u32 nI, u32 nJ, u32 nLb,
+                                                             u32 tilesR, int* err, const __grid_constant__ Consts C) {
+  extern __shared__ __align__(128) u64 sm[];
+  __shared__ __align__(8) uint64_t bars[M::kStages];
+  __shared__ int abort_flag;
+  constexpr int TM = M::kTM, TN = M::kTN, JB = M::kJB, ST = M::kStages;
+
+  const u32 N = C.N, L = C.L;
+  const u32 chunks = N >> 5;
+  const u32 chunk = blockIdx.x % chunks;
   const u32 tile = blockIdx.x / chunks;
+  const u32 r0 = (tile % tilesR) * M::kRows, c0 = (tile / tilesR) * M::kCols;
   const u32 l = blockIdx.y;
   const PrimeConsts& P = C.p[l];
-  const u32 I0 = (tile % tilesI) * kMacTI;
-  const u32 B0 = (tile / tilesI) * kMacTB;
-  const u64 N = C.N, L = C.L;
-  constexpr u32 M26 = (1u << 26) - 1;
+  const u32 rows = 2 * nLb;
+  const u32 nrows = min((u32)M::kRows, rows - r0), ncols = min((u32)M::kCols, nI - c0);
+  const u32 nstages = (nJ + JB - 1) / JB;
+  const u32 warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const u32 wr = warp % M::kWR, wc = warp / M::kWR;
 
-  u64 acc[kMacTI][kMacTB][2][3];
-#pragma unroll
-  for (int a = 0; a < kMacTI; ++a)
-#pragma unroll
-    for (int bb = 0; bb < kMacTB; ++bb)
-#pragma unroll
-      for (int c = 0; c < 2; ++c) acc[a][bb][c][0] = acc[a][bb][c][1] = acc[a][bb][c][2] = 0;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < ST; ++st) mbar_init(&bars[st], 1);
+    mbar_init_fence();
+    abort_flag = 0;
+  }
+  __syncthreads();
 
-  for (u32 J = 0; J < nJ; ++J) {
-    u32 x0[kMacTI], x1[kMacTI];
-#pragma unroll
-    for (int a = 0; a < kMacTI; ++a) {
-      u32 I = I0 + a;
-      u64 v = I < nI ? __ldg(pt + (((u64)I * nJ + J) * L + l) * N + s) : 0;
-      x0[a] = (u32)v & M26;
-      x1[a] = (u32)(v >> 26);
+  // warp 0: stream k-blocks [JB k, JB k + jb) of every operand row of the tile into stage st
+  auto issue = [&](u32 k, u32 st) {
+    const u32 J0 = k * JB, jb = min((u32)JB, nJ - J0);
+    const u32 bytes = jb * 32 * sizeof(u64);
+    if (lane == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bars[st], (nrows + ncols) * bytes);
     }
-    u32 y0[kMacTB][2], y1[kMacTB][2];
+    __syncwarp();
+    u64* stage = sm + st * M::kStageWords;
+    for (u32 i = lane; i < nrows + ncols; i += 32) {
+      const bool is_row = i < nrows;
+      const u64* src = is_row ? ctN + chunked_index(r0 + i, J0, l, chunk << 5, nJ, L, N)
+                              : pt + chunked_index(c0 + (i - nrows), J0, l, chunk << 5, nJ, L, N);
+      u64* dst = stage + (is_row ? i : M::kRows + (i - nrows)) * (JB * 32);
+      bulk_copy_g2s(dst, src, bytes, &bars[st]);
+    }
+  };
+
+  if (warp == 0)
+    for (u32 k = 0; k < (u32)ST && k < nstages; ++k) issue(k, k);
+
+  u64 lo[TM][TN], mid[TM][TN], hi[TM][TN];
 #pragma unroll
-    for (int bb = 0; bb < kMacTB; ++bb) {
-      u32 Lb = B0 + bb;
+  for (int a = 0; a < TM; ++a)
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        u64 v = Lb < nLb ? __ldg(ctN + ((((u64)Lb * nJ + J) * 2 + c) * L + l) * N + s) : 0;
-        y0[bb][c] = (u32)v & M26;
-        y1[bb][c] = (u32)(v >> 26);
+    for (int b = 0; b < TN; ++b) lo[a][b] = mid[a][b] = hi[a][b] = 0;
+
+  for (u32 k = 0; k < nstages; ++k) {
+    const u32 st = k % ST;
+    if (threadIdx.x == 0) {
+      if (!mbar_wait_bounded(&bars[st], (k / ST) & 1, kWaitLimitNs)) {
+        abort_flag = 1;
+        atomicExch(err, 1);
+        // let every other copy this block issued land (bounded) before the block exits
+        for (u32 k2 = k + 1; k2 < nstages && k2 < k + ST; ++k2)
+          mbar_wait_bounded(&bars[k2 % ST], (k2 / ST) & 1, kWaitLimitNs);
       }
     }
+    __syncthreads();
+    if (abort_flag) return;
+    const u64* stage = sm + st * M::kStageWords;
+    const u32 jb = min((u32)JB, nJ - k * JB);
+#pragma unroll 2
+    for (u32 jj = 0; jj < jb; ++jj) {
+      u32 p0[TN], p1[TN], ps[TN];
 #pragma unroll
-    for (int a = 0; a < kMacTI; ++a)
+      for (int b = 0; b < TN; ++b)
+        split25(stage[(M::kRows + wc * TN + b) * (JB * 32) + jj * 32 + lane], p0[b], p1[b], ps[b]);
 #pragma unroll
-      for (int bb = 0; bb < kMacTB; ++bb)
+      for (int a = 0; a < TM; ++a) {
+        u32 x0, x1, xs;
+        split25(stage[(wr * TM + a) * (JB * 32) + jj * 32 + lane], x0, x1, xs);
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          acc[a][bb][c][0] += (u64)x0[a] * y0[bb][c];
-          acc[a][bb][c][1] += (u64)x0[a] * y1[bb][c];
-          acc[a][bb][c][1] += (u64)x1[a] * y0[bb][c];
-          acc[a][bb][c][2] += (u64)x1[a] * y1[bb][c];
+        for (int b = 0; b < TN; ++b) {
+          lo[a][b] += (u64)x0 * p0[b];
+          hi[a][b] += (u64)x1 * p1[b];
+          mid[a][b] += (u64)xs * ps[b];
         }
+      }
+    }
+    __syncthreads();
+    if (warp == 0 && k + ST < nstages) issue(k + ST, st);
   }
 
+  const u32 s = (chunk << 5) + lane;
 #pragma unroll
-  for (int a = 0; a < kMacTI; ++a)
+  for (int a = 0; a < TM; ++a) {
+    const u32 r = r0 + wr * TM + a;
+    if (r >= rows) continue;
 #pragma unroll
-    for (int bb = 0; bb < kMacTB; ++bb) {
-      u32 I = I0 + a, Lb = B0 + bb;
-      if (I >= nI || Lb >= nLb) continue;
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        u64 r0 = reduce_word(acc[a][bb][c][0], P);
-        u64 r1 = csub(mul_shoup(acc[a][bb][c][1], P.r26, P.r26_sh, P.q), P.q);
-        u64 r2 = csub(mul_shoup(acc[a][bb][c][2], P.r52, P.r52_sh, P.q), P.q);
-        out[((((u64)Lb * nI + I) * 2 + c) * L + l) * N + s] = add_mod(add_mod(r0, r1, P.q), r2, P.q);
-      }
+    for (int b = 0; b < TN; ++b) {
+      const u32 I = c0 + wc * TN + b;
+      if (I >= nI) continue;
+      const u64 cross = mid[a][b] - lo[a][b] - hi[a][b];  // sum of x0 y1 + x1 y0
+      u64 v = reduce_word(lo[a][b], P);
+      v = add_mod(v, csub(mul_shoup(cross, P.r25, P.r25_sh, P.q), P.q), P.q);
+      v = add_mod(v, csub(mul_shoup(hi[a][b], P.r50, P.r50_sh, P.q), P.q), P.q);
+      out[((((u64)(r >> 1) * nI + I) * 2 + (r & 1)) * L + l) * N + s] = v;
     }
+  }
+}
+
+// The configuration the library launches.
+using MacProd = MacCfg<4, 4, 2, 2, 8, 2>;
+constexpr int kMacMinBlocks = 2;
+
+// Forward NTT of the input ciphertexts of a product into the slot-chunked operand layout.
+// Input poly p = ((Lb nJ + J) 2 + c) L + l of the wire format [Lb nJ + J][2][L][N].
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_forward_mm_t(const u64* src, u64* ctN, u32 nJ,
+                                                                        const __grid_constant__ Consts C) {
+  using S = NttShape<LOGN>;
+  extern __shared__ u64 sm[];
+  const u64 poly = blockIdx.x;
+  const u32 l = poly % C.L;
+  const u32 c = (poly / C.L) % 2;
+  const u32 LbJ = (u32)(poly / (2 * C.L));
+  const u32 Lb = LbJ / nJ, J = LbJ % nJ;
+  const PrimeConsts& P = C.p[l];
+  const u64* sp = src + poly * S::N;
+  const u64 row = (u64)Lb * 2 + c;
+  ntt_forward_block<S>(sm, P, [&](u32 e) { return sp[e]; },
+                       [&](u32 e, u64 v) { ctN[chunked_index(row, J, l, e, nJ, C.L, S::N)] = v; });
 }
 
 // One block per output polynomial (o, c, l): inverse NTT; for c = 0 subtract
@@ -401,6 +579,7 @@ cudaError_t configure_kernels(const Consts&) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   };
   set((const void*)k_ntt_forward, one);
+  set((const void*)k_ntt_forward_mm_small, one);
   set((const void*)k_ntt_inverse, one);
   set((const void*)k_poly_mul, two);
   set((const void*)k_keygen, one);
@@ -408,16 +587,46 @@ cudaError_t configure_kernels(const Consts&) {
   set((const void*)k_decrypt, all);
   set((const void*)k_encode_weights, one);
   set((const void*)k_intt_mask, one);
+  set((const void*)k_mac_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
+#define HE_SET_T(LOGN)                                                                             \
+  set((const void*)k_ntt_forward_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
+  set((const void*)k_ntt_inverse_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
+  set((const void*)k_encode_weights_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));       \
+  set((const void*)k_ntt_forward_mm_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));       \
+  set((const void*)k_intt_mask_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));
+  HE_SET_T(9) HE_SET_T(10) HE_SET_T(11) HE_SET_T(12) HE_SET_T(13)
+#undef HE_SET_T
   return e;
 }
 
+// Launch KERNEL<LOGN> with NttShape<LOGN> threads / shared memory when N >= 512.
+#define HE_DISPATCH_T(KERNEL, GRID, ST, ...)                                                              \
+  switch (C.logN) {                                                                                       \
+    case 9: KERNEL<9><<<GRID, NttShape<9>::T, NttShape<9>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break;     \
+    case 10: KERNEL<10><<<GRID, NttShape<10>::T, NttShape<10>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
+    case 11: KERNEL<11><<<GRID, NttShape<11>::T, NttShape<11>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
+    case 12: KERNEL<12><<<GRID, NttShape<12>::T, NttShape<12>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
+    case 13: KERNEL<13><<<GRID, NttShape<13>::T, NttShape<13>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
+    default: break;                                                                                       \
+  }
+
 cudaError_t launch_ntt_forward(const Consts& C, const u64* src, u64* dst, u64 npolys, cudaStream_t st) {
-  if (npolys) k_ntt_forward<<<(unsigned)npolys, kNttThreads, poly_smem(C), st>>>(src, dst, C);
+  if (!npolys) return cudaGetLastError();
+  if (C.logN >= 9) {
+    HE_DISPATCH_T(k_ntt_forward_t, (unsigned)npolys, st, src, dst, C)
+  } else {
+    k_ntt_forward<<<(unsigned)npolys, kNttThreads, poly_smem(C), st>>>(src, dst, C);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_ntt_inverse(const Consts& C, const u64* src, u64* dst, u64 npolys, cudaStream_t st) {
-  if (npolys) k_ntt_inverse<<<(unsigned)npolys, kNttThreads, poly_smem(C), st>>>(src, dst, C);
+  if (!npolys) return cudaGetLastError();
+  if (C.logN >= 9) {
+    HE_DISPATCH_T(k_ntt_inverse_t, (unsigned)npolys, st, src, dst, C)
+  } else {
+    k_ntt_inverse<<<(unsigned)npolys, kNttThreads, poly_smem(C), st>>>(src, dst, C);
+  }
   return cudaGetLastError();
 }
 
@@ -466,23 +675,49 @@ cudaError_t launch_unmask(const Consts& C, u64 seed, u32 m, u32 n, Blk b, u32 nI
 cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u64* pt,
                                   cudaStream_t st) {
   u64 polys = (u64)nI * nJ * C.L;
-  if (polys) k_encode_weights<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(W, k, n, b, nJ, pt, C);
+  if (!polys) return cudaGetLastError();
+  if (C.logN >= 9) {
+    HE_DISPATCH_T(k_encode_weights_t, (unsigned)polys, st, W, k, n, b, nJ, pt, C)
+  } else {
+    k_encode_weights<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(W, k, n, b, nJ, pt, C);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out, u32 nI, u32 nJ, u32 nLb,
+template <class M, int MINB>
+cudaError_t launch_mac_cfg(const Consts& C, const u64* ctN, const u64* pt, u64* out, u32 nI, u32 nJ, u32 nLb, int* err,
+                           cudaStream_t st) {
+  const u32 tilesR = (2 * nLb + M::kRows - 1) / M::kRows, tilesC = (nI + M::kCols - 1) / M::kCols;
+  if ((u64)tilesR * tilesC * nJ == 0) return cudaGetLastError();
+  dim3 grid((unsigned)((u64)(C.N >> 5) * tilesR * tilesC), C.L);
+  k_mac_t<M, MINB><<<grid, M::kThreads, M::kSmemBytes, st>>>(ctN, pt, out, nI, nJ, nLb, tilesR, err, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out, u32 nI, u32 nJ, u32 nLb, int* err,
                        cudaStream_t st) {
-  u32 tilesI = (nI + kMacTI - 1) / kMacTI, tilesB = (nLb + kMacTB - 1) / kMacTB;
-  if ((u64)tilesI * tilesB == 0) return cudaGetLastError();
-  u64 chunks = (C.N + kMacThreads - 1) / kMacThreads;
-  dim3 grid((unsigned)(chunks * tilesI * tilesB), C.L);
-  k_mac<<<grid, kMacThreads, 0, st>>>(ctN, pt, out, nI, nJ, nLb, tilesI, C);
+  return launch_mac_cfg<MacProd, kMacMinBlocks>(C, ctN, pt, out, nI, nJ, nLb, err, st);
+}
+
+cudaError_t launch_ntt_forward_mm(const Consts& C, const u64* ct_in, u64* ctN, u32 nJ, u32 nLb, cudaStream_t st) {
+  const u64 polys = (u64)nLb * nJ * 2 * C.L;
+  if (!polys) return cudaGetLastError();
+  if (C.logN >= 9) {
+    HE_DISPATCH_T(k_ntt_forward_mm_t, (unsigned)polys, st, ct_in, ctN, nJ, C)
+  } else {
+    k_ntt_forward_mm_small<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(ct_in, ctN, nJ, C);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_intt_mask(const Consts& C, u64* out, u64 out_cts, u64 seed, cudaStream_t st) {
   u64 polys = out_cts * 2 * C.L;
-  if (polys) k_intt_mask<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(out, seed, C);
+  if (!polys) return cudaGetLastError();
+  if (C.logN >= 9) {
+    HE_DISPATCH_T(k_intt_mask_t, (unsigned)polys, st, out, seed, C)
+  } else {
+    k_intt_mask<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(out, seed, C);
+  }
   return cudaGetLastError();
 }
 

@@ -1,23 +1,29 @@
-// ntt.cuh -- block-level negacyclic NTT over one residue polynomial held in
-// shared memory (the polynomial product of the footnote in Sec. 3.1.3 is
-// NTT, slot-wise product, inverse NTT).
+// ntt.cuh -- block-level negacyclic NTT over one residue polynomial (the polynomial
+// product of the footnote in Sec. 3.1.3 is NTT, slot-wise product, inverse NTT).
 //
-// Forward: Cooley-Tukey with the psi powers merged into the twiddles
-// (psi^{brev(k)}), natural-order input, bit-reversed slot order out.
-// Inverse: Gentleman-Sande with psi^{-brev(k)}, bit-reversed in, natural out,
-// followed by the N^{-1} scaling.
+// Forward: Cooley-Tukey with the psi powers merged into the twiddles (psi^{brev(k)}),
+// natural-order input, bit-reversed slot order out: slot j holds a(psi^{2 brev(j) + 1}).
+// Inverse: Gentleman-Sande with psi^{-brev(k)}, bit-reversed in, natural out, times N^{-1}.
 //
-// Lazy reduction: forward butterflies keep values in [0, q + 2 q s) after
-// stage s (no conditional subtraction; q < 2^50 keeps 13 stages below 2^55);
-// the inverse keeps [0, 2q).  Both return fully reduced values in [0, q).
+// Register-blocked form (N >= 512): a block of T = N / R threads, R = 2^LOGR values per
+// thread.  The log2(N) butterfly stages are cut into passes of at most LOGR stages; in a
+// pass every thread holds whole radix-2^RS groups in registers, runs the RS stages there and
+// exchanges through shared memory only between passes (3 round trips for N = 4096 / 8192
+// instead of one per stage).  Shared memory is padded (one word every 2^LOGR) so the
+// contiguous groups of the innermost pass are free of bank conflicts.
+//
+// Lazy reduction: forward butterflies keep values in [0, q + 2 q s) after stage s (no
+// conditional subtraction; q < 2^50 keeps 13 stages below 2^55); the inverse keeps
+// [0, 2q).  Both produce fully reduced values in [0, q).
 #pragma once
 
 #include "he_common.cuh"
 
 namespace he {
 
-// All threads of the block must call these (they synchronize internally).
-// Input: a[0..N) in [0, q).  Output: a[0..N) in [0, q), slot j = a(psi^{2 brev(j) + 1}).
+// ------------------------------------------------------------------ simple form (N < 512)
+
+// All threads of the block call these.  Input a[0..N) in [0, q); output in [0, q).
 __device__ __forceinline__ void ntt_forward_smem(u64* a, u32 logN, const PrimeConsts& P) {
   const u32 half = 1u << (logN - 1);
   const u64 two_q = P.two_q, q = P.q;
@@ -41,7 +47,7 @@ __device__ __forceinline__ void ntt_forward_smem(u64* a, u32 logN, const PrimeCo
   __syncthreads();
 }
 
-// Input: a[0..N) in [0, 2q), slot order of ntt_forward_smem.  Output: coefficients in [0, q).
+// Input a[0..N) in [0, 2q), slot order of the forward transform.  Output in [0, q).
 __device__ __forceinline__ void ntt_inverse_smem(u64* a, u32 logN, const PrimeConsts& P) {
   const u32 half = 1u << (logN - 1);
   const u64 two_q = P.two_q, q = P.q;
@@ -63,6 +69,208 @@ __device__ __forceinline__ void ntt_inverse_smem(u64* a, u32 logN, const PrimeCo
   const u32 N = 1u << logN;
   for (u32 i = threadIdx.x; i < N; i += blockDim.x) a[i] = csub(mul_shoup(a[i], P.ninv, P.ninv_sh, q), q);
   __syncthreads();
+}
+
+// ------------------------------------------------------------------ register-blocked form
+
+template <int LOGN>
+struct NttShape {
+  static constexpr int kLogN = LOGN;
+  static constexpr int N = 1 << LOGN;
+  static constexpr int LOGR = LOGN >= 13 ? 5 : 4;  // values per thread: 16, or 32 for N = 8192
+  static constexpr int R = 1 << LOGR;
+  static constexpr int T = N / R;                   // threads per block
+  static constexpr int P = (LOGN + LOGR - 1) / LOGR;  // passes
+  static constexpr int RS0 = LOGN - LOGR * (P - 1);   // stages of the outermost pass
+  static constexpr int kSmemWords = N + (N >> LOGR);  // padded
+  __device__ __forceinline__ static u32 pad(u32 e) { return e + (e >> LOGR); }
+};
+
+// One forward (Cooley-Tukey) pass over stages [S0, S0 + RS) on the R values in x:
+// x[h * 2^RS + j] is element e = blk * 2^(LOGN - S0) + off + j * t_last of group
+// g = tid + T * h, with t_last = 2^(LOGN - S0 - RS), blk = g / t_last, off = g % t_last.
+template <class S, int S0, int RS>
+__device__ __forceinline__ void fwd_pass_regs(u64 (&x)[S::R], const PrimeConsts& P) {
+  constexpr int G = S::R >> RS;
+  constexpr int TLAST_LOG = S::kLogN - S0 - RS;
+  const u64 two_q = P.two_q, q = P.q;
+#pragma unroll
+  for (int h = 0; h < G; ++h) {
+    const u32 g = threadIdx.x + S::T * h;
+    const u32 blk = g >> TLAST_LOG;
+#pragma unroll
+    for (int u = 0; u < RS; ++u) {
+      const int span = 1 << (RS - 1 - u);
+#pragma unroll
+      for (int j = 0; j < (1 << RS); ++j) {
+        if (j & span) continue;
+        const u32 widx = (1u << (S0 + u)) + (blk << u) + (j >> (RS - u));
+        const u64 w = __ldg(P.psi + widx), wsh = __ldg(P.psi_sh + widx);
+        u64& A = x[h * (1 << RS) + j];
+        u64& Bv = x[h * (1 << RS) + j + span];
+        const u64 U = A;
+        const u64 V = mul_shoup(Bv, w, wsh, q);
+        A = U + V;
+        Bv = U - V + two_q;
+      }
+    }
+  }
+}
+
+template <class S, int S0, int RS>
+__device__ __forceinline__ u32 fwd_elem(int h, int j) {
+  constexpr int TLAST_LOG = S::kLogN - S0 - RS;
+  const u32 g = threadIdx.x + S::T * h;
+  return ((g >> TLAST_LOG) << (S::kLogN - S0)) + (g & ((1u << TLAST_LOG) - 1)) + ((u32)j << TLAST_LOG);
+}
+
+template <class S, int S0, int RS>
+__device__ __forceinline__ void fwd_load_smem(u64 (&x)[S::R], const u64* sm) {
+#pragma unroll
+  for (int h = 0; h < (S::R >> RS); ++h)
+#pragma unroll
+    for (int j = 0; j < (1 << RS); ++j) x[h * (1 << RS) + j] = sm[S::pad(fwd_elem<S, S0, RS>(h, j))];
+}
+
+template <class S, int S0, int RS>
+__device__ __forceinline__ void fwd_store_smem(const u64 (&x)[S::R], u64* sm) {
+#pragma unroll
+  for (int h = 0; h < (S::R >> RS); ++h)
+#pragma unroll
+    for (int j = 0; j < (1 << RS); ++j) sm[S::pad(fwd_elem<S, S0, RS>(h, j))] = x[h * (1 << RS) + j];
+}
+
+// Remaining forward passes, recursively (S0 = first stage of the pass).
+template <class S, int S0>
+__device__ __forceinline__ void fwd_rest(u64 (&x)[S::R], u64* sm, const PrimeConsts& P) {
+  if constexpr (S0 < S::kLogN) {
+    fwd_load_smem<S, S0, S::LOGR>(x, sm);
+    fwd_pass_regs<S, S0, S::LOGR>(x, P);
+    if constexpr (S0 + S::LOGR < S::kLogN) {
+      fwd_store_smem<S, S0, S::LOGR>(x, sm);
+      __syncthreads();
+      fwd_rest<S, S0 + S::LOGR>(x, sm, P);
+    }
+  }
+}
+
+// Forward NTT of one polynomial by the whole block (blockDim.x == S::T).
+//   load(e)      -> coefficient e in [0, q) (called for every e, first pass pattern,
+//                   coalesced across the warp);
+//   store(e, v)  <- slot e, fully reduced (called for every e in increasing-e order per
+//                   thread stride, coalesced);
+//   sm: S::kSmemWords words of shared memory.  Synchronizes internally.
+template <class S, class Load, class Store>
+__device__ __forceinline__ void ntt_forward_block(u64* sm, const PrimeConsts& P, Load&& load, Store&& store) {
+  u64 x[S::R];
+#pragma unroll
+  for (int h = 0; h < (S::R >> S::RS0); ++h)
+#pragma unroll
+    for (int j = 0; j < (1 << S::RS0); ++j) x[h * (1 << S::RS0) + j] = load(fwd_elem<S, 0, S::RS0>(h, j));
+  fwd_pass_regs<S, 0, S::RS0>(x, P);
+  fwd_store_smem<S, 0, S::RS0>(x, sm);
+  __syncthreads();
+  fwd_rest<S, S::RS0>(x, sm, P);
+  // last pass ended with contiguous groups in registers: reduce, stage, copy out coalesced
+  constexpr int S0L = S::kLogN - S::LOGR;
+#pragma unroll
+  for (int j = 0; j < S::R; ++j) x[j] = reduce_word(x[j], P);
+  __syncthreads();
+  fwd_store_smem<S, S0L, S::LOGR>(x, sm);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < S::R; ++i) {
+    const u32 e = threadIdx.x + S::T * i;
+    store(e, sm[S::pad(e)]);
+  }
+}
+
+// ---- inverse (Gentleman-Sande).  Pass over stages [S0, S0 + RS): group g has elements
+// e = blk * 2^(S0 + RS) + off + j * 2^S0, blk = g >> S0, off = g & (2^S0 - 1).
+
+template <class S, int S0, int RS>
+__device__ __forceinline__ u32 inv_elem(int h, int j) {
+  const u32 g = threadIdx.x + S::T * h;
+  return ((g >> S0) << (S0 + RS)) + (g & ((1u << S0) - 1)) + ((u32)j << S0);
+}
+
+template <class S, int S0, int RS>
+__device__ __forceinline__ void inv_pass_regs(u64 (&x)[S::R], const PrimeConsts& P) {
+  constexpr int G = S::R >> RS;
+  const u64 two_q = P.two_q, q = P.q;
+#pragma unroll
+  for (int h = 0; h < G; ++h) {
+    const u32 g = threadIdx.x + S::T * h;
+    const u32 blk = g >> S0;
+#pragma unroll
+    for (int u = 0; u < RS; ++u) {
+      const int span = 1 << u;
+#pragma unroll
+      for (int j = 0; j < (1 << RS); ++j) {
+        if (j & span) continue;
+        const u32 widx = (u32)(S::N >> (S0 + u + 1)) + (blk << (RS - u - 1)) + (j >> (u + 1));
+        const u64 w = __ldg(P.ipsi + widx), wsh = __ldg(P.ipsi_sh + widx);
+        u64& A = x[h * (1 << RS) + j];
+        u64& Bv = x[h * (1 << RS) + j + span];
+        const u64 U = A, V = Bv;
+        A = csub(U + V, two_q);
+        Bv = mul_shoup(U - V + two_q, w, wsh, q);
+      }
+    }
+  }
+}
+
+template <class S, int S0, int RS>
+__device__ __forceinline__ void inv_load_smem(u64 (&x)[S::R], const u64* sm) {
+#pragma unroll
+  for (int h = 0; h < (S::R >> RS); ++h)
+#pragma unroll
+    for (int j = 0; j < (1 << RS); ++j) x[h * (1 << RS) + j] = sm[S::pad(inv_elem<S, S0, RS>(h, j))];
+}
+
+template <class S, int S0, int RS>
+__device__ __forceinline__ void inv_store_smem(const u64 (&x)[S::R], u64* sm) {
+#pragma unroll
+  for (int h = 0; h < (S::R >> RS); ++h)
+#pragma unroll
+    for (int j = 0; j < (1 << RS); ++j) sm[S::pad(inv_elem<S, S0, RS>(h, j))] = x[h * (1 << RS) + j];
+}
+
+template <class S, int S0>
+__device__ __forceinline__ void inv_middle(u64 (&x)[S::R], u64* sm, const PrimeConsts& P) {
+  // passes of LOGR stages starting at S0, up to the last (outermost) pass of RS0 stages
+  if constexpr (S0 + S::RS0 < S::kLogN) {
+    inv_load_smem<S, S0, S::LOGR>(x, sm);
+    inv_pass_regs<S, S0, S::LOGR>(x, P);
+    inv_store_smem<S, S0, S::LOGR>(x, sm);
+    __syncthreads();
+    inv_middle<S, S0 + S::LOGR>(x, sm, P);
+  }
+}
+
+// Inverse NTT of one polynomial by the whole block (blockDim.x == S::T).
+//   load(e)     -> slot e in [0, 2q) (called in coalesced order);
+//   store(e, v) <- coefficient e in [0, q) (outermost-pass pattern, coalesced).
+template <class S, class Load, class Store>
+__device__ __forceinline__ void ntt_inverse_block(u64* sm, const PrimeConsts& P, Load&& load, Store&& store) {
+#pragma unroll
+  for (int i = 0; i < S::R; ++i) {
+    const u32 e = threadIdx.x + S::T * i;
+    sm[S::pad(e)] = load(e);
+  }
+  __syncthreads();
+  u64 x[S::R];
+  inv_middle<S, 0>(x, sm, P);
+  constexpr int S0L = S::kLogN - S::RS0;
+  inv_load_smem<S, S0L, S::RS0>(x, sm);
+  inv_pass_regs<S, S0L, S::RS0>(x, P);
+#pragma unroll
+  for (int h = 0; h < (S::R >> S::RS0); ++h)
+#pragma unroll
+    for (int j = 0; j < (1 << S::RS0); ++j) {
+      const u64 v = csub(mul_shoup(x[h * (1 << S::RS0) + j], P.ninv, P.ninv_sh, P.q), P.q);
+      store(inv_elem<S, S0L, S::RS0>(h, j), v);
+    }
 }
 
 }  // namespace he
