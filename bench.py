@@ -126,7 +126,8 @@ class ClockSampler:
 
 
 class Layer:
-    """Device state of one layer's products: resident weights, input ciphertexts, outputs."""
+    """Device state of one layer's products: resident weights, input ciphertexts, outputs.
+    Products that occur once per head run as one same-shape batch (he_matmul_batch)."""
 
     def __init__(self, B, ctx, prods, rank, want_host):
         import numpy as np
@@ -143,66 +144,73 @@ class Layer:
         for p in prods:
             blk = ctx.default_blocking(p.m, p.k, p.n)
             si = ctx.sizes(p.m, p.k, p.n, blk)
-            max_ws = max(max_ws, si["workspace_bytes"])
+            cnt = p.count
+            max_ws = max(max_ws, cnt * si["workspace_bytes"])
             max_hostws = max(max_hostws, B.matmul_host_workspace_words(ctx, p.m, p.k, p.n, blk))
-            for h in range(p.count):
-                seed = 10_000 * (rank + 1) + idx
-                X = S.uniform_share((p.m, p.k), seed)
-                if p.share_weights:
-                    W = S.uniform_share((p.k, p.n), seed + 500_000)
-                else:
-                    W = S.fixed_point_weights((p.k, p.n), seed + 500_000)
-                Xd = torch.from_numpy(X.view(np.int64).reshape(-1)).to(dev)
-                Wd = torch.from_numpy(W.view(np.int64).reshape(-1)).to(dev)
-                polys = B.he_pack_input(ctx, Xd, p.m, p.k, blk)
-                ct_in = B.he_encrypt(ctx, self.sk, polys, seed + 900_000)
-                call = dict(p=p, blk=blk, si=si, ct_in=ct_in, out=ctx.empty(si["out_words"]), idx=idx)
-                if p.share_weights:
-                    call["W"] = Wd  # the server's share, encoded on every step
-                    max_pt = max(max_pt, si["pt_words"])
-                else:
-                    call["pt"] = B.he_encode_weights(ctx, Wd, p.k, p.n, blk)  # resident NTT-form weights
-                if want_host:
-                    call["in_host"] = ct_in.cpu().pin_memory()
-                    call["out_host"] = torch.empty(si["out_words"], dtype=torch.int64).pin_memory()
-                self.calls.append(call)
-                idx += 1
+            seed = 10_000 * (rank + 1) + idx
+            Xs = [S.uniform_share((p.m, p.k), seed + b) for b in range(cnt)]
+            if p.share_weights:
+                Ws = [S.uniform_share((p.k, p.n), seed + 500_000 + b) for b in range(cnt)]
+            else:
+                Ws = [S.fixed_point_weights((p.k, p.n), seed + 500_000 + b) for b in range(cnt)]
+            Xd = torch.from_numpy(np.concatenate([x.reshape(-1) for x in Xs]).view(np.int64)).to(dev)
+            Wd = torch.from_numpy(np.concatenate([w.reshape(-1) for w in Ws]).view(np.int64)).to(dev)
+            polys = ctx.empty(cnt * si["packed_words"])
+            for b in range(cnt):
+                B.he_pack_input(ctx, Xd[b * p.m * p.k:(b + 1) * p.m * p.k], p.m, p.k, blk,
+                                polys=polys[b * si["packed_words"]:(b + 1) * si["packed_words"]])
+            ct_in = B.he_encrypt(ctx, self.sk, polys, seed + 900_000)
+            call = dict(p=p, blk=blk, si=si, cnt=cnt, ct_in=ct_in, out=ctx.empty(cnt * si["out_words"]), idx=idx)
+            if p.share_weights:
+                call["W"] = Wd  # the server's shares, encoded on every step
+                max_pt = max(max_pt, cnt * si["pt_words"])
+            else:
+                call["pt"] = B.he_encode_weights_batch(ctx, Wd, p.k, p.n, blk, cnt)  # resident NTT-form weights
+            if want_host:
+                call["in_host"] = ct_in.cpu().pin_memory()
+                call["out_host"] = torch.empty(cnt * si["out_words"], dtype=torch.int64).pin_memory()
+            self.calls.append(call)
+            idx += cnt
         self.ws = ctx.empty(max((max_ws + 7) // 8, 1))
         self.pt_tmp = ctx.empty(max(max_pt, 1))
         self.host_ws = ctx.empty(max_hostws) if want_host else None
-        self.macs = sum(c["p"].m * c["p"].k * c["p"].n for c in self.calls)
+        self.macs = sum(c["p"].m * c["p"].k * c["p"].n * c["cnt"] for c in self.calls)
+        self.products = sum(c["cnt"] for c in self.calls)
         torch.cuda.synchronize()
 
     def step(self, step_idx, host=False):
         B, ctx = self.B, self.ctx
         for c in self.calls:
-            p, blk = c["p"], c["blk"]
+            p, blk, cnt, si = c["p"], c["blk"], c["cnt"], c["si"]
             pt = c.get("pt")
             if pt is None:
-                pt = B.he_encode_weights(ctx, c["W"], p.k, p.n, blk, pt=self.pt_tmp)
+                pt = B.he_encode_weights_batch(ctx, c["W"], p.k, p.n, blk, cnt, pt=self.pt_tmp)
             seed = (step_idx << 20) | c["idx"]
             if host:
-                B.he_matmul_host(ctx, c["in_host"], pt, p.m, p.k, p.n, blk, seed, c["out_host"], self.host_ws)
+                for b in range(cnt):  # host buffers: one C-ABI call per product
+                    iw, ow, pw = si["in_words"], si["out_words"], si["pt_words"]
+                    B.he_matmul_host(ctx, c["in_host"][b * iw:(b + 1) * iw], pt[b * pw:(b + 1) * pw], p.m, p.k, p.n,
+                                     blk, seed + b, c["out_host"][b * ow:(b + 1) * ow], self.host_ws)
             else:
-                B.he_matmul(ctx, c["ct_in"], pt, p.m, p.k, p.n, blk, seed, c["out"], self.ws)
+                B.he_matmul_batch(ctx, c["ct_in"], pt, p.m, p.k, p.n, blk, cnt, seed, c["out"], self.ws)
 
     def algorithmic_bytes(self):
         """Per kernel family: algorithmic HBM bytes of one step (reads + writes, 8-byte words)."""
-        L, N = self.ctx.L, self.ctx.N
         tot = {"mac": 0, "ntt_forward": 0, "intt_mask": 0, "encode_weights": 0}
         for c in self.calls:
-            si, p = c["si"], c["p"]
+            si, p, cnt = c["si"], c["p"], c["cnt"]
             pt_b, in_b, out_b = 8 * si["pt_words"], 8 * si["in_words"], 8 * si["out_words"]
-            tot["mac"] += pt_b + in_b + out_b
-            tot["ntt_forward"] += 2 * in_b
-            tot["intt_mask"] += 2 * out_b
+            tot["mac"] += cnt * (pt_b + in_b + out_b)
+            tot["ntt_forward"] += cnt * 2 * in_b
+            tot["intt_mask"] += cnt * 2 * out_b
             if p.share_weights:
-                tot["encode_weights"] += 8 * p.k * p.n + pt_b
+                tot["encode_weights"] += cnt * (8 * p.k * p.n + pt_b)
         return tot
 
     def slot_macs(self):
-        """Slot-wise modular multiply-accumulates of one step (2 L per plain MAC at full packing)."""
-        return sum(c["si"]["nI"] * c["si"]["nJ"] * c["si"]["nLb"] * 2 * self.ctx.L * self.ctx.N for c in self.calls)
+        """Slot-wise modular multiply-accumulates of one step."""
+        L, N = self.ctx.L, self.ctx.N
+        return sum(c["cnt"] * c["si"]["nI"] * c["si"]["nJ"] * c["si"]["nLb"] * 2 * L * N for c in self.calls)
 
 
 def kernel_source_hash():
@@ -380,8 +388,8 @@ def gpu_arm(args, world, rank, local):
     # end to end: host buffers through he_matmul_host (H2D + compute + D2H inside the region)
     e2e = None
     if want_host:
-        h2d = sum(8 * c["si"]["in_words"] for c in layer.calls)
-        d2h = sum(8 * c["si"]["out_words"] for c in layer.calls)
+        h2d = sum(8 * c["cnt"] * c["si"]["in_words"] for c in layer.calls)
+        d2h = sum(8 * c["cnt"] * c["si"]["out_words"] for c in layer.calls)
         layer.step(9000, host=True)
         barrier(world)
         torch.cuda.synchronize()
@@ -407,7 +415,8 @@ def gpu_arm(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N_POLY, "L": L_PRIMES, "log2_t": 37,
-                   "products_per_step": len(layer.calls), "plain_macs_per_step": layer.macs,
+                   "products_per_step": layer.products, "launch_groups_per_step": len(layer.calls),
+                   "plain_macs_per_step": layer.macs,
                    "blockings_mkn": blks, "parallelism": f"replicas x{world} (independent layers, no collective)",
                    "l2": "inputs larger than L2: one step reads/writes ~3 GB of ciphertexts/weights"},
         "latency_ms": {"p50": statistics.median(per), "p99": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))]},

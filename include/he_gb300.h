@@ -158,6 +158,10 @@ HE_API int he_unpack_output(he_ctx* ctx, const uint64_t* dec, uint32_t m, uint32
 HE_API int he_encode_weights(he_ctx* ctx, const uint64_t* W, uint32_t k, uint32_t n, const he_blocking* blk, uint64_t* pt,
                       void* stream);
 
+/* he_encode_weights for `batch` matrices W + b * k * n into pt + b * pt_words. */
+HE_API int he_encode_weights_batch(he_ctx* ctx, const uint64_t* W, uint32_t k, uint32_t n, const he_blocking* blk,
+                                   uint32_t batch, uint64_t* pt, void* stream);
+
 /* Step 3 of Algorithm 1 for every output block: [[c_{Lb,I}]] = sum_J
  * a_{I,J} * [[b_{Lb,J}]] (NTT, slot-wise multiply-accumulate, inverse NTT),
  * then the re-mask c0 <- c0 - round(q s / t) with the server's share s of
@@ -179,6 +183,15 @@ HE_API int he_matmul(he_ctx* ctx, const uint64_t* ct_in, const uint64_t* pt, uin
 HE_API int he_matmul_host(he_ctx* ctx, const uint64_t* ct_in_host, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
                    const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out_host, void* workspace,
                    size_t workspace_bytes, void* stream);
+
+/* `batch` independent products of one shape and blocking in one set of launches (e.g.
+ * the per-head attention cross terms of a layer).  Item b reads ct_in + b * in_words and
+ * pt + b * pt_words, writes ct_out + b * out_words, and is re-masked with seed
+ * mask_seed + b: the result is bit-identical to `batch` he_matmul calls with those
+ * seeds.  workspace >= batch * he_sizes().workspace_bytes.  batch * L <= 65535. */
+HE_API int he_matmul_batch(he_ctx* ctx, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
+                           const he_blocking* blk, uint32_t batch, uint64_t mask_seed, uint32_t flags,
+                           uint64_t* ct_out, void* workspace, size_t workspace_bytes, void* stream);
 
 /* he_matmul for callers that cannot allocate device memory.  Some callers have no
  * way to obtain a workspace: a serving process whose device memory is already

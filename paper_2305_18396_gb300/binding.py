@@ -76,6 +76,8 @@ def _load():
         "he_matmul": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u64, u32, P, P, sz, P]),
         "he_matmul_host": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u64, u32, P, P, sz, P]),
         "he_matmul_noalloc": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u64, u32, P, P]),
+        "he_matmul_batch": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u32, u64, u32, P, P, sz, P]),
+        "he_encode_weights_batch": (ctypes.c_int, [P, P, u32, u32, pB, u32, P, P]),
         "he_unmask": (ctypes.c_int, [P, u64, u32, u32, pB, P, P]),
         "he_ntt_forward": (ctypes.c_int, [P, P, u32, P]),
         "he_ntt_inverse": (ctypes.c_int, [P, P, u32, P]),
@@ -230,6 +232,29 @@ def he_encode_weights(ctx, W, k, n, blk, pt=None, stream=None):
     pt = ctx.empty(si["pt_words"]) if pt is None else ctx._dev(pt, si["pt_words"], "pt")
     _check(lib.he_encode_weights(ctx.h, _ptr(W), k, n, _blk(blk), _ptr(pt), _stream(stream)))
     return pt
+
+
+def he_encode_weights_batch(ctx, W, k, n, blk, batch, pt=None, stream=None):
+    si = ctx.sizes(1, k, n, blk)
+    ctx._dev(W, batch * k * n, "W")
+    words = batch * si["pt_words"]
+    pt = ctx.empty(words) if pt is None else ctx._dev(pt, words, "pt")
+    _check(lib.he_encode_weights_batch(ctx.h, _ptr(W), k, n, _blk(blk), batch, _ptr(pt), _stream(stream)))
+    return pt
+
+
+def he_matmul_batch(ctx, ct_in, pt, m, k, n, blk, batch, mask_seed, ct_out=None, workspace=None,
+                    flags=HE_FLAGS_NONE, stream=None):
+    """`batch` same-shape products back to back; item b is masked with seed mask_seed + b."""
+    si = ctx.sizes(m, k, n, blk)
+    ctx._dev(ct_in, batch * si["in_words"], "ct_in")
+    ctx._dev(pt, batch * si["pt_words"], "pt")
+    ct_out = ctx.empty(batch * si["out_words"]) if ct_out is None else ctx._dev(ct_out, batch * si["out_words"], "ct_out")
+    ws_words = batch * ((si["workspace_bytes"] + 7) // 8)
+    workspace = ctx.empty(max(ws_words, 1)) if workspace is None else ctx._dev(workspace, ws_words, "workspace")
+    _check(lib.he_matmul_batch(ctx.h, _ptr(ct_in), _ptr(pt), m, k, n, _blk(blk), batch, mask_seed, flags,
+                               _ptr(ct_out), _ptr(workspace), workspace.numel() * 8, _stream(stream)))
+    return ct_out
 
 
 def he_matmul(ctx, ct_in, pt, m, k, n, blk, mask_seed, ct_out=None, workspace=None, flags=HE_FLAGS_NONE,

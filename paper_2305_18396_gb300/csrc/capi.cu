@@ -456,31 +456,37 @@ int he_unmask(he_ctx* c, uint64_t mask_seed, uint32_t m, uint32_t n, const he_bl
   });
 }
 
-int he_encode_weights(he_ctx* c, const uint64_t* W, uint32_t k, uint32_t n, const he_blocking* blk, uint64_t* pt,
-                      void* stream) {
+int he_encode_weights_batch(he_ctx* c, const uint64_t* W, uint32_t k, uint32_t n, const he_blocking* blk,
+                            uint32_t batch, uint64_t* pt, void* stream) {
   if (!c) return fail(HE_EINVAL, "ctx is NULL");
   if (int r = check_blk(c, blk)) return r;
-  if (!k || !n) return HE_OK;
+  if (!k || !n || !batch) return HE_OK;
   if (!W || !pt) return fail(HE_EINVAL, "NULL buffer");
   if (int r = set_device(c)) return r;
   Shape s = shape_of(1, k, n, blk);
   return launch(c, KEncode, (cudaStream_t)stream, "encode_weights", [&] {
-    return he::launch_encode_weights(c->C, W, k, n, to_blk(blk), s.nI, s.nJ, pt, (cudaStream_t)stream);
+    return he::launch_encode_weights(c->C, W, k, n, to_blk(blk), s.nI, s.nJ, batch, pt, (cudaStream_t)stream);
   });
 }
 
+int he_encode_weights(he_ctx* c, const uint64_t* W, uint32_t k, uint32_t n, const he_blocking* blk, uint64_t* pt,
+                      void* stream) {
+  return he_encode_weights_batch(c, W, k, n, blk, 1, pt, stream);
+}
+
 static int matmul_device(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
-                         const he_blocking* blk, uint64_t mask_seed, uint64_t* ct_out, void* ws, cudaStream_t st) {
+                         const he_blocking* blk, uint32_t batch, uint64_t mask_seed, uint64_t* ct_out, void* ws,
+                         cudaStream_t st) {
   Shape s = shape_of(m, k, n, blk);
   u64* ctN = (u64*)ws;
   int r = launch(c, KNttFwd, st, "matmul: forward NTT",
-                 [&] { return he::launch_ntt_forward_mm(c->C, ct_in, ctN, s.nJ, s.nLb, st); });
+                 [&] { return he::launch_ntt_forward_mm(c->C, ct_in, ctN, s.nJ, s.nLb, batch, st); });
   if (r) return r;
   r = launch(c, KMac, st, "matmul: multiply-accumulate",
-             [&] { return he::launch_mac(c->C, ctN, pt, ct_out, s.nI, s.nJ, s.nLb, c->d_err, st); });
+             [&] { return he::launch_mac(c->C, ctN, pt, ct_out, s.nI, s.nJ, s.nLb, batch, c->d_err, st); });
   if (r) return r;
   return launch(c, KInttMask, st, "matmul: inverse NTT + mask",
-                [&] { return he::launch_intt_mask(c->C, ct_out, (u64)s.nLb * s.nI, mask_seed, st); });
+                [&] { return he::launch_intt_mask(c->C, ct_out, (u64)s.nLb * s.nI, batch, mask_seed, st); });
 }
 
 static int matmul_checks(he_ctx* c, uint32_t m, uint32_t k, uint32_t n, const he_blocking* blk, uint32_t flags,
@@ -502,7 +508,21 @@ int he_matmul(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, 
   if (!ct_in || !pt || !ct_out || !workspace) return fail(HE_EINVAL, "NULL buffer");
   if (workspace_bytes < si.workspace_bytes) return fail(HE_ENOMEM, "workspace smaller than he_sizes().workspace_bytes");
   if (int r = set_device(c)) return r;
-  return matmul_device(c, ct_in, pt, m, k, n, blk, mask_seed, ct_out, workspace, (cudaStream_t)stream);
+  return matmul_device(c, ct_in, pt, m, k, n, blk, 1, mask_seed, ct_out, workspace, (cudaStream_t)stream);
+}
+
+int he_matmul_batch(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
+                    const he_blocking* blk, uint32_t batch, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out,
+                    void* workspace, size_t workspace_bytes, void* stream) {
+  he_size_info si;
+  if (int r = matmul_checks(c, m, k, n, blk, flags, &si)) return r;
+  if (!m || !k || !n || !batch) return HE_OK;
+  if ((u64)batch * c->C.L > 65535) return fail(HE_EINVAL, "batch * L must be <= 65535");
+  if (!ct_in || !pt || !ct_out || !workspace) return fail(HE_EINVAL, "NULL buffer");
+  if (workspace_bytes / batch < si.workspace_bytes)
+    return fail(HE_ENOMEM, "workspace smaller than batch * he_sizes().workspace_bytes");
+  if (int r = set_device(c)) return r;
+  return matmul_device(c, ct_in, pt, m, k, n, blk, batch, mask_seed, ct_out, workspace, (cudaStream_t)stream);
 }
 
 int he_matmul_host(he_ctx* c, const uint64_t* ct_in_host, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
@@ -520,7 +540,7 @@ int he_matmul_host(he_ctx* c, const uint64_t* ct_in_host, const uint64_t* pt, ui
   u64* d_out = d_in + si.in_words;
   cudaError_t e = cudaMemcpyAsync(d_in, ct_in_host, si.in_words * 8, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "matmul_host: upload");
-  if (int r = matmul_device(c, d_in, pt, m, k, n, blk, mask_seed, d_out, workspace, st)) return r;
+  if (int r = matmul_device(c, d_in, pt, m, k, n, blk, 1, mask_seed, d_out, workspace, st)) return r;
   e = cudaMemcpyAsync(ct_out_host, d_out, si.out_words * 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "matmul_host: download");
@@ -542,7 +562,7 @@ int he_matmul_noalloc(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint
   void* scratch = nullptr;
   cudaError_t e = he::noalloc_scratch_address(c->device, &scratch);
   if (e != cudaSuccess) return cuda_fail(e, "matmul_noalloc: scratch address");
-  return matmul_device(c, ct_in, pt, m, k, n, blk, mask_seed, ct_out, scratch, (cudaStream_t)stream);
+  return matmul_device(c, ct_in, pt, m, k, n, blk, 1, mask_seed, ct_out, scratch, (cudaStream_t)stream);
 }
 
 int he_ntt_forward(he_ctx* c, uint64_t* polys, uint32_t cnt, void* stream) {

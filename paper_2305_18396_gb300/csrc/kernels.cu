@@ -82,20 +82,23 @@ __global__ void __launch_bounds__(kNttThreads) k_poly_mul(const u64* a, const u6
 
 // Forward NTT of matmul inputs for N < 512 into the slot-chunked layout (see k_mac_t).
 __host__ __device__ constexpr u64 chunked_index(u64 row, u32 J, u32 l, u32 s, u32 nJ, u32 L, u32 N);
-__global__ void __launch_bounds__(kNttThreads) k_ntt_forward_mm_small(const u64* src, u64* ctN, u32 nJ,
+__global__ void __launch_bounds__(kNttThreads) k_ntt_forward_mm_small(const u64* src, u64* ctN, u32 nJ, u32 nLb,
                                                                       const __grid_constant__ Consts C) {
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
-  const u32 l = poly % C.L;
-  const u32 c = (poly / C.L) % 2;
-  const u32 LbJ = (u32)(poly / (2 * C.L));
+  const u64 item_polys = (u64)nLb * nJ * 2 * C.L;
+  const u64 item = poly / item_polys, local = poly % item_polys;
+  const u32 l = local % C.L;
+  const u32 c = (local / C.L) % 2;
+  const u32 LbJ = (u32)(local / (2 * C.L));
   const u32 Lb = LbJ / nJ, J = LbJ % nJ;
   const PrimeConsts& P = C.p[l];
+  u64* dst = ctN + item * item_polys * C.N;
   for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) sm[i] = src[poly * C.N + i];
   __syncthreads();
   ntt_forward_smem(sm, C.logN, P);
   for (u32 i = threadIdx.x; i < C.N; i += blockDim.x)
-    ctN[chunked_index((u64)Lb * 2 + c, J, l, i, nJ, C.L, C.N)] = sm[i];
+    dst[chunked_index((u64)Lb * 2 + c, J, l, i, nJ, C.L, C.N)] = sm[i];
 }
 
 // Register-blocked versions for N >= 512 (blockDim = NttShape<LOGN>::T).
@@ -278,10 +281,13 @@ __global__ void k_unmask(u64 seed, u32 m, u32 n, Blk b, u32 nI, u64* share, cons
 
 // pi_A: a_{I,J}[i k_b + k_b - 1 - j] = W[J k_b + j][I n_b + i], centred lift, mod q_l, NTT.
 // pt layout [nI][nJ][L][N]; one block per (I, J, l).
-__global__ void __launch_bounds__(kNttThreads) k_encode_weights(const u64* W, u32 k, u32 n, Blk b, u32 nJ, u64* pt,
+__global__ void __launch_bounds__(kNttThreads) k_encode_weights(const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u64* pt,
                                                                 const __grid_constant__ Consts C) {
   extern __shared__ u64 sm[];
-  const u64 poly = blockIdx.x;
+  const u64 item_polys = (u64)nI * nJ * C.L;
+  const u64 item = blockIdx.x / item_polys, poly = blockIdx.x % item_polys;
+  W += item * k * n;
+  pt += item * item_polys * C.N;
   const u32 l = poly % C.L;
   const u32 IJ = (u32)(poly / C.L);
   const u32 I = IJ / nJ, J = IJ % nJ;
@@ -306,11 +312,14 @@ __global__ void __launch_bounds__(kNttThreads) k_encode_weights(const u64* W, u3
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T) k_encode_weights_t(const u64* W, u32 k, u32 n, Blk b, u32 nJ,
-                                                                        u64* pt, const __grid_constant__ Consts C) {
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_encode_weights_t(const u64* W, u32 k, u32 n, Blk b, u32 nI,
+                                                                        u32 nJ, u64* pt, const __grid_constant__ Consts C) {
   using S = NttShape<LOGN>;
   extern __shared__ u64 sm[];
-  const u64 poly = blockIdx.x;
+  const u64 item_polys = (u64)nI * nJ * C.L;
+  const u64 item = blockIdx.x / item_polys, poly = blockIdx.x % item_polys;
+  W += item * k * n;
+  pt += item * item_polys * S::N;
   const u32 l = poly % C.L;
   const u32 IJ = (u32)(poly / C.L);
   const u32 I = IJ / nJ, J = IJ % nJ;
@@ -329,14 +338,16 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_encode_weights_t(const u6
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T) k_intt_mask_t(u64* out, u64 seed,
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_intt_mask_t(u64* out, u64 out_cts, u64 seed,
                                                                    const __grid_constant__ Consts C) {
   using S = NttShape<LOGN>;
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
+  const u64 item = poly / (out_cts * 2 * C.L);  // batch item: re-masked with seed + item
+  seed += item;
   const u32 l = poly % C.L;
   const u32 c = (poly / C.L) % 2;
-  const u32 o = (u32)(poly / (2 * C.L));
+  const u32 o = (u32)((poly / (2 * C.L)) % out_cts);
   const PrimeConsts& P = C.p[l];
   u64* d = out + poly * S::N;
   ntt_inverse_block<S>(sm, P, [&](u32 e) { return d[e]; }, [&](u32 e, u64 v) {
@@ -398,7 +409,11 @@ __global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restri
   const u32 chunk = blockIdx.x % chunks;
   const u32 tile = blockIdx.x / chunks;
   const u32 r0 = (tile % tilesR) * M::kRows, c0 = (tile / tilesR) * M::kCols;
-  const u32 l = blockIdx.y;
+  const u32 l = blockIdx.y % L;
+  const u64 item = blockIdx.y / L;  // batch item
+  ctN += item * ((u64)nLb * nJ * 2 * L * N);
+  pt += item * ((u64)nI * nJ * L * N);
+  out += item * ((u64)nLb * nI * 2 * L * N);
   const PrimeConsts& P = C.p[l];
   const u32 rows = 2 * nLb;
   const u32 nrows = min((u32)M::kRows, rows - r0), ncols = min((u32)M::kCols, nI - c0);
@@ -503,30 +518,36 @@ constexpr int kMacMinBlocks = 2;
 // Forward NTT of the input ciphertexts of a product into the slot-chunked operand layout.
 // Input poly p = ((Lb nJ + J) 2 + c) L + l of the wire format [Lb nJ + J][2][L][N].
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_forward_mm_t(const u64* src, u64* ctN, u32 nJ,
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_forward_mm_t(const u64* src, u64* ctN, u32 nJ, u32 nLb,
                                                                         const __grid_constant__ Consts C) {
   using S = NttShape<LOGN>;
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
-  const u32 l = poly % C.L;
-  const u32 c = (poly / C.L) % 2;
-  const u32 LbJ = (u32)(poly / (2 * C.L));
+  const u64 item_polys = (u64)nLb * nJ * 2 * C.L;
+  const u64 item = poly / item_polys, local = poly % item_polys;
+  const u32 l = local % C.L;
+  const u32 c = (local / C.L) % 2;
+  const u32 LbJ = (u32)(local / (2 * C.L));
   const u32 Lb = LbJ / nJ, J = LbJ % nJ;
   const PrimeConsts& P = C.p[l];
   const u64* sp = src + poly * S::N;
+  u64* dst = ctN + item * item_polys * S::N;
   const u64 row = (u64)Lb * 2 + c;
   ntt_forward_block<S>(sm, P, [&](u32 e) { return sp[e]; },
-                       [&](u32 e, u64 v) { ctN[chunked_index(row, J, l, e, nJ, C.L, S::N)] = v; });
+                       [&](u32 e, u64 v) { dst[chunked_index(row, J, l, e, nJ, C.L, S::N)] = v; });
 }
 
 // One block per output polynomial (o, c, l): inverse NTT; for c = 0 subtract
 // round(q s_i / t) where s_i is the mask of output o (Algorithm 1, step 3).
-__global__ void __launch_bounds__(kNttThreads) k_intt_mask(u64* out, u64 seed, const __grid_constant__ Consts C) {
+__global__ void __launch_bounds__(kNttThreads) k_intt_mask(u64* out, u64 out_cts, u64 seed,
+                                                          const __grid_constant__ Consts C) {
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
+  const u64 item = poly / (out_cts * 2 * C.L);  // batch item: re-masked with seed + item
+  seed += item;
   const u32 l = poly % C.L;
   const u32 c = (poly / C.L) % 2;
-  const u32 o = (u32)(poly / (2 * C.L));
+  const u32 o = (u32)((poly / (2 * C.L)) % out_cts);
   const PrimeConsts& P = C.p[l];
   u64* d = out + poly * C.N;
   for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) sm[i] = d[i];
@@ -672,51 +693,52 @@ cudaError_t launch_unmask(const Consts& C, u64 seed, u32 m, u32 n, Blk b, u32 nI
   return cudaGetLastError();
 }
 
-cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u64* pt,
-                                  cudaStream_t st) {
-  u64 polys = (u64)nI * nJ * C.L;
+cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u32 batch,
+                                  u64* pt, cudaStream_t st) {
+  u64 polys = (u64)nI * nJ * C.L * batch;
   if (!polys) return cudaGetLastError();
   if (C.logN >= 9) {
-    HE_DISPATCH_T(k_encode_weights_t, (unsigned)polys, st, W, k, n, b, nJ, pt, C)
+    HE_DISPATCH_T(k_encode_weights_t, (unsigned)polys, st, W, k, n, b, nI, nJ, pt, C)
   } else {
-    k_encode_weights<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(W, k, n, b, nJ, pt, C);
+    k_encode_weights<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(W, k, n, b, nI, nJ, pt, C);
   }
   return cudaGetLastError();
 }
 
 template <class M, int MINB>
-cudaError_t launch_mac_cfg(const Consts& C, const u64* ctN, const u64* pt, u64* out, u32 nI, u32 nJ, u32 nLb, int* err,
-                           cudaStream_t st) {
+cudaError_t launch_mac_cfg(const Consts& C, const u64* ctN, const u64* pt, u64* out, u32 nI, u32 nJ, u32 nLb, u32 batch,
+                           int* err, cudaStream_t st) {
   const u32 tilesR = (2 * nLb + M::kRows - 1) / M::kRows, tilesC = (nI + M::kCols - 1) / M::kCols;
-  if ((u64)tilesR * tilesC * nJ == 0) return cudaGetLastError();
-  dim3 grid((unsigned)((u64)(C.N >> 5) * tilesR * tilesC), C.L);
+  if ((u64)tilesR * tilesC * nJ * batch == 0) return cudaGetLastError();
+  dim3 grid((unsigned)((u64)(C.N >> 5) * tilesR * tilesC), C.L * batch);
   k_mac_t<M, MINB><<<grid, M::kThreads, M::kSmemBytes, st>>>(ctN, pt, out, nI, nJ, nLb, tilesR, err, C);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out, u32 nI, u32 nJ, u32 nLb, int* err,
-                       cudaStream_t st) {
-  return launch_mac_cfg<MacProd, kMacMinBlocks>(C, ctN, pt, out, nI, nJ, nLb, err, st);
+cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out, u32 nI, u32 nJ, u32 nLb, u32 batch,
+                       int* err, cudaStream_t st) {
+  return launch_mac_cfg<MacProd, kMacMinBlocks>(C, ctN, pt, out, nI, nJ, nLb, batch, err, st);
 }
 
-cudaError_t launch_ntt_forward_mm(const Consts& C, const u64* ct_in, u64* ctN, u32 nJ, u32 nLb, cudaStream_t st) {
-  const u64 polys = (u64)nLb * nJ * 2 * C.L;
+cudaError_t launch_ntt_forward_mm(const Consts& C, const u64* ct_in, u64* ctN, u32 nJ, u32 nLb, u32 batch,
+                                  cudaStream_t st) {
+  const u64 polys = (u64)nLb * nJ * 2 * C.L * batch;
   if (!polys) return cudaGetLastError();
   if (C.logN >= 9) {
-    HE_DISPATCH_T(k_ntt_forward_mm_t, (unsigned)polys, st, ct_in, ctN, nJ, C)
+    HE_DISPATCH_T(k_ntt_forward_mm_t, (unsigned)polys, st, ct_in, ctN, nJ, nLb, C)
   } else {
-    k_ntt_forward_mm_small<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(ct_in, ctN, nJ, C);
+    k_ntt_forward_mm_small<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(ct_in, ctN, nJ, nLb, C);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_intt_mask(const Consts& C, u64* out, u64 out_cts, u64 seed, cudaStream_t st) {
-  u64 polys = out_cts * 2 * C.L;
+cudaError_t launch_intt_mask(const Consts& C, u64* out, u64 out_cts, u32 batch, u64 seed, cudaStream_t st) {
+  u64 polys = out_cts * 2 * C.L * batch;
   if (!polys) return cudaGetLastError();
   if (C.logN >= 9) {
-    HE_DISPATCH_T(k_intt_mask_t, (unsigned)polys, st, out, seed, C)
+    HE_DISPATCH_T(k_intt_mask_t, (unsigned)polys, st, out, out_cts, seed, C)
   } else {
-    k_intt_mask<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(out, seed, C);
+    k_intt_mask<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(out, out_cts, seed, C);
   }
   return cudaGetLastError();
 }

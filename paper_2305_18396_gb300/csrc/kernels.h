@@ -28,17 +28,20 @@ cudaError_t launch_unpack(const Consts& C, const u64* dec, u32 m, u32 n, Blk b, 
                           cudaStream_t st);
 cudaError_t launch_unmask(const Consts& C, u64 seed, u32 m, u32 n, Blk b, u32 nI, u64* share, cudaStream_t st);
 
-cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u64* pt,
-                                  cudaStream_t st);
+// Products come in batches of identical shape laid out back to back (batch = 1 for one).
+cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u32 batch,
+                                  u64* pt, cudaStream_t st);
 // Slot-wise sum_J pt[I][J] * ctN[Lb][J] for every output (Lb, I), both components, all primes.
 // Forward NTT of a product's input ciphertexts (wire format) into the slot-chunked
 // operand layout the multiply-accumulate kernel streams.
-cudaError_t launch_ntt_forward_mm(const Consts& C, const u64* ct_in, u64* ctN, u32 nJ, u32 nLb, cudaStream_t st);
+cudaError_t launch_ntt_forward_mm(const Consts& C, const u64* ct_in, u64* ctN, u32 nJ, u32 nLb, u32 batch,
+                                  cudaStream_t st);
 // err: device int set to 1 if a bounded wait inside the kernel expired.
-cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out, u32 nI, u32 nJ, u32 nLb, int* err,
-                       cudaStream_t st);
-// Inverse NTT of every output polynomial, then c0 -= round(q s / t) for the mask of output o.
-cudaError_t launch_intt_mask(const Consts& C, u64* out, u64 out_cts, u64 seed, cudaStream_t st);
+cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out, u32 nI, u32 nJ, u32 nLb, u32 batch,
+                       int* err, cudaStream_t st);
+// Inverse NTT of every output polynomial, then c0 -= round(q s / t) for the mask of output o
+// (batch item b uses seed + b).
+cudaError_t launch_intt_mask(const Consts& C, u64* out, u64 out_cts, u32 batch, u64 seed, cudaStream_t st);
 
 // Fixed device scratch of he_matmul_noalloc (no allocation at call time).
 constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;

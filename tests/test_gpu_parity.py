@@ -278,3 +278,30 @@ def test_bert_base_layer_products_sampled(B, prod):
             for i in range(min(n_b, n - I * n_b)):
                 pos = l * n_b * k_b + i * k_b + k_b - 1
                 assert (int(dec[row][pos]) + int(mask[pos])) % P.t == int(ref[Lb * m_b + l, I * n_b + i])
+
+
+# ------------------------------------------------------------------ same-shape batches
+
+
+@pytest.mark.parametrize("N,L,m,k,n,blk", [(4096, 2, 128, 64, 128, (64, 8, 8)), (1024, 2, 9, 30, 17, (4, 8, 8)),
+                                           (256, 2, 5, 7, 3, (2, 4, 4))])
+def test_matmul_batch_equals_single_calls_and_oracle(B, N, L, m, k, n, blk):
+    ctx, P = ctx_for(B, N, L)
+    batch = 3
+    s = O.keygen(P, S.SEED_KEY)
+    Xs = [S.uniform_share((m, k), 60 + b) for b in range(batch)]
+    Ws = [S.uniform_share((k, n), 70 + b) for b in range(batch)]
+    cts = [O.encrypt(P, s, O.pack_input(X, blk, N), 80 + b) for b, X in enumerate(Xs)]
+    si = ctx.sizes(m, k, n, blk)
+    pt = B.he_encode_weights_batch(ctx, to_dev(np.stack(Ws)), k, n, blk, batch)
+    for b in range(batch):  # batched encode == single encodes
+        single = B.he_encode_weights(ctx, to_dev(Ws[b]), k, n, blk)
+        assert torch.equal(pt[b * si["pt_words"]:(b + 1) * si["pt_words"]], single)
+    out = to_np(B.he_matmul_batch(ctx, to_dev(np.stack(cts)), pt, m, k, n, blk, batch, 500))
+    ow = si["out_words"]
+    for b in range(batch):
+        single = to_np(B.he_matmul(ctx, to_dev(cts[b]), pt[b * si["pt_words"]:(b + 1) * si["pt_words"]], m, k, n,
+                                   blk, 500 + b))
+        assert np.array_equal(out[b * ow:(b + 1) * ow], single)
+    want = O.matmul(P, cts[1], Ws[1], m, k, n, blk, 501)
+    assert np.array_equal(out[ow:2 * ow].reshape(want.shape), want)
