@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--full-c0", action="store_true",
+                    help="return all of c0 instead of only the decoded coefficients (Sec. 3.1.3)")
     return ap.parse_args()
 
 
@@ -129,13 +131,13 @@ class Layer:
     """Device state of one layer's products: resident weights, input ciphertexts, outputs.
     Products that occur once per head run as one same-shape batch (he_matmul_batch)."""
 
-    def __init__(self, B, ctx, prods, rank, want_host):
+    def __init__(self, B, ctx, prods, rank, want_host, flags):
         import numpy as np
         import torch
 
         from paper_2305_18396_gb300 import synthetic as S
 
-        self.B, self.ctx = B, ctx
+        self.B, self.ctx, self.flags = B, ctx, flags
         self.calls = []
         dev = ctx.device
         self.sk = B.he_keygen(ctx, S.SEED_KEY + 1000 * rank)
@@ -144,9 +146,11 @@ class Layer:
         for p in prods:
             blk = ctx.default_blocking(p.m, p.k, p.n)
             si = ctx.sizes(p.m, p.k, p.n, blk)
+            ow, wb = B._out_ws(si, flags)
+            si = dict(si, out=ow, ws=wb)
             cnt = p.count
-            max_ws = max(max_ws, cnt * si["workspace_bytes"])
-            max_hostws = max(max_hostws, B.matmul_host_workspace_words(ctx, p.m, p.k, p.n, blk))
+            max_ws = max(max_ws, cnt * wb)
+            max_hostws = max(max_hostws, B.matmul_host_workspace_words(ctx, p.m, p.k, p.n, blk, flags))
             seed = 10_000 * (rank + 1) + idx
             Xs = [S.uniform_share((p.m, p.k), seed + b) for b in range(cnt)]
             if p.share_weights:
@@ -160,7 +164,7 @@ class Layer:
                 B.he_pack_input(ctx, Xd[b * p.m * p.k:(b + 1) * p.m * p.k], p.m, p.k, blk,
                                 polys=polys[b * si["packed_words"]:(b + 1) * si["packed_words"]])
             ct_in = B.he_encrypt(ctx, self.sk, polys, seed + 900_000)
-            call = dict(p=p, blk=blk, si=si, cnt=cnt, ct_in=ct_in, out=ctx.empty(cnt * si["out_words"]), idx=idx)
+            call = dict(p=p, blk=blk, si=si, cnt=cnt, ct_in=ct_in, out=ctx.empty(cnt * si["out"]), idx=idx)
             if p.share_weights:
                 call["W"] = Wd  # the server's shares, encoded on every step
                 max_pt = max(max_pt, cnt * si["pt_words"])
@@ -168,7 +172,7 @@ class Layer:
                 call["pt"] = B.he_encode_weights_batch(ctx, Wd, p.k, p.n, blk, cnt)  # resident NTT-form weights
             if want_host:
                 call["in_host"] = ct_in.cpu().pin_memory()
-                call["out_host"] = torch.empty(cnt * si["out_words"], dtype=torch.int64).pin_memory()
+                call["out_host"] = torch.empty(cnt * si["out"], dtype=torch.int64).pin_memory()
             self.calls.append(call)
             idx += cnt
         self.ws = ctx.empty(max((max_ws + 7) // 8, 1))
@@ -188,21 +192,28 @@ class Layer:
             seed = (step_idx << 20) | c["idx"]
             if host:
                 for b in range(cnt):  # host buffers: one C-ABI call per product
-                    iw, ow, pw = si["in_words"], si["out_words"], si["pt_words"]
+                    iw, ow, pw = si["in_words"], si["out"], si["pt_words"]
                     B.he_matmul_host(ctx, c["in_host"][b * iw:(b + 1) * iw], pt[b * pw:(b + 1) * pw], p.m, p.k, p.n,
-                                     blk, seed + b, c["out_host"][b * ow:(b + 1) * ow], self.host_ws)
+                                     blk, seed + b, c["out_host"][b * ow:(b + 1) * ow], self.host_ws, flags=self.flags)
             else:
-                B.he_matmul_batch(ctx, c["ct_in"], pt, p.m, p.k, p.n, blk, cnt, seed, c["out"], self.ws)
+                B.he_matmul_batch(ctx, c["ct_in"], pt, p.m, p.k, p.n, blk, cnt, seed, c["out"], self.ws,
+                                  flags=self.flags)
 
     def algorithmic_bytes(self):
         """Per kernel family: algorithmic HBM bytes of one step (reads + writes, 8-byte words)."""
         tot = {"mac": 0, "ntt_forward": 0, "intt_mask": 0, "encode_weights": 0}
         for c in self.calls:
             si, p, cnt = c["si"], c["p"], c["cnt"]
-            pt_b, in_b, out_b = 8 * si["pt_words"], 8 * si["in_words"], 8 * si["out_words"]
-            tot["mac"] += cnt * (pt_b + in_b + out_b)
+            pt_b, in_b = 8 * si["pt_words"], 8 * si["in_words"]
+            full_b = 8 * si["out_words"]  # the multiply-accumulate writes both components in full (NTT domain)
+            c1_b = full_b // 2
+            tot["mac"] += cnt * (pt_b + in_b + full_b)
             tot["ntt_forward"] += cnt * 2 * in_b
-            tot["intt_mask"] += cnt * 2 * out_b
+            if self.flags:  # c1: read + write; c0: read in full, write the kept coefficients
+                tot["intt_mask"] += cnt * 2 * c1_b
+                tot["intt_c0_targets"] = tot.get("intt_c0_targets", 0) + cnt * (c1_b + 8 * si["out"] - c1_b)
+            else:
+                tot["intt_mask"] += cnt * 2 * full_b
             if p.share_weights:
                 tot["encode_weights"] += cnt * (8 * p.k * p.n + pt_b)
         return tot
@@ -330,7 +341,8 @@ def gpu_arm(args, world, rank, local):
     ctx = B.Context(N_POLY, L_PRIMES, device=local)
     prods = workloads.bert_layer_products(**workloads.BERT_BASE)
     want_host = not args.no_e2e
-    layer = Layer(B, ctx, prods, rank, want_host)
+    flags = B.HE_FLAGS_NONE if args.full_c0 else B.HE_DROP_C0
+    layer = Layer(B, ctx, prods, rank, want_host, flags)
     stream = torch.cuda.current_stream()
 
     for w in range(max(args.warmup, 3) if args.warmup else 0):
@@ -389,7 +401,7 @@ def gpu_arm(args, world, rank, local):
     e2e = None
     if want_host:
         h2d = sum(8 * c["cnt"] * c["si"]["in_words"] for c in layer.calls)
-        d2h = sum(8 * c["cnt"] * c["si"]["out_words"] for c in layer.calls)
+        d2h = sum(8 * c["cnt"] * c["si"]["out"] for c in layer.calls)
         layer.step(9000, host=True)
         barrier(world)
         torch.cuda.synchronize()
@@ -417,6 +429,8 @@ def gpu_arm(args, world, rank, local):
         "config": {"workload": WORKLOAD, "N": N_POLY, "L": L_PRIMES, "log2_t": 37,
                    "products_per_step": layer.products, "launch_groups_per_step": len(layer.calls),
                    "plain_macs_per_step": layer.macs,
+                   "output": "full ciphertexts" if args.full_c0 else
+                   "c1 + c0 at the decoded coefficients only (Sec. 3.1.3, HE_DROP_C0)",
                    "blockings_mkn": blks, "parallelism": f"replicas x{world} (independent layers, no collective)",
                    "l2": "inputs larger than L2: one step reads/writes ~3 GB of ciphertexts/weights"},
         "latency_ms": {"p50": statistics.median(per), "p99": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))]},

@@ -59,6 +59,13 @@ extern "C" {
 
 /* ---- flags for he_matmul ------------------------------------------------ */
 #define HE_FLAGS_NONE 0u
+/* Compact output (Sec. 3.1.3, "Reducing the communication cost"): decrypting
+ * coefficient e needs only (c0)_e and all of c1, and pi_C^{-1} reads only the
+ * coefficients e = i k_b + k_b - 1.  With this flag each output ciphertext is
+ * [c0 at those e: L x (N / k_b)][c1: L x N] (he_sizes().out_words_compact words in
+ * all) and c0 is computed only there.  Needs a power-of-two k_b.  The kept words
+ * equal the corresponding words of the full output bit for bit. */
+#define HE_DROP_C0 1u
 
 typedef struct he_ctx he_ctx;
 
@@ -76,6 +83,8 @@ typedef struct {
   uint64_t pt_words;        /* words of the opaque encoded-weight buffer     */
   uint64_t packed_words;    /* in_cts * N: he_pack_input output              */
   uint64_t workspace_bytes; /* device workspace he_matmul needs              */
+  uint64_t out_words_compact;       /* output words with HE_DROP_C0 (0 if k_b is not a power of two) */
+  uint64_t workspace_bytes_compact; /* workspace with HE_DROP_C0                                    */
 } he_size_info;
 
 /* Most recent error message of the calling thread ("" if none). */
@@ -169,8 +178,10 @@ HE_API int he_encode_weights_batch(he_ctx* ctx, const uint64_t* W, uint32_t k, u
  * counter (i, o, 4, 0), key = mask_seed.  Use a fresh mask_seed per call.
  * ct_in: device [in_cts][2][L][N]; pt: from he_encode_weights with the same
  * k, n and blk; ct_out: device [out_cts][2][L][N]; workspace: device,
- * >= he_sizes().workspace_bytes (HE_ENOMEM if smaller).  flags: HE_FLAGS_NONE.
- * ct_out must not overlap ct_in, pt or workspace. */
+ * >= he_sizes().workspace_bytes (HE_ENOMEM if smaller).
+ * ct_out must not overlap ct_in, pt or workspace.  flags: HE_FLAGS_NONE or HE_DROP_C0
+ * (then ct_out holds he_sizes().out_words_compact words and the workspace must be
+ * >= he_sizes().workspace_bytes_compact). */
 HE_API int he_matmul(he_ctx* ctx, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
               const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out, void* workspace,
               size_t workspace_bytes, void* stream);
@@ -213,6 +224,12 @@ HE_API int he_matmul_batch(he_ctx* ctx, const uint64_t* ct_in, const uint64_t* p
 #define HE_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 HE_API int he_matmul_noalloc(he_ctx* ctx, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k,
                              uint32_t n, const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out,
+                             void* stream);
+
+/* Client side of HE_DROP_C0: expand cnt compact ciphertexts (k_b of the product's
+ * blocking) to full [cnt][2][L][N] ciphertexts, c0 zero outside the kept
+ * coefficients, for he_decrypt (whose other coefficients are then meaningless). */
+HE_API int he_expand_compact(he_ctx* ctx, const uint64_t* ct_compact, uint32_t cnt, uint32_t k_b, uint64_t* ct_full,
                              void* stream);
 
 /* Server's share pi_C^{-1}(s) of X W for the masks of he_matmul(mask_seed):

@@ -18,6 +18,7 @@ from . import build as _build
 
 HE_OK, HE_EINVAL, HE_ENOMEM, HE_ECUDA, HE_ETIMEOUT, HE_ENOISE = range(6)
 HE_FLAGS_NONE = 0
+HE_DROP_C0 = 1
 _NAMES = {1: "HE_EINVAL", 2: "HE_ENOMEM", 3: "HE_ECUDA", 4: "HE_ETIMEOUT", 5: "HE_ENOISE"}
 
 
@@ -38,7 +39,8 @@ class SizeInfo(ctypes.Structure):
     _fields_ = [("nI", ctypes.c_uint32), ("nJ", ctypes.c_uint32), ("nLb", ctypes.c_uint32),
                 ("in_cts", ctypes.c_uint64), ("out_cts", ctypes.c_uint64), ("pts", ctypes.c_uint64),
                 ("in_words", ctypes.c_uint64), ("out_words", ctypes.c_uint64), ("pt_words", ctypes.c_uint64),
-                ("packed_words", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64)]
+                ("packed_words", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64),
+                ("out_words_compact", ctypes.c_uint64), ("workspace_bytes_compact", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -79,6 +81,7 @@ def _load():
         "he_matmul_batch": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u32, u64, u32, P, P, sz, P]),
         "he_encode_weights_batch": (ctypes.c_int, [P, P, u32, u32, pB, u32, P, P]),
         "he_unmask": (ctypes.c_int, [P, u64, u32, u32, pB, P, P]),
+        "he_expand_compact": (ctypes.c_int, [P, P, u32, u32, P, P]),
         "he_ntt_forward": (ctypes.c_int, [P, P, u32, P]),
         "he_ntt_inverse": (ctypes.c_int, [P, P, u32, P]),
         "he_poly_mul": (ctypes.c_int, [P, P, P, P, u32, P]),
@@ -243,14 +246,22 @@ def he_encode_weights_batch(ctx, W, k, n, blk, batch, pt=None, stream=None):
     return pt
 
 
+def _out_ws(si, flags):
+    """(output words, workspace bytes) of one product for these flags."""
+    if flags & HE_DROP_C0:
+        return si["out_words_compact"], si["workspace_bytes_compact"]
+    return si["out_words"], si["workspace_bytes"]
+
+
 def he_matmul_batch(ctx, ct_in, pt, m, k, n, blk, batch, mask_seed, ct_out=None, workspace=None,
                     flags=HE_FLAGS_NONE, stream=None):
     """`batch` same-shape products back to back; item b is masked with seed mask_seed + b."""
     si = ctx.sizes(m, k, n, blk)
+    ow, wb = _out_ws(si, flags)
     ctx._dev(ct_in, batch * si["in_words"], "ct_in")
     ctx._dev(pt, batch * si["pt_words"], "pt")
-    ct_out = ctx.empty(batch * si["out_words"]) if ct_out is None else ctx._dev(ct_out, batch * si["out_words"], "ct_out")
-    ws_words = batch * ((si["workspace_bytes"] + 7) // 8)
+    ct_out = ctx.empty(batch * ow) if ct_out is None else ctx._dev(ct_out, batch * ow, "ct_out")
+    ws_words = batch * ((wb + 7) // 8)
     workspace = ctx.empty(max(ws_words, 1)) if workspace is None else ctx._dev(workspace, ws_words, "workspace")
     _check(lib.he_matmul_batch(ctx.h, _ptr(ct_in), _ptr(pt), m, k, n, _blk(blk), batch, mask_seed, flags,
                                _ptr(ct_out), _ptr(workspace), workspace.numel() * 8, _stream(stream)))
@@ -260,10 +271,11 @@ def he_matmul_batch(ctx, ct_in, pt, m, k, n, blk, batch, mask_seed, ct_out=None,
 def he_matmul(ctx, ct_in, pt, m, k, n, blk, mask_seed, ct_out=None, workspace=None, flags=HE_FLAGS_NONE,
               stream=None):
     si = ctx.sizes(m, k, n, blk)
+    ow, wb = _out_ws(si, flags)
     ctx._dev(ct_in, si["in_words"], "ct_in")
     ctx._dev(pt, si["pt_words"], "pt")
-    ct_out = ctx.empty(si["out_words"]) if ct_out is None else ctx._dev(ct_out, si["out_words"], "ct_out")
-    ws_words = (si["workspace_bytes"] + 7) // 8
+    ct_out = ctx.empty(ow) if ct_out is None else ctx._dev(ct_out, ow, "ct_out")
+    ws_words = (wb + 7) // 8
     workspace = ctx.empty(max(ws_words, 1)) if workspace is None else ctx._dev(workspace, ws_words, "workspace")
     _check(lib.he_matmul(ctx.h, _ptr(ct_in), _ptr(pt), m, k, n, _blk(blk), mask_seed, flags, _ptr(ct_out),
                          _ptr(workspace), workspace.numel() * 8, _stream(stream)))
@@ -285,23 +297,33 @@ def he_matmul_noalloc(ctx, ct_in, pt, m, k, n, blk, mask_seed, ct_out, flags=HE_
     return ct_out
 
 
-def matmul_host_workspace_words(ctx, m, k, n, blk):
+def matmul_host_workspace_words(ctx, m, k, n, blk, flags=HE_FLAGS_NONE):
     si = ctx.sizes(m, k, n, blk)
-    return (si["workspace_bytes"] + 7) // 8 + si["in_words"] + si["out_words"]
+    ow, wb = _out_ws(si, flags)
+    return (wb + 7) // 8 + si["in_words"] + ow
 
 
 def he_matmul_host(ctx, ct_in_host, pt, m, k, n, blk, mask_seed, ct_out_host, workspace, flags=HE_FLAGS_NONE,
                    stream=None):
     """ct_in_host / ct_out_host: CPU tensors (pinned for asynchronous copies)."""
     si = ctx.sizes(m, k, n, blk)
-    for t, w, name in ((ct_in_host, si["in_words"], "ct_in_host"), (ct_out_host, si["out_words"], "ct_out_host")):
+    ow, _ = _out_ws(si, flags)
+    for t, w, name in ((ct_in_host, si["in_words"], "ct_in_host"), (ct_out_host, ow, "ct_out_host")):
         if t.device.type != "cpu" or not t.is_contiguous() or t.numel() < w:
             raise ValueError(f"{name} must be a contiguous CPU tensor of >= {w} words")
-    ctx._dev(workspace, matmul_host_workspace_words(ctx, m, k, n, blk), "workspace")
+    ctx._dev(workspace, matmul_host_workspace_words(ctx, m, k, n, blk, flags), "workspace")
     _check(lib.he_matmul_host(ctx.h, _ptr(ct_in_host), _ptr(ctx._dev(pt, si["pt_words"], "pt")), m, k, n, _blk(blk),
                               mask_seed, flags, _ptr(ct_out_host), _ptr(workspace), workspace.numel() * 8,
                               _stream(stream)))
     return ct_out_host
+
+
+def he_expand_compact(ctx, ct_compact, cnt, k_b, ct_full=None, stream=None):
+    """Client side of HE_DROP_C0: compact ciphertexts -> full ones (c0 zero off the kept coefficients)."""
+    words = cnt * 2 * ctx.L * ctx.N
+    ct_full = ctx.empty(words) if ct_full is None else ctx._dev(ct_full, words, "ct_full")
+    _check(lib.he_expand_compact(ctx.h, _ptr(ct_compact), cnt, k_b, _ptr(ct_full), _stream(stream)))
+    return ct_full
 
 
 def he_unmask(ctx, mask_seed, m, n, blk, share=None, stream=None):

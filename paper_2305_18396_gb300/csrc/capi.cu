@@ -116,9 +116,13 @@ struct ProfRec {
   cudaEvent_t e0, e1;
 };
 
-enum Kind { KNttFwd, KNttInv, KPolyMul, KKeygen, KEncrypt, KDecrypt, KPack, KUnpack, KUnmask, KEncode, KMac, KInttMask, KCount };
-static const char* kKindNames[KCount] = {"ntt_forward", "ntt_inverse", "poly_mul", "keygen", "encrypt", "decrypt",
-                                         "pack", "unpack", "unmask", "encode_weights", "mac", "intt_mask"};
+enum Kind {
+  KNttFwd, KNttInv, KPolyMul, KKeygen, KEncrypt, KDecrypt, KPack, KUnpack, KUnmask, KEncode, KMac, KInttMask, KInttC0,
+  KExpand, KCount
+};
+static const char* kKindNames[KCount] = {"ntt_forward", "ntt_inverse", "poly_mul", "keygen", "encrypt",
+                                         "decrypt", "pack", "unpack", "unmask", "encode_weights",
+                                         "mac", "intt_mask", "intt_c0_targets", "expand_compact"};
 
 struct he_ctx {
   int device = 0;
@@ -341,6 +345,9 @@ int he_sizes(const he_ctx* c, uint32_t m, uint32_t k, uint32_t n, const he_block
   out->pt_words = out->pts * L * N;
   out->packed_words = out->in_cts * N;
   out->workspace_bytes = out->in_words * sizeof(u64);  // NTT of the input ciphertexts
+  const u64 Nc = pow2(blk->k_b) ? N / blk->k_b : 0;
+  out->out_words_compact = Nc ? out->out_cts * L * (Nc + N) : 0;
+  out->workspace_bytes_compact = (out->in_words + out->out_cts * L * N) * sizeof(u64);
   return HE_OK;
 }
 
@@ -474,26 +481,54 @@ int he_encode_weights(he_ctx* c, const uint64_t* W, uint32_t k, uint32_t n, cons
   return he_encode_weights_batch(c, W, k, n, blk, 1, pt, stream);
 }
 
+static u32 log2u(u32 x) {
+  u32 r = 0;
+  while ((1u << r) < x) ++r;
+  return r;
+}
+
 static int matmul_device(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
-                         const he_blocking* blk, uint32_t batch, uint64_t mask_seed, uint64_t* ct_out, void* ws,
-                         cudaStream_t st) {
+                         const he_blocking* blk, uint32_t batch, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out,
+                         void* ws, cudaStream_t st) {
   Shape s = shape_of(m, k, n, blk);
+  const u64 N = c->C.N, L = c->C.L;
+  const u64 out_cts = (u64)s.nLb * s.nI;
   u64* ctN = (u64*)ws;
   int r = launch(c, KNttFwd, st, "matmul: forward NTT",
                  [&] { return he::launch_ntt_forward_mm(c->C, ct_in, ctN, s.nJ, s.nLb, batch, st); });
   if (r) return r;
-  r = launch(c, KMac, st, "matmul: multiply-accumulate",
-             [&] { return he::launch_mac(c->C, ctN, pt, ct_out, s.nI, s.nJ, s.nLb, batch, c->d_err, st); });
+  if (!(flags & HE_DROP_C0)) {
+    r = launch(c, KMac, st, "matmul: multiply-accumulate", [&] {
+      return he::launch_mac(c->C, ctN, pt, ct_out, 2 * L * N, ct_out + L * N, 2 * L * N, s.nI, s.nJ, s.nLb, batch,
+                            c->d_err, st);
+    });
+    if (r) return r;
+    return launch(c, KInttMask, st, "matmul: inverse NTT + mask",
+                  [&] { return he::launch_intt_mask(c->C, ct_out, out_cts, batch, mask_seed, st); });
+  }
+  // compact output: per ciphertext [c0 at the decoded coefficients: L x N/k_b][c1: L x N]
+  const u32 logkb = log2u(blk->k_b);
+  const u64 Nc = N >> logkb, ct_stride = L * (Nc + N);
+  u64* c0_ntt = ctN + (u64)batch * s.nLb * s.nJ * 2 * L * N;  // after the inputs' NTT in the workspace
+  r = launch(c, KMac, st, "matmul: multiply-accumulate", [&] {
+    return he::launch_mac(c->C, ctN, pt, c0_ntt, L * N, ct_out + L * Nc, ct_stride, s.nI, s.nJ, s.nLb, batch, c->d_err,
+                          st);
+  });
   if (r) return r;
-  return launch(c, KInttMask, st, "matmul: inverse NTT + mask",
-                [&] { return he::launch_intt_mask(c->C, ct_out, (u64)s.nLb * s.nI, batch, mask_seed, st); });
+  r = launch(c, KInttMask, st, "matmul: inverse NTT of c1",
+             [&] { return he::launch_intt_c1(c->C, ct_out + L * Nc, ct_stride, out_cts * batch, st); });
+  if (r) return r;
+  return launch(c, KInttC0, st, "matmul: pruned inverse NTT + mask of c0", [&] {
+    return he::launch_intt_c0_targets(c->C, c0_ntt, ct_out, ct_stride, out_cts, batch, logkb, mask_seed, st);
+  });
 }
 
 static int matmul_checks(he_ctx* c, uint32_t m, uint32_t k, uint32_t n, const he_blocking* blk, uint32_t flags,
                          he_size_info* si) {
   if (!c) return fail(HE_EINVAL, "ctx is NULL");
   if (int r = check_blk(c, blk)) return r;
-  if (flags != HE_FLAGS_NONE) return fail(HE_EINVAL, "unknown flags");
+  if (flags & ~(uint32_t)HE_DROP_C0) return fail(HE_EINVAL, "unknown flags");
+  if ((flags & HE_DROP_C0) && !pow2(blk->k_b)) return fail(HE_EINVAL, "HE_DROP_C0 needs a power-of-two k_b");
   he_sizes(c, m, k, n, blk, si);
   if (si->nJ > 4096) return fail(HE_EINVAL, "at most 4096 k-blocks (k / k_b) per product");
   return HE_OK;
@@ -506,9 +541,10 @@ int he_matmul(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, 
   if (int r = matmul_checks(c, m, k, n, blk, flags, &si)) return r;
   if (!m || !k || !n) return HE_OK;
   if (!ct_in || !pt || !ct_out || !workspace) return fail(HE_EINVAL, "NULL buffer");
-  if (workspace_bytes < si.workspace_bytes) return fail(HE_ENOMEM, "workspace smaller than he_sizes().workspace_bytes");
+  const u64 need = (flags & HE_DROP_C0) ? si.workspace_bytes_compact : si.workspace_bytes;
+  if (workspace_bytes < need) return fail(HE_ENOMEM, "workspace smaller than he_sizes() requires for these flags");
   if (int r = set_device(c)) return r;
-  return matmul_device(c, ct_in, pt, m, k, n, blk, 1, mask_seed, ct_out, workspace, (cudaStream_t)stream);
+  return matmul_device(c, ct_in, pt, m, k, n, blk, 1, mask_seed, flags, ct_out, workspace, (cudaStream_t)stream);
 }
 
 int he_matmul_batch(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
@@ -519,10 +555,11 @@ int he_matmul_batch(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32
   if (!m || !k || !n || !batch) return HE_OK;
   if ((u64)batch * c->C.L > 65535) return fail(HE_EINVAL, "batch * L must be <= 65535");
   if (!ct_in || !pt || !ct_out || !workspace) return fail(HE_EINVAL, "NULL buffer");
-  if (workspace_bytes / batch < si.workspace_bytes)
-    return fail(HE_ENOMEM, "workspace smaller than batch * he_sizes().workspace_bytes");
+  const u64 need = (flags & HE_DROP_C0) ? si.workspace_bytes_compact : si.workspace_bytes;
+  if (workspace_bytes / batch < need)
+    return fail(HE_ENOMEM, "workspace smaller than batch x what he_sizes() requires for these flags");
   if (int r = set_device(c)) return r;
-  return matmul_device(c, ct_in, pt, m, k, n, blk, batch, mask_seed, ct_out, workspace, (cudaStream_t)stream);
+  return matmul_device(c, ct_in, pt, m, k, n, blk, batch, mask_seed, flags, ct_out, workspace, (cudaStream_t)stream);
 }
 
 int he_matmul_host(he_ctx* c, const uint64_t* ct_in_host, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
@@ -532,16 +569,19 @@ int he_matmul_host(he_ctx* c, const uint64_t* ct_in_host, const uint64_t* pt, ui
   if (int r = matmul_checks(c, m, k, n, blk, flags, &si)) return r;
   if (!m || !k || !n) return HE_OK;
   if (!ct_in_host || !pt || !ct_out_host || !workspace) return fail(HE_EINVAL, "NULL buffer");
-  const u64 need = si.workspace_bytes + 8 * (si.in_words + si.out_words);
+  const bool compact = flags & HE_DROP_C0;
+  const u64 ws_need = compact ? si.workspace_bytes_compact : si.workspace_bytes;
+  const u64 out_words = compact ? si.out_words_compact : si.out_words;
+  const u64 need = ws_need + 8 * (si.in_words + out_words);
   if (workspace_bytes < need) return fail(HE_ENOMEM, "workspace smaller than he_matmul_host needs");
   if (int r = set_device(c)) return r;
   cudaStream_t st = (cudaStream_t)stream;
-  u64* d_in = (u64*)((char*)workspace + si.workspace_bytes);
+  u64* d_in = (u64*)((char*)workspace + ws_need);
   u64* d_out = d_in + si.in_words;
   cudaError_t e = cudaMemcpyAsync(d_in, ct_in_host, si.in_words * 8, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "matmul_host: upload");
-  if (int r = matmul_device(c, d_in, pt, m, k, n, blk, 1, mask_seed, d_out, workspace, st)) return r;
-  e = cudaMemcpyAsync(ct_out_host, d_out, si.out_words * 8, cudaMemcpyDeviceToHost, st);
+  if (int r = matmul_device(c, d_in, pt, m, k, n, blk, 1, mask_seed, flags, d_out, workspace, st)) return r;
+  e = cudaMemcpyAsync(ct_out_host, d_out, out_words * 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "matmul_host: download");
   return HE_OK;
@@ -554,6 +594,7 @@ int he_matmul_noalloc(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint
   if (int r = matmul_checks(c, m, k, n, blk, flags, &si)) return r;
   if (!m || !k || !n) return HE_OK;
   if (!ct_in || !pt || !ct_out) return fail(HE_EINVAL, "NULL buffer");
+  if (flags != HE_FLAGS_NONE) return fail(HE_EINVAL, "he_matmul_noalloc takes no flags");
   if (si.workspace_bytes > HE_NOALLOC_SCRATCH_BYTES)
     return fail(HE_EINVAL, "product needs " + std::to_string(si.workspace_bytes) +
                                " bytes of scratch; he_matmul_noalloc has " +
@@ -562,7 +603,19 @@ int he_matmul_noalloc(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint
   void* scratch = nullptr;
   cudaError_t e = he::noalloc_scratch_address(c->device, &scratch);
   if (e != cudaSuccess) return cuda_fail(e, "matmul_noalloc: scratch address");
-  return matmul_device(c, ct_in, pt, m, k, n, blk, 1, mask_seed, ct_out, scratch, (cudaStream_t)stream);
+  return matmul_device(c, ct_in, pt, m, k, n, blk, 1, mask_seed, flags, ct_out, scratch, (cudaStream_t)stream);
+}
+
+int he_expand_compact(he_ctx* c, const uint64_t* ct_compact, uint32_t cnt, uint32_t k_b, uint64_t* ct_full,
+                      void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (!pow2(k_b) || k_b > c->C.N) return fail(HE_EINVAL, "k_b must be a power of two <= N");
+  if (!cnt) return HE_OK;
+  if (!ct_compact || !ct_full) return fail(HE_EINVAL, "NULL buffer");
+  if (int r = set_device(c)) return r;
+  return launch(c, KExpand, (cudaStream_t)stream, "expand_compact", [&] {
+    return he::launch_expand_compact(c->C, ct_compact, cnt, log2u(k_b), ct_full, (cudaStream_t)stream);
+  });
 }
 
 int he_ntt_forward(he_ctx* c, uint64_t* polys, uint32_t cnt, void* stream) {

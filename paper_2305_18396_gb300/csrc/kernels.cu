@@ -82,6 +82,10 @@ __global__ void __launch_bounds__(kNttThreads) k_poly_mul(const u64* a, const u6
 
 // Forward NTT of matmul inputs for N < 512 into the slot-chunked layout (see k_mac_t).
 __host__ __device__ constexpr u64 chunked_index(u64 row, u32 J, u32 l, u32 s, u32 nJ, u32 L, u32 N);
+
+// Operand word of the multiply-accumulate: a residue v < 2^50 stored pre-split as
+// v mod 2^25 in the low half and floor(v / 2^25) in the high half.
+__device__ __forceinline__ u64 split_word(u64 v) { return (v & ((1ull << 25) - 1)) | ((v >> 25) << 32); }
 __global__ void __launch_bounds__(kNttThreads) k_ntt_forward_mm_small(const u64* src, u64* ctN, u32 nJ, u32 nLb,
                                                                       const __grid_constant__ Consts C) {
   extern __shared__ u64 sm[];
@@ -98,7 +102,7 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_forward_mm_small(const u64*
   __syncthreads();
   ntt_forward_smem(sm, C.logN, P);
   for (u32 i = threadIdx.x; i < C.N; i += blockDim.x)
-    dst[chunked_index((u64)Lb * 2 + c, J, l, i, nJ, C.L, C.N)] = sm[i];
+    dst[chunked_index((u64)Lb * 2 + c, J, l, i, nJ, C.L, C.N)] = split_word(sm[i]);
 }
 
 // Register-blocked versions for N >= 512 (blockDim = NttShape<LOGN>::T).
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(kNttThreads) k_encode_weights(const u64* W, u3
   }
   __syncthreads();
   ntt_forward_smem(sm, C.logN, P);
-  for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) pt[chunked_index(I, J, l, i, nJ, C.L, C.N)] = sm[i];
+  for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) pt[chunked_index(I, J, l, i, nJ, C.L, C.N)] = split_word(sm[i]);
 }
 
 template <int LOGN>
@@ -334,7 +338,8 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_encode_weights_t(const u6
     u64 w = W[(u64)row * n + col] & C.tmask;
     return w >= half_t ? P.q - (C.tmask + 1 - w) : w;  // centred lift [-t/2, t/2)
   };
-  ntt_forward_block<S>(sm, P, load, [&](u32 e, u64 v) { pt[chunked_index(I, J, l, e, nJ, C.L, S::N)] = v; });
+  ntt_forward_block<S>(sm, P, load,
+                       [&](u32 e, u64 v) { pt[chunked_index(I, J, l, e, nJ, C.L, S::N)] = split_word(v); });
 }
 
 template <int LOGN>
@@ -371,15 +376,28 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_intt_mask_t(u64* out, u64
 // stage, warp 0 streams JB consecutive k-blocks of every operand row of the tile into
 // shared memory -- one 1-D bulk copy (TMA) of JB * 256 contiguous bytes per row --
 // completing on the stage's mbarrier; STAGES stages are in flight.  Each thread owns one
-// slot and a TM x TN register tile.  Operands < 2^50 are split x = x0 + 2^25 x1 and
-// multiplied Karatsuba-style: three mad.wide.u32 per slot product into lo / mid / hi
+// slot and a TM x TN register tile.  Operands < 2^50 are stored split, x = x0 + 2^25 x1
+// (split_word), and multiplied Karatsuba-style: three mad.wide.u32 per slot product into lo / mid / hi
 // 64-bit columns (no carries for nJ <= 4096), reduced once per output at the end.
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: a copy that never lands is an error
 
-__device__ __forceinline__ void split25(u64 v, u32& a0, u32& a1, u32& as) {
-  a0 = (u32)v & ((1u << 25) - 1);
-  a1 = (u32)(v >> 25);
+// Operands arrive pre-split (split_word): halves of the word, plus their sum for Karatsuba.
+__device__ __forceinline__ void split25(u64 w, u32& a0, u32& a1, u32& as) {
+  a0 = (u32)w;
+  a1 = (u32)(w >> 32);
   as = a0 + a1;
+}
+
+// Where the multiply-accumulate writes component c of (global) output ciphertext g:
+// base[c] + g * ct_stride[c] + l * N + slot.
+struct OutPlace {
+  u64* base[2];
+  u64 ct_stride[2];
+};
+
+// acc += a * b with a 32 x 32 -> 64-bit product (one mad.wide.u32).
+__device__ __forceinline__ void mad_wide(u64& acc, u32 a, u32 b) {
+  asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
 
 __host__ __device__ constexpr u64 chunked_index(u64 row, u32 J, u32 l, u32 s, u32 nJ, u32 L, u32 N) {
@@ -397,7 +415,7 @@ struct MacCfg {
 
 template <class M, int MINB>
 __global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restrict__ ctN, const u64* __restrict__ pt,
-                                                             u64* __restrict__ out, u32 nI, u32 nJ, u32 nLb,
+                                                             OutPlace out, u32 nI, u32 nJ, u32 nLb,
                                                              u32 tilesR, int* err, const __grid_constant__ Consts C) {
   extern __shared__ __align__(128) u64 sm[];
   __shared__ __align__(8) uint64_t bars[M::kStages];
@@ -413,7 +431,7 @@ __global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restri
   const u64 item = blockIdx.y / L;  // batch item
   ctN += item * ((u64)nLb * nJ * 2 * L * N);
   pt += item * ((u64)nI * nJ * L * N);
-  out += item * ((u64)nLb * nI * 2 * L * N);
+  const u64 ct0 = item * ((u64)nLb * nI);  // global index of this item's first output ciphertext
   const PrimeConsts& P = C.p[l];
   const u32 rows = 2 * nLb;
   const u32 nrows = min((u32)M::kRows, rows - r0), ncols = min((u32)M::kCols, nI - c0);
@@ -471,23 +489,30 @@ __global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restri
     if (abort_flag) return;
     const u64* stage = sm + st * M::kStageWords;
     const u32 jb = min((u32)JB, nJ - k * JB);
-#pragma unroll 2
-    for (u32 jj = 0; jj < jb; ++jj) {
+    const u64* prow = stage + (M::kRows + wc * TN) * (JB * 32) + lane;  // this thread's column operands
+    const u64* crow = stage + (wr * TM) * (JB * 32) + lane;             // this thread's row operands
+    // one k-block: TN column and TM row operands (pre-split words), TM x TN x 3 mad.wide
+    auto kblock = [&](u32 jj) {
       u32 p0[TN], p1[TN], ps[TN];
 #pragma unroll
-      for (int b = 0; b < TN; ++b)
-        split25(stage[(M::kRows + wc * TN + b) * (JB * 32) + jj * 32 + lane], p0[b], p1[b], ps[b]);
+      for (int b = 0; b < TN; ++b) split25(prow[b * (JB * 32) + jj * 32], p0[b], p1[b], ps[b]);
 #pragma unroll
       for (int a = 0; a < TM; ++a) {
         u32 x0, x1, xs;
-        split25(stage[(wr * TM + a) * (JB * 32) + jj * 32 + lane], x0, x1, xs);
+        split25(crow[a * (JB * 32) + jj * 32], x0, x1, xs);
 #pragma unroll
         for (int b = 0; b < TN; ++b) {
-          lo[a][b] += (u64)x0 * p0[b];
-          hi[a][b] += (u64)x1 * p1[b];
-          mid[a][b] += (u64)xs * ps[b];
+          mad_wide(lo[a][b], x0, p0[b]);
+          mad_wide(hi[a][b], x1, p1[b]);
+          mad_wide(mid[a][b], xs, ps[b]);
         }
       }
+    };
+    if (jb == (u32)JB) {  // full stage: constant offsets, fully unrolled
+#pragma unroll
+      for (int jj = 0; jj < JB; ++jj) kblock(jj);
+    } else {
+      for (u32 jj = 0; jj < jb; ++jj) kblock(jj);
     }
     __syncthreads();
     if (warp == 0 && k + ST < nstages) issue(k + ST, st);
@@ -506,13 +531,14 @@ __global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restri
       u64 v = reduce_word(lo[a][b], P);
       v = add_mod(v, csub(mul_shoup(cross, P.r25, P.r25_sh, P.q), P.q), P.q);
       v = add_mod(v, csub(mul_shoup(hi[a][b], P.r50, P.r50_sh, P.q), P.q), P.q);
-      out[((((u64)(r >> 1) * nI + I) * 2 + (r & 1)) * L + l) * N + s] = v;
+      const u32 c = r & 1;
+      out.base[c][(ct0 + (u64)(r >> 1) * nI + I) * out.ct_stride[c] + (u64)l * N + s] = v;
     }
   }
 }
 
 // The configuration the library launches.
-using MacProd = MacCfg<4, 4, 2, 2, 8, 2>;
+using MacProd = MacCfg<4, 2, 2, 4, 8, 2>;
 constexpr int kMacMinBlocks = 2;
 
 // Forward NTT of the input ciphertexts of a product into the slot-chunked operand layout.
@@ -534,7 +560,90 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_forward_mm_t(const u6
   u64* dst = ctN + item * item_polys * S::N;
   const u64 row = (u64)Lb * 2 + c;
   ntt_forward_block<S>(sm, P, [&](u32 e) { return sp[e]; },
-                       [&](u32 e, u64 v) { dst[chunked_index(row, J, l, e, nJ, C.L, S::N)] = v; });
+                       [&](u32 e, u64 v) { dst[chunked_index(row, J, l, e, nJ, C.L, S::N)] = split_word(v); });
+}
+
+// Compact-output mode: inverse NTT of the c1 polynomials only, in place.  Ciphertext g's
+// c1 for prime l sits at base + g * ct_stride + l * N.
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_intt_c1_t(u64* base, u64 ct_stride,
+                                                                 const __grid_constant__ Consts C) {
+  using S = NttShape<LOGN>;
+  extern __shared__ u64 sm[];
+  const u64 poly = blockIdx.x;
+  u64* d = base + (poly / C.L) * ct_stride + (poly % C.L) * (u64)S::N;
+  ntt_inverse_block<S>(sm, C.p[poly % C.L], [&](u32 e) { return d[e]; }, [&](u32 e, u64 v) { d[e] = v; });
+}
+
+__global__ void __launch_bounds__(kNttThreads) k_intt_c1_small(u64* base, u64 ct_stride,
+                                                               const __grid_constant__ Consts C) {
+  extern __shared__ u64 sm[];
+  const u64 poly = blockIdx.x;
+  u64* d = base + (poly / C.L) * ct_stride + (poly % C.L) * (u64)C.N;
+  for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) sm[i] = d[i];
+  __syncthreads();
+  ntt_inverse_smem(sm, C.logN, C.p[poly % C.L]);
+  for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) d[i] = sm[i];
+}
+
+// Compact-output mode (Sec. 3.1.3, "Reducing the communication cost"): the client only
+// decrypts the coefficients pi_C^{-1} reads, e = g k_b + k_b - 1, and decryption of
+// coefficient e needs only (c0)_e; so c0 is inverse-transformed only at those e.  The
+// Gentleman-Sande stages of span < k_b combine slots within groups of k_b; of their outputs
+// only position k_b - 1 of each group feeds the wanted coefficients, so those stages keep
+// one butterfly branch (k_b - 1 products per group), and the stages of span >= k_b run on
+// the N / k_b surviving values.  The arithmetic on the kept branch is exactly that of the
+// full inverse transform, so the kept coefficients are bit-identical to it.
+// src: NTT-domain c0 of global ciphertext g, prime l at src + (g L + l) N.
+// dst: compact c0 (N / k_b words per prime) at dst + g * ct_stride + l * (N / k_b); masked.
+__global__ void __launch_bounds__(kNttThreads) k_intt_c0_targets(const u64* src, u64* dst, u64 ct_stride, u64 out_cts,
+                                                                 u32 logkb, u64 seed, const __grid_constant__ Consts C) {
+  extern __shared__ u64 sm[];
+  const u64 poly = blockIdx.x;
+  const u32 l = poly % C.L;
+  const u64 g_ct = poly / C.L;
+  const u64 item = g_ct / out_cts;
+  const u32 o = (u32)(g_ct % out_cts);
+  const PrimeConsts& P = C.p[l];
+  const u32 N = C.N, logN = C.logN, Nc = N >> logkb;
+  const u64 q = P.q, two_q = P.two_q;
+  u64* z = sm + N;  // compact values
+  for (u32 i = threadIdx.x; i < N; i += blockDim.x) sm[i] = src[poly * N + i];
+  __syncthreads();
+  // pruned stages s < log2 k_b: keep positions whose low s+1 bits are all ones
+  for (u32 s = 0; s < logkb; ++s) {
+    const u32 span = 1u << s, ones = (2u << s) - 1;
+    for (u32 t = threadIdx.x; t < (N >> (s + 1)); t += blockDim.x) {
+      const u32 p = (t << (s + 1)) | ones;
+      const u32 widx = (N >> (s + 1)) + (p >> (s + 1));
+      const u64 U = sm[p - span], V = sm[p];
+      sm[p] = mul_shoup(U - V + two_q, __ldg(P.ipsi + widx), __ldg(P.ipsi_sh + widx), q);
+    }
+    __syncthreads();
+  }
+  const u32 kb = 1u << logkb;
+  for (u32 g = threadIdx.x; g < Nc; g += blockDim.x) z[g] = sm[g * kb + kb - 1];
+  __syncthreads();
+  // remaining stages on the compact array (span 2^(s - log2 k_b) there)
+  for (u32 s = logkb; s < logN; ++s) {
+    const u32 cs = s - logkb, span = 1u << cs;
+    for (u32 b = threadIdx.x; b < (Nc >> 1); b += blockDim.x) {
+      const u32 grp = b >> cs;
+      const u32 j = (grp << (cs + 1)) + (b & (span - 1));
+      const u32 widx = (N >> (s + 1)) + grp;
+      const u64 U = z[j], V = z[j + span];
+      z[j] = csub(U + V, two_q);
+      z[j + span] = mul_shoup(U - V + two_q, __ldg(P.ipsi + widx), __ldg(P.ipsi_sh + widx), q);
+    }
+    __syncthreads();
+  }
+  u64* d = dst + g_ct * ct_stride + (u64)l * Nc;
+  for (u32 g = threadIdx.x; g < Nc; g += blockDim.x) {
+    u64 v = csub(mul_shoup(z[g], P.ninv, P.ninv_sh, q), q);
+    const u32 e = g * kb + kb - 1;
+    const u64 sv = lo64(draw(seed + item, e, o, kDomainMask, 0)) & C.tmask;
+    d[g] = sub_mod(v, delta_residue(sv, C, P), q);
+  }
 }
 
 // One block per output polynomial (o, c, l): inverse NTT; for c = 0 subtract
@@ -601,6 +710,8 @@ cudaError_t configure_kernels(const Consts&) {
   };
   set((const void*)k_ntt_forward, one);
   set((const void*)k_ntt_forward_mm_small, one);
+  set((const void*)k_intt_c1_small, one);
+  set((const void*)k_intt_c0_targets, two);
   set((const void*)k_ntt_inverse, one);
   set((const void*)k_poly_mul, two);
   set((const void*)k_keygen, one);
@@ -614,7 +725,8 @@ cudaError_t configure_kernels(const Consts&) {
   set((const void*)k_ntt_inverse_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
   set((const void*)k_encode_weights_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));       \
   set((const void*)k_ntt_forward_mm_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));       \
-  set((const void*)k_intt_mask_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));
+  set((const void*)k_intt_mask_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
+  set((const void*)k_intt_c1_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));
   HE_SET_T(9) HE_SET_T(10) HE_SET_T(11) HE_SET_T(12) HE_SET_T(13)
 #undef HE_SET_T
   return e;
@@ -706,8 +818,8 @@ cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, B
 }
 
 template <class M, int MINB>
-cudaError_t launch_mac_cfg(const Consts& C, const u64* ctN, const u64* pt, u64* out, u32 nI, u32 nJ, u32 nLb, u32 batch,
-                           int* err, cudaStream_t st) {
+cudaError_t launch_mac_cfg(const Consts& C, const u64* ctN, const u64* pt, OutPlace out, u32 nI, u32 nJ, u32 nLb,
+                           u32 batch, int* err, cudaStream_t st) {
   const u32 tilesR = (2 * nLb + M::kRows - 1) / M::kRows, tilesC = (nI + M::kCols - 1) / M::kCols;
   if ((u64)tilesR * tilesC * nJ * batch == 0) return cudaGetLastError();
   dim3 grid((unsigned)((u64)(C.N >> 5) * tilesR * tilesC), C.L * batch);
@@ -715,9 +827,14 @@ cudaError_t launch_mac_cfg(const Consts& C, const u64* ctN, const u64* pt, u64* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out, u32 nI, u32 nJ, u32 nLb, u32 batch,
-                       int* err, cudaStream_t st) {
-  return launch_mac_cfg<MacProd, kMacMinBlocks>(C, ctN, pt, out, nI, nJ, nLb, batch, err, st);
+cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out0, u64 stride0, u64* out1, u64 stride1,
+                       u32 nI, u32 nJ, u32 nLb, u32 batch, int* err, cudaStream_t st) {
+  OutPlace o;
+  o.base[0] = out0;
+  o.base[1] = out1;
+  o.ct_stride[0] = stride0;
+  o.ct_stride[1] = stride1;
+  return launch_mac_cfg<MacProd, kMacMinBlocks>(C, ctN, pt, o, nI, nJ, nLb, batch, err, st);
 }
 
 cudaError_t launch_ntt_forward_mm(const Consts& C, const u64* ct_in, u64* ctN, u32 nJ, u32 nLb, u32 batch,
@@ -740,6 +857,55 @@ cudaError_t launch_intt_mask(const Consts& C, u64* out, u64 out_cts, u32 batch, 
   } else {
     k_intt_mask<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(out, out_cts, seed, C);
   }
+  return cudaGetLastError();
+}
+
+}  // namespace he
+
+namespace he {
+
+cudaError_t launch_intt_c1(const Consts& C, u64* base, u64 ct_stride, u64 cts, cudaStream_t st) {
+  const u64 polys = cts * C.L;
+  if (!polys) return cudaGetLastError();
+  if (C.logN >= 9) {
+    HE_DISPATCH_T(k_intt_c1_t, (unsigned)polys, st, base, ct_stride, C)
+  } else {
+    k_intt_c1_small<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(base, ct_stride, C);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_intt_c0_targets(const Consts& C, const u64* src, u64* dst, u64 ct_stride, u64 out_cts, u32 batch,
+                                   u32 logkb, u64 seed, cudaStream_t st) {
+  const u64 polys = out_cts * batch * C.L;
+  if (!polys) return cudaGetLastError();
+  const size_t smem = (size_t)(C.N + (C.N >> logkb)) * sizeof(u64);
+  k_intt_c0_targets<<<(unsigned)polys, kNttThreads, smem, st>>>(src, dst, ct_stride, out_cts, logkb, seed, C);
+  return cudaGetLastError();
+}
+
+}  // namespace he
+
+namespace he {
+
+// Compact ciphertext [c0 at e = i k_b + k_b - 1: L x N/k_b][c1: L x N] -> full [2][L][N]
+// with zeros at the c0 coefficients the compact form leaves out.
+__global__ void k_expand_compact(const u64* src, u64 cnt, u32 logkb, u64* dst, const __grid_constant__ Consts C) {
+  const u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  const u64 N = C.N, L = C.L, Nc = N >> logkb;
+  if (idx >= cnt * 2 * L * N) return;
+  const u64 e = idx % N, l = (idx / N) % L, comp = (idx / (N * L)) % 2, g = idx / (2 * L * N);
+  const u64* sct = src + g * L * (Nc + N);
+  const u64 kb = 1ull << logkb;
+  u64 v;
+  if (comp == 1) v = sct[L * Nc + l * N + e];
+  else v = (e % kb == kb - 1) ? sct[l * Nc + e / kb] : 0;
+  dst[idx] = v;
+}
+
+cudaError_t launch_expand_compact(const Consts& C, const u64* src, u64 cnt, u32 logkb, u64* dst, cudaStream_t st) {
+  const u64 total = cnt * 2 * C.L * C.N;
+  if (total) k_expand_compact<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(src, cnt, logkb, dst, C);
   return cudaGetLastError();
 }
 

@@ -36,9 +36,19 @@ cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, B
 // operand layout the multiply-accumulate kernel streams.
 cudaError_t launch_ntt_forward_mm(const Consts& C, const u64* ct_in, u64* ctN, u32 nJ, u32 nLb, u32 batch,
                                   cudaStream_t st);
-// err: device int set to 1 if a bounded wait inside the kernel expired.
-cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out, u32 nI, u32 nJ, u32 nLb, u32 batch,
-                       int* err, cudaStream_t st);
+// err: device int set to 1 if a bounded wait inside the kernel expired.  Component c of
+// global output ciphertext g (item * out_cts + Lb * nI + I), prime l, is written at
+// out_c + g * stride_c + l * N (NTT domain).
+cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out0, u64 stride0, u64* out1, u64 stride1,
+                       u32 nI, u32 nJ, u32 nLb, u32 batch, int* err, cudaStream_t st);
+// Compact-output mode: in-place inverse NTT of the c1 polynomials (c1 of ciphertext g at
+// base + g * ct_stride), and the pruned inverse NTT + mask of c0 at the coefficients
+// e = i k_b + k_b - 1 only (NTT-domain c0 of ciphertext g at src + g L N).
+cudaError_t launch_intt_c1(const Consts& C, u64* base, u64 ct_stride, u64 cts, cudaStream_t st);
+// Compact ciphertexts -> full ciphertexts with zero c0 outside the kept coefficients.
+cudaError_t launch_expand_compact(const Consts& C, const u64* src, u64 cnt, u32 logkb, u64* dst, cudaStream_t st);
+cudaError_t launch_intt_c0_targets(const Consts& C, const u64* src, u64* dst, u64 ct_stride, u64 out_cts, u32 batch,
+                                   u32 logkb, u64 seed, cudaStream_t st);
 // Inverse NTT of every output polynomial, then c0 -= round(q s / t) for the mask of output o
 // (batch item b uses seed + b).
 cudaError_t launch_intt_mask(const Consts& C, u64* out, u64 out_cts, u32 batch, u64 seed, cudaStream_t st);

@@ -305,3 +305,44 @@ def test_matmul_batch_equals_single_calls_and_oracle(B, N, L, m, k, n, blk):
         assert np.array_equal(out[b * ow:(b + 1) * ow], single)
     want = O.matmul(P, cts[1], Ws[1], m, k, n, blk, 501)
     assert np.array_equal(out[ow:2 * ow].reshape(want.shape), want)
+
+
+# ------------------------------------------------------------------ compact output (HE_DROP_C0)
+
+
+@pytest.mark.parametrize("N,L,m,k,n,blk,batch", [
+    (4096, 2, 16, 64, 64, (8, 32, 16), 1),
+    (4096, 2, 9, 70, 37, (4, 32, 32), 1),
+    (1024, 2, 7, 20, 9, (4, 8, 16), 2),
+    (64, 2, 5, 6, 7, (2, 4, 8), 1),
+    (8192, 3, 7, 33, 20, (8, 32, 32), 1),
+    (4096, 2, 3, 5, 2, (1, 1, 1), 1),
+    (4096, 2, 2, 300, 3, (1, 256, 16), 1),
+])
+def test_matmul_compact_c0(B, N, L, m, k, n, blk, batch):
+    """With HE_DROP_C0 the output keeps c1 and c0 only at the decoded coefficients
+    e = i k_b + k_b - 1 (Sec. 3.1.3); every kept word equals the oracle's full output, and
+    the client's expand + decrypt + unpack plus the server's unmask give X W mod t."""
+    ctx, P = ctx_for(B, N, L)
+    s = O.keygen(P, S.SEED_KEY)
+    Xs = [S.uniform_share((m, k), 90 + b) for b in range(batch)]
+    Ws = [S.fixed_point_weights((k, n), 95 + b) for b in range(batch)]
+    cts = [O.encrypt(P, s, O.pack_input(X, blk, N), 97 + b) for b, X in enumerate(Xs)]
+    pt = B.he_encode_weights_batch(ctx, to_dev(np.stack(Ws)), k, n, blk, batch)
+    out = B.he_matmul_batch(ctx, to_dev(np.stack(cts)), pt, m, k, n, blk, batch, 700, flags=B.HE_DROP_C0)
+    si = ctx.sizes(m, k, n, blk)
+    kb, out_cts, ow = blk[1], si["out_cts"], si["out_words_compact"]
+    Nc = N // kb
+    assert ow == out_cts * L * (Nc + N)
+    got_all = to_np(out)
+    sk = B.he_keygen(ctx, S.SEED_KEY)
+    for b in range(batch):
+        want = O.matmul(P, cts[b], Ws[b], m, k, n, blk, 700 + b)
+        got = got_all[b * ow:(b + 1) * ow].reshape(out_cts, L * (Nc + N))
+        assert np.array_equal(got[:, L * Nc:].reshape(out_cts, L, N), want[:, 1])
+        assert np.array_equal(got[:, :L * Nc].reshape(out_cts, L, Nc), want[:, 0, :, kb - 1::kb])
+        full = B.he_expand_compact(ctx, out[b * ow:(b + 1) * ow], out_cts, kb)
+        dec, _ = B.he_decrypt(ctx, sk, full)
+        client = to_np(B.he_unpack_output(ctx, dec, m, n, blk), (m, n))
+        server = to_np(B.he_unmask(ctx, 700 + b, m, n, blk), (m, n))
+        assert np.array_equal((client + server) % np.uint64(P.t), O.plain_matmul_mod_t(Xs[b], Ws[b], P.t))
