@@ -144,7 +144,7 @@ class Layer:
         max_ws = max_pt = max_hostws = 0
         idx = 0
         for p in prods:
-            blk = ctx.default_blocking(p.m, p.k, p.n)
+            blk = ctx.default_blocking(p.m, p.k, p.n, p.share_weights)
             si = ctx.sizes(p.m, p.k, p.n, blk)
             ow, wb = B._out_ws(si, flags)
             si = dict(si, out=ow, ws=wb)
@@ -276,7 +276,7 @@ def oracle_sample(kind="baseline"):
     s = O.keygen(P, S.SEED_KEY)
     jobs = []
     for i, p in enumerate(heads):
-        blk = he_choose_blocking(N_POLY, L_PRIMES, p.m, p.k, p.n)
+        blk = he_choose_blocking(N_POLY, L_PRIMES, p.m, p.k, p.n, p.share_weights)
         X = S.uniform_share((p.m, p.k), 100 + i)
         W = S.uniform_share((p.k, p.n), 200 + i) if p.share_weights else S.fixed_point_weights((p.k, p.n), 200 + i)
         ct = O.encrypt(P, s, O.pack_input(X, blk, N_POLY), 300 + i)

@@ -112,13 +112,18 @@ HE_API int he_get_params(const he_ctx* ctx, uint32_t* N, uint32_t* L, uint32_t* 
 HE_API int he_sizes(const he_ctx* ctx, uint32_t m, uint32_t k, uint32_t n, const he_blocking* blk, he_size_info* out);
 
 /* Host-side: the blocking this library picks for a shape: powers of two with
- * m_b k_b n_b <= N minimising the algorithmic HBM bytes of he_matmul (weights
- * read once, input ciphertexts read and their NTT written and read back once,
- * output ciphertexts written once); ties go to the larger m_b, then k_b. */
-HE_API int he_default_blocking(const he_ctx* ctx, uint32_t m, uint32_t k, uint32_t n, he_blocking* out);
+ * m_b k_b n_b <= N (at most 4096 k-blocks) minimising a GB300 cost model of he_matmul:
+ * transform work (NTT of the input polynomials, inverse NTT of the outputs and, if
+ * weights_per_call is non-zero -- weights encoded on every call, e.g. the server's
+ * share in an attention product -- the NTT of the weights), multiply-accumulate
+ * work divided by its output-tile fill, and algorithmic HBM bytes.  Ties go to the
+ * larger m_b, then k_b. */
+HE_API int he_default_blocking(const he_ctx* ctx, uint32_t m, uint32_t k, uint32_t n, uint32_t weights_per_call,
+                               he_blocking* out);
 
 /* The same choice without a context (no GPU needed): N a power of two, L >= 1. */
-HE_API int he_choose_blocking(uint32_t N, uint32_t L, uint32_t m, uint32_t k, uint32_t n, he_blocking* out);
+HE_API int he_choose_blocking(uint32_t N, uint32_t L, uint32_t m, uint32_t k, uint32_t n, uint32_t weights_per_call,
+                              he_blocking* out);
 
 /* ---- test client (Sec. 2.2 BFV; encrypt/decrypt are the client's side) -- */
 

@@ -67,8 +67,8 @@ def _load():
         "he_ctx_free": (ctypes.c_int, [P]),
         "he_get_params": (ctypes.c_int, [P, pu32, pu32, pu32, pu64, pu64]),
         "he_sizes": (ctypes.c_int, [P, u32, u32, u32, pB, pS]),
-        "he_default_blocking": (ctypes.c_int, [P, u32, u32, u32, pB]),
-        "he_choose_blocking": (ctypes.c_int, [u32, u32, u32, u32, u32, pB]),
+        "he_default_blocking": (ctypes.c_int, [P, u32, u32, u32, u32, pB]),
+        "he_choose_blocking": (ctypes.c_int, [u32, u32, u32, u32, u32, u32, pB]),
         "he_keygen": (ctypes.c_int, [P, u64, P, P]),
         "he_encrypt": (ctypes.c_int, [P, P, P, u32, u64, P, P]),
         "he_decrypt": (ctypes.c_int, [P, P, P, u32, P, P, pi32, P]),
@@ -157,9 +157,9 @@ class Context:
         _check(lib.he_sizes(self.h, m, k, n, _blk(blk), ctypes.byref(si)))
         return si.as_dict()
 
-    def default_blocking(self, m, k, n):
+    def default_blocking(self, m, k, n, weights_per_call=False):
         b = Blocking()
-        _check(lib.he_default_blocking(self.h, m, k, n, ctypes.byref(b)))
+        _check(lib.he_default_blocking(self.h, m, k, n, 1 if weights_per_call else 0, ctypes.byref(b)))
         return b.as_tuple()
 
     # ---- allocation helpers (device memory comes from torch)
@@ -174,10 +174,10 @@ class Context:
         return t
 
 
-def he_choose_blocking(N, L, m, k, n):
+def he_choose_blocking(N, L, m, k, n, weights_per_call=False):
     """Host-only: the blocking the library picks for an (m x k) . (k x n) product."""
     b = Blocking()
-    _check(lib.he_choose_blocking(N, L, m, k, n, ctypes.byref(b)))
+    _check(lib.he_choose_blocking(N, L, m, k, n, 1 if weights_per_call else 0, ctypes.byref(b)))
     return b.as_tuple()
 
 

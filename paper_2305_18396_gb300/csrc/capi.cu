@@ -2,6 +2,7 @@
 // checking, context set-up (primes, roots, twiddle tables, constants), buffer
 // sizing, the default blocking, launch bookkeeping and event profiling.
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -351,28 +352,44 @@ int he_sizes(const he_ctx* c, uint32_t m, uint32_t k, uint32_t n, const he_block
   return HE_OK;
 }
 
-int he_choose_blocking(uint32_t Nw, uint32_t Lw, uint32_t m, uint32_t k, uint32_t n, he_blocking* out) {
+int he_choose_blocking(uint32_t Nw, uint32_t Lw, uint32_t m, uint32_t k, uint32_t n, uint32_t weights_per_call,
+                       he_blocking* out) {
   if (!out) return fail(HE_EINVAL, "NULL argument");
   if (!pow2(Nw) || Lw < 1) return fail(HE_EINVAL, "N must be a power of two and L >= 1");
-  const u64 N = Nw, L = Lw;
+  const double N = Nw, L = Lw;
+  // Cost model of one product on GB300 (seconds; constants measured with bench.py):
+  //   transforms: 45 ns per length-4096 residue polynomial (scaled by N log N), counting the
+  //     NTT of every input polynomial, the inverse NTT of every output polynomial and, when
+  //     the weights are encoded per call, the NTT of every weight polynomial;
+  //   multiply-accumulate: 0.8 ps per slot product, divided by the fill of the kernel's
+  //     8-row x 8-column output tiles;
+  //   memory: algorithmic bytes at 6.75 TB/s.
+  const double t_poly = 45e-9 * (N * std::log2(N)) / (4096.0 * 12.0);
+  const double t_slot = 0.8e-12, hbm = 6.75e12;
   auto cap = [&](u32 d) {
     u64 p = 1;
-    while (p < d && p < N) p <<= 1;
+    while (p < d && p < Nw) p <<= 1;
     return p;
   };
   const u64 cm = cap(m ? m : 1), ck = cap(k ? k : 1), cn = cap(n ? n : 1);
   double best = -1;
   he_blocking bb{1, 1, 1};
   for (u64 mb = 1; mb <= cm; mb <<= 1)
-    for (u64 kb = 1; kb <= ck && mb * kb <= N; kb <<= 1)
-      for (u64 nb = 1; nb <= cn && mb * kb * nb <= N; nb <<= 1) {
-        u64 nI = (n + nb - 1) / nb, nJ = (k + kb - 1) / kb, nLb = (m + mb - 1) / mb;
-        // pt read + input ct read + NTT'd inputs written and read + outputs written
-        double bytes = 8.0 * N * L * ((double)nI * nJ + 2.0 * nLb * nJ * 3 + 2.0 * nLb * nI);
-        bool better = best < 0 || bytes < best ||
-                      (bytes == best && (mb > bb.m_b || (mb == bb.m_b && kb > bb.k_b)));
+    for (u64 kb = 1; kb <= ck && mb * kb <= Nw; kb <<= 1)
+      for (u64 nb = 1; nb <= cn && mb * kb * nb <= Nw; nb <<= 1) {
+        const double nI = (double)((n + nb - 1) / nb), nJ = (double)((k + kb - 1) / kb),
+                     nLb = (double)((m + mb - 1) / mb);
+        if (nJ > 4096) continue;
+        const double pts = nI * nJ, in = nLb * nJ, outc = nLb * nI;
+        const double polys = 2 * L * in + 2 * L * outc + (weights_per_call ? L * pts : 0);
+        const double rows = 2 * nLb, fill = (rows / (8 * std::ceil(rows / 8))) * (nI / (8 * std::ceil(nI / 8)));
+        const double slots = nI * nJ * nLb * 2 * L * N;
+        const double bytes = 8 * N * L * (pts * (weights_per_call ? 3 : 1) + 6 * in + 4 * outc);
+        const double t = polys * t_poly + slots * t_slot / fill + bytes / hbm;
+        const bool better = best < 0 || t < best * (1 - 1e-9) ||
+                            (t <= best * (1 + 1e-9) && (mb > bb.m_b || (mb == bb.m_b && kb > bb.k_b)));
         if (better) {
-          best = bytes;
+          best = t;
           bb = {(u32)mb, (u32)kb, (u32)nb};
         }
       }
@@ -380,9 +397,10 @@ int he_choose_blocking(uint32_t Nw, uint32_t Lw, uint32_t m, uint32_t k, uint32_
   return HE_OK;
 }
 
-int he_default_blocking(const he_ctx* c, uint32_t m, uint32_t k, uint32_t n, he_blocking* out) {
+int he_default_blocking(const he_ctx* c, uint32_t m, uint32_t k, uint32_t n, uint32_t weights_per_call,
+                        he_blocking* out) {
   if (!c) return fail(HE_EINVAL, "ctx is NULL");
-  return he_choose_blocking(c->C.N, c->C.L, m, k, n, out);
+  return he_choose_blocking(c->C.N, c->C.L, m, k, n, weights_per_call, out);
 }
 
 int he_keygen(he_ctx* c, uint64_t seed, uint64_t* sk, void* stream) {

@@ -404,9 +404,10 @@ __host__ __device__ constexpr u64 chunked_index(u64 row, u32 J, u32 l, u32 s, u3
   return ((row * L + l) * (N >> 5) + (s >> 5)) * (u64)nJ * 32 + (u64)J * 32 + (s & 31);
 }
 
-template <int TM, int TN, int WR, int WC, int JB, int STAGES>
+template <int TM, int TN, int WR, int WC, int JB, int STAGES, int CPB = 1>
 struct MacCfg {
   static constexpr int kTM = TM, kTN = TN, kWR = WR, kWC = WC, kJB = JB, kStages = STAGES;
+  static constexpr int kChunksPerBlock = CPB;  // 32-slot chunks one block streams back to back
   static constexpr int kRows = TM * WR, kCols = TN * WC;
   static constexpr int kThreads = 32 * WR * WC;
   static constexpr int kStageWords = (kRows + kCols) * JB * 32;
@@ -420,12 +421,14 @@ __global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restri
   extern __shared__ __align__(128) u64 sm[];
   __shared__ __align__(8) uint64_t bars[M::kStages];
   __shared__ int abort_flag;
-  constexpr int TM = M::kTM, TN = M::kTN, JB = M::kJB, ST = M::kStages;
+  constexpr int TM = M::kTM, TN = M::kTN, JB = M::kJB, ST = M::kStages, CPB = M::kChunksPerBlock;
 
   const u32 N = C.N, L = C.L;
   const u32 chunks = N >> 5;
-  const u32 chunk = blockIdx.x % chunks;
-  const u32 tile = blockIdx.x / chunks;
+  const u32 groups = (chunks + CPB - 1) / CPB;
+  const u32 chunk0 = (blockIdx.x % groups) * CPB;
+  const u32 nch = min((u32)CPB, chunks - chunk0);
+  const u32 tile = blockIdx.x / groups;
   const u32 r0 = (tile % tilesR) * M::kRows, c0 = (tile / tilesR) * M::kCols;
   const u32 l = blockIdx.y % L;
   const u64 item = blockIdx.y / L;  // batch item
@@ -435,7 +438,8 @@ __global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restri
   const PrimeConsts& P = C.p[l];
   const u32 rows = 2 * nLb;
   const u32 nrows = min((u32)M::kRows, rows - r0), ncols = min((u32)M::kCols, nI - c0);
-  const u32 nstages = (nJ + JB - 1) / JB;
+  const u32 nsp = (nJ + JB - 1) / JB;  // stages per chunk
+  const u32 nstages = nch * nsp;
   const u32 warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const u32 wr = warp % M::kWR, wc = warp / M::kWR;
 
@@ -446,8 +450,10 @@ __global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restri
   }
   __syncthreads();
 
-  // warp 0: stream k-blocks [JB k, JB k + jb) of every operand row of the tile into stage st
-  auto issue = [&](u32 k, u32 st) {
+  // warp 0: stream k-blocks [JB k, JB k + jb) of chunk chunk0 + i / nsp (k = i % nsp) of
+  // every operand row of the tile into stage st
+  auto issue = [&](u32 i, u32 st) {
+    const u32 chunk = chunk0 + i / nsp, k = i % nsp;
     const u32 J0 = k * JB, jb = min((u32)JB, nJ - J0);
     const u32 bytes = jb * 32 * sizeof(u64);
     if (lane == 0) {
@@ -456,17 +462,17 @@ __global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restri
     }
     __syncwarp();
     u64* stage = sm + st * M::kStageWords;
-    for (u32 i = lane; i < nrows + ncols; i += 32) {
-      const bool is_row = i < nrows;
-      const u64* src = is_row ? ctN + chunked_index(r0 + i, J0, l, chunk << 5, nJ, L, N)
-                              : pt + chunked_index(c0 + (i - nrows), J0, l, chunk << 5, nJ, L, N);
-      u64* dst = stage + (is_row ? i : M::kRows + (i - nrows)) * (JB * 32);
+    for (u32 t = lane; t < nrows + ncols; t += 32) {
+      const bool is_row = t < nrows;
+      const u64* src = is_row ? ctN + chunked_index(r0 + t, J0, l, chunk << 5, nJ, L, N)
+                              : pt + chunked_index(c0 + (t - nrows), J0, l, chunk << 5, nJ, L, N);
+      u64* dst = stage + (is_row ? t : M::kRows + (t - nrows)) * (JB * 32);
       bulk_copy_g2s(dst, src, bytes, &bars[st]);
     }
   };
 
   if (warp == 0)
-    for (u32 k = 0; k < (u32)ST && k < nstages; ++k) issue(k, k);
+    for (u32 i = 0; i < (u32)ST && i < nstages; ++i) issue(i, i);
 
   u64 lo[TM][TN], mid[TM][TN], hi[TM][TN];
 #pragma unroll
@@ -474,20 +480,21 @@ __global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restri
 #pragma unroll
     for (int b = 0; b < TN; ++b) lo[a][b] = mid[a][b] = hi[a][b] = 0;
 
-  for (u32 k = 0; k < nstages; ++k) {
-    const u32 st = k % ST;
+  for (u32 i = 0; i < nstages; ++i) {
+    const u32 st = i % ST;
     if (threadIdx.x == 0) {
-      if (!mbar_wait_bounded(&bars[st], (k / ST) & 1, kWaitLimitNs)) {
+      if (!mbar_wait_bounded(&bars[st], (i / ST) & 1, kWaitLimitNs)) {
         abort_flag = 1;
         atomicExch(err, 1);
         // let every other copy this block issued land (bounded) before the block exits
-        for (u32 k2 = k + 1; k2 < nstages && k2 < k + ST; ++k2)
-          mbar_wait_bounded(&bars[k2 % ST], (k2 / ST) & 1, kWaitLimitNs);
+        for (u32 i2 = i + 1; i2 < nstages && i2 < i + ST; ++i2)
+          mbar_wait_bounded(&bars[i2 % ST], (i2 / ST) & 1, kWaitLimitNs);
       }
     }
     __syncthreads();
     if (abort_flag) return;
     const u64* stage = sm + st * M::kStageWords;
+    const u32 k = i % nsp;
     const u32 jb = min((u32)JB, nJ - k * JB);
     const u64* prow = stage + (M::kRows + wc * TN) * (JB * 32) + lane;  // this thread's column operands
     const u64* crow = stage + (wr * TM) * (JB * 32) + lane;             // this thread's row operands
@@ -514,31 +521,33 @@ __global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restri
     } else {
       for (u32 jj = 0; jj < jb; ++jj) kblock(jj);
     }
-    __syncthreads();
-    if (warp == 0 && k + ST < nstages) issue(k + ST, st);
-  }
-
-  const u32 s = (chunk << 5) + lane;
+    if (k == nsp - 1) {  // chunk complete: reduce, store, restart the accumulators
+      const u32 s = ((chunk0 + i / nsp) << 5) + lane;
 #pragma unroll
-  for (int a = 0; a < TM; ++a) {
-    const u32 r = r0 + wr * TM + a;
-    if (r >= rows) continue;
+      for (int a = 0; a < TM; ++a) {
+        const u32 r = r0 + wr * TM + a;
 #pragma unroll
-    for (int b = 0; b < TN; ++b) {
-      const u32 I = c0 + wc * TN + b;
-      if (I >= nI) continue;
-      const u64 cross = mid[a][b] - lo[a][b] - hi[a][b];  // sum of x0 y1 + x1 y0
-      u64 v = reduce_word(lo[a][b], P);
-      v = add_mod(v, csub(mul_shoup(cross, P.r25, P.r25_sh, P.q), P.q), P.q);
-      v = add_mod(v, csub(mul_shoup(hi[a][b], P.r50, P.r50_sh, P.q), P.q), P.q);
-      const u32 c = r & 1;
-      out.base[c][(ct0 + (u64)(r >> 1) * nI + I) * out.ct_stride[c] + (u64)l * N + s] = v;
+        for (int b = 0; b < TN; ++b) {
+          const u32 I = c0 + wc * TN + b;
+          if (r < rows && I < nI) {
+            const u64 cross = mid[a][b] - lo[a][b] - hi[a][b];  // sum of x0 y1 + x1 y0
+            u64 v = reduce_word(lo[a][b], P);
+            v = add_mod(v, csub(mul_shoup(cross, P.r25, P.r25_sh, P.q), P.q), P.q);
+            v = add_mod(v, csub(mul_shoup(hi[a][b], P.r50, P.r50_sh, P.q), P.q), P.q);
+            const u32 c = r & 1;
+            out.base[c][(ct0 + (u64)(r >> 1) * nI + I) * out.ct_stride[c] + (u64)l * N + s] = v;
+          }
+          lo[a][b] = mid[a][b] = hi[a][b] = 0;
+        }
+      }
     }
+    __syncthreads();
+    if (warp == 0 && i + ST < nstages) issue(i + ST, st);
   }
 }
 
 // The configuration the library launches.
-using MacProd = MacCfg<4, 2, 2, 4, 8, 2>;
+using MacProd = MacCfg<4, 2, 2, 4, 8, 2, 1>;
 constexpr int kMacMinBlocks = 2;
 
 // Forward NTT of the input ciphertexts of a product into the slot-chunked operand layout.
@@ -822,7 +831,8 @@ cudaError_t launch_mac_cfg(const Consts& C, const u64* ctN, const u64* pt, OutPl
                            u32 batch, int* err, cudaStream_t st) {
   const u32 tilesR = (2 * nLb + M::kRows - 1) / M::kRows, tilesC = (nI + M::kCols - 1) / M::kCols;
   if ((u64)tilesR * tilesC * nJ * batch == 0) return cudaGetLastError();
-  dim3 grid((unsigned)((u64)(C.N >> 5) * tilesR * tilesC), C.L * batch);
+  const u64 groups = ((C.N >> 5) + M::kChunksPerBlock - 1) / M::kChunksPerBlock;
+  dim3 grid((unsigned)(groups * tilesR * tilesC), C.L * batch);
   k_mac_t<M, MINB><<<grid, M::kThreads, M::kSmemBytes, st>>>(ctN, pt, out, nI, nJ, nLb, tilesR, err, C);
   return cudaGetLastError();
 }

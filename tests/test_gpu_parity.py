@@ -254,7 +254,7 @@ def test_bert_base_layer_products_sampled(B, prod):
     N, L = 4096, 2
     ctx, P = ctx_for(B, N, L)
     m, k, n = prod.m, prod.k, prod.n
-    blk = ctx.default_blocking(m, k, n)
+    blk = ctx.default_blocking(m, k, n, prod.share_weights)
     X = S.uniform_share((m, k), S.SEED_X)
     W = S.uniform_share((k, n), S.SEED_W) if prod.share_weights else S.fixed_point_weights((k, n), S.SEED_W)
     s = O.keygen(P, S.SEED_KEY)
