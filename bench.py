@@ -36,7 +36,7 @@ WORKLOAD = "bert-base layer linear products, seq 128 (QKV, attn-out, FFN1, FFN2 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -94,7 +94,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
                  "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (FileNotFoundError, OSError):
             self.proc = None
@@ -271,7 +271,7 @@ def oracle_sample(kind="baseline"):
     heads = [p for p in prods if p.share_weights]
     heads = heads + [heads[0]]  # qk_x1 has the shape of qk_x0
     if kind == "baseline":
-        heads = heads + [p for p in prods if p.name == "attn_out"]
+        heads = heads + [p for p in prods if p.name in ("attn_out", "qkv")]
     P = O.Params(N_POLY, L_PRIMES)
     s = O.keygen(P, S.SEED_KEY)
     jobs = []
@@ -298,7 +298,7 @@ def cpu_baseline():
     macs, dt = run_oracle(P, jobs, O, 12345)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": macs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one head's 4 attention cross products + the attn-out product ({macs} plain MACs, "
+            "sample": f"one head's 4 attention cross products + the QKV and attn-out products ({macs} plain MACs, "
                       f"{dt:.1f} s), full Pi_MatMul (encode, NTT, MAC, INTT, mask) on the host cores"}
 
 
@@ -345,6 +345,7 @@ def gpu_arm(args, world, rank, local):
     layer = Layer(B, ctx, prods, rank, want_host, flags)
     stream = torch.cuda.current_stream()
 
+    mad_peak, mad_per_sm_clk = B.he_probe_mad_wide(ctx)
     for w in range(max(args.warmup, 3) if args.warmup else 0):
         layer.step(w)
     torch.cuda.synchronize()
@@ -373,14 +374,14 @@ def gpu_arm(args, world, rank, local):
 
     # roofline: per-kernel event timing (separate pass, same steps)
     B.he_profile_enable(ctx, True)
-    for k in range(max(3, min(args.steps, 10))):
+    steps_prof = max(3, min(args.steps, 10))
+    for k in range(steps_prof):
         layer.step(5000 + k)
     stats = B.he_profile_read(ctx)
     B.he_profile_enable(ctx, False)
     alg = layer.algorithmic_bytes()
     pk, pk_src = peaks()
     dom = max(stats, key=lambda k: stats[k]["total_ms"])
-    steps_prof = max(3, min(args.steps, 10))
     total_prof_ms = sum(v["total_ms"] for v in stats.values())
     kern = {}
     for name, v in stats.items():
@@ -388,14 +389,28 @@ def gpu_arm(args, world, rank, local):
         kern[name] = {"launches": v["launches"], "ms": round(v["total_ms"], 3),
                       "share": round(v["total_ms"] / total_prof_ms, 4),
                       "gbs": round(b / (v["total_ms"] / 1e3) / 1e9, 1) if b else None}
-    achieved = alg.get(dom, 0) * steps_prof / stats[dom]["launches"] / (stats[dom]["total_ms"] / stats[dom]["launches"] / 1e3) / 1e9
+    per_launch_s = stats[dom]["total_ms"] / stats[dom]["launches"] / 1e3
     launches_per_step = stats[dom]["launches"] / steps_prof
-    traffic = recorded_traffic(dom)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / pk["hbm_gbs"], 4), "peak_source": pk_src,
-                "algorithmic_bytes_per_launch": alg.get(dom, 0) / launches_per_step,
-                "traffic": traffic, "kernels": kern,
-                "slot_macs_per_s": layer.slot_macs() * steps_prof / (stats["mac"]["total_ms"] / 1e3) if "mac" in stats else None}
+    bytes_per_launch = alg.get(dom, 0) / launches_per_step
+    hbm_gbs = bytes_per_launch / per_launch_s / 1e9
+    if dom == "mac":
+        # integer-pipe bound: three mad.wide.u32 per slot product (Karatsuba), peak measured by
+        # he_probe_mad_wide on this GPU (per-SM rate x SMs x clock)
+        ops_per_launch = 3 * layer.slot_macs() / launches_per_step
+        achieved = ops_per_launch / per_launch_s
+        roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved / 1e12, 3),
+                    "peak": round(mad_peak / 1e12, 3), "unit": "T mad.wide.u32/s", "frac": round(achieved / mad_peak, 4),
+                    "peak_source": f"measured: he_probe_mad_wide, {mad_per_sm_clk:.1f} per SM per clock",
+                    "ops_per_launch": ops_per_launch,
+                    "hbm": {"achieved": round(hbm_gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                            "frac": round(hbm_gbs / pk["hbm_gbs"], 4), "peak_source": pk_src}}
+    else:
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(hbm_gbs, 1), "peak": pk["hbm_gbs"],
+                    "unit": "GB/s", "frac": round(hbm_gbs / pk["hbm_gbs"], 4), "peak_source": pk_src}
+    roofline.update({"algorithmic_bytes_per_launch": bytes_per_launch, "traffic": recorded_traffic(dom),
+                     "kernels": kern,
+                     "slot_macs_per_s": layer.slot_macs() * steps_prof / (stats["mac"]["total_ms"] / 1e3)
+                     if "mac" in stats else None})
 
     # end to end: host buffers through he_matmul_host (H2D + compute + D2H inside the region)
     e2e = None
@@ -431,7 +446,7 @@ def gpu_arm(args, world, rank, local):
                    "plain_macs_per_step": layer.macs,
                    "output": "full ciphertexts" if args.full_c0 else
                    "c1 + c0 at the decoded coefficients only (Sec. 3.1.3, HE_DROP_C0)",
-                   "blockings_mkn": blks, "parallelism": f"replicas x{world} (independent layers, no collective)",
+                   "blockings_mkn": blks, "kernel_source_hash": kernel_source_hash(), "parallelism": f"replicas x{world} (independent layers, no collective)",
                    "l2": "inputs larger than L2: one step reads/writes ~3 GB of ciphertexts/weights"},
         "latency_ms": {"p50": statistics.median(per), "p99": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))]},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

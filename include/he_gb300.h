@@ -255,6 +255,12 @@ HE_API int he_ntt_inverse(he_ctx* ctx, uint64_t* polys, uint32_t cnt, void* stre
  * (NTT, slot-wise product, inverse NTT; footnote of Sec. 3.1.3).  c may alias a. */
 HE_API int he_poly_mul(he_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t* c, uint32_t cnt, void* stream);
 
+/* Failure-detection check: launches one kernel whose bounded wait (the same one the
+ * multiply-accumulate uses for its data copies) waits on a barrier nothing completes,
+ * gives up after limit_ms (1..2000) and records the error; he_device_status then
+ * returns HE_ETIMEOUT.  The context stays usable. */
+HE_API int he_test_wait_timeout(he_ctx* ctx, uint32_t limit_ms, void* stream);
+
 /* Host-side copy of the library's Gaussian inversion table (2 * 19 words). */
 HE_API int he_gauss_cdt(uint64_t* out, uint32_t cap);
 
@@ -275,6 +281,14 @@ HE_API int he_profile_read(he_ctx* ctx, he_kernel_stat* out, uint32_t cap, uint3
  * HE_ETIMEOUT if so (the flag is then cleared; the affected outputs are invalid),
  * HE_OK otherwise. */
 HE_API int he_device_status(he_ctx* ctx, void* stream);
+
+/* Integer roofline probe: times dependency-free chains of mad.wide.u32 (the
+ * instruction the multiply-accumulate kernel is built on) over every SM and returns
+ * the achieved rate (operations/s) and, optionally, per SM per (maximum) clock.
+ * scratch: device, >= (number of SMs) x 2048 words.  Synchronizes the stream.  Not
+ * part of the protocol: it supplies the peak for roofline reporting. */
+HE_API int he_probe_mad_wide(he_ctx* ctx, uint64_t* scratch, size_t scratch_words, double* ops_per_s,
+                             double* per_sm_per_clock, void* stream);
 
 /* Number of kernels this context has launched since creation. */
 HE_API int he_launch_count(const he_ctx* ctx, uint64_t* out);

@@ -90,6 +90,8 @@ def _load():
         "he_profile_read": (ctypes.c_int, [P, ctypes.POINTER(KernelStat), u32, pu32]),
         "he_launch_count": (ctypes.c_int, [P, pu64]),
         "he_device_status": (ctypes.c_int, [P, P]),
+        "he_test_wait_timeout": (ctypes.c_int, [P, u32, P]),
+        "he_probe_mad_wide": (ctypes.c_int, [P, P, sz, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(so, name)
@@ -373,6 +375,20 @@ def he_profile_read(ctx):
 def he_device_status(ctx, stream=None):
     """Raises HEError(HE_ETIMEOUT) if a kernel's bounded wait expired since the last check."""
     _check(lib.he_device_status(ctx.h, _stream(stream)))
+
+
+def he_test_wait_timeout(ctx, limit_ms=100, stream=None):
+    _check(lib.he_test_wait_timeout(ctx.h, limit_ms, _stream(stream)))
+
+
+def he_probe_mad_wide(ctx, stream=None):
+    """(mad.wide.u32 operations/s, per SM per clock) measured on the context's GPU."""
+    sms = torch.cuda.get_device_properties(ctx.device).multi_processor_count
+    scratch = ctx.empty(sms * 2048)
+    ops, per = ctypes.c_double(), ctypes.c_double()
+    _check(lib.he_probe_mad_wide(ctx.h, _ptr(scratch), scratch.numel(), ctypes.byref(ops), ctypes.byref(per),
+                                 _stream(stream)))
+    return ops.value, per.value
 
 
 def he_launch_count(ctx):

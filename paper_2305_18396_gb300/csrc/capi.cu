@@ -119,11 +119,11 @@ struct ProfRec {
 
 enum Kind {
   KNttFwd, KNttInv, KPolyMul, KKeygen, KEncrypt, KDecrypt, KPack, KUnpack, KUnmask, KEncode, KMac, KInttMask, KInttC0,
-  KExpand, KCount
+  KExpand, KProbe, KCount
 };
 static const char* kKindNames[KCount] = {"ntt_forward", "ntt_inverse", "poly_mul", "keygen", "encrypt",
                                          "decrypt", "pack", "unpack", "unmask", "encode_weights",
-                                         "mac", "intt_mask", "intt_c0_targets", "expand_compact"};
+                                         "mac", "intt_mask", "intt_c0_targets", "expand_compact", "probe"};
 
 struct he_ctx {
   int device = 0;
@@ -731,6 +731,33 @@ int he_device_status(he_ctx* c, void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "device status readback");
   return flag ? fail(HE_ETIMEOUT, "a kernel's bounded wait for its data expired; results of that call are invalid")
               : HE_OK;
+}
+
+int he_probe_mad_wide(he_ctx* c, uint64_t* scratch, size_t scratch_words, double* ops_per_s, double* per_sm_per_clock,
+                      void* stream) {
+  if (!c || !scratch || !ops_per_s) return fail(HE_EINVAL, "NULL argument");
+  if (int r = set_device(c)) return r;
+  int sms = 0, clk_khz = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, c->device);
+  if ((u64)sms * 8 * 256 > scratch_words) return fail(HE_EINVAL, "scratch needs SMs x 2048 words");
+  float ms = 0;
+  cudaError_t e = he::probe_mad_wide(sms, scratch, &ms, (cudaStream_t)stream);
+  c->launches.fetch_add(2, std::memory_order_relaxed);
+  if (e != cudaSuccess) return cuda_fail(e, "probe_mad_wide");
+  const double ops = (double)sms * 8 * 256 * 2048 * 64;
+  *ops_per_s = ops / (ms * 1e-3);
+  if (per_sm_per_clock) *per_sm_per_clock = *ops_per_s / sms / (clk_khz * 1e3);
+  return HE_OK;
+}
+
+int he_test_wait_timeout(he_ctx* c, uint32_t limit_ms, void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (!limit_ms || limit_ms > 2000) return fail(HE_EINVAL, "limit_ms must be in [1, 2000]");
+  if (int r = set_device(c)) return r;
+  return launch(c, KProbe, (cudaStream_t)stream, "wait timeout check", [&] {
+    return he::launch_wait_timeout_check((uint64_t)limit_ms * 1000000ull, c->d_err, (cudaStream_t)stream);
+  });
 }
 
 int he_launch_count(const he_ctx* c, uint64_t* out) {

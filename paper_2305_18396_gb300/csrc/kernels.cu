@@ -920,3 +920,67 @@ cudaError_t launch_expand_compact(const Consts& C, const u64* src, u64 cnt, u32 
 }
 
 }  // namespace he
+
+namespace he {
+
+// Integer roofline probe: independent mad.wide.u32 chains (16 accumulators per thread,
+// operands fixed per thread), the instruction the multiply-accumulate kernel is built on.
+__global__ void __launch_bounds__(256) k_probe_mad_wide(u32 seed, int iters, u64* out) {
+  u32 a[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = (seed ^ (threadIdx.x * 2654435761u)) + 977u * i;
+  const u32 b = seed | 1u;
+  u64 acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int i = 0; i < 16; ++i) asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[i]) : "r"(a[i]), "r"(b));
+  }
+  u64 x = 0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) x ^= acc[i];
+  out[(u64)blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+
+cudaError_t probe_mad_wide(int sms, u64* out, float* ms, cudaStream_t st) {
+  const int blocks = sms * 8, iters = 2048;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return e;
+  k_probe_mad_wide<<<blocks, 256, 0, st>>>(7u, 16, out);  // warm-up
+  cudaEventRecord(e0, st);
+  k_probe_mad_wide<<<blocks, 256, 0, st>>>(7u, iters, out);
+  cudaEventRecord(e1, st);
+  e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
+}
+
+}  // namespace he
+
+namespace he {
+
+// Failure-detection check: one thread waits, with the library's bounded wait, on an
+// mbarrier that nothing arrives on; when the limit expires it records the error flag the
+// host reads through he_device_status.  No copy is in flight and nothing else waits.
+__global__ void k_wait_timeout_check(uint64_t limit_ns, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  mbar_init_fence();
+  if (!mbar_wait_bounded(&bar, 0, limit_ns)) atomicExch(err, 1);
+}
+
+cudaError_t launch_wait_timeout_check(uint64_t limit_ns, int* err, cudaStream_t st) {
+  k_wait_timeout_check<<<1, 32, 0, st>>>(limit_ns, err);
+  return cudaGetLastError();
+}
+
+}  // namespace he

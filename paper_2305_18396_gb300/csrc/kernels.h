@@ -53,6 +53,13 @@ cudaError_t launch_intt_c0_targets(const Consts& C, const u64* src, u64* dst, u6
 // (batch item b uses seed + b).
 cudaError_t launch_intt_mask(const Consts& C, u64* out, u64 out_cts, u32 batch, u64 seed, cudaStream_t st);
 
+// Integer roofline probe: times sms * 8 blocks of 256 threads, each 2048 x 64 mad.wide.u32
+// (`out`: sms * 8 * 256 words of scratch).
+cudaError_t probe_mad_wide(int sms, u64* out, float* ms, cudaStream_t st);
+
+// Runs one bounded wait on an mbarrier nothing completes (limit_ns), setting *err on expiry.
+cudaError_t launch_wait_timeout_check(uint64_t limit_ns, int* err, cudaStream_t st);
+
 // Fixed device scratch of he_matmul_noalloc (no allocation at call time).
 constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
 constexpr int kMaxDevices = 64;

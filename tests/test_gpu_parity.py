@@ -346,3 +346,22 @@ def test_matmul_compact_c0(B, N, L, m, k, n, blk, batch):
         client = to_np(B.he_unpack_output(ctx, dec, m, n, blk), (m, n))
         server = to_np(B.he_unmask(ctx, 700 + b, m, n, blk), (m, n))
         assert np.array_equal((client + server) % np.uint64(P.t), O.plain_matmul_mod_t(Xs[b], Ws[b], P.t))
+
+
+# ------------------------------------------------------------------ failure detection
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(B):
+    """A kernel wait that can never complete gives up after its limit, the host reads
+    HE_ETIMEOUT through he_device_status, the flag clears, and the context keeps working."""
+    ctx, P = ctx_for(B, 4096, 2)
+    B.he_device_status(ctx)  # clean
+    B.he_test_wait_timeout(ctx, 50)
+    with pytest.raises(B.HEError) as e:
+        B.he_device_status(ctx)
+    assert e.value.code == B.HE_ETIMEOUT
+    B.he_device_status(ctx)  # cleared
+    X = S.uniform_share((16, 64), S.SEED_X)
+    W = S.fixed_point_weights((64, 64), S.SEED_W)
+    _run_case(B, 4096, 2, 16, 64, 64, (8, 32, 16), W, X)
+    B.he_device_status(ctx)
