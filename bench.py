@@ -228,10 +228,7 @@ def kernel_source_hash():
     """Fingerprint of the multiply-accumulate kernel's source: its configuration, body and the
     headers it includes (a DRAM-traffic figure recorded for an older fingerprint is stale)."""
     csrc = ROOT / "paper_2305_18396_gb300" / "csrc"
-    k = (csrc / "kernels.cu").read_text()
-    a = k.index("template <int TM, int TN, int WR, int WC, int JB, int STAGES")
-    b = k.index("constexpr int kMacMinBlocks")
-    h = hashlib.sha256(k[a:b].encode())
+    h = hashlib.sha256((csrc / "mac.cuh").read_bytes())
     for f in ("async.cuh", "he_common.cuh"):
         h.update((csrc / f).read_bytes())
     return h.hexdigest()[:16]

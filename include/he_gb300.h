@@ -209,6 +209,26 @@ HE_API int he_matmul_batch(he_ctx* ctx, const uint64_t* ct_in, const uint64_t* p
                            const he_blocking* blk, uint32_t batch, uint64_t mask_seed, uint32_t flags,
                            uint64_t* ct_out, void* workspace, size_t workspace_bytes, void* stream);
 
+/* One product of a multi-product launch. */
+typedef struct {
+  const uint64_t* ct_in; /* device, in_words                                   */
+  const uint64_t* pt;    /* device, from he_encode_weights with this k, n, blk  */
+  uint64_t* ct_out;      /* device, out_words (out_words_compact with DROP_C0)  */
+  uint32_t m, k, n;
+  he_blocking blk;
+  uint32_t flags;        /* HE_FLAGS_NONE or HE_DROP_C0                          */
+  uint64_t mask_seed;
+} he_product;
+
+/* Up to 64 products of any shapes, blockings and output modes (e.g. the requests a
+ * serving loop has admitted) in one set of launches: one forward-NTT grid, one
+ * multiply-accumulate grid and one or two inverse-NTT grids over the union of the
+ * products' work.  Each product's output is bit-identical to its own he_matmul call.
+ * workspace: device, >= he_multi_workspace_bytes(ctx, count, items). */
+HE_API int he_matmul_multi(he_ctx* ctx, uint32_t count, const he_product* items, void* workspace,
+                           size_t workspace_bytes, void* stream);
+HE_API int he_multi_workspace_bytes(const he_ctx* ctx, uint32_t count, const he_product* items, size_t* bytes);
+
 /* he_matmul for callers that cannot allocate device memory.  Some callers have no
  * way to obtain a workspace: a serving process whose device memory is already
  * reserved by another allocator (where cudaMalloc would fail, or would stall the

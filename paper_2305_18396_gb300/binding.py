@@ -46,6 +46,12 @@ class SizeInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class Product(ctypes.Structure):
+    _fields_ = [("ct_in", ctypes.c_void_p), ("pt", ctypes.c_void_p), ("ct_out", ctypes.c_void_p),
+                ("m", ctypes.c_uint32), ("k", ctypes.c_uint32), ("n", ctypes.c_uint32), ("blk", Blocking),
+                ("flags", ctypes.c_uint32), ("mask_seed", ctypes.c_uint64)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
@@ -79,6 +85,8 @@ def _load():
         "he_matmul_host": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u64, u32, P, P, sz, P]),
         "he_matmul_noalloc": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u64, u32, P, P]),
         "he_matmul_batch": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u32, u64, u32, P, P, sz, P]),
+        "he_matmul_multi": (ctypes.c_int, [P, u32, ctypes.POINTER(Product), P, sz, P]),
+        "he_multi_workspace_bytes": (ctypes.c_int, [P, u32, ctypes.POINTER(Product), ctypes.POINTER(sz)]),
         "he_encode_weights_batch": (ctypes.c_int, [P, P, u32, u32, pB, u32, P, P]),
         "he_unmask": (ctypes.c_int, [P, u64, u32, u32, pB, P, P]),
         "he_expand_compact": (ctypes.c_int, [P, P, u32, u32, P, P]),
@@ -268,6 +276,29 @@ def he_matmul_batch(ctx, ct_in, pt, m, k, n, blk, batch, mask_seed, ct_out=None,
     _check(lib.he_matmul_batch(ctx.h, _ptr(ct_in), _ptr(pt), m, k, n, _blk(blk), batch, mask_seed, flags,
                                _ptr(ct_out), _ptr(workspace), workspace.numel() * 8, _stream(stream)))
     return ct_out
+
+
+def make_products(items):
+    """items: dicts with ct_in, pt, ct_out (device tensors), m, k, n, blk, flags, mask_seed."""
+    arr = (Product * len(items))()
+    for a, x in zip(arr, items):
+        a.ct_in, a.pt, a.ct_out = x["ct_in"].data_ptr(), x["pt"].data_ptr(), x["ct_out"].data_ptr()
+        a.m, a.k, a.n = x["m"], x["k"], x["n"]
+        a.blk = Blocking(*x["blk"])
+        a.flags, a.mask_seed = x.get("flags", HE_FLAGS_NONE), x["mask_seed"]
+    return arr
+
+
+def he_multi_workspace_bytes(ctx, products):
+    out = ctypes.c_size_t()
+    _check(lib.he_multi_workspace_bytes(ctx.h, len(products), products, ctypes.byref(out)))
+    return out.value
+
+
+def he_matmul_multi(ctx, products, workspace, stream=None):
+    """products: from make_products (keeps the descriptor array alive for the call)."""
+    _check(lib.he_matmul_multi(ctx.h, len(products), products, _ptr(workspace), workspace.numel() * 8,
+                               _stream(stream)))
 
 
 def he_matmul(ctx, ct_in, pt, m, k, n, blk, mask_seed, ct_out=None, workspace=None, flags=HE_FLAGS_NONE,

@@ -1,6 +1,7 @@
 // capi.cu -- the extern "C" boundary declared in include/he_gb300.h: argument
 // checking, context set-up (primes, roots, twiddle tables, constants), buffer
 // sizing, the default blocking, launch bookkeeping and event profiling.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -11,6 +12,7 @@
 
 #include "../../include/he_gb300.h"
 #include "kernels.h"
+#include "multi.h"
 
 using he::u32;
 using he::u64;
@@ -286,6 +288,7 @@ int he_params_init(he_ctx** out, uint32_t N, uint32_t L, const uint64_t* q, uint
   e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(c->d_tables, host.data(), host.size() * sizeof(u64), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = he::configure_kernels(C);
+  if (e == cudaSuccess) e = he::configure_multi_kernels();
   if (e != cudaSuccess) {
     cudaFree(c->d_tables);
     cudaFree(c->d_err);
@@ -622,6 +625,103 @@ int he_matmul_noalloc(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint
   cudaError_t e = he::noalloc_scratch_address(c->device, &scratch);
   if (e != cudaSuccess) return cuda_fail(e, "matmul_noalloc: scratch address");
   return matmul_device(c, ct_in, pt, m, k, n, blk, 1, mask_seed, flags, ct_out, scratch, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- multi-product launch
+
+namespace {
+
+struct MultiPlan {
+  he::MultiTable T;
+  u64 fwd = 0, mac = 0, inv = 0, c0 = 0, ws_bytes = 0;
+  u32 max_nc = 0;
+};
+
+// Validates the products and lays out the table; workspace may be NULL (size query).
+int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* workspace, MultiPlan* P) {
+  if (count > (u32)he::kMaxMulti) return fail(HE_EINVAL, "at most 64 products per multi-product launch");
+  if (count && !items) return fail(HE_EINVAL, "items is NULL");
+  const u64 N = c->C.N, L = c->C.L;
+  const u32 rows_t = he::mac_tile_rows(), cols_t = he::mac_tile_cols();
+  P->T.count = 0;
+  u64 off = 0;
+  for (u32 i = 0; i < count; ++i) {
+    const he_product& x = items[i];
+    if (int r = check_blk(c, &x.blk)) return r;
+    if (x.flags & ~(uint32_t)HE_DROP_C0) return fail(HE_EINVAL, "unknown flags");
+    const bool compact = x.flags & HE_DROP_C0;
+    if (compact && !pow2(x.blk.k_b)) return fail(HE_EINVAL, "HE_DROP_C0 needs a power-of-two k_b");
+    if (!x.m || !x.k || !x.n) continue;
+    if (!x.ct_in || !x.pt || !x.ct_out) return fail(HE_EINVAL, "NULL buffer in a product");
+    Shape s = shape_of(x.m, x.k, x.n, &x.blk);
+    if (s.nJ > 4096) return fail(HE_EINVAL, "at most 4096 k-blocks per product");
+    he::MultiItem& it = P->T.it[P->T.count++];
+    memset(&it, 0, sizeof(it));
+    it.ct_in = x.ct_in;
+    it.pt = x.pt;
+    it.out = x.ct_out;
+    it.mask_seed = x.mask_seed;
+    it.nI = s.nI;
+    it.nJ = s.nJ;
+    it.nLb = s.nLb;
+    it.compact = compact;
+    it.logkb = compact ? log2u(x.blk.k_b) : 0;
+    it.tilesR = (2 * s.nLb + rows_t - 1) / rows_t;
+    it.tilesC = (s.nI + cols_t - 1) / cols_t;
+    const u64 in_words = (u64)s.nLb * s.nJ * 2 * L * N, out_cts = (u64)s.nLb * s.nI;
+    off = (off + 255) & ~(u64)255;
+    it.ctN = workspace ? (u64*)(workspace + off) : nullptr;
+    off += in_words * 8;
+    if (compact) {
+      off = (off + 255) & ~(u64)255;
+      it.c0_ntt = workspace ? (u64*)(workspace + off) : nullptr;
+      off += out_cts * L * N * 8;
+      P->max_nc = std::max<u32>(P->max_nc, (u32)(N >> it.logkb));
+    }
+    it.fwd_begin = P->fwd;
+    it.mac_begin = P->mac;
+    it.inv_begin = P->inv;
+    it.c0_begin = P->c0;
+    P->fwd += (u64)s.nLb * s.nJ * 2 * L;
+    P->mac += (N >> 5) * it.tilesR * it.tilesC * L;
+    P->inv += out_cts * (compact ? 1 : 2) * L;
+    P->c0 += compact ? out_cts * L : 0;
+  }
+  P->ws_bytes = off;
+  if (P->fwd >= (1ull << 31) || P->mac >= (1ull << 31) || P->inv >= (1ull << 31))
+    return fail(HE_EINVAL, "multi-product launch too large");
+  return HE_OK;
+}
+
+}  // namespace
+
+int he_multi_workspace_bytes(const he_ctx* c, uint32_t count, const he_product* items, size_t* bytes) {
+  if (!c || !bytes) return fail(HE_EINVAL, "NULL argument");
+  MultiPlan P;
+  if (int r = plan_multi(c, count, items, nullptr, &P)) return r;
+  *bytes = P.ws_bytes;
+  return HE_OK;
+}
+
+int he_matmul_multi(he_ctx* c, uint32_t count, const he_product* items, void* workspace, size_t workspace_bytes,
+                    void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  MultiPlan P;
+  if (int r = plan_multi(c, count, items, (char*)workspace, &P)) return r;
+  if (!P.T.count) return HE_OK;
+  if (!workspace) return fail(HE_EINVAL, "workspace is NULL");
+  if (workspace_bytes < P.ws_bytes) return fail(HE_ENOMEM, "workspace smaller than he_multi_workspace_bytes()");
+  if (int r = set_device(c)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  int r = launch(c, KNttFwd, st, "multi: forward NTT", [&] { return he::launch_fwd_multi(c->C, P.T, P.fwd, st); });
+  if (!r)
+    r = launch(c, KMac, st, "multi: multiply-accumulate",
+               [&] { return he::launch_mac_multi(c->C, P.T, P.mac, c->d_err, st); });
+  if (!r) r = launch(c, KInttMask, st, "multi: inverse NTT", [&] { return he::launch_inv_multi(c->C, P.T, P.inv, st); });
+  if (!r && P.c0)
+    r = launch(c, KInttC0, st, "multi: pruned inverse NTT of c0",
+               [&] { return he::launch_c0_multi(c->C, P.T, P.c0, P.max_nc, st); });
+  return r;
 }
 
 int he_expand_compact(he_ctx* c, const uint64_t* ct_compact, uint32_t cnt, uint32_t k_b, uint64_t* ct_full,

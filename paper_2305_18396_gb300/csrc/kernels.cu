@@ -12,6 +12,7 @@
 
 #include "async.cuh"
 #include "kernels.h"
+#include "mac.cuh"
 #include "ntt.cuh"
 
 namespace he {
@@ -81,11 +82,8 @@ __global__ void __launch_bounds__(kNttThreads) k_poly_mul(const u64* a, const u6
 }
 
 // Forward NTT of matmul inputs for N < 512 into the slot-chunked layout (see k_mac_t).
-__host__ __device__ constexpr u64 chunked_index(u64 row, u32 J, u32 l, u32 s, u32 nJ, u32 L, u32 N);
 
-// Operand word of the multiply-accumulate: a residue v < 2^50 stored pre-split as
-// v mod 2^25 in the low half and floor(v / 2^25) in the high half.
-__device__ __forceinline__ u64 split_word(u64 v) { return (v & ((1ull << 25) - 1)) | ((v >> 25) << 32); }
+
 __global__ void __launch_bounds__(kNttThreads) k_ntt_forward_mm_small(const u64* src, u64* ctN, u32 nJ, u32 nLb,
                                                                       const __grid_constant__ Consts C) {
   extern __shared__ u64 sm[];
@@ -364,191 +362,27 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_intt_mask_t(u64* out, u64
   });
 }
 
-// Slot-wise multiply-accumulate (Algorithm 1 step 3 in the NTT domain).  For each
-// prime l and slot s the outputs form a small matrix product over the k-blocks J:
-//   out[r][I] = sum_J ct[r][J] * pt[I][J],   r = (Lb, component c) rows, I columns.
-//
-// Operand layout ("slot-chunked"): both the NTT of the input ciphertexts and the
-// encoded weights store, for every row (resp. column), prime and chunk of 32 slots, the
-// 32-slot vectors of all nJ k-blocks contiguously:
-//   word ((row * L + l) * (N / 32) + s / 32) * nJ * 32 + J * 32 + s % 32.
-// A block owns one 32-slot chunk of one prime and a (kRows x kCols) output tile.  Per
-// stage, warp 0 streams JB consecutive k-blocks of every operand row of the tile into
-// shared memory -- one 1-D bulk copy (TMA) of JB * 256 contiguous bytes per row --
-// completing on the stage's mbarrier; STAGES stages are in flight.  Each thread owns one
-// slot and a TM x TN register tile.  Operands < 2^50 are stored split, x = x0 + 2^25 x1
-// (split_word), and multiplied Karatsuba-style: three mad.wide.u32 per slot product into lo / mid / hi
-// 64-bit columns (no carries for nJ <= 4096), reduced once per output at the end.
-constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: a copy that never lands is an error
-
-// Operands arrive pre-split (split_word): halves of the word, plus their sum for Karatsuba.
-__device__ __forceinline__ void split25(u64 w, u32& a0, u32& a1, u32& as) {
-  a0 = (u32)w;
-  a1 = (u32)(w >> 32);
-  as = a0 + a1;
-}
-
-// Where the multiply-accumulate writes component c of (global) output ciphertext g:
-// base[c] + g * ct_stride[c] + l * N + slot.
-struct OutPlace {
-  u64* base[2];
-  u64 ct_stride[2];
-};
-
-// acc += a * b with a 32 x 32 -> 64-bit product (one mad.wide.u32).
-__device__ __forceinline__ void mad_wide(u64& acc, u32 a, u32 b) {
-  asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
-}
-
-__host__ __device__ constexpr u64 chunked_index(u64 row, u32 J, u32 l, u32 s, u32 nJ, u32 L, u32 N) {
-  return ((row * L + l) * (N >> 5) + (s >> 5)) * (u64)nJ * 32 + (u64)J * 32 + (s & 31);
-}
-
-template <int TM, int TN, int WR, int WC, int JB, int STAGES, int CPB = 1>
-struct MacCfg {
-  static constexpr int kTM = TM, kTN = TN, kWR = WR, kWC = WC, kJB = JB, kStages = STAGES;
-  static constexpr int kChunksPerBlock = CPB;  // 32-slot chunks one block streams back to back
-  static constexpr int kRows = TM * WR, kCols = TN * WC;
-  static constexpr int kThreads = 32 * WR * WC;
-  static constexpr int kStageWords = (kRows + kCols) * JB * 32;
-  static constexpr size_t kSmemBytes = (size_t)STAGES * kStageWords * sizeof(u64);
-};
-
+// Slot-wise multiply-accumulate of one product or a same-shape batch: the block body is
+// mac_tile (mac.cuh); grid x = (chunk group, output tile), grid y = (batch item, prime).
 template <class M, int MINB>
 __global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restrict__ ctN, const u64* __restrict__ pt,
                                                              OutPlace out, u32 nI, u32 nJ, u32 nLb,
                                                              u32 tilesR, int* err, const __grid_constant__ Consts C) {
   extern __shared__ __align__(128) u64 sm[];
-  __shared__ __align__(8) uint64_t bars[M::kStages];
-  __shared__ int abort_flag;
-  constexpr int TM = M::kTM, TN = M::kTN, JB = M::kJB, ST = M::kStages, CPB = M::kChunksPerBlock;
-
-  const u32 N = C.N, L = C.L;
-  const u32 chunks = N >> 5;
+  constexpr int CPB = M::kChunksPerBlock;
+  const u32 chunks = C.N >> 5;
   const u32 groups = (chunks + CPB - 1) / CPB;
   const u32 chunk0 = (blockIdx.x % groups) * CPB;
   const u32 nch = min((u32)CPB, chunks - chunk0);
   const u32 tile = blockIdx.x / groups;
   const u32 r0 = (tile % tilesR) * M::kRows, c0 = (tile / tilesR) * M::kCols;
-  const u32 l = blockIdx.y % L;
-  const u64 item = blockIdx.y / L;  // batch item
-  ctN += item * ((u64)nLb * nJ * 2 * L * N);
-  pt += item * ((u64)nI * nJ * L * N);
-  const u64 ct0 = item * ((u64)nLb * nI);  // global index of this item's first output ciphertext
-  const PrimeConsts& P = C.p[l];
-  const u32 rows = 2 * nLb;
-  const u32 nrows = min((u32)M::kRows, rows - r0), ncols = min((u32)M::kCols, nI - c0);
-  const u32 nsp = (nJ + JB - 1) / JB;  // stages per chunk
-  const u32 nstages = nch * nsp;
-  const u32 warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const u32 wr = warp % M::kWR, wc = warp / M::kWR;
-
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < ST; ++st) mbar_init(&bars[st], 1);
-    mbar_init_fence();
-    abort_flag = 0;
-  }
-  __syncthreads();
-
-  // warp 0: stream k-blocks [JB k, JB k + jb) of chunk chunk0 + i / nsp (k = i % nsp) of
-  // every operand row of the tile into stage st
-  auto issue = [&](u32 i, u32 st) {
-    const u32 chunk = chunk0 + i / nsp, k = i % nsp;
-    const u32 J0 = k * JB, jb = min((u32)JB, nJ - J0);
-    const u32 bytes = jb * 32 * sizeof(u64);
-    if (lane == 0) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&bars[st], (nrows + ncols) * bytes);
-    }
-    __syncwarp();
-    u64* stage = sm + st * M::kStageWords;
-    for (u32 t = lane; t < nrows + ncols; t += 32) {
-      const bool is_row = t < nrows;
-      const u64* src = is_row ? ctN + chunked_index(r0 + t, J0, l, chunk << 5, nJ, L, N)
-                              : pt + chunked_index(c0 + (t - nrows), J0, l, chunk << 5, nJ, L, N);
-      u64* dst = stage + (is_row ? t : M::kRows + (t - nrows)) * (JB * 32);
-      bulk_copy_g2s(dst, src, bytes, &bars[st]);
-    }
-  };
-
-  if (warp == 0)
-    for (u32 i = 0; i < (u32)ST && i < nstages; ++i) issue(i, i);
-
-  u64 lo[TM][TN], mid[TM][TN], hi[TM][TN];
-#pragma unroll
-  for (int a = 0; a < TM; ++a)
-#pragma unroll
-    for (int b = 0; b < TN; ++b) lo[a][b] = mid[a][b] = hi[a][b] = 0;
-
-  for (u32 i = 0; i < nstages; ++i) {
-    const u32 st = i % ST;
-    if (threadIdx.x == 0) {
-      if (!mbar_wait_bounded(&bars[st], (i / ST) & 1, kWaitLimitNs)) {
-        abort_flag = 1;
-        atomicExch(err, 1);
-        // let every other copy this block issued land (bounded) before the block exits
-        for (u32 i2 = i + 1; i2 < nstages && i2 < i + ST; ++i2)
-          mbar_wait_bounded(&bars[i2 % ST], (i2 / ST) & 1, kWaitLimitNs);
-      }
-    }
-    __syncthreads();
-    if (abort_flag) return;
-    const u64* stage = sm + st * M::kStageWords;
-    const u32 k = i % nsp;
-    const u32 jb = min((u32)JB, nJ - k * JB);
-    const u64* prow = stage + (M::kRows + wc * TN) * (JB * 32) + lane;  // this thread's column operands
-    const u64* crow = stage + (wr * TM) * (JB * 32) + lane;             // this thread's row operands
-    // one k-block: TN column and TM row operands (pre-split words), TM x TN x 3 mad.wide
-    auto kblock = [&](u32 jj) {
-      u32 p0[TN], p1[TN], ps[TN];
-#pragma unroll
-      for (int b = 0; b < TN; ++b) split25(prow[b * (JB * 32) + jj * 32], p0[b], p1[b], ps[b]);
-#pragma unroll
-      for (int a = 0; a < TM; ++a) {
-        u32 x0, x1, xs;
-        split25(crow[a * (JB * 32) + jj * 32], x0, x1, xs);
-#pragma unroll
-        for (int b = 0; b < TN; ++b) {
-          mad_wide(lo[a][b], x0, p0[b]);
-          mad_wide(hi[a][b], x1, p1[b]);
-          mad_wide(mid[a][b], xs, ps[b]);
-        }
-      }
-    };
-    if (jb == (u32)JB) {  // full stage: constant offsets, fully unrolled
-#pragma unroll
-      for (int jj = 0; jj < JB; ++jj) kblock(jj);
-    } else {
-      for (u32 jj = 0; jj < jb; ++jj) kblock(jj);
-    }
-    if (k == nsp - 1) {  // chunk complete: reduce, store, restart the accumulators
-      const u32 s = ((chunk0 + i / nsp) << 5) + lane;
-#pragma unroll
-      for (int a = 0; a < TM; ++a) {
-        const u32 r = r0 + wr * TM + a;
-#pragma unroll
-        for (int b = 0; b < TN; ++b) {
-          const u32 I = c0 + wc * TN + b;
-          if (r < rows && I < nI) {
-            const u64 cross = mid[a][b] - lo[a][b] - hi[a][b];  // sum of x0 y1 + x1 y0
-            u64 v = reduce_word(lo[a][b], P);
-            v = add_mod(v, csub(mul_shoup(cross, P.r25, P.r25_sh, P.q), P.q), P.q);
-            v = add_mod(v, csub(mul_shoup(hi[a][b], P.r50, P.r50_sh, P.q), P.q), P.q);
-            const u32 c = r & 1;
-            out.base[c][(ct0 + (u64)(r >> 1) * nI + I) * out.ct_stride[c] + (u64)l * N + s] = v;
-          }
-          lo[a][b] = mid[a][b] = hi[a][b] = 0;
-        }
-      }
-    }
-    __syncthreads();
-    if (warp == 0 && i + ST < nstages) issue(i + ST, st);
-  }
+  const u32 l = blockIdx.y % C.L;
+  const u64 item = blockIdx.y / C.L;  // batch item
+  const u64 per_in = (u64)nLb * nJ * 2 * C.L * C.N, per_pt = (u64)nI * nJ * C.L * C.N;
+  mac_tile<M>(ctN + item * per_in, pt + item * per_pt, out, item * ((u64)nLb * nI), nI, nJ, nLb, r0, c0, chunk0, nch,
+              l, err, C, sm);
 }
 
-// The configuration the library launches.
-using MacProd = MacCfg<4, 2, 2, 4, 8, 2, 1>;
-constexpr int kMacMinBlocks = 2;
 
 // Forward NTT of the input ciphertexts of a product into the slot-chunked operand layout.
 // Input poly p = ((Lb nJ + J) 2 + c) L + l of the wire format [Lb nJ + J][2][L][N].
@@ -613,46 +447,8 @@ __global__ void __launch_bounds__(kNttThreads) k_intt_c0_targets(const u64* src,
   const u64 g_ct = poly / C.L;
   const u64 item = g_ct / out_cts;
   const u32 o = (u32)(g_ct % out_cts);
-  const PrimeConsts& P = C.p[l];
-  const u32 N = C.N, logN = C.logN, Nc = N >> logkb;
-  const u64 q = P.q, two_q = P.two_q;
-  u64* z = sm + N;  // compact values
-  for (u32 i = threadIdx.x; i < N; i += blockDim.x) sm[i] = src[poly * N + i];
-  __syncthreads();
-  // pruned stages s < log2 k_b: keep positions whose low s+1 bits are all ones
-  for (u32 s = 0; s < logkb; ++s) {
-    const u32 span = 1u << s, ones = (2u << s) - 1;
-    for (u32 t = threadIdx.x; t < (N >> (s + 1)); t += blockDim.x) {
-      const u32 p = (t << (s + 1)) | ones;
-      const u32 widx = (N >> (s + 1)) + (p >> (s + 1));
-      const u64 U = sm[p - span], V = sm[p];
-      sm[p] = mul_shoup(U - V + two_q, __ldg(P.ipsi + widx), __ldg(P.ipsi_sh + widx), q);
-    }
-    __syncthreads();
-  }
-  const u32 kb = 1u << logkb;
-  for (u32 g = threadIdx.x; g < Nc; g += blockDim.x) z[g] = sm[g * kb + kb - 1];
-  __syncthreads();
-  // remaining stages on the compact array (span 2^(s - log2 k_b) there)
-  for (u32 s = logkb; s < logN; ++s) {
-    const u32 cs = s - logkb, span = 1u << cs;
-    for (u32 b = threadIdx.x; b < (Nc >> 1); b += blockDim.x) {
-      const u32 grp = b >> cs;
-      const u32 j = (grp << (cs + 1)) + (b & (span - 1));
-      const u32 widx = (N >> (s + 1)) + grp;
-      const u64 U = z[j], V = z[j + span];
-      z[j] = csub(U + V, two_q);
-      z[j + span] = mul_shoup(U - V + two_q, __ldg(P.ipsi + widx), __ldg(P.ipsi_sh + widx), q);
-    }
-    __syncthreads();
-  }
-  u64* d = dst + g_ct * ct_stride + (u64)l * Nc;
-  for (u32 g = threadIdx.x; g < Nc; g += blockDim.x) {
-    u64 v = csub(mul_shoup(z[g], P.ninv, P.ninv_sh, q), q);
-    const u32 e = g * kb + kb - 1;
-    const u64 sv = lo64(draw(seed + item, e, o, kDomainMask, 0)) & C.tmask;
-    d[g] = sub_mod(v, delta_residue(sv, C, P), q);
-  }
+  ntt_inverse_c0_targets(src + poly * C.N, dst + g_ct * ct_stride + (u64)l * (C.N >> logkb), logkb, seed + item, o, l,
+                         C, sm);
 }
 
 // One block per output polynomial (o, c, l): inverse NTT; for c = 0 subtract

@@ -1,0 +1,235 @@
+// multi.cu -- one set of launches for a list of products of different shapes (different
+// m, k, n, blockings, weights, output modes): the forward NTT of every product's inputs,
+// the multiply-accumulate of every product, the inverse NTTs and the masks each run as a
+// single grid over the union of all products' work.  A product descriptor table travels
+// as a kernel parameter; each block finds its product by binary search over per-kernel
+// prefix sums of block counts.
+#include "async.cuh"
+#include "kernels.h"
+#include "mac.cuh"
+#include "multi.h"
+#include "ntt.cuh"
+
+namespace he {
+
+namespace {
+
+constexpr int kThreadsSmall = 256;
+
+// Largest i with begin(i) <= b (items sorted by their prefix sums).
+template <class F>
+__device__ __forceinline__ u32 find_item(const MultiTable& T, u64 b, F begin) {
+  u32 lo = 0, hi = T.count - 1;
+  while (lo < hi) {
+    const u32 mid = (lo + hi + 1) >> 1;
+    if (begin(T.it[mid]) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_fwd_multi_t(const __grid_constant__ MultiTable T,
+                                                                   const __grid_constant__ Consts C) {
+  using S = NttShape<LOGN>;
+  extern __shared__ u64 sm[];
+  const u32 i = find_item(T, blockIdx.x, [](const MultiItem& x) { return x.fwd_begin; });
+  const MultiItem& it = T.it[i];
+  const u64 local = blockIdx.x - it.fwd_begin;
+  const u32 l = local % C.L, c = (local / C.L) % 2;
+  const u32 LbJ = (u32)(local / (2 * C.L));
+  const u32 Lb = LbJ / it.nJ, J = LbJ % it.nJ;
+  const u64* sp = it.ct_in + local * S::N;
+  const u64 row = (u64)Lb * 2 + c;
+  ntt_forward_block<S>(sm, C.p[l], [&](u32 e) { return sp[e]; },
+                       [&](u32 e, u64 v) { it.ctN[chunked_index(row, J, l, e, it.nJ, C.L, S::N)] = split_word(v); });
+}
+
+__global__ void __launch_bounds__(kThreadsSmall) k_fwd_multi_small(const __grid_constant__ MultiTable T,
+                                                                   const __grid_constant__ Consts C) {
+  extern __shared__ u64 sm[];
+  const u32 i = find_item(T, blockIdx.x, [](const MultiItem& x) { return x.fwd_begin; });
+  const MultiItem& it = T.it[i];
+  const u64 local = blockIdx.x - it.fwd_begin;
+  const u32 l = local % C.L, c = (local / C.L) % 2;
+  const u32 LbJ = (u32)(local / (2 * C.L));
+  const u32 Lb = LbJ / it.nJ, J = LbJ % it.nJ;
+  for (u32 e = threadIdx.x; e < C.N; e += blockDim.x) sm[e] = it.ct_in[local * C.N + e];
+  __syncthreads();
+  ntt_forward_smem(sm, C.logN, C.p[l]);
+  for (u32 e = threadIdx.x; e < C.N; e += blockDim.x)
+    it.ctN[chunked_index((u64)Lb * 2 + c, J, l, e, it.nJ, C.L, C.N)] = split_word(sm[e]);
+}
+
+template <class M, int MINB>
+__global__ void __launch_bounds__(M::kThreads, MINB) k_mac_multi_t(const __grid_constant__ MultiTable T, int* err,
+                                                                   const __grid_constant__ Consts C) {
+  extern __shared__ __align__(128) u64 sm[];
+  const u32 i = find_item(T, blockIdx.x, [](const MultiItem& x) { return x.mac_begin; });
+  const MultiItem& it = T.it[i];
+  const u64 local = blockIdx.x - it.mac_begin;
+  const u32 chunks = C.N >> 5;
+  const u32 chunk = local % chunks;
+  const u64 rest = local / chunks;
+  const u32 tiles = it.tilesR * it.tilesC;
+  const u32 tile = rest % tiles, l = (u32)(rest / tiles);
+  const u32 r0 = (tile % it.tilesR) * M::kRows, c0 = (tile / it.tilesR) * M::kCols;
+  const u64 N = C.N, L = C.L;
+  OutPlace out;
+  if (it.compact) {
+    const u64 Nc = N >> it.logkb;
+    out.base[0] = it.c0_ntt;
+    out.ct_stride[0] = L * N;
+    out.base[1] = it.out + L * Nc;
+    out.ct_stride[1] = L * (Nc + N);
+  } else {
+    out.base[0] = it.out;
+    out.base[1] = it.out + L * N;
+    out.ct_stride[0] = out.ct_stride[1] = 2 * L * N;
+  }
+  mac_tile<M>(it.ctN, it.pt, out, 0, it.nI, it.nJ, it.nLb, r0, c0, chunk, 1, l, err, C, sm);
+}
+
+// Inverse NTT: compact products transform their c1 polynomials in place; full products
+// transform every output polynomial and re-mask c0.
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_inv_multi_t(const __grid_constant__ MultiTable T,
+                                                                   const __grid_constant__ Consts C) {
+  using S = NttShape<LOGN>;
+  extern __shared__ u64 sm[];
+  const u32 i = find_item(T, blockIdx.x, [](const MultiItem& x) { return x.inv_begin; });
+  const MultiItem& it = T.it[i];
+  const u64 local = blockIdx.x - it.inv_begin;
+  const u64 N = S::N, L = C.L;
+  const u32 l = local % L;
+  if (it.compact) {
+    const u64 Nc = N >> it.logkb;
+    u64* d = it.out + (local / L) * L * (Nc + N) + L * Nc + l * N;
+    ntt_inverse_block<S>(sm, C.p[l], [&](u32 e) { return d[e]; }, [&](u32 e, u64 v) { d[e] = v; });
+  } else {
+    const u32 c = (local / L) % 2;
+    const u32 o = (u32)(local / (2 * L));
+    const PrimeConsts& P = C.p[l];
+    u64* d = it.out + local * N;
+    ntt_inverse_block<S>(sm, P, [&](u32 e) { return d[e]; }, [&](u32 e, u64 v) {
+      if (c == 0) {
+        const u64 sv = lo64(draw(it.mask_seed, e, o, kDomainMask, 0)) & C.tmask;
+        v = sub_mod(v, delta_residue(sv, C, P), P.q);
+      }
+      d[e] = v;
+    });
+  }
+}
+
+__global__ void __launch_bounds__(kThreadsSmall) k_inv_multi_small(const __grid_constant__ MultiTable T,
+                                                                   const __grid_constant__ Consts C) {
+  extern __shared__ u64 sm[];
+  const u32 i = find_item(T, blockIdx.x, [](const MultiItem& x) { return x.inv_begin; });
+  const MultiItem& it = T.it[i];
+  const u64 local = blockIdx.x - it.inv_begin;
+  const u64 N = C.N, L = C.L;
+  const u32 l = local % L;
+  const PrimeConsts& P = C.p[l];
+  u64* d;
+  u32 c = 1, o = 0;
+  if (it.compact) {
+    const u64 Nc = N >> it.logkb;
+    d = it.out + (local / L) * L * (Nc + N) + L * Nc + l * N;
+  } else {
+    c = (local / L) % 2;
+    o = (u32)(local / (2 * L));
+    d = it.out + local * N;
+  }
+  for (u32 e = threadIdx.x; e < N; e += blockDim.x) sm[e] = d[e];
+  __syncthreads();
+  ntt_inverse_smem(sm, C.logN, P);
+  for (u32 e = threadIdx.x; e < N; e += blockDim.x) {
+    u64 v = sm[e];
+    if (c == 0) {
+      const u64 sv = lo64(draw(it.mask_seed, e, o, kDomainMask, 0)) & C.tmask;
+      v = sub_mod(v, delta_residue(sv, C, P), P.q);
+    }
+    d[e] = v;
+  }
+}
+
+// Pruned inverse NTT + mask of c0 for the compact products (one block per (o, l)).
+__global__ void __launch_bounds__(kThreadsSmall) k_c0_multi(const __grid_constant__ MultiTable T,
+                                                            const __grid_constant__ Consts C) {
+  extern __shared__ u64 sm[];
+  const u32 i = find_item(T, blockIdx.x, [](const MultiItem& x) { return x.c0_begin; });
+  const MultiItem& it = T.it[i];
+  const u64 local = blockIdx.x - it.c0_begin;
+  const u64 N = C.N, L = C.L, Nc = N >> it.logkb;
+  const u32 l = local % L;
+  const u32 o = (u32)(local / L);
+  ntt_inverse_c0_targets(it.c0_ntt + local * N, it.out + (u64)o * L * (Nc + N) + l * Nc, it.logkb, it.mask_seed, o, l,
+                         C, sm);
+}
+
+#define HE_MULTI_DISPATCH(KERNEL, GRID, ST, ...)                                                                   \
+  switch (C.logN) {                                                                                                \
+    case 9: KERNEL<9><<<GRID, NttShape<9>::T, NttShape<9>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break;     \
+    case 10: KERNEL<10><<<GRID, NttShape<10>::T, NttShape<10>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
+    case 11: KERNEL<11><<<GRID, NttShape<11>::T, NttShape<11>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
+    case 12: KERNEL<12><<<GRID, NttShape<12>::T, NttShape<12>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
+    case 13: KERNEL<13><<<GRID, NttShape<13>::T, NttShape<13>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
+    default: break;                                                                                                \
+  }
+
+}  // namespace
+
+cudaError_t configure_multi_kernels() {
+  const int one = 8192 * (int)sizeof(u64);
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f, int bytes) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  };
+  set((const void*)k_fwd_multi_small, one);
+  set((const void*)k_inv_multi_small, one);
+  set((const void*)k_c0_multi, 2 * one);
+  set((const void*)k_mac_multi_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
+#define HE_SET_MULTI(LOGN)                                                                        \
+  set((const void*)k_fwd_multi_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
+  set((const void*)k_inv_multi_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));
+  HE_SET_MULTI(9) HE_SET_MULTI(10) HE_SET_MULTI(11) HE_SET_MULTI(12) HE_SET_MULTI(13)
+#undef HE_SET_MULTI
+  return e;
+}
+
+u32 mac_tile_rows() { return MacProd::kRows; }
+u32 mac_tile_cols() { return MacProd::kCols; }
+
+cudaError_t launch_fwd_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st) {
+  if (!blocks) return cudaGetLastError();
+  if (C.logN >= 9) {
+    HE_MULTI_DISPATCH(k_fwd_multi_t, (unsigned)blocks, st, T, C)
+  } else {
+    k_fwd_multi_small<<<(unsigned)blocks, kThreadsSmall, C.N * sizeof(u64), st>>>(T, C);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mac_multi(const Consts& C, const MultiTable& T, u64 blocks, int* err, cudaStream_t st) {
+  if (blocks) k_mac_multi_t<MacProd, kMacMinBlocks><<<(unsigned)blocks, MacProd::kThreads, MacProd::kSmemBytes, st>>>(
+      T, err, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inv_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st) {
+  if (!blocks) return cudaGetLastError();
+  if (C.logN >= 9) {
+    HE_MULTI_DISPATCH(k_inv_multi_t, (unsigned)blocks, st, T, C)
+  } else {
+    k_inv_multi_small<<<(unsigned)blocks, kThreadsSmall, C.N * sizeof(u64), st>>>(T, C);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c0_multi(const Consts& C, const MultiTable& T, u64 blocks, u32 max_nc, cudaStream_t st) {
+  if (blocks)
+    k_c0_multi<<<(unsigned)blocks, kThreadsSmall, (size_t)(C.N + max_nc) * sizeof(u64), st>>>(T, C);
+  return cudaGetLastError();
+}
+
+}  // namespace he

@@ -1,0 +1,37 @@
+// multi.h -- descriptor table and launchers of the multi-product launch (multi.cu).
+#pragma once
+
+#include "he_common.cuh"
+
+namespace he {
+
+constexpr int kMaxMulti = 64;  // products per multi-product launch
+
+// One product of a multi-product launch.  *_begin: first block of this product in each
+// kernel's grid (prefix sums in product order).
+struct MultiItem {
+  const u64* ct_in;  // input ciphertexts, wire format
+  const u64* pt;     // encoded weights (slot-chunked)
+  u64* out;          // output ciphertexts (full or compact)
+  u64* ctN;          // workspace: NTT of the inputs (slot-chunked)
+  u64* c0_ntt;       // workspace (compact output only): NTT-domain c0 of every output
+  u64 mask_seed;
+  u64 fwd_begin, mac_begin, inv_begin, c0_begin;
+  u32 nI, nJ, nLb, logkb;
+  u32 compact, tilesR, tilesC, pad;
+};
+
+struct MultiTable {
+  u32 count, pad;
+  MultiItem it[kMaxMulti];
+};
+
+cudaError_t configure_multi_kernels();
+u32 mac_tile_rows();
+u32 mac_tile_cols();
+cudaError_t launch_fwd_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
+cudaError_t launch_mac_multi(const Consts& C, const MultiTable& T, u64 blocks, int* err, cudaStream_t st);
+cudaError_t launch_inv_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
+cudaError_t launch_c0_multi(const Consts& C, const MultiTable& T, u64 blocks, u32 max_nc, cudaStream_t st);
+
+}  // namespace he

@@ -273,4 +273,51 @@ __device__ __forceinline__ void ntt_inverse_block(u64* sm, const PrimeConsts& P,
     }
 }
 
+// Compact-output mode, one c0 polynomial (prime l) of output ciphertext o: inverse NTT kept
+// only at the coefficients e = g k_b + k_b - 1, then c0_e - round(q s_e / t) for the mask
+// s of output o under `seed`.  src: N NTT-domain words; dst: N / k_b words.  sm: N + N/k_b
+// words of shared memory.  All threads of the block call it.
+__device__ __forceinline__ void ntt_inverse_c0_targets(const u64* src, u64* dst, u32 logkb, u64 seed, u32 o, u32 l,
+                                                       const Consts& C, u64* sm) {
+  const PrimeConsts& P = C.p[l];
+  const u32 N = C.N, logN = C.logN, Nc = N >> logkb;
+  const u64 q = P.q, two_q = P.two_q;
+  u64* z = sm + N;  // compact values
+  for (u32 i = threadIdx.x; i < N; i += blockDim.x) sm[i] = src[i];
+  __syncthreads();
+  // pruned stages s < log2 k_b: keep positions whose low s+1 bits are all ones
+  for (u32 s = 0; s < logkb; ++s) {
+    const u32 span = 1u << s, ones = (2u << s) - 1;
+    for (u32 t = threadIdx.x; t < (N >> (s + 1)); t += blockDim.x) {
+      const u32 p = (t << (s + 1)) | ones;
+      const u32 widx = (N >> (s + 1)) + (p >> (s + 1));
+      const u64 U = sm[p - span], V = sm[p];
+      sm[p] = mul_shoup(U - V + two_q, __ldg(P.ipsi + widx), __ldg(P.ipsi_sh + widx), q);
+    }
+    __syncthreads();
+  }
+  const u32 kb = 1u << logkb;
+  for (u32 g = threadIdx.x; g < Nc; g += blockDim.x) z[g] = sm[g * kb + kb - 1];
+  __syncthreads();
+  // remaining stages on the compact array (span 2^(s - log2 k_b) there)
+  for (u32 s = logkb; s < logN; ++s) {
+    const u32 cs = s - logkb, span = 1u << cs;
+    for (u32 b = threadIdx.x; b < (Nc >> 1); b += blockDim.x) {
+      const u32 grp = b >> cs;
+      const u32 j = (grp << (cs + 1)) + (b & (span - 1));
+      const u32 widx = (N >> (s + 1)) + grp;
+      const u64 U = z[j], V = z[j + span];
+      z[j] = csub(U + V, two_q);
+      z[j + span] = mul_shoup(U - V + two_q, __ldg(P.ipsi + widx), __ldg(P.ipsi_sh + widx), q);
+    }
+    __syncthreads();
+  }
+  for (u32 g = threadIdx.x; g < Nc; g += blockDim.x) {
+    u64 v = csub(mul_shoup(z[g], P.ninv, P.ninv_sh, q), q);
+    const u32 e = g * kb + kb - 1;
+    const u64 sv = lo64(draw(seed, e, o, kDomainMask, 0)) & C.tmask;
+    dst[g] = sub_mod(v, delta_residue(sv, C, P), q);
+  }
+}
+
 }  // namespace he

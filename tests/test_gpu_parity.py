@@ -365,3 +365,45 @@ def test_bounded_wait_reports_timeout_and_context_survives(B):
     W = S.fixed_point_weights((64, 64), S.SEED_W)
     _run_case(B, 4096, 2, 16, 64, 64, (8, 32, 16), W, X)
     B.he_device_status(ctx)
+
+
+# ------------------------------------------------------------------ multi-product launch
+
+
+@pytest.mark.parametrize("N,L", [(4096, 2), (256, 2)])
+def test_matmul_multi_equals_single_calls(B, N, L):
+    """Products of different shapes, blockings and output modes in one multi-product launch
+    give exactly what their own he_matmul calls give (and one matches the oracle)."""
+    ctx, P = ctx_for(B, N, L)
+    s = O.keygen(P, S.SEED_KEY)
+    sk = B.he_keygen(ctx, S.SEED_KEY)
+    shapes = [(16, 64, 64, None, 0), (9, 70, 37, None, B.HE_DROP_C0), (128, 64, 128, None, B.HE_DROP_C0),
+              (5, 7, 3, (1, 1, 1), 0), (33, 100, 20, None, 0), (0, 5, 5, (1, 1, 1), 0)]
+    items, singles, oracle_case = [], [], None
+    for idx, (m, k, n, blk, flags) in enumerate(shapes):
+        blk = blk or ctx.default_blocking(max(m, 1), k, n)
+        si = ctx.sizes(m, k, n, blk)
+        X = S.uniform_share((m, k), 300 + idx)
+        W = S.fixed_point_weights((k, n), 400 + idx)
+        ct_in = B.he_encrypt(ctx, sk, B.he_pack_input(ctx, to_dev(X), m, k, blk), 500 + idx) if m else ctx.empty(1)
+        pt = B.he_encode_weights(ctx, to_dev(W), k, n, blk)
+        ow = si["out_words_compact"] if flags else si["out_words"]
+        items.append(dict(ct_in=ct_in, pt=pt, ct_out=ctx.empty(max(ow, 1)), m=m, k=k, n=n, blk=blk, flags=flags,
+                          mask_seed=600 + idx))
+        if m:
+            singles.append(to_np(B.he_matmul(ctx, ct_in, pt, m, k, n, blk, 600 + idx, flags=flags)))
+        else:
+            singles.append(None)
+        if idx == 0:
+            oracle_case = (X, W, m, k, n, blk)
+    prods = B.make_products(items)
+    ws = ctx.empty(max(B.he_multi_workspace_bytes(ctx, prods) // 8 + 1, 1))
+    B.he_matmul_multi(ctx, prods, ws)
+    for it, single in zip(items, singles):
+        if single is not None:
+            assert np.array_equal(to_np(it["ct_out"])[:single.size], single)
+    X, W, m, k, n, blk = oracle_case
+    ct_or = O.encrypt(P, s, O.pack_input(X, blk, N), 500)
+    assert np.array_equal(to_np(items[0]["ct_in"]), ct_or.reshape(-1))
+    want = O.matmul(P, ct_or, W, m, k, n, blk, 600)
+    assert np.array_equal(to_np(items[0]["ct_out"]), want.reshape(-1))
