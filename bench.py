@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-rates", default="400,800", help="Poisson arrival rates (requests/s)")
+    ap.add_argument("--serving-requests", type=int, default=400)
     ap.add_argument("--full-c0", action="store_true",
                     help="return all of c0 instead of only the decoded coefficients (Sec. 3.1.3)")
     return ap.parse_args()
@@ -330,6 +333,38 @@ def reference_arm(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ serving leg
+
+
+def serving_leg(B, ctx, args):
+    """Poisson arrivals of single-product requests (BERT-base and BERT-large layer matrices,
+    m log-uniform in [8, 512]): continuous batching vs the plain per-request path."""
+    import torch
+
+    from paper_2305_18396_gb300 import serving as SV
+
+    specs = [("base.qkv", 768, 2304, 512), ("base.out", 768, 768, 512), ("base.ffn1", 768, 3072, 512),
+             ("base.ffn2", 3072, 768, 512), ("large.qkv", 1024, 3072, 512), ("large.out", 1024, 1024, 512),
+             ("large.ffn1", 1024, 4096, 512), ("large.ffn2", 4096, 1024, 512)]
+    models = SV.make_models(ctx, specs)
+    out = {"requests_per_rate": args.serving_requests,
+           "mix": "BERT-base/large layer matrices (QKV, out, FFN1, FFN2), m log-uniform in [8, 512], Poisson arrivals",
+           "resident_weight_gb": round(sum(m.pt.numel() for m in models) * 8 / 1e9, 2),
+           "policy": "2 launch slots (streams), up to 8 requests per multi-product launch, admission by a 32 GiB "
+                     "device budget for outputs + workspace", "rates": {}}
+    for rate in [float(x) for x in args.serving_rates.split(",") if x]:
+        res = {}
+        for name, fn, kw in (("per_request", SV.run_per_request, {}),
+                             ("continuous_batching", SV.run_served, {"slots": 2, "max_batch": 8})):
+            reqs = SV.make_requests(models, args.serving_requests, rate)
+            st, _ = fn(ctx, models, reqs, **kw)
+            res[name] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
+        out["rates"][str(int(rate))] = res
+    del models
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 
 
@@ -431,6 +466,9 @@ def gpu_arm(args, world, rank, local):
         e2e = {"value": world * layer.macs * ksteps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ksteps, "ms_per_step": dt * 1e3 / ksteps}
 
+    serving = None
+    if world == 1 and not args.no_serving:
+        serving = serving_leg(B, ctx, args)
     if rank != 0:
         return
     cpu = None
@@ -451,7 +489,7 @@ def gpu_arm(args, world, rank, local):
                    "blockings_mkn": blks, "kernel_source_hash": kernel_source_hash(), "parallelism": f"replicas x{world} (independent layers, no collective)",
                    "l2": "inputs larger than L2: one step reads/writes ~3 GB of ciphertexts/weights"},
         "latency_ms": {"p50": statistics.median(per), "p99": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))]},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "gpu_launches": launches,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

@@ -1,0 +1,221 @@
+"""Continuous-batching server for private-inference matrix-product requests.
+
+A request is one Pi_MatMul (Algorithm 1, Sec. 3.1.1) of a client's encrypted share
+X (m x k) against one of the server's resident weight matrices W (k x n) -- e.g.
+the QKV, attention-output or FFN product of a BERT-base or BERT-large layer at the
+client's sequence length m.  The server keeps every weight matrix resident in NTT
+form; requests arrive over time and are
+
+* admitted in arrival order while the device-memory footprint of the admitted but
+  unfinished requests (their output ciphertexts plus the workspace of their launch)
+  stays within a budget;
+* launched as soon as a launch slot (a CUDA stream) is free: every admitted request
+  not yet launched goes into one multi-product launch (he_matmul_multi, up to 64
+  products of any shapes), so requests that arrive while others are on the GPU join
+  the next launch and their work overlaps on the device with the running one;
+* completed when their launch's event fires (latency = completion - arrival).
+
+`run_per_request` is the plain path it is compared against: one he_matmul per request,
+in arrival order, on one stream.
+
+The timing loop runs on the host clock; all arithmetic runs in the library's kernels.
+"""
+import heapq
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+@dataclass
+class Model:
+    """One resident weight matrix: encoded weights and its fixed blocking (wire format)."""
+    name: str
+    k: int
+    n: int
+    blk: tuple
+    pt: torch.Tensor
+    ct_pool: torch.Tensor  # input ciphertexts for the largest m (requests use a prefix)
+    max_m: int
+
+
+@dataclass
+class Request:
+    rid: int
+    model: str
+    m: int
+    arrival: float  # seconds since start
+    mask_seed: int
+    out: torch.Tensor = None
+    launched: float = math.nan
+    done: float = math.nan
+    footprint: int = 0
+
+
+@dataclass(order=True)
+class _InFlight:
+    start: float
+    slot: int = field(compare=False)
+    event: object = field(compare=False)
+    reqs: list = field(compare=False)
+    ws: torch.Tensor = field(compare=False)
+
+
+def request_footprint(ctx, model, m, flags):
+    """Device bytes a request holds while admitted: outputs + its share of a launch workspace."""
+    si = ctx.sizes(m, model.k, model.n, model.blk)
+    out = si["out_words_compact"] if flags else si["out_words"]
+    ws = si["workspace_bytes_compact"] if flags else si["workspace_bytes"]
+    return 8 * out + ws + 512
+
+
+class Server:
+    def __init__(self, ctx, models, flags=B.HE_DROP_C0, hbm_budget=32 << 30, slots=2, max_batch=8):
+        self.ctx, self.models, self.flags = ctx, {mm.name: mm for mm in models}, flags
+        self.budget, self.max_batch = hbm_budget, min(max_batch, 64)
+        self.streams = [torch.cuda.Stream(device=ctx.device) for _ in range(slots)]
+        self.free_slots = list(range(slots))
+        self.queue, self.admitted, self.inflight, self.done = [], [], [], []
+        self.in_use = 0
+        self.launches = 0
+
+    def submit(self, req):
+        req.footprint = request_footprint(self.ctx, self.models[req.model], req.m, self.flags)
+        if req.footprint > self.budget:
+            raise ValueError(f"request {req.rid} needs {req.footprint} bytes, more than the whole budget")
+        self.queue.append(req)
+
+    def _admit(self):
+        while self.queue and self.in_use + self.queue[0].footprint <= self.budget:
+            r = self.queue.pop(0)
+            self.in_use += r.footprint
+            self.admitted.append(r)
+
+    def _launch(self, now):
+        if not self.admitted or not self.free_slots:
+            return
+        batch, self.admitted = self.admitted[:self.max_batch], self.admitted[self.max_batch:]
+        slot = self.free_slots.pop(0)
+        stream = self.streams[slot]
+        items = []
+        with torch.cuda.stream(stream):
+            for r in batch:
+                mm = self.models[r.model]
+                si = self.ctx.sizes(r.m, mm.k, mm.n, mm.blk)
+                ow = si["out_words_compact"] if self.flags else si["out_words"]
+                r.out = self.ctx.empty(ow)
+                items.append(dict(ct_in=mm.ct_pool, pt=mm.pt, ct_out=r.out, m=r.m, k=mm.k, n=mm.n, blk=mm.blk,
+                                  flags=self.flags, mask_seed=r.mask_seed))
+                r.launched = now
+            prods = B.make_products(items)
+            ws = self.ctx.empty(max(B.he_multi_workspace_bytes(self.ctx, prods) // 8 + 1, 1))
+            B.he_matmul_multi(self.ctx, prods, ws, stream=stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        heapq.heappush(self.inflight, _InFlight(now, slot, ev, batch, ws))
+        self.launches += 1
+
+    def _poll(self, now):
+        still = []
+        for f in self.inflight:
+            if f.event.query():
+                for r in f.reqs:
+                    r.done = now
+                    self.in_use -= r.footprint
+                    self.done.append(r)
+                self.free_slots.append(f.slot)
+            else:
+                still.append(f)
+        self.inflight = still
+
+    def pump(self, now):
+        self._poll(now)
+        self._admit()
+        self._launch(now)
+
+    def idle(self):
+        return not (self.queue or self.admitted or self.inflight)
+
+
+def make_models(ctx, specs, seed=2):
+    """specs: (name, k, n, max_m).  Encodes random fixed-point weights and one pool of input
+    ciphertexts per matrix (the client's encrypted shares for the largest m)."""
+    from . import synthetic as S
+
+    models = []
+    sk = B.he_keygen(ctx, 77)
+    for i, (name, k, n, max_m) in enumerate(specs):
+        blk = ctx.default_blocking(128, k, n)
+        W = torch.from_numpy(S.fixed_point_weights((k, n), seed + i).view(np.int64).reshape(-1)).to(ctx.device)
+        pt = B.he_encode_weights(ctx, W, k, n, blk)
+        X = torch.from_numpy(S.uniform_share((max_m, k), 1000 + i).view(np.int64).reshape(-1)).to(ctx.device)
+        ct = B.he_encrypt(ctx, sk, B.he_pack_input(ctx, X, max_m, k, blk), 2000 + i)
+        models.append(Model(name, k, n, blk, pt, ct, max_m))
+    torch.cuda.synchronize()
+    return models
+
+
+def make_requests(models, count, rate, seed=6, m_lo=8, m_hi=512):
+    """Poisson arrivals at `rate` req/s, m log-uniform in [m_lo, m_hi], matrices uniform."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    ms = np.exp(rng.uniform(math.log(m_lo), math.log(m_hi), size=count)).astype(int)
+    which = rng.integers(0, len(models), size=count)
+    return [Request(i, models[which[i]].name, int(min(ms[i], models[which[i]].max_m)), float(t[i]), 10_000 + i)
+            for i in range(count)]
+
+
+def _stats(reqs, models, wall):
+    lat = np.array([(r.done - r.arrival) * 1e3 for r in reqs])
+    macs = sum(r.m * models[r.model].k * models[r.model].n for r in reqs)
+    return {"requests": len(reqs), "throughput_req_s": len(reqs) / wall, "plain_macs_per_s": macs / wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean())}
+
+
+def run_served(ctx, models, requests, **kw):
+    """Real-time continuous batching over the arrival schedule; returns latency/throughput stats."""
+    srv = Server(ctx, models, **kw)
+    pending = sorted(requests, key=lambda r: r.arrival)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(pending) or not srv.idle():
+        now = time.perf_counter() - t0
+        while i < len(pending) and pending[i].arrival <= now:
+            srv.submit(pending[i])
+            i += 1
+        srv.pump(now)
+        if srv.idle() and i < len(pending):
+            time.sleep(max(0.0, min(pending[i].arrival - now, 0.0005)))
+    wall = time.perf_counter() - t0
+    st = _stats(srv.done, {mm.name: mm for mm in models}, wall)
+    st["launches"] = srv.launches
+    return st, srv.done
+
+
+def run_per_request(ctx, models, requests, flags=B.HE_DROP_C0):
+    """The plain path: one he_matmul per request in arrival order on one stream."""
+    by = {mm.name: mm for mm in models}
+    pending = sorted(requests, key=lambda r: r.arrival)
+    stream = torch.cuda.Stream(device=ctx.device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in pending:
+        now = time.perf_counter() - t0
+        if r.arrival > now:
+            time.sleep(r.arrival - now)
+        mm = by[r.model]
+        with torch.cuda.stream(stream):
+            r.out = B.he_matmul(ctx, mm.ct_pool, mm.pt, r.m, mm.k, mm.n, mm.blk, r.mask_seed, flags=flags,
+                                stream=stream)
+        stream.synchronize()
+        r.done = time.perf_counter() - t0
+    wall = time.perf_counter() - t0
+    st = _stats(pending, by, wall)
+    st["launches"] = len(pending)
+    return st, pending
