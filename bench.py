@@ -153,7 +153,7 @@ class Layer:
             si = dict(si, out=ow, ws=wb)
             cnt = p.count
             max_ws = max(max_ws, cnt * wb)
-            max_hostws = max(max_hostws, B.matmul_host_workspace_words(ctx, p.m, p.k, p.n, blk, flags))
+            max_hostws = max(max_hostws, cnt * B.matmul_host_workspace_words(ctx, p.m, p.k, p.n, blk, flags))
             seed = 10_000 * (rank + 1) + idx
             Xs = [S.uniform_share((p.m, p.k), seed + b) for b in range(cnt)]
             if p.share_weights:
@@ -180,27 +180,42 @@ class Layer:
             idx += cnt
         self.ws = ctx.empty(max((max_ws + 7) // 8, 1))
         self.pt_tmp = ctx.empty(max(max_pt, 1))
-        self.host_ws = ctx.empty(max_hostws) if want_host else None
+        self.host_ws = [ctx.empty(max_hostws), ctx.empty(max_hostws)] if want_host else None
+        self.host_streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)] if want_host else None
+        self.enc_done = torch.cuda.Event()
+        self.torch = torch
         self.macs = sum(c["p"].m * c["p"].k * c["p"].n * c["cnt"] for c in self.calls)
         self.products = sum(c["cnt"] for c in self.calls)
         torch.cuda.synchronize()
 
     def step(self, step_idx, host=False):
         B, ctx = self.B, self.ctx
+        k = 0
         for c in self.calls:
             p, blk, cnt, si = c["p"], c["blk"], c["cnt"], c["si"]
             pt = c.get("pt")
             if pt is None:
                 pt = B.he_encode_weights_batch(ctx, c["W"], p.k, p.n, blk, cnt, pt=self.pt_tmp)
+                if host:  # the host-buffer calls below run on two side streams
+                    self.enc_done.record()
             seed = (step_idx << 20) | c["idx"]
             if host:
-                for b in range(cnt):  # host buffers: one C-ABI call per product
-                    iw, ow, pw = si["in_words"], si["out"], si["pt_words"]
-                    B.he_matmul_host(ctx, c["in_host"][b * iw:(b + 1) * iw], pt[b * pw:(b + 1) * pw], p.m, p.k, p.n,
-                                     blk, seed + b, c["out_host"][b * ow:(b + 1) * ow], self.host_ws, flags=self.flags)
+                # host buffers: one C-ABI call per launch group, alternating two streams (each with
+                # its own workspace) so one call's transfers overlap the other's kernels
+                st = self.host_streams[k % 2]
+                if pt is not c.get("pt"):
+                    st.wait_event(self.enc_done)
+                B.he_matmul_batch_host(ctx, c["in_host"], pt, p.m, p.k, p.n, blk, cnt, seed, c["out_host"],
+                                       self.host_ws[k % 2], flags=self.flags | B.HE_ASYNC, stream=st)
+                if pt is not c.get("pt"):  # the next per-step encode reuses pt_tmp
+                    self.torch.cuda.current_stream().wait_stream(st)
+                k += 1
             else:
                 B.he_matmul_batch(ctx, c["ct_in"], pt, p.m, p.k, p.n, blk, cnt, seed, c["out"], self.ws,
                                   flags=self.flags)
+        if host:
+            for st in self.host_streams:
+                st.synchronize()
 
     def algorithmic_bytes(self):
         """Per kernel family: algorithmic HBM bytes of one step (reads + writes, 8-byte words)."""

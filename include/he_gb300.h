@@ -66,6 +66,12 @@ extern "C" {
  * all) and c0 is computed only there.  Needs a power-of-two k_b.  The kept words
  * equal the corresponding words of the full output bit for bit. */
 #define HE_DROP_C0 1u
+/* he_matmul_host only: return once the copies and kernels are enqueued on `stream`
+ * instead of waiting for ct_out_host; the caller synchronizes the stream before
+ * reading ct_out_host (and must keep both host buffers and the workspace alive until
+ * then).  With pinned host buffers this lets calls on different streams overlap their
+ * transfers with each other's kernels. */
+#define HE_ASYNC 2u
 
 typedef struct he_ctx he_ctx;
 
@@ -194,11 +200,20 @@ HE_API int he_matmul(he_ctx* ctx, const uint64_t* ct_in, const uint64_t* pt, uin
 /* The same product with the ciphertexts in HOST memory (pinned memory gives
  * asynchronous copies): ct_in_host is copied to the device workspace, the
  * product is computed as by he_matmul, and the output is copied back to
- * ct_out_host; the call returns once ct_out_host holds the result.
+ * ct_out_host; the call returns once ct_out_host holds the result (or, with HE_ASYNC,
+ * once everything is enqueued on `stream`).
  * workspace: device, >= he_sizes().workspace_bytes + 8 * (in_words + out_words). */
 HE_API int he_matmul_host(he_ctx* ctx, const uint64_t* ct_in_host, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
                    const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out_host, void* workspace,
                    size_t workspace_bytes, void* stream);
+
+/* he_matmul_batch with the ciphertexts in HOST memory (layouts as he_matmul_batch):
+ * copies in, computes, copies out, as he_matmul_host does for one product.
+ * workspace: device, >= batch times what he_matmul_host needs for one product. */
+HE_API int he_matmul_batch_host(he_ctx* ctx, const uint64_t* ct_in_host, const uint64_t* pt, uint32_t m, uint32_t k,
+                                uint32_t n, const he_blocking* blk, uint32_t batch, uint64_t mask_seed,
+                                uint32_t flags, uint64_t* ct_out_host, void* workspace, size_t workspace_bytes,
+                                void* stream);
 
 /* `batch` independent products of one shape and blocking in one set of launches (e.g.
  * the per-head attention cross terms of a layer).  Item b reads ct_in + b * in_words and

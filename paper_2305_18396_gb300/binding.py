@@ -19,6 +19,7 @@ from . import build as _build
 HE_OK, HE_EINVAL, HE_ENOMEM, HE_ECUDA, HE_ETIMEOUT, HE_ENOISE = range(6)
 HE_FLAGS_NONE = 0
 HE_DROP_C0 = 1
+HE_ASYNC = 2
 _NAMES = {1: "HE_EINVAL", 2: "HE_ENOMEM", 3: "HE_ECUDA", 4: "HE_ETIMEOUT", 5: "HE_ENOISE"}
 
 
@@ -83,6 +84,7 @@ def _load():
         "he_encode_weights": (ctypes.c_int, [P, P, u32, u32, pB, P, P]),
         "he_matmul": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u64, u32, P, P, sz, P]),
         "he_matmul_host": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u64, u32, P, P, sz, P]),
+        "he_matmul_batch_host": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u32, u64, u32, P, P, sz, P]),
         "he_matmul_noalloc": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u64, u32, P, P]),
         "he_matmul_batch": (ctypes.c_int, [P, P, P, u32, u32, u32, pB, u32, u64, u32, P, P, sz, P]),
         "he_matmul_multi": (ctypes.c_int, [P, u32, ctypes.POINTER(Product), P, sz, P]),
@@ -357,6 +359,21 @@ def he_expand_compact(ctx, ct_compact, cnt, k_b, ct_full=None, stream=None):
     ct_full = ctx.empty(words) if ct_full is None else ctx._dev(ct_full, words, "ct_full")
     _check(lib.he_expand_compact(ctx.h, _ptr(ct_compact), cnt, k_b, _ptr(ct_full), _stream(stream)))
     return ct_full
+
+
+def he_matmul_batch_host(ctx, ct_in_host, pt, m, k, n, blk, batch, mask_seed, ct_out_host, workspace,
+                         flags=HE_FLAGS_NONE, stream=None):
+    """Batched products with host (pinned) input/output buffers; see he_matmul_host."""
+    si = ctx.sizes(m, k, n, blk)
+    ow, _ = _out_ws(si, flags)
+    for t, w, name in ((ct_in_host, batch * si["in_words"], "ct_in_host"), (ct_out_host, batch * ow, "ct_out_host")):
+        if t.device.type != "cpu" or not t.is_contiguous() or t.numel() < w:
+            raise ValueError(f"{name} must be a contiguous CPU tensor of >= {w} words")
+    ctx._dev(workspace, batch * matmul_host_workspace_words(ctx, m, k, n, blk, flags), "workspace")
+    _check(lib.he_matmul_batch_host(ctx.h, _ptr(ct_in_host), _ptr(ctx._dev(pt, batch * si["pt_words"], "pt")), m, k,
+                                    n, _blk(blk), batch, mask_seed, flags, _ptr(ct_out_host), _ptr(workspace),
+                                    workspace.numel() * 8, _stream(stream)))
+    return ct_out_host
 
 
 def he_unmask(ctx, mask_seed, m, n, blk, share=None, stream=None):

@@ -548,7 +548,7 @@ static int matmul_checks(he_ctx* c, uint32_t m, uint32_t k, uint32_t n, const he
                          he_size_info* si) {
   if (!c) return fail(HE_EINVAL, "ctx is NULL");
   if (int r = check_blk(c, blk)) return r;
-  if (flags & ~(uint32_t)HE_DROP_C0) return fail(HE_EINVAL, "unknown flags");
+  if (flags & ~(uint32_t)(HE_DROP_C0 | HE_ASYNC)) return fail(HE_EINVAL, "unknown flags");
   if ((flags & HE_DROP_C0) && !pow2(blk->k_b)) return fail(HE_EINVAL, "HE_DROP_C0 needs a power-of-two k_b");
   he_sizes(c, m, k, n, blk, si);
   if (si->nJ > 4096) return fail(HE_EINVAL, "at most 4096 k-blocks (k / k_b) per product");
@@ -559,6 +559,7 @@ int he_matmul(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, 
               const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out, void* workspace,
               size_t workspace_bytes, void* stream) {
   he_size_info si;
+  if (flags & HE_ASYNC) return fail(HE_EINVAL, "HE_ASYNC applies to he_matmul_host only");
   if (int r = matmul_checks(c, m, k, n, blk, flags, &si)) return r;
   if (!m || !k || !n) return HE_OK;
   if (!ct_in || !pt || !ct_out || !workspace) return fail(HE_EINVAL, "NULL buffer");
@@ -572,6 +573,7 @@ int he_matmul_batch(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32
                     const he_blocking* blk, uint32_t batch, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out,
                     void* workspace, size_t workspace_bytes, void* stream) {
   he_size_info si;
+  if (flags & HE_ASYNC) return fail(HE_EINVAL, "HE_ASYNC applies to he_matmul_host only");
   if (int r = matmul_checks(c, m, k, n, blk, flags, &si)) return r;
   if (!m || !k || !n || !batch) return HE_OK;
   if ((u64)batch * c->C.L > 65535) return fail(HE_EINVAL, "batch * L must be <= 65535");
@@ -583,29 +585,37 @@ int he_matmul_batch(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32
   return matmul_device(c, ct_in, pt, m, k, n, blk, batch, mask_seed, flags, ct_out, workspace, (cudaStream_t)stream);
 }
 
-int he_matmul_host(he_ctx* c, const uint64_t* ct_in_host, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
-                   const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out_host,
-                   void* workspace, size_t workspace_bytes, void* stream) {
+int he_matmul_batch_host(he_ctx* c, const uint64_t* ct_in_host, const uint64_t* pt, uint32_t m, uint32_t k,
+                         uint32_t n, const he_blocking* blk, uint32_t batch, uint64_t mask_seed, uint32_t flags,
+                         uint64_t* ct_out_host, void* workspace, size_t workspace_bytes, void* stream) {
   he_size_info si;
   if (int r = matmul_checks(c, m, k, n, blk, flags, &si)) return r;
-  if (!m || !k || !n) return HE_OK;
+  if (!m || !k || !n || !batch) return HE_OK;
+  if ((u64)batch * c->C.L > 65535) return fail(HE_EINVAL, "batch * L must be <= 65535");
   if (!ct_in_host || !pt || !ct_out_host || !workspace) return fail(HE_EINVAL, "NULL buffer");
   const bool compact = flags & HE_DROP_C0;
-  const u64 ws_need = compact ? si.workspace_bytes_compact : si.workspace_bytes;
-  const u64 out_words = compact ? si.out_words_compact : si.out_words;
-  const u64 need = ws_need + 8 * (si.in_words + out_words);
+  const u64 ws_need = (u64)batch * (compact ? si.workspace_bytes_compact : si.workspace_bytes);
+  const u64 in_words = (u64)batch * si.in_words, out_words = (u64)batch * (compact ? si.out_words_compact : si.out_words);
+  const u64 need = ws_need + 8 * (in_words + out_words);
   if (workspace_bytes < need) return fail(HE_ENOMEM, "workspace smaller than he_matmul_host needs");
   if (int r = set_device(c)) return r;
   cudaStream_t st = (cudaStream_t)stream;
   u64* d_in = (u64*)((char*)workspace + ws_need);
-  u64* d_out = d_in + si.in_words;
-  cudaError_t e = cudaMemcpyAsync(d_in, ct_in_host, si.in_words * 8, cudaMemcpyHostToDevice, st);
+  u64* d_out = d_in + in_words;
+  cudaError_t e = cudaMemcpyAsync(d_in, ct_in_host, in_words * 8, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "matmul_host: upload");
-  if (int r = matmul_device(c, d_in, pt, m, k, n, blk, 1, mask_seed, flags, d_out, workspace, st)) return r;
+  if (int r = matmul_device(c, d_in, pt, m, k, n, blk, batch, mask_seed, flags, d_out, workspace, st)) return r;
   e = cudaMemcpyAsync(ct_out_host, d_out, out_words * 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && !(flags & HE_ASYNC)) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "matmul_host: download");
   return HE_OK;
+}
+
+int he_matmul_host(he_ctx* c, const uint64_t* ct_in_host, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
+                   const he_blocking* blk, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out_host,
+                   void* workspace, size_t workspace_bytes, void* stream) {
+  return he_matmul_batch_host(c, ct_in_host, pt, m, k, n, blk, 1, mask_seed, flags, ct_out_host, workspace,
+                              workspace_bytes, stream);
 }
 
 int he_matmul_noalloc(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,

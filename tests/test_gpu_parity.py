@@ -407,3 +407,33 @@ def test_matmul_multi_equals_single_calls(B, N, L):
     assert np.array_equal(to_np(items[0]["ct_in"]), ct_or.reshape(-1))
     want = O.matmul(P, ct_or, W, m, k, n, blk, 600)
     assert np.array_equal(to_np(items[0]["ct_out"]), want.reshape(-1))
+
+
+def test_matmul_host_async_two_streams(B):
+    """HE_ASYNC host-buffer calls on two streams (own workspaces) equal the device-buffer path."""
+    ctx, P = ctx_for(B, 4096, 2)
+    sk = B.he_keygen(ctx, 3)
+    outs, refs, keep = [], [], []
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for i, (m, k, n) in enumerate([(16, 64, 64), (40, 96, 48), (8, 256, 32)]):
+        blk = ctx.default_blocking(m, k, n)
+        X = S.uniform_share((m, k), 900 + i)
+        W = S.fixed_point_weights((k, n), 910 + i)
+        ct = B.he_encrypt(ctx, sk, B.he_pack_input(ctx, to_dev(X), m, k, blk), 920 + i)
+        pt = B.he_encode_weights(ctx, to_dev(W), k, n, blk)
+        flags = B.HE_DROP_C0 if i % 2 else B.HE_FLAGS_NONE
+        refs.append(to_np(B.he_matmul(ctx, ct, pt, m, k, n, blk, 930 + i, flags=flags)))
+        si = ctx.sizes(m, k, n, blk)
+        ow = si["out_words_compact"] if flags else si["out_words"]
+        host_in = ct.cpu().pin_memory()
+        host_out = torch.zeros(ow, dtype=torch.int64).pin_memory()
+        ws = ctx.empty(B.matmul_host_workspace_words(ctx, m, k, n, blk, flags))
+        torch.cuda.synchronize()
+        B.he_matmul_host(ctx, host_in, pt, m, k, n, blk, 930 + i, host_out, ws, flags=flags | B.HE_ASYNC,
+                         stream=streams[i % 2])
+        outs.append(host_out)
+        keep += [host_in, ws]
+    for s_ in streams:
+        s_.synchronize()
+    for o, r in zip(outs, refs):
+        assert np.array_equal(o.numpy().view(np.uint64), r)
