@@ -53,6 +53,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
+// Plain arrival (count 1) on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Warp-uniform bounded wait: every lane polls the barrier (so every lane observes the
+// completed phase), the warp leaves together once all lanes saw it, or together with
+// `false` once any lane's clock passes the limit.  Call with all 32 lanes.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = global_timer_ns();
+  while (true) {
+    const bool ok = mbar_try_wait(bar, parity);
+    if (__all_sync(0xffffffffu, ok)) return true;
+    const bool late = global_timer_ns() - t0 > limit_ns;
+    if (__any_sync(0xffffffffu, late)) return false;
+  }
+}
+
 // Order this thread's earlier generic-proxy shared-memory accesses before later
 // async-proxy ones (bulk copies into a buffer the block just finished reading).
 __device__ __forceinline__ void fence_proxy_async_smem() {

@@ -362,6 +362,34 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_intt_mask_t(u64* out, u64
   });
 }
 
+// Warp-specialized form (mac_tile_ws): M::kThreads consumer threads + one producer warp.
+template <class M, int MINB>
+__global__ void __launch_bounds__(M::kThreads + 32, MINB) k_mac_ws_t(const u64* __restrict__ ctN,
+                                                                     const u64* __restrict__ pt, OutPlace out, u32 nI,
+                                                                     u32 nJ, u32 nLb, u32 tilesR, int* err,
+                                                                     const __grid_constant__ Consts C) {
+  extern __shared__ __align__(128) u64 sm[];
+  const u32 chunks = C.N >> 5;
+  const u32 chunk = blockIdx.x % chunks;
+  const u32 tile = blockIdx.x / chunks;
+  const u32 r0 = (tile % tilesR) * M::kRows, c0 = (tile / tilesR) * M::kCols;
+  const u32 l = blockIdx.y % C.L;
+  const u64 item = blockIdx.y / C.L;
+  const u64 per_in = (u64)nLb * nJ * 2 * C.L * C.N, per_pt = (u64)nI * nJ * C.L * C.N;
+  mac_tile_ws<M>(ctN + item * per_in, pt + item * per_pt, out, item * ((u64)nLb * nI), nI, nJ, nLb, r0, c0, chunk, l,
+                 err, C, sm);
+}
+
+template <class M, int MINB>
+cudaError_t launch_mac_ws_cfg(const Consts& C, const u64* ctN, const u64* pt, OutPlace out, u32 nI, u32 nJ, u32 nLb,
+                              u32 batch, int* err, cudaStream_t st) {
+  const u32 tilesR = (2 * nLb + M::kRows - 1) / M::kRows, tilesC = (nI + M::kCols - 1) / M::kCols;
+  if ((u64)tilesR * tilesC * nJ * batch == 0) return cudaGetLastError();
+  dim3 grid((unsigned)((u64)(C.N >> 5) * tilesR * tilesC), C.L * batch);
+  k_mac_ws_t<M, MINB><<<grid, M::kThreads + 32, M::kSmemBytes, st>>>(ctN, pt, out, nI, nJ, nLb, tilesR, err, C);
+  return cudaGetLastError();
+}
+
 // Slot-wise multiply-accumulate of one product or a same-shape batch: the block body is
 // mac_tile (mac.cuh); grid x = (chunk group, output tile), grid y = (batch item, prime).
 template <class M, int MINB>
@@ -525,6 +553,7 @@ cudaError_t configure_kernels(const Consts&) {
   set((const void*)k_encode_weights, one);
   set((const void*)k_intt_mask, one);
   set((const void*)k_mac_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
+  set((const void*)k_mac_ws_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
 #define HE_SET_T(LOGN)                                                                             \
   set((const void*)k_ntt_forward_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
   set((const void*)k_ntt_inverse_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
@@ -640,7 +669,7 @@ cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out0
   o.base[1] = out1;
   o.ct_stride[0] = stride0;
   o.ct_stride[1] = stride1;
-  return launch_mac_cfg<MacProd, kMacMinBlocks>(C, ctN, pt, o, nI, nJ, nLb, batch, err, st);
+  return launch_mac_ws_cfg<MacProd, kMacMinBlocks>(C, ctN, pt, o, nI, nJ, nLb, batch, err, st);
 }
 
 cudaError_t launch_ntt_forward_mm(const Consts& C, const u64* ct_in, u64* ctN, u32 nJ, u32 nLb, u32 batch,

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kThreadsSmall) k_fwd_multi_small(const __grid_
 }
 
 template <class M, int MINB>
-__global__ void __launch_bounds__(M::kThreads, MINB) k_mac_multi_t(const __grid_constant__ MultiTable T, int* err,
+__global__ void __launch_bounds__(M::kThreads + 32, MINB) k_mac_multi_t(const __grid_constant__ MultiTable T, int* err,
                                                                    const __grid_constant__ Consts C) {
   extern __shared__ __align__(128) u64 sm[];
   const u32 i = find_item(T, blockIdx.x, [](const MultiItem& x) { return x.mac_begin; });
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(M::kThreads, MINB) k_mac_multi_t(const __grid_
     out.base[1] = it.out + L * N;
     out.ct_stride[0] = out.ct_stride[1] = 2 * L * N;
   }
-  mac_tile<M>(it.ctN, it.pt, out, 0, it.nI, it.nJ, it.nLb, r0, c0, chunk, 1, l, err, C, sm);
+  mac_tile_ws<M>(it.ctN, it.pt, out, 0, it.nI, it.nJ, it.nLb, r0, c0, chunk, l, err, C, sm);
 }
 
 // Inverse NTT: compact products transform their c1 polynomials in place; full products
@@ -211,8 +211,9 @@ cudaError_t launch_fwd_multi(const Consts& C, const MultiTable& T, u64 blocks, c
 }
 
 cudaError_t launch_mac_multi(const Consts& C, const MultiTable& T, u64 blocks, int* err, cudaStream_t st) {
-  if (blocks) k_mac_multi_t<MacProd, kMacMinBlocks><<<(unsigned)blocks, MacProd::kThreads, MacProd::kSmemBytes, st>>>(
-      T, err, C);
+  if (blocks)
+    k_mac_multi_t<MacProd, kMacMinBlocks><<<(unsigned)blocks, MacProd::kThreads + 32, MacProd::kSmemBytes, st>>>(
+        T, err, C);
   return cudaGetLastError();
 }
 
