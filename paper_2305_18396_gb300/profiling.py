@@ -1,0 +1,102 @@
+"""Profiling drivers: small, self-contained invocations of the product for `ncu` captures,
+and a reader for the per-launch CSV that `ncu --metrics gpu__time_duration.sum --csv`
+writes.
+
+    python -m paper_2305_18396_gb300.profiling case M K N [--repeat R] [--full-c0]
+    python -m paper_2305_18396_gb300.profiling launches launches.csv
+
+`case` runs one Pi_MatMul (Algorithm 1) of an M x K share against a K x N weight matrix
+at N=4096, L=2 through the public binding: key generation, packing, encryption and
+weight encoding once, then R products (compact output, Sec. 3.1.3, unless --full-c0),
+then a device status check.  The products are the launches worth capturing; everything
+before them is set-up.
+
+`launches` aggregates an ncu launch list by kernel: launches, total device time, share.
+"""
+import argparse
+import collections
+import csv
+import sys
+
+import numpy as np
+
+
+def run_case(m, k, n, repeat=3, compact=True, logN=12, L=2):
+    import torch
+
+    from . import binding as B
+    from . import synthetic as S
+
+    ctx = B.Context(1 << logN, L)
+    blk = ctx.default_blocking(m, k, n)
+    X = torch.from_numpy(S.uniform_share((m, k), 1).view(np.int64).reshape(-1)).to(ctx.device)
+    W = torch.from_numpy(S.fixed_point_weights((k, n), 2).view(np.int64).reshape(-1)).to(ctx.device)
+    sk = B.he_keygen(ctx, 3)
+    ct = B.he_encrypt(ctx, sk, B.he_pack_input(ctx, X, m, k, blk), 4)
+    pt = B.he_encode_weights(ctx, W, k, n, blk)
+    flags = B.HE_DROP_C0 if compact else 0
+    out = None
+    for i in range(repeat):
+        out = B.he_matmul(ctx, ct, pt, m, k, n, blk, 5 + i, ct_out=out, flags=flags)
+    torch.cuda.synchronize()
+    B.he_device_status(ctx)
+    return blk, ctx.sizes(m, k, n, blk)
+
+
+def summarize_launches(path, skip_prefixes=(), skip_first=0, metric="gpu__time_duration.sum"):
+    """Per kernel: (launches, total) of `metric` from an ncu --csv launch list (durations in
+    microseconds), leaving out the first `skip_first` launches and kernels named by a prefix."""
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    hdr = None
+    with open(path, newline="") as f:
+        for r in csv.reader(f):
+            if "Kernel Name" in r:
+                hdr = r
+                continue
+            if not hdr or len(r) != len(hdr):
+                continue
+            d = dict(zip(hdr, r))
+            if d.get("Metric Name") != metric or int(d["ID"]) < skip_first:
+                continue
+            v, u = float(d["Metric Value"].replace(",", "")), d["Metric Unit"]
+            if metric == "gpu__time_duration.sum":
+                v = v / 1e3 if u in ("ns", "nsecond") else v * 1e3 if u in ("ms", "msecond") else v
+            elif u.endswith("byte"):
+                v *= {"Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(u, 1.0)
+            name = d["Kernel Name"].split("(")[0].replace("void ", "").strip()
+            if any(name.startswith(p) for p in skip_prefixes):
+                continue
+            agg[name][0] += 1
+            agg[name][1] += v
+    return dict(agg)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    c = sub.add_parser("case")
+    c.add_argument("m", type=int)
+    c.add_argument("k", type=int)
+    c.add_argument("n", type=int)
+    c.add_argument("--repeat", type=int, default=3)
+    c.add_argument("--full-c0", action="store_true")
+    s = sub.add_parser("launches")
+    s.add_argument("csv")
+    s.add_argument("--skip", action="append", default=[], help="kernel-name prefix to leave out")
+    s.add_argument("--skip-first", type=int, default=0, help="leave out the first launches (set-up)")
+    s.add_argument("--metric", default="gpu__time_duration.sum")
+    a = ap.parse_args(argv)
+    if a.cmd == "case":
+        blk, si = run_case(a.m, a.k, a.n, a.repeat, not a.full_c0)
+        print("ok", blk, si)
+    else:
+        agg = summarize_launches(a.csv, tuple(a.skip), a.skip_first, a.metric)
+        tot = sum(v[1] for v in agg.values()) or 1.0
+        print(f"| kernel | launches | total {a.metric} | per launch | share |\n|---|---|---|---|---|")
+        for name, (cnt, x) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+            print(f"| `{name}` | {cnt} | {x:.1f} | {x / cnt:.1f} | {100 * x / tot:.1f}% |")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
