@@ -163,13 +163,14 @@ def keygen(P, seed):
     return s
 
 
-def encrypt(P, s, plain, seed):
-    """plain [cnt][N] in Z_t -> ciphertexts [cnt][2][L][N]."""
+def encrypt(P, s, plain, seed, obj0=0):
+    """plain [cnt][N] in Z_t -> ciphertexts [cnt][2][L][N]; ciphertext j is object obj0 + j
+    of the seed's random streams (so a slice of a larger batch can be encrypted alone)."""
     plain = np.ascontiguousarray(plain, dtype=np.uint64)
     cnt = plain.shape[0]
     ct = np.zeros((cnt, 2, P.L, P.N), dtype=np.uint64)
     s = np.ascontiguousarray(s, dtype=np.int64)
-    lib.or_encrypt(P.N, P.L, p64(P.q_arr), p64(P.psi_arr), P.log2t, pi64(s), p64(plain), cnt, seed, p64(ct))
+    lib.or_encrypt(P.N, P.L, p64(P.q_arr), p64(P.psi_arr), P.log2t, pi64(s), p64(plain), cnt, obj0, seed, p64(ct))
     return ct
 
 
@@ -225,18 +226,25 @@ def matmul(P, ct_in, W, m, k, n, blk, mask_seed, sel=None):
     Returns [len(sel)][2][L][N] in coefficient form."""
     check_blocking(P.N, blk)
     nI, nJ, nLb = blocks(m, k, n, blk)
-    ct_in = np.ascontiguousarray(ct_in, dtype=np.uint64)
-    if ct_in.shape != (nLb * nJ, 2, P.L, P.N):
-        raise ValueError(f"input ciphertexts must be {(nLb * nJ, 2, P.L, P.N)}, got {ct_in.shape}")
     sel = list(range(nLb * nI)) if sel is None else [int(o) for o in sel]
     I_list = sorted({o % nI for o in sel})
     Lb_list = sorted({o // nI for o in sel})
     I_pos = {I: p for p, I in enumerate(I_list)}
     Lb_pos = {Lb: p for p, Lb in enumerate(Lb_list)}
+    if isinstance(ct_in, dict):  # only the input rows the selected outputs read: {Lb: [nJ][2][L][N]}
+        cts = np.stack([np.ascontiguousarray(ct_in[Lb], dtype=np.uint64) for Lb in Lb_list])
+        if cts.shape[1:] != (nJ, 2, P.L, P.N):
+            raise ValueError(f"input rows must be {(nJ, 2, P.L, P.N)}, got {cts.shape[1:]}")
+    else:
+        ct_in = np.ascontiguousarray(ct_in, dtype=np.uint64)
+        if ct_in.shape != (nLb * nJ, 2, P.L, P.N):
+            raise ValueError(f"input ciphertexts must be {(nLb * nJ, 2, P.L, P.N)}, got {ct_in.shape}")
+        cts = ct_in.reshape(nLb, nJ, 2, P.L, P.N)[Lb_list]
 
-    pt_t = encode_weights_coeff(W, blk, P.N)[I_list]                  # [nI'][nJ][N]
+    # pi_A block I reads only columns I n_b .. I n_b + n_b - 1 of W: encode those alone
+    n_b = blk[2]
+    pt_t = np.concatenate([encode_weights_coeff(W[:, I * n_b:(I + 1) * n_b], blk, P.N) for I in I_list])
     pt_ntt = ntt_forward(P, centred_lift_residues(P, pt_t))          # [nI'][nJ][L][N]
-    cts = ct_in.reshape(nLb, nJ, 2, P.L, P.N)[Lb_list]
     ct_ntt = ntt_forward(P, cts)                                     # [nLb'][nJ][2][L][N]
 
     sel_local = np.array([Lb_pos[o // nI] * len(I_list) + I_pos[o % nI] for o in sel], dtype=np.uint32)

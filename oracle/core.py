@@ -49,7 +49,7 @@ def _load():
         "or_gauss_cdt": (None, [_u64p]),
         "or_gauss_bound": (u32, []),
         "or_delta_residues": (None, [_u64p, u32, u32, u64, _u64p]),
-        "or_encrypt": (None, [u32, u32, _u64p, _u64p, u32, _i64p, _u64p, u32, u64, _u64p]),
+        "or_encrypt": (None, [u32, u32, _u64p, _u64p, u32, _i64p, _u64p, u32, u32, u64, _u64p]),
         "or_decrypt_residues": (None, [u32, u32, _u64p, _u64p, _i64p, _u64p, u32, _u64p]),
         "or_ctpt_accumulate": (None, [u32, u32, _u64p, _u64p, _u64p, u32, u32, u32, _u32p, u32, _u64p]),
         "or_apply_mask": (None, [u32, u32, _u64p, u32, u64, _u32p, u32, _u64p]),

@@ -320,7 +320,7 @@ void or_delta_residues(const u64* q, u32 L, u32 log2t, u64 m, u64* out) {
 /* ------------------------------------------------------------------ */
 
 void or_encrypt(u32 N, u32 L, const u64* q, const u64* psi, u32 log2t, const i64* s,
-                const u64* m, u32 cnt, u64 seed, u64* ct) {
+                const u64* m, u32 cnt, u32 obj0, u64 seed, u64* ct) {
 #pragma omp parallel for schedule(dynamic)
   for (long j = 0; j < (long)cnt; j++) {
     i64* e = (i64*)malloc(sizeof(i64) * N);
@@ -328,11 +328,12 @@ void or_encrypt(u32 N, u32 L, const u64* q, const u64* psi, u32 log2t, const i64
     u64* sl = (u64*)malloc(sizeof(u64) * N);
     u64* as = (u64*)malloc(sizeof(u64) * N);
     u64 delta[OR_MAX_PRIMES];
-    or_sample_gauss(seed, (u32)j, N, e);
+    const u32 obj = obj0 + (u32)j; /* ciphertext index: the object word of every draw */
+    or_sample_gauss(seed, obj, N, e);
     for (u32 l = 0; l < L; l++) {
       u64* c0 = ct + (((size_t)j * 2 + 0) * L + l) * N;
       u64* c1 = ct + (((size_t)j * 2 + 1) * L + l) * N;
-      or_sample_uniform(seed, (u32)j, l, q[l], N, a);
+      or_sample_uniform(seed, obj, l, q[l], N, a);
       for (u32 i = 0; i < N; i++) sl[i] = reduce_signed(s[i], q[l]);
       negacyclic_mul_ntt(a, sl, as, N, q[l], psi[l]);
       for (u32 i = 0; i < N; i++) {

@@ -416,3 +416,35 @@ def test_matmul_sampled_outputs_equal_full():
     sel = [0, 4, 7, full.shape[0] - 1]
     part = O.matmul(P, ct_in, W, m, k, n, blk, 5, sel=sel)
     assert np.array_equal(part, full[sel])
+
+
+def test_encrypt_slice_at_object_offset_equals_batch_rows():
+    """Ciphertext j of a batch depends only on (seed, j): encrypting rows a..b alone at
+    object offset a gives exactly rows a..b of the whole batch."""
+    P = O.Params(256, 2)
+    s = O.keygen(P, 3)
+    m = S.uniform_plaintexts(7, P.N, 12)
+    full = O.encrypt(P, s, m, 9)
+    part = O.encrypt(P, s, m[3:6], 9, obj0=3)
+    assert np.array_equal(part, full[3:6])
+    assert not np.array_equal(O.encrypt(P, s, m[3:6], 9), full[3:6])
+
+
+def test_matmul_from_selected_input_rows_equals_full():
+    """The sampled product reads only the input rows Lb of its outputs; given just those rows
+    (each encrypted alone at its object offset) it equals the full evaluation."""
+    P = O.Params(1024, 2)
+    m, k, n, blk = 13, 20, 11, (4, 8, 4)
+    X = S.uniform_share((m, k), 1)
+    W = S.fixed_point_weights((k, n), 2)
+    s = O.keygen(P, 3)
+    nI, nJ, nLb = O.blocks(m, k, n, blk)
+    full_in = O.encrypt(P, s, O.pack_input(X, blk, P.N), 4)
+    full = O.matmul(P, full_in, W, m, k, n, blk, 5)
+    sel = [1, nI * 2 + 2, nI * nLb - 1]
+    rows = {}
+    for Lb in sorted({o // nI for o in sel}):
+        polys = O.pack_input(X[Lb * blk[0]:(Lb + 1) * blk[0]], blk, P.N)
+        rows[Lb] = O.encrypt(P, s, polys, 4, obj0=Lb * nJ)
+        assert np.array_equal(rows[Lb], full_in[Lb * nJ:(Lb + 1) * nJ])
+    assert np.array_equal(O.matmul(P, rows, W, m, k, n, blk, 5, sel=sel), full[sel])
