@@ -9,10 +9,16 @@ form; requests arrive over time and are
 * admitted in arrival order while the device-memory footprint of the admitted but
   unfinished requests (their output ciphertexts plus the workspace of their launch)
   stays within a budget;
-* launched as soon as a launch slot (a CUDA stream) is free: every admitted request
-  not yet launched goes into one multi-product launch (he_matmul_multi, up to 64
-  products of any shapes), so requests that arrive while others are on the GPU join
-  the next launch and their work overlaps on the device with the running one;
+* launched as soon as a launch slot is free: the oldest admitted request, and after it
+  the admitted requests that fit a work cap (their estimated device time, summed, at
+  most `batch_work_factor` above the oldest's, or `batch_floor_ms`), go into one
+  multi-product launch (he_matmul_multi, up to 64 products of any shapes), so requests
+  that arrive while others are on the GPU join the next launch and their work overlaps
+  on the device with the running one.  The cap keeps a long request from being delayed
+  by the requests that arrived after it;
+* run on a stream whose CUDA priority is below that of every launch still in flight
+  (the highest when the device is idle): the oldest launch keeps the SMs it can fill,
+  later launches take the SMs it leaves idle (its tail, its small grids);
 * completed when their launch's event fires (latency = completion - arrival).
 
 `run_per_request` is the plain path it is compared against: one he_matmul per request,
@@ -54,15 +60,23 @@ class Request:
     launched: float = math.nan
     done: float = math.nan
     footprint: int = 0
+    est: float = 0.0  # estimated device seconds inside a multi-product launch
+
+
+# Device-time estimate of one product inside a multi-product launch: a fixed part per
+# product plus its plaintext MACs at the rate the BERT-shaped products reach.
+EST_FIXED_S = 20e-6
+EST_MACS_PER_S = 2.5e11
 
 
 @dataclass(order=True)
 class _InFlight:
     start: float
-    slot: int = field(compare=False)
+    level: int = field(compare=False)
     event: object = field(compare=False)
     reqs: list = field(compare=False)
     ws: torch.Tensor = field(compare=False)
+    stream: object = field(compare=False)
 
 
 def request_footprint(ctx, model, m, flags):
@@ -73,18 +87,34 @@ def request_footprint(ctx, model, m, flags):
     return 8 * out + ws + 512
 
 
+def priority_levels(n=4):
+    """Up to `n` CUDA stream priorities, highest first (lower number = higher priority)."""
+    least, greatest = torch.cuda.Stream.priority_range()
+    return [p for p in range(greatest, least + 1)][:n] or [0]
+
+
 class Server:
-    def __init__(self, ctx, models, flags=B.HE_DROP_C0, hbm_budget=32 << 30, slots=2, max_batch=8):
+    def __init__(self, ctx, models, flags=B.HE_DROP_C0, hbm_budget=32 << 30, slots=2, max_batch=8,
+                 batch_work_factor=0.25, batch_floor_ms=1.0, priorities=True, keep_outputs=True):
         self.ctx, self.models, self.flags = ctx, {mm.name: mm for mm in models}, flags
         self.budget, self.max_batch = hbm_budget, min(max_batch, 64)
-        self.streams = [torch.cuda.Stream(device=ctx.device) for _ in range(slots)]
-        self.free_slots = list(range(slots))
+        self.slots = slots
+        self.work_factor, self.floor_s = batch_work_factor, batch_floor_ms * 1e-3
+        self.keep = keep_outputs
+        levels = priority_levels() if priorities else [0]
+        # a fixed set of streams, `slots` per priority level; buffers are allocated on the
+        # stream that builds the server and handed to a launch stream with record_stream, so
+        # the caching allocator keeps one pool instead of one per launch stream
+        self.streams = [[torch.cuda.Stream(device=ctx.device, priority=p) for _ in range(slots)] for p in levels]
+        self.alloc_stream = torch.cuda.current_stream(ctx.device)
         self.queue, self.admitted, self.inflight, self.done = [], [], [], []
         self.in_use = 0
         self.launches = 0
 
     def submit(self, req):
-        req.footprint = request_footprint(self.ctx, self.models[req.model], req.m, self.flags)
+        mm = self.models[req.model]
+        req.footprint = request_footprint(self.ctx, mm, req.m, self.flags)
+        req.est = EST_FIXED_S + req.m * mm.k * mm.n / EST_MACS_PER_S
         if req.footprint > self.budget:
             raise ValueError(f"request {req.rid} needs {req.footprint} bytes, more than the whole budget")
         self.queue.append(req)
@@ -95,28 +125,46 @@ class Server:
             self.in_use += r.footprint
             self.admitted.append(r)
 
+    def _take_batch(self):
+        """The oldest admitted request plus, in arrival order, those that fit the work cap."""
+        first = self.admitted[0]
+        cap = max(self.floor_s, first.est * (1.0 + self.work_factor)) if self.work_factor is not None else math.inf
+        batch, rest, total = [first], [], first.est
+        for r in self.admitted[1:]:
+            if len(batch) < self.max_batch and total + r.est <= cap:
+                batch.append(r)
+                total += r.est
+            else:
+                rest.append(r)
+        self.admitted = rest
+        return batch
+
     def _launch(self, now):
-        if not self.admitted or not self.free_slots:
+        if not self.admitted or len(self.inflight) >= self.slots:
             return
-        batch, self.admitted = self.admitted[:self.max_batch], self.admitted[self.max_batch:]
-        slot = self.free_slots.pop(0)
-        stream = self.streams[slot]
+        batch = self._take_batch()
+        # below every launch in flight, so the oldest work keeps priority on the SMs
+        level = min(max((f.level for f in self.inflight), default=-1) + 1, len(self.streams) - 1)
+        busy = {id(f.stream) for f in self.inflight}
+        stream = next(st for st in self.streams[level] if id(st) not in busy)
         items = []
-        with torch.cuda.stream(stream):
-            for r in batch:
-                mm = self.models[r.model]
-                si = self.ctx.sizes(r.m, mm.k, mm.n, mm.blk)
-                ow = si["out_words_compact"] if self.flags else si["out_words"]
-                r.out = self.ctx.empty(ow)
-                items.append(dict(ct_in=mm.ct_pool, pt=mm.pt, ct_out=r.out, m=r.m, k=mm.k, n=mm.n, blk=mm.blk,
-                                  flags=self.flags, mask_seed=r.mask_seed))
-                r.launched = now
-            prods = B.make_products(items)
-            ws = self.ctx.empty(max(B.he_multi_workspace_bytes(self.ctx, prods) // 8 + 1, 1))
-            B.he_matmul_multi(self.ctx, prods, ws, stream=stream)
-            ev = torch.cuda.Event()
-            ev.record(stream)
-        heapq.heappush(self.inflight, _InFlight(now, slot, ev, batch, ws))
+        for r in batch:
+            mm = self.models[r.model]
+            si = self.ctx.sizes(r.m, mm.k, mm.n, mm.blk)
+            ow = si["out_words_compact"] if self.flags else si["out_words"]
+            r.out = self.ctx.empty(ow)
+            r.out.record_stream(stream)
+            items.append(dict(ct_in=mm.ct_pool, pt=mm.pt, ct_out=r.out, m=r.m, k=mm.k, n=mm.n, blk=mm.blk,
+                              flags=self.flags, mask_seed=r.mask_seed))
+            r.launched = now
+        prods = B.make_products(items)
+        ws = self.ctx.empty(max(B.he_multi_workspace_bytes(self.ctx, prods) // 8 + 1, 1))
+        ws.record_stream(stream)
+        stream.wait_stream(self.alloc_stream)  # the buffers' previous users are done
+        B.he_matmul_multi(self.ctx, prods, ws, stream=stream)
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        heapq.heappush(self.inflight, _InFlight(now, level, ev, batch, ws, stream))
         self.launches += 1
 
     def _poll(self, now):
@@ -126,8 +174,9 @@ class Server:
                 for r in f.reqs:
                     r.done = now
                     self.in_use -= r.footprint
+                    if not self.keep:
+                        r.out = None
                     self.done.append(r)
-                self.free_slots.append(f.slot)
             else:
                 still.append(f)
         self.inflight = still
@@ -135,7 +184,8 @@ class Server:
     def pump(self, now):
         self._poll(now)
         self._admit()
-        self._launch(now)
+        while self.admitted and len(self.inflight) < self.slots:
+            self._launch(now)
 
     def idle(self):
         return not (self.queue or self.admitted or self.inflight)
@@ -198,7 +248,7 @@ def run_served(ctx, models, requests, **kw):
     return st, srv.done
 
 
-def run_per_request(ctx, models, requests, flags=B.HE_DROP_C0):
+def run_per_request(ctx, models, requests, flags=B.HE_DROP_C0, keep_outputs=True):
     """The plain path: one he_matmul per request in arrival order on one stream."""
     by = {mm.name: mm for mm in models}
     pending = sorted(requests, key=lambda r: r.arrival)
@@ -215,6 +265,8 @@ def run_per_request(ctx, models, requests, flags=B.HE_DROP_C0):
                                 stream=stream)
         stream.synchronize()
         r.done = time.perf_counter() - t0
+        if not keep_outputs:
+            r.out = None
     wall = time.perf_counter() - t0
     st = _stats(pending, by, wall)
     st["launches"] = len(pending)
