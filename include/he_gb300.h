@@ -131,6 +131,23 @@ HE_API int he_default_blocking(const he_ctx* ctx, uint32_t m, uint32_t k, uint32
 HE_API int he_choose_blocking(uint32_t N, uint32_t L, uint32_t m, uint32_t k, uint32_t n, uint32_t weights_per_call,
                               he_blocking* out);
 
+/* Measured choice of the blocking (an autotuner; the paper has no counterpart).  Takes
+ * the `candidates` cheapest blockings under he_choose_blocking's cost model (0 means 6,
+ * at most 16; with HE_DROP_C0 only power-of-two k_b), times each on pseudo-random inputs
+ * of this shape -- weight encoding (inside the timed region when weights_per_call),
+ * then the product of `batch` (0 means 1) same-shape items with `flags` -- and returns
+ * the fastest in *out and its time per call (ms, best of three after a warm-up) in
+ * *best_ms.  scratch: caller-owned device memory of scratch_bytes; with scratch == NULL
+ * nothing runs and *scratch_needed receives the bytes the largest candidate needs
+ * (scratch_needed may be NULL otherwise).  Synchronizes `stream`.  m, k or n = 0 returns
+ * the model's choice untimed.  The blocking is the wire format: the client must pack
+ * with the one returned.  Errors: HE_EINVAL (bad flags, batch * L > 65535), HE_ENOMEM
+ * (scratch too small), HE_ECUDA, HE_ETIMEOUT. */
+HE_API int he_autotune_blocking(he_ctx* ctx, uint32_t m, uint32_t k, uint32_t n, uint32_t weights_per_call,
+                                uint32_t flags, uint32_t batch, uint32_t candidates, void* scratch,
+                                size_t scratch_bytes, size_t* scratch_needed, he_blocking* out, float* best_ms,
+                                void* stream);
+
 /* ---- test client (Sec. 2.2 BFV; encrypt/decrypt are the client's side) -- */
 
 /* Secret key s with ternary coefficients, coefficient i = (u mod 3) - 1 for the
@@ -277,6 +294,31 @@ HE_API int he_expand_compact(he_ctx* ctx, const uint64_t* ct_compact, uint32_t c
  * server_share: device [m][n] (requires k only through blk->k_b). */
 HE_API int he_unmask(he_ctx* ctx, uint64_t mask_seed, uint32_t m, uint32_t n, const he_blocking* blk, uint64_t* server_share,
               void* stream);
+
+/* ---- server-local share products (Sec. 3.1.1) -------------------------- */
+
+/* The server's own plaintext side of a linear layer.  A fully connected layer gives the
+ * server the share W<x>_0's mask share plus W<x>_1 + b; an attention product gives it
+ * its cross-term mask shares plus <X>_1 <Y>_1 (Sec. 3.1.1, "Fully connected" and
+ * "Attention").  This computes
+ *     out = (acc + X W + bias) mod t
+ * X: device [m][k], W: device [k][n], bias: device [n] or NULL, acc: device [m][n] or
+ * NULL (may be the same buffer as out), out: device [m][n]; every value in Z_t (only
+ * the low log2_t bits of X, W, bias and acc matter: t divides 2^64 and the arithmetic
+ * wraps mod 2^64 before the final reduction).  k = 0 gives acc + bias.  Errors:
+ * HE_EINVAL for a NULL ctx, X (k > 0), W (k > 0) or out; HE_ECUDA on a launch failure. */
+HE_API int he_share_matmul(he_ctx* ctx, const uint64_t* X, const uint64_t* W, const uint64_t* bias,
+                           const uint64_t* acc, uint32_t m, uint32_t k, uint32_t n, uint64_t* out, void* stream);
+
+/* he_unmask into an existing share: with HE_UNMASK_ACCUMULATE the mask share of the
+ * Pi_MatMul of an (m x k) . (k x n) product (blocking blk, mask_seed) is added mod t to
+ * out instead of overwriting it; with HE_UNMASK_TRANSPOSE it goes to out as its
+ * transpose, out being [n][m] (the cross term of an attention product that runs in the
+ * transposed form of the Sec. 3.1.1 footnote).  out: device memory, caller-owned. */
+#define HE_UNMASK_ACCUMULATE 4u
+#define HE_UNMASK_TRANSPOSE 8u
+HE_API int he_unmask_acc(he_ctx* ctx, uint64_t mask_seed, uint32_t m, uint32_t n, const he_blocking* blk,
+                         uint32_t flags, uint64_t* out, void* stream);
 
 /* ---- test hooks --------------------------------------------------------- */
 

@@ -17,6 +17,7 @@ Layouts (all uint64, C order):
   output ciphertexts  [nLb * nI][2][L][N]   index Lb * nI + I, coefficient form
   shares              [m][n]                 values in Z_t
 """
+import ctypes
 import math
 
 import numpy as np
@@ -275,3 +276,24 @@ def plain_matmul_mod_t(X, W, t):
     Xo = X.astype(object)
     Wo = W.astype(object)
     return (Xo.dot(Wo) % t).astype(np.uint64)
+
+
+# ---------------------------------------------------------------- server-local share products
+
+
+def share_matmul(X, W, bias=None, acc=None, log2t=37):
+    """Sec. 3.1.1: the server's plaintext side of a linear layer, (acc + X W + bias) mod t,
+    X [m][k], W [k][n], bias [n], acc [m][n] (each optional but X, W)."""
+    X = np.ascontiguousarray(X, dtype=np.uint64)
+    W = np.ascontiguousarray(W, dtype=np.uint64)
+    m, k = X.shape
+    k2, n = W.shape
+    if k2 != k:
+        raise ValueError("inner dimensions differ")
+    out = np.zeros((m, n), dtype=np.uint64)
+    b = None if bias is None else np.ascontiguousarray(bias, dtype=np.uint64).reshape(n)
+    a = None if acc is None else np.ascontiguousarray(acc, dtype=np.uint64).reshape(m, n)
+    null = ctypes.POINTER(ctypes.c_uint64)()
+    lib.or_share_matmul(m, k, n, p64(X) if X.size else null, p64(W) if W.size else null,
+                        null if b is None else p64(b), null if a is None else p64(a), log2t, p64(out))
+    return out

@@ -54,6 +54,7 @@ def _load():
         "or_ctpt_accumulate": (None, [u32, u32, _u64p, _u64p, _u64p, u32, u32, u32, _u32p, u32, _u64p]),
         "or_apply_mask": (None, [u32, u32, _u64p, u32, u64, _u32p, u32, _u64p]),
         "or_max_primes": (ctypes.c_int, []),
+        "or_share_matmul": (None, [u32, u32, u32, _u64p, _u64p, _u64p, _u64p, u32, _u64p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(so, name)

@@ -427,3 +427,22 @@ void or_apply_mask(u32 N, u32 L, const u64* q, u32 log2t, u64 seed, const u32* o
 }
 
 int or_max_primes(void) { return OR_MAX_PRIMES; }
+
+/* Server-local share product of a linear layer (Sec. 3.1.1, "Fully connected" and
+ * "Attention"): out = (acc + X W + bias) mod 2^log2t, row-major, bias [n] and acc [m][n]
+ * optional (NULL).  The definition as a triple loop in 64-bit unsigned arithmetic: it
+ * wraps mod 2^64, and 2^log2t divides 2^64, so the final mask is the exact residue. */
+void or_share_matmul(u32 m, u32 k, u32 n, const u64* X, const u64* W, const u64* bias, const u64* acc,
+                     u32 log2t, u64* out) {
+  const u64 tmask = (log2t >= 64) ? ~(u64)0 : (((u64)1 << log2t) - 1);
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < (long)m; i++) {
+    for (u32 j = 0; j < n; j++) {
+      u64 s = 0;
+      for (u32 l = 0; l < k; l++) s += X[(size_t)i * k + l] * W[(size_t)l * n + j];
+      if (bias) s += bias[j];
+      if (acc) s += acc[(size_t)i * n + j];
+      out[(size_t)i * n + j] = s & tmask;
+    }
+  }
+}

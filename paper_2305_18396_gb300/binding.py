@@ -91,6 +91,10 @@ def _load():
         "he_multi_workspace_bytes": (ctypes.c_int, [P, u32, ctypes.POINTER(Product), ctypes.POINTER(sz)]),
         "he_encode_weights_batch": (ctypes.c_int, [P, P, u32, u32, pB, u32, P, P]),
         "he_unmask": (ctypes.c_int, [P, u64, u32, u32, pB, P, P]),
+        "he_unmask_acc": (ctypes.c_int, [P, u64, u32, u32, pB, u32, P, P]),
+        "he_autotune_blocking": (ctypes.c_int, [P, u32, u32, u32, u32, u32, u32, u32, P, sz, ctypes.POINTER(sz), pB,
+                                                ctypes.POINTER(ctypes.c_float), P]),
+        "he_share_matmul": (ctypes.c_int, [P, P, P, P, P, u32, u32, u32, P, P]),
         "he_expand_compact": (ctypes.c_int, [P, P, u32, u32, P, P]),
         "he_ntt_forward": (ctypes.c_int, [P, P, u32, P]),
         "he_ntt_inverse": (ctypes.c_int, [P, P, u32, P]),
@@ -173,6 +177,22 @@ class Context:
         b = Blocking()
         _check(lib.he_default_blocking(self.h, m, k, n, 1 if weights_per_call else 0, ctypes.byref(b)))
         return b.as_tuple()
+
+    def autotune_blocking(self, m, k, n, weights_per_call=False, flags=0, batch=1, candidates=0, stream=None):
+        """Measured blocking (he_autotune_blocking): returns (blocking, ms per call)."""
+        need = ctypes.c_size_t(0)
+        b = Blocking()
+        ms = ctypes.c_float(0)
+        wpc = 1 if weights_per_call else 0
+        _check(lib.he_autotune_blocking(self.h, m, k, n, wpc, flags, batch, candidates, None, 0,
+                                        ctypes.byref(need), ctypes.byref(b), ctypes.byref(ms), _stream(stream)))
+        if m and k and n:
+            scratch = self.empty(max(need.value // 8 + 1, 1))
+            _check(lib.he_autotune_blocking(self.h, m, k, n, wpc, flags, batch, candidates, _ptr(scratch),
+                                            scratch.numel() * 8, None, ctypes.byref(b), ctypes.byref(ms),
+                                            _stream(stream)))
+            del scratch
+        return b.as_tuple(), ms.value
 
     # ---- allocation helpers (device memory comes from torch)
     def empty(self, words):
@@ -380,6 +400,35 @@ def he_unmask(ctx, mask_seed, m, n, blk, share=None, stream=None):
     share = ctx.empty(m * n) if share is None else ctx._dev(share, m * n, "share")
     _check(lib.he_unmask(ctx.h, mask_seed, m, n, _blk(blk), _ptr(share), _stream(stream)))
     return share
+
+
+HE_UNMASK_ACCUMULATE = 4
+HE_UNMASK_TRANSPOSE = 8
+
+
+def he_unmask_acc(ctx, mask_seed, m, n, blk, out, flags=HE_UNMASK_ACCUMULATE, stream=None):
+    """out (+)= the server's mask share of an (m x n) product, or its transpose into an n x m out."""
+    ctx._dev(out, m * n, "out")
+    _check(lib.he_unmask_acc(ctx.h, mask_seed, m, n, _blk(blk), flags, _ptr(out), _stream(stream)))
+    return out
+
+
+def he_share_matmul(ctx, X, W, m, k, n, bias=None, acc=None, out=None, stream=None):
+    """Server-local share product: out = (acc + X W + bias) mod t, row-major device tensors."""
+    out = ctx.empty(m * n) if out is None else ctx._dev(out, m * n, "out")
+    if not m or not n:
+        return out
+    if k:
+        ctx._dev(X, m * k, "X")
+        ctx._dev(W, k * n, "W")
+    if bias is not None:
+        ctx._dev(bias, n, "bias")
+    if acc is not None:
+        ctx._dev(acc, m * n, "acc")
+    _check(lib.he_share_matmul(ctx.h, _ptr(X) if k else None, _ptr(W) if k else None,
+                               None if bias is None else _ptr(bias), None if acc is None else _ptr(acc),
+                               m, k, n, _ptr(out), _stream(stream)))
+    return out
 
 
 def he_ntt_forward(ctx, polys, stream=None):

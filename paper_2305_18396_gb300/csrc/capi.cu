@@ -121,11 +121,12 @@ struct ProfRec {
 
 enum Kind {
   KNttFwd, KNttInv, KPolyMul, KKeygen, KEncrypt, KDecrypt, KPack, KUnpack, KUnmask, KEncode, KMac, KInttMask, KInttC0,
-  KExpand, KProbe, KCount
+  KExpand, KProbe, KShare, KCount
 };
 static const char* kKindNames[KCount] = {"ntt_forward", "ntt_inverse", "poly_mul", "keygen", "encrypt",
                                          "decrypt", "pack", "unpack", "unmask", "encode_weights",
-                                         "mac", "intt_mask", "intt_c0_targets", "expand_compact", "probe"};
+                                         "mac", "intt_mask", "intt_c0_targets", "expand_compact", "probe",
+                                         "share_matmul"};
 
 struct he_ctx {
   int device = 0;
@@ -355,18 +356,25 @@ int he_sizes(const he_ctx* c, uint32_t m, uint32_t k, uint32_t n, const he_block
   return HE_OK;
 }
 
-int he_choose_blocking(uint32_t Nw, uint32_t Lw, uint32_t m, uint32_t k, uint32_t n, uint32_t weights_per_call,
-                       he_blocking* out) {
-  if (!out) return fail(HE_EINVAL, "NULL argument");
-  if (!pow2(Nw) || Lw < 1) return fail(HE_EINVAL, "N must be a power of two and L >= 1");
+namespace {
+
+struct Candidate {
+  he_blocking b;
+  double cost;  // model seconds
+};
+
+// Every power-of-two blocking of an (m x k) . (k x n) product with m_b k_b n_b <= N and
+// no block larger than the next power of two of its dimension, sorted by a cost model of
+// one product on GB300 (seconds; constants measured with bench.py):
+//   transforms: 45 ns per length-4096 residue polynomial (scaled by N log N), counting the
+//     NTT of every input polynomial, the inverse NTT of every output polynomial and, when
+//     the weights are encoded per call, the NTT of every weight polynomial;
+//   multiply-accumulate: 0.8 ps per slot product, divided by the fill of the kernel's
+//     8-row x 8-column output tiles;
+//   memory: algorithmic bytes at 6.75 TB/s.
+// Ties go to the larger m_b, then the larger k_b.
+std::vector<Candidate> blocking_candidates(u32 Nw, u32 Lw, u32 m, u32 k, u32 n, u32 weights_per_call) {
   const double N = Nw, L = Lw;
-  // Cost model of one product on GB300 (seconds; constants measured with bench.py):
-  //   transforms: 45 ns per length-4096 residue polynomial (scaled by N log N), counting the
-  //     NTT of every input polynomial, the inverse NTT of every output polynomial and, when
-  //     the weights are encoded per call, the NTT of every weight polynomial;
-  //   multiply-accumulate: 0.8 ps per slot product, divided by the fill of the kernel's
-  //     8-row x 8-column output tiles;
-  //   memory: algorithmic bytes at 6.75 TB/s.
   const double t_poly = 45e-9 * (N * std::log2(N)) / (4096.0 * 12.0);
   const double t_slot = 0.8e-12, hbm = 6.75e12;
   auto cap = [&](u32 d) {
@@ -375,8 +383,7 @@ int he_choose_blocking(uint32_t Nw, uint32_t Lw, uint32_t m, uint32_t k, uint32_
     return p;
   };
   const u64 cm = cap(m ? m : 1), ck = cap(k ? k : 1), cn = cap(n ? n : 1);
-  double best = -1;
-  he_blocking bb{1, 1, 1};
+  std::vector<Candidate> out;
   for (u64 mb = 1; mb <= cm; mb <<= 1)
     for (u64 kb = 1; kb <= ck && mb * kb <= Nw; kb <<= 1)
       for (u64 nb = 1; nb <= cn && mb * kb * nb <= Nw; nb <<= 1) {
@@ -388,15 +395,24 @@ int he_choose_blocking(uint32_t Nw, uint32_t Lw, uint32_t m, uint32_t k, uint32_
         const double rows = 2 * nLb, fill = (rows / (8 * std::ceil(rows / 8))) * (nI / (8 * std::ceil(nI / 8)));
         const double slots = nI * nJ * nLb * 2 * L * N;
         const double bytes = 8 * N * L * (pts * (weights_per_call ? 3 : 1) + 6 * in + 4 * outc);
-        const double t = polys * t_poly + slots * t_slot / fill + bytes / hbm;
-        const bool better = best < 0 || t < best * (1 - 1e-9) ||
-                            (t <= best * (1 + 1e-9) && (mb > bb.m_b || (mb == bb.m_b && kb > bb.k_b)));
-        if (better) {
-          best = t;
-          bb = {(u32)mb, (u32)kb, (u32)nb};
-        }
+        out.push_back({{(u32)mb, (u32)kb, (u32)nb}, polys * t_poly + slots * t_slot / fill + bytes / hbm});
       }
-  *out = bb;
+  std::stable_sort(out.begin(), out.end(), [](const Candidate& a, const Candidate& b) {
+    if (a.cost < b.cost * (1 - 1e-9)) return true;
+    if (b.cost < a.cost * (1 - 1e-9)) return false;
+    return a.b.m_b != b.b.m_b ? a.b.m_b > b.b.m_b : a.b.k_b > b.b.k_b;
+  });
+  return out;
+}
+
+}  // namespace
+
+int he_choose_blocking(uint32_t Nw, uint32_t Lw, uint32_t m, uint32_t k, uint32_t n, uint32_t weights_per_call,
+                       he_blocking* out) {
+  if (!out) return fail(HE_EINVAL, "NULL argument");
+  if (!pow2(Nw) || Lw < 1) return fail(HE_EINVAL, "N must be a power of two and L >= 1");
+  const std::vector<Candidate> c = blocking_candidates(Nw, Lw, m, k, n, weights_per_call);
+  *out = c.empty() ? he_blocking{1, 1, 1} : c.front().b;
   return HE_OK;
 }
 
@@ -482,6 +498,37 @@ int he_unmask(he_ctx* c, uint64_t mask_seed, uint32_t m, uint32_t n, const he_bl
   return launch(c, KUnmask, (cudaStream_t)stream, "unmask", [&] {
     return he::launch_unmask(c->C, mask_seed, m, n, to_blk(blk), s.nI, server_share, (cudaStream_t)stream);
   });
+}
+
+int he_unmask_acc(he_ctx* c, uint64_t mask_seed, uint32_t m, uint32_t n, const he_blocking* blk, uint32_t flags,
+                  uint64_t* out, void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (int r = check_blk(c, blk)) return r;
+  if (flags & ~(HE_UNMASK_ACCUMULATE | HE_UNMASK_TRANSPOSE)) return fail(HE_EINVAL, "unknown flags");
+  if (!m || !n) return HE_OK;
+  if (!out) return fail(HE_EINVAL, "NULL buffer");
+  if (int r = set_device(c)) return r;
+  Shape s = shape_of(m, 1, n, blk);
+  return launch(c, KUnmask, (cudaStream_t)stream, "unmask_acc", [&] {
+    return he::launch_unmask_acc(c->C, mask_seed, m, n, to_blk(blk), s.nI, (flags & HE_UNMASK_ACCUMULATE) != 0,
+                                 (flags & HE_UNMASK_TRANSPOSE) != 0, out, (cudaStream_t)stream);
+  });
+}
+
+int he_share_matmul(he_ctx* c, const uint64_t* X, const uint64_t* W, const uint64_t* bias, const uint64_t* acc,
+                    uint32_t m, uint32_t k, uint32_t n, uint64_t* out, void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (!m || !n) return HE_OK;
+  if (!out || (k && (!X || !W))) return fail(HE_EINVAL, "NULL buffer");
+  if (int r = set_device(c)) return r;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const u32 splits = k ? he::share_matmul_splits(m, k, n, sms > 0 ? sms : 1) : 1;
+  int r = launch(c, KShare, (cudaStream_t)stream, "share_matmul", [&] {
+    return he::launch_share_matmul(c->C, X, W, bias, acc, m, k, n, splits, out, (cudaStream_t)stream);
+  });
+  if (r == HE_OK && splits > 1) c->launches.fetch_add(2, std::memory_order_relaxed);  // set-up + finishing pass
+  return r;
 }
 
 int he_encode_weights_batch(he_ctx* c, const uint64_t* W, uint32_t k, uint32_t n, const he_blocking* blk,
@@ -583,6 +630,94 @@ int he_matmul_batch(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32
     return fail(HE_ENOMEM, "workspace smaller than batch x what he_sizes() requires for these flags");
   if (int r = set_device(c)) return r;
   return matmul_device(c, ct_in, pt, m, k, n, blk, batch, mask_seed, flags, ct_out, workspace, (cudaStream_t)stream);
+}
+
+int he_autotune_blocking(he_ctx* c, uint32_t m, uint32_t k, uint32_t n, uint32_t weights_per_call, uint32_t flags,
+                         uint32_t batch, uint32_t candidates, void* scratch, size_t scratch_bytes,
+                         size_t* scratch_needed, he_blocking* out, float* best_ms, void* stream) {
+  if (!c || !out) return fail(HE_EINVAL, "NULL argument");
+  if (flags & ~(uint32_t)HE_DROP_C0) return fail(HE_EINVAL, "flags other than HE_DROP_C0");
+  if ((u64)(batch ? batch : 1) * c->C.L > 65535) return fail(HE_EINVAL, "batch * L must be <= 65535");
+  batch = batch ? batch : 1;
+  candidates = candidates ? std::min(candidates, 16u) : 6u;
+  std::vector<Candidate> all = blocking_candidates(c->C.N, c->C.L, m, k, n, weights_per_call);
+  std::vector<he_blocking> cand;
+  for (const Candidate& x : all) {
+    if ((flags & HE_DROP_C0) && !pow2(x.b.k_b)) continue;
+    cand.push_back(x.b);
+    if (cand.size() == candidates) break;
+  }
+  if (cand.empty()) return fail(HE_EINVAL, "no blocking fits");
+  *out = cand.front();
+  if (best_ms) *best_ms = 0.f;
+  if (!m || !k || !n) return HE_OK;
+  // scratch: [W: batch k n][pt][ct_in][ct_out][workspace], each 256-byte aligned
+  auto up = [](u64 b) { return (b + 255) & ~(u64)255; };
+  struct Parts { u64 w, pt, in, out, ws; };
+  auto parts = [&](const he_blocking& b) {
+    he_size_info si;
+    he_sizes(c, m, k, n, &b, &si);
+    const bool compact = flags & HE_DROP_C0;
+    return Parts{up(8ull * batch * k * n), up(8ull * batch * si.pt_words), up(8ull * batch * si.in_words),
+                 up(8ull * batch * (compact ? si.out_words_compact : si.out_words)),
+                 up((u64)batch * (compact ? si.workspace_bytes_compact : si.workspace_bytes))};
+  };
+  u64 need = 0;
+  for (const he_blocking& b : cand) {
+    const Parts p = parts(b);
+    need = std::max(need, p.w + p.pt + p.in + p.out + p.ws);
+  }
+  if (scratch_needed) *scratch_needed = need;
+  if (!scratch) return HE_OK;
+  if (scratch_bytes < need) return fail(HE_ENOMEM, "scratch smaller than *scratch_needed");
+  if (int r = set_device(c)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = get_event(c), e1 = get_event(c);
+  float best = -1.f;
+  int rc = HE_OK;
+  for (size_t ci = 0; ci < cand.size() && rc == HE_OK; ++ci) {
+    const he_blocking& b = cand[ci];
+    const Parts p = parts(b);
+    uint8_t* base = (uint8_t*)scratch;
+    u64* W = (u64*)base;
+    u64* pt = (u64*)(base + p.w);
+    u64* ct = (u64*)(base + p.w + p.pt);
+    u64* o = (u64*)(base + p.w + p.pt + p.in);
+    void* ws = base + p.w + p.pt + p.in + p.out;
+    Shape s = shape_of(m, k, n, &b);
+    auto encode = [&] {
+      return launch(c, KEncode, st, "autotune: encode", [&] {
+        return he::launch_encode_weights(c->C, W, k, n, to_blk(&b), s.nI, s.nJ, batch, pt, st);
+      });
+    };
+    if ((rc = launch(c, KProbe, st, "autotune: fill", [&] {
+           cudaError_t e = he::launch_fill_random(c->C, W, p.w / 8, 0x5eedull, 1, st);
+           return e == cudaSuccess ? he::launch_fill_random(c->C, ct, p.in / 8, 0x5eedull + 1, 0, st) : e;
+         })))
+      break;
+    if (!weights_per_call && (rc = encode())) break;
+    float cand_best = -1.f;
+    for (int rep = 0; rep < 4 && rc == HE_OK; ++rep) {  // one warm-up, three timed
+      cudaEventRecord(e0, st);
+      if (weights_per_call) rc = encode();
+      if (rc == HE_OK) rc = matmul_device(c, ct, pt, m, k, n, &b, batch, 1, flags, o, ws, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep && (cand_best < 0 || ms < cand_best)) cand_best = ms;
+    }
+    if (rc == HE_OK && (best < 0 || cand_best < best)) {
+      best = cand_best;
+      *out = b;
+    }
+  }
+  c->pool.push_back(e0);
+  c->pool.push_back(e1);
+  if (rc != HE_OK) return rc;
+  if (int r = he_device_status(c, stream)) return r;
+  if (best_ms) *best_ms = best;
+  return HE_OK;
 }
 
 int he_matmul_batch_host(he_ctx* c, const uint64_t* ct_in_host, const uint64_t* pt, uint32_t m, uint32_t k,

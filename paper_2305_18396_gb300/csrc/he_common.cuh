@@ -19,6 +19,7 @@ constexpr u32 kDomainSecret = 1;
 constexpr u32 kDomainUniform = 2;
 constexpr u32 kDomainError = 3;
 constexpr u32 kDomainMask = 4;
+constexpr u32 kDomainFill = 7;  // timing data of the autotuner (never a key, error or mask)
 
 // Per-prime constants.  "_sh" fields are Shoup companions w' = floor(w 2^64 / q).
 struct PrimeConsts {

@@ -633,6 +633,20 @@ cudaError_t launch_unpack(const Consts& C, const u64* dec, u32 m, u32 n, Blk b, 
   return cudaGetLastError();
 }
 
+// Pseudo-random data for timing runs (the autotuner): mode 0 fills residues mod q_l in the
+// [..][L][N] layout (prime l = (e / N) mod L), mode 1 values in Z_t.
+__global__ void k_fill_random(u64* dst, u64 words, u64 seed, int mode, const __grid_constant__ Consts C) {
+  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < words; e += (u64)gridDim.x * blockDim.x) {
+    const u64 r = lo64(draw(seed, (u32)e, (u32)(e >> 32), kDomainFill, 0));
+    dst[e] = mode == 0 ? r % C.p[(e / C.N) % C.L].q : r & C.tmask;
+  }
+}
+
+cudaError_t launch_fill_random(const Consts& C, u64* dst, u64 words, u64 seed, int mode, cudaStream_t st) {
+  if (words) k_fill_random<<<1216, 256, 0, st>>>(dst, words, seed, mode, C);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_unmask(const Consts& C, u64 seed, u32 m, u32 n, Blk b, u32 nI, u64* share, cudaStream_t st) {
   u64 total = (u64)m * n;
   if (total) k_unmask<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(seed, m, n, b, nI, share, C);

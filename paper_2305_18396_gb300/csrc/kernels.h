@@ -27,6 +27,13 @@ cudaError_t launch_pack(const Consts& C, const u64* X, u32 m, u32 k, Blk b, u32 
 cudaError_t launch_unpack(const Consts& C, const u64* dec, u32 m, u32 n, Blk b, u32 nI, u64* share,
                           cudaStream_t st);
 cudaError_t launch_unmask(const Consts& C, u64 seed, u32 m, u32 n, Blk b, u32 nI, u64* share, cudaStream_t st);
+cudaError_t launch_fill_random(const Consts& C, u64* dst, u64 words, u64 seed, int mode, cudaStream_t st);
+// share.cu: server-local share products and mask-share accumulation
+u32 share_matmul_splits(u32 m, u32 k, u32 n, int sms);
+cudaError_t launch_share_matmul(const Consts& C, const u64* X, const u64* W, const u64* bias, const u64* acc, u32 m,
+                                u32 k, u32 n, u32 splits, u64* out, cudaStream_t st);
+cudaError_t launch_unmask_acc(const Consts& C, u64 seed, u32 m, u32 n, Blk b, u32 nI, int accumulate, int transpose,
+                              u64* out, cudaStream_t st);
 
 // Products come in batches of identical shape laid out back to back (batch = 1 for one).
 cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u32 batch,

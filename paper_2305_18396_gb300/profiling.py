@@ -3,6 +3,7 @@ and a reader for the per-launch CSV that `ncu --metrics gpu__time_duration.sum -
 writes.
 
     python -m paper_2305_18396_gb300.profiling case M K N [--repeat R] [--full-c0]
+    python -m paper_2305_18396_gb300.profiling share M K N [--repeat R]
     python -m paper_2305_18396_gb300.profiling launches launches.csv
 
 `case` runs one Pi_MatMul (Algorithm 1) of an M x K share against a K x N weight matrix
@@ -43,6 +44,24 @@ def run_case(m, k, n, repeat=3, compact=True, logN=12, L=2):
     return blk, ctx.sizes(m, k, n, blk)
 
 
+def run_share_case(m, k, n, repeat=3):
+    """he_share_matmul (server-local product, Sec. 3.1.1) of an m x k by k x n share."""
+    import torch
+
+    from . import binding as B
+    from . import synthetic as S
+
+    ctx = B.Context(4096, 2)
+    X = torch.from_numpy(S.uniform_share((m, k), 1).view(np.int64).reshape(-1)).to(ctx.device)
+    W = torch.from_numpy(S.uniform_share((k, n), 2).view(np.int64).reshape(-1)).to(ctx.device)
+    bias = torch.from_numpy(S.uniform_share((1, n), 3).view(np.int64).reshape(-1)).to(ctx.device)
+    out = ctx.empty(m * n)
+    for _ in range(repeat):
+        B.he_share_matmul(ctx, X, W, m, k, n, bias=bias, out=out)
+    torch.cuda.synchronize()
+    B.he_device_status(ctx)
+
+
 def summarize_launches(path, skip_prefixes=(), skip_first=0, metric="gpu__time_duration.sum"):
     """Per kernel: (launches, total) of `metric` from an ncu --csv launch list (durations in
     microseconds), leaving out the first `skip_first` launches and kernels named by a prefix."""
@@ -80,6 +99,11 @@ def main(argv=None):
     c.add_argument("n", type=int)
     c.add_argument("--repeat", type=int, default=3)
     c.add_argument("--full-c0", action="store_true")
+    sh = sub.add_parser("share")
+    sh.add_argument("m", type=int)
+    sh.add_argument("k", type=int)
+    sh.add_argument("n", type=int)
+    sh.add_argument("--repeat", type=int, default=3)
     s = sub.add_parser("launches")
     s.add_argument("csv")
     s.add_argument("--skip", action="append", default=[], help="kernel-name prefix to leave out")
@@ -89,6 +113,9 @@ def main(argv=None):
     if a.cmd == "case":
         blk, si = run_case(a.m, a.k, a.n, a.repeat, not a.full_c0)
         print("ok", blk, si)
+    elif a.cmd == "share":
+        run_share_case(a.m, a.k, a.n, a.repeat)
+        print("ok")
     else:
         agg = summarize_launches(a.csv, tuple(a.skip), a.skip_first, a.metric)
         tot = sum(v[1] for v in agg.values()) or 1.0

@@ -448,3 +448,90 @@ def test_matmul_from_selected_input_rows_equals_full():
         rows[Lb] = O.encrypt(P, s, polys, 4, obj0=Lb * nJ)
         assert np.array_equal(rows[Lb], full_in[Lb * nJ:(Lb + 1) * nJ])
     assert np.array_equal(O.matmul(P, rows, W, m, k, n, blk, 5, sel=sel), full[sel])
+
+
+# ------------------------------------------------------------------ server-local share products
+
+
+def _share_matmul_bigint(X, W, bias, acc, t):
+    m, k = X.shape
+    n = W.shape[1]
+    out = np.zeros((m, n), dtype=np.uint64)
+    for i in range(m):
+        for j in range(n):
+            s = sum(int(X[i, l]) * int(W[l, j]) for l in range(k))
+            s += int(bias[j]) if bias is not None else 0
+            s += int(acc[i, j]) if acc is not None else 0
+            out[i, j] = s % t
+    return out
+
+
+@pytest.mark.parametrize("m,k,n", [(1, 1, 1), (3, 5, 4), (7, 1, 9), (2, 0, 3), (6, 13, 5)])
+def test_share_matmul_equals_bigint_definition(m, k, n):
+    t = 1 << 37
+    rng = np.random.default_rng(m * 100 + k * 10 + n)
+    X = rng.integers(0, t, size=(m, k), dtype=np.uint64)
+    W = rng.integers(0, t, size=(k, n), dtype=np.uint64)
+    X[:, :1] = t - 1  # the largest residues make every product and sum wrap 64 bits
+    bias = rng.integers(0, t, size=n, dtype=np.uint64)
+    acc = rng.integers(0, t, size=(m, n), dtype=np.uint64)
+    for b, a in ((None, None), (bias, None), (None, acc), (bias, acc)):
+        assert np.array_equal(O.share_matmul(X, W, b, a), _share_matmul_bigint(X, W, b, a, t))
+
+
+def test_share_matmul_identity_and_linearity():
+    t = 1 << 37
+    rng = np.random.default_rng(5)
+    X = rng.integers(0, t, size=(4, 6), dtype=np.uint64)
+    assert np.array_equal(O.share_matmul(X, np.eye(6, dtype=np.uint64)), X)
+    W1 = rng.integers(0, t, size=(6, 3), dtype=np.uint64)
+    W2 = rng.integers(0, t, size=(6, 3), dtype=np.uint64)
+    lhs = O.share_matmul(X, (W1 + W2) % np.uint64(t))
+    rhs = (O.share_matmul(X, W1) + O.share_matmul(X, W2)) % np.uint64(t)
+    assert np.array_equal(lhs, rhs)
+
+
+def test_fully_connected_layer_shares_sum_to_xw_plus_b():
+    """Sec. 3.1.1, fully connected: the client's share is its decryption of Pi_MatMul(W, <x>_0);
+    the server's is its mask share + W<x>_1 + b; together they are x W + b mod t."""
+    P = O.Params(1024, 2)
+    m, k, n, blk = 6, 20, 9, (4, 8, 4)
+    x0 = S.uniform_share((m, k), 41)
+    x1 = S.uniform_share((m, k), 42)
+    W = S.fixed_point_weights((k, n), 43)
+    b = S.uniform_share((1, n), 44).reshape(n)
+    s = O.keygen(P, 1)
+    out = O.matmul(P, O.encrypt(P, s, O.pack_input(x0, blk, P.N), 2), W, m, k, n, blk, 3)
+    dec, _ = O.decrypt(P, s, out)
+    y0 = O.unpack_output(dec, m, n, blk)
+    y1 = O.share_matmul(x1, W, b, O.unmask(P, 3, m, n, blk))
+    x = (x0 + x1) % np.uint64(P.t)
+    want = _share_matmul_bigint(x, W, b, None, P.t)
+    assert np.array_equal((y0 + y1) % np.uint64(P.t), want)
+
+
+def test_attention_product_shares_sum_to_xy():
+    """Sec. 3.1.1, attention: Z = X Y from shares.  Cross term <X>_0 <Y>_1 runs directly
+    (client encrypts <X>_0); cross term <X>_1 <Y>_0 runs in the transposed form of the
+    footnote (client encrypts <Y>_0^T, server operand <X>_1^T) and both parties transpose
+    their shares of it.  Client: cross shares + <X>_0 <Y>_0; server: cross mask shares +
+    <X>_1 <Y>_1."""
+    P = O.Params(1024, 2)
+    m, k, n = 5, 7, 6
+    X0, X1 = S.uniform_share((m, k), 51), S.uniform_share((m, k), 52)
+    Y0, Y1 = S.uniform_share((k, n), 53), S.uniform_share((k, n), 54)
+    s = O.keygen(P, 1)
+    blk1, blk2 = (4, 8, 4), (4, 4, 8)
+    t = np.uint64(P.t)
+    # cross term 1: <X>_0 . <Y>_1 (m x n)
+    o1 = O.matmul(P, O.encrypt(P, s, O.pack_input(X0, blk1, P.N), 2), Y1, m, k, n, blk1, 3)
+    c1 = O.unpack_output(O.decrypt(P, s, o1)[0], m, n, blk1)
+    # cross term 2: (<X>_1 . <Y>_0)^T = <Y>_0^T . <X>_1^T (n x m)
+    Y0T, X1T = np.ascontiguousarray(Y0.T), np.ascontiguousarray(X1.T)
+    o2 = O.matmul(P, O.encrypt(P, s, O.pack_input(Y0T, blk2, P.N), 4), X1T, n, k, m, blk2, 5)
+    c2 = O.unpack_output(O.decrypt(P, s, o2)[0], n, m, blk2)
+    Z0 = (c1 + c2.T + O.share_matmul(X0, Y0)) % t
+    Z1 = (O.share_matmul(X1, Y1) + O.unmask(P, 3, m, n, blk1) + O.unmask(P, 5, n, m, blk2).T) % t
+    X = (X0 + X1) % t
+    Y = (Y0 + Y1) % t
+    assert np.array_equal((Z0 + Z1) % t, _share_matmul_bigint(X, Y, None, None, P.t))
