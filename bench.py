@@ -42,8 +42,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-rates", default="400,800", help="Poisson arrival rates (requests/s)")
-    ap.add_argument("--serving-requests", type=int, default=400)
+    ap.add_argument("--serving-rates", default="100,400,800", help="Poisson arrival rates (requests/s)")
+    ap.add_argument("--serving-requests", type=int, default=1000)
+    ap.add_argument("--launch", default="multi", choices=["multi", "groups"],
+                    help="multi: the whole layer as one multi-product launch per step; groups: one batched "
+                         "launch per product shape")
+    ap.add_argument("--blocking", default="tuned", choices=["tuned", "model"],
+                    help="tuned: he_autotune_blocking per product at set-up; model: the cost model's choice")
     ap.add_argument("--full-c0", action="store_true",
                     help="return all of c0 instead of only the decoded coefficients (Sec. 3.1.3)")
     return ap.parse_args()
@@ -134,7 +139,7 @@ class Layer:
     """Device state of one layer's products: resident weights, input ciphertexts, outputs.
     Products that occur once per head run as one same-shape batch (he_matmul_batch)."""
 
-    def __init__(self, B, ctx, prods, rank, want_host, flags):
+    def __init__(self, B, ctx, prods, rank, want_host, flags, tune=True, multi=True):
         import numpy as np
         import torch
 
@@ -147,7 +152,10 @@ class Layer:
         max_ws = max_pt = max_hostws = 0
         idx = 0
         for p in prods:
-            blk = ctx.default_blocking(p.m, p.k, p.n, p.share_weights)
+            if tune:  # measured choice among the cost model's best blockings (set-up, untimed)
+                blk = ctx.autotune_blocking(p.m, p.k, p.n, p.share_weights, flags, p.count)[0]
+            else:
+                blk = ctx.default_blocking(p.m, p.k, p.n, p.share_weights)
             si = ctx.sizes(p.m, p.k, p.n, blk)
             ow, wb = B._out_ws(si, flags)
             si = dict(si, out=ow, ws=wb)
@@ -180,6 +188,24 @@ class Layer:
             idx += cnt
         self.ws = ctx.empty(max((max_ws + 7) // 8, 1))
         self.pt_tmp = ctx.empty(max(max_pt, 1))
+        # one multi-product launch per step: every product of the layer as one item (the
+        # server's per-step shares encoded into a buffer per launch group first)
+        self.multi = multi
+        if multi:
+            items = []
+            for c in self.calls:
+                p, si, cnt = c["p"], c["si"], c["cnt"]
+                if "pt" not in c:
+                    c["pt_step"] = ctx.empty(cnt * si["pt_words"])
+                pt_all = c.get("pt", c.get("pt_step"))
+                for b in range(cnt):
+                    items.append(dict(ct_in=c["ct_in"][b * si["in_words"]:(b + 1) * si["in_words"]],
+                                      pt=pt_all[b * si["pt_words"]:(b + 1) * si["pt_words"]],
+                                      ct_out=c["out"][b * si["out"]:(b + 1) * si["out"]], m=p.m, k=p.k, n=p.n,
+                                      blk=c["blk"], flags=flags, mask_seed=0))
+            self.items = items
+            self.prods = B.make_products(items)
+            self.multi_ws = ctx.empty(B.he_multi_workspace_bytes(ctx, self.prods) // 8 + 1)
         self.host_ws = [ctx.empty(max_hostws), ctx.empty(max_hostws)] if want_host else None
         self.host_streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)] if want_host else None
         self.enc_done = torch.cuda.Event()
@@ -190,6 +216,18 @@ class Layer:
 
     def step(self, step_idx, host=False):
         B, ctx = self.B, self.ctx
+        if self.multi and not host:
+            i = 0
+            for c in self.calls:
+                p, cnt = c["p"], c["cnt"]
+                if "pt_step" in c:
+                    B.he_encode_weights_batch(ctx, c["W"], p.k, p.n, c["blk"], cnt, pt=c["pt_step"])
+                seed = (step_idx << 20) | c["idx"]
+                for b in range(cnt):
+                    self.prods[i].mask_seed = seed + b
+                    i += 1
+            B.he_matmul_multi(ctx, self.prods, self.multi_ws)
+            return
         k = 0
         for c in self.calls:
             p, blk, cnt, si = c["p"], c["blk"], c["cnt"], c["si"]
@@ -252,16 +290,18 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel):
-    """DRAM traffic per launch from the committed ncu summary, if it was taken on this source."""
+def recorded_traffic(kernel, launch):
+    """DRAM traffic per launch from the committed ncu summary, if it was taken on this source
+    and in this launch mode (per-group launches and the whole-layer launch differ in size)."""
     for f in (ROOT / "profiles").glob("*.md"):
         txt = f.read_text()
         m = re.search(r"^traffic_kernel:\s*(\S+)\s*$", txt, re.M)
         if not m or m.group(1) != kernel:
             continue
         src = re.search(r"^source_hash:\s*(\S+)\s*$", txt, re.M)
-        val = re.search(r"^traffic_bytes_per_launch_full_step_avg:\s*([0-9.eE+]+)\s*$", txt, re.M)
-        if src and val and src.group(1) == kernel_source_hash():
+        mode = re.search(r"^traffic_launch:\s*(\S+)\s*$", txt, re.M)
+        val = re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*$", txt, re.M)
+        if src and val and mode and src.group(1) == kernel_source_hash() and mode.group(1) == launch:
             return float(val.group(1))
     return None
 
@@ -365,12 +405,15 @@ def serving_leg(B, ctx, args):
     out = {"requests_per_rate": args.serving_requests,
            "mix": "BERT-base/large layer matrices (QKV, out, FFN1, FFN2), m log-uniform in [8, 512], Poisson arrivals",
            "resident_weight_gb": round(sum(m.pt.numel() for m in models) * 8 / 1e9, 2),
-           "policy": "2 launch slots (streams), up to 8 requests per multi-product launch, admission by a 32 GiB "
-                     "device budget for outputs + workspace", "rates": {}}
+           "policy": "2 launches in flight, each on a stream of lower CUDA priority than those running; a launch "
+                     "takes the oldest admitted request plus, in arrival order, requests whose estimated device "
+                     "time fits 1.25 x the oldest's (at least 1 ms), up to 8; admission by a 32 GiB device "
+                     "budget for outputs + workspace; outputs released on completion", "rates": {}}
     for rate in [float(x) for x in args.serving_rates.split(",") if x]:
         res = {}
-        for name, fn, kw in (("per_request", SV.run_per_request, {}),
-                             ("continuous_batching", SV.run_served, {"slots": 2, "max_batch": 8})):
+        for name, fn, kw in (("per_request", SV.run_per_request, {"keep_outputs": False}),
+                             ("continuous_batching", SV.run_served,
+                              {"slots": 2, "max_batch": 8, "keep_outputs": False})):
             reqs = SV.make_requests(models, args.serving_requests, rate)
             st, _ = fn(ctx, models, reqs, **kw)
             res[name] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
@@ -378,6 +421,52 @@ def serving_leg(B, ctx, args):
     del models
     torch.cuda.empty_cache()
     return out
+
+
+# ------------------------------------------------------------------ server-local share products
+
+
+def share_products_leg(B, ctx, prods, mad_peak, reps=20):
+    """The server's plaintext side of the same layer (Sec. 3.1.1): W<x>_1 + b for the four
+    fully connected products and <X>_1 <Y>_1 for every per-head attention product, through
+    he_share_matmul, device-resident, timed with events over `reps` passes."""
+    import numpy as np
+    import torch
+
+    from paper_2305_18396_gb300 import synthetic as S
+
+    calls, macs = [], 0
+    for i, p in enumerate(prods):
+        X = torch.from_numpy(S.uniform_share((p.m, p.k), 900 + i).view(np.int64).reshape(-1)).to(ctx.device)
+        W = torch.from_numpy(S.uniform_share((p.k, p.n), 950 + i).view(np.int64).reshape(-1)).to(ctx.device)
+        bias = None if p.share_weights else torch.from_numpy(
+            S.uniform_share((1, p.n), 990 + i).view(np.int64).reshape(-1)).to(ctx.device)
+        calls.append((p, X, W, bias, ctx.empty(p.m * p.n)))
+        macs += p.m * p.k * p.n * p.count
+    stream = torch.cuda.current_stream()
+
+    def one_pass():
+        for p, X, W, bias, out in calls:
+            for _ in range(p.count):
+                B.he_share_matmul(ctx, X, W, p.m, p.k, p.n, bias=bias, out=out)
+
+    for _ in range(3):
+        one_pass()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        one_pass()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    rate = macs / (ms / 1e3)
+    # three integer multiply-adds per MAC (one 32x32->64, two 32-bit), against the measured
+    # mad.wide.u32 rate of the integer pipe
+    return {"what": "server-local W<x>_1 + b (4 FC products) and <X>_1 <Y>_1 (24 per-head products) of the "
+                    "same layer, he_share_matmul, inputs resident", "macs_per_pass": macs,
+            "ms_per_pass": round(ms, 4), "value": rate, "unit": "MAC/s",
+            "integer_ops_per_mac": 3, "frac_of_integer_peak": round(3 * rate / mad_peak, 4)}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -394,7 +483,7 @@ def gpu_arm(args, world, rank, local):
     prods = workloads.bert_layer_products(**workloads.BERT_BASE)
     want_host = not args.no_e2e
     flags = B.HE_FLAGS_NONE if args.full_c0 else B.HE_DROP_C0
-    layer = Layer(B, ctx, prods, rank, want_host, flags)
+    layer = Layer(B, ctx, prods, rank, want_host, flags, tune=args.blocking == "tuned", multi=args.launch == "multi")
     stream = torch.cuda.current_stream()
 
     mad_peak, mad_per_sm_clk = B.he_probe_mad_wide(ctx)
@@ -459,7 +548,7 @@ def gpu_arm(args, world, rank, local):
     else:
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(hbm_gbs, 1), "peak": pk["hbm_gbs"],
                     "unit": "GB/s", "frac": round(hbm_gbs / pk["hbm_gbs"], 4), "peak_source": pk_src}
-    roofline.update({"algorithmic_bytes_per_launch": bytes_per_launch, "traffic": recorded_traffic(dom),
+    roofline.update({"algorithmic_bytes_per_launch": bytes_per_launch, "traffic": recorded_traffic(dom, args.launch),
                      "kernels": kern,
                      "slot_macs_per_s": layer.slot_macs() * steps_prof / (stats["mac"]["total_ms"] / 1e3)
                      if "mac" in stats else None})
@@ -481,6 +570,8 @@ def gpu_arm(args, world, rank, local):
         e2e = {"value": world * layer.macs * ksteps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ksteps, "ms_per_step": dt * 1e3 / ksteps}
 
+    share = share_products_leg(B, ctx, prods, mad_peak)
+
     serving = None
     if world == 1 and not args.no_serving:
         serving = serving_leg(B, ctx, args)
@@ -497,14 +588,16 @@ def gpu_arm(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N_POLY, "L": L_PRIMES, "log2_t": 37,
-                   "products_per_step": layer.products, "launch_groups_per_step": len(layer.calls),
+                   "products_per_step": layer.products,
+                   "launch_groups_per_step": 1 if layer.multi else len(layer.calls),
                    "plain_macs_per_step": layer.macs,
                    "output": "full ciphertexts" if args.full_c0 else
                    "c1 + c0 at the decoded coefficients only (Sec. 3.1.3, HE_DROP_C0)",
-                   "blockings_mkn": blks, "kernel_source_hash": kernel_source_hash(), "parallelism": f"replicas x{world} (independent layers, no collective)",
+                   "blockings_mkn": blks, "blocking_choice": args.blocking, "launch": args.launch, "kernel_source_hash": kernel_source_hash(), "parallelism": f"replicas x{world} (independent layers, no collective)",
                    "l2": "inputs larger than L2: one step reads/writes ~3 GB of ciphertexts/weights"},
         "latency_ms": {"p50": statistics.median(per), "p99": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))]},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "gpu_launches": launches,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "share_products": share,
+        "gpu_launches": launches,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
