@@ -369,9 +369,11 @@ __global__ void __launch_bounds__(M::kThreads + 32, MINB) k_mac_ws_t(const u64* 
                                                                      u32 nJ, u32 nLb, u32 tilesR, int* err,
                                                                      const __grid_constant__ Consts C) {
   extern __shared__ __align__(128) u64 sm[];
-  const u32 chunks = C.N >> 5;
-  const u32 chunk = blockIdx.x % chunks;
-  const u32 tile = blockIdx.x / chunks;
+  // tile-fastest: the blocks of one 32-slot chunk (all output tiles) run together, so the
+  // operand rows of that chunk are re-read from L2 rather than DRAM
+  const u32 tiles = tilesR * ((nI + M::kCols - 1) / M::kCols);
+  const u32 tile = blockIdx.x % tiles;
+  const u32 chunk = blockIdx.x / tiles;
   const u32 r0 = (tile % tilesR) * M::kRows, c0 = (tile / tilesR) * M::kCols;
   const u32 l = blockIdx.y % C.L;
   const u64 item = blockIdx.y / C.L;

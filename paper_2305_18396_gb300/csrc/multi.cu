@@ -69,10 +69,10 @@ __global__ void __launch_bounds__(M::kThreads + 32, MINB) k_mac_multi_t(const __
   const MultiItem& it = T.it[i];
   const u64 local = blockIdx.x - it.mac_begin;
   const u32 chunks = C.N >> 5;
-  const u32 chunk = local % chunks;
-  const u64 rest = local / chunks;
   const u32 tiles = it.tilesR * it.tilesC;
-  const u32 tile = rest % tiles, l = (u32)(rest / tiles);
+  const u32 tile = local % tiles;  // tile-fastest: a chunk's operand rows are reused from L2
+  const u64 rest = local / tiles;
+  const u32 chunk = rest % chunks, l = (u32)(rest / chunks);
   const u32 r0 = (tile % it.tilesR) * M::kRows, c0 = (tile / it.tilesR) * M::kCols;
   const u64 N = C.N, L = C.L;
   OutPlace out;

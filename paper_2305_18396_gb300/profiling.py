@@ -17,6 +17,7 @@ before them is set-up.
 import argparse
 import collections
 import csv
+import re
 import sys
 
 import numpy as np
@@ -62,10 +63,17 @@ def run_share_case(m, k, n, repeat=3):
     B.he_device_status(ctx)
 
 
-def summarize_launches(path, skip_prefixes=(), skip_first=0, metric="gpu__time_duration.sum"):
+def _short(name):
+    return re.sub(r"^.*?unnamed>::", "", name.split("(")[0].replace("void ", "")).strip()
+
+
+def summarize_launches(path, skip_prefixes=(), skip_first=0, metric="gpu__time_duration.sum", first=None, back=0,
+                       last=None):
     """Per kernel: (launches, total) of `metric` from an ncu --csv launch list (durations in
-    microseconds), leaving out the first `skip_first` launches and kernels named by a prefix."""
-    agg = collections.defaultdict(lambda: [0, 0.0])
+    microseconds).  Leaves out the first `skip_first` launches and kernels named by a prefix;
+    with `first` / `last` keeps only the window from `back` launches before the first launch
+    whose name contains `first` to the last launch whose name contains `last`."""
+    rows = []
     hdr = None
     with open(path, newline="") as f:
         for r in csv.reader(f):
@@ -82,11 +90,18 @@ def summarize_launches(path, skip_prefixes=(), skip_first=0, metric="gpu__time_d
                 v = v / 1e3 if u in ("ns", "nsecond") else v * 1e3 if u in ("ms", "msecond") else v
             elif u.endswith("byte"):
                 v *= {"Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(u, 1.0)
-            name = d["Kernel Name"].split("(")[0].replace("void ", "").strip()
-            if any(name.startswith(p) for p in skip_prefixes):
-                continue
-            agg[name][0] += 1
-            agg[name][1] += v
+            rows.append((_short(d["Kernel Name"]), v))
+    lo, hi = 0, len(rows)
+    if first:
+        lo = max(0, next(i for i, (nm, _) in enumerate(rows) if first in nm) - back)
+    if last:
+        hi = max(i for i, (nm, _) in enumerate(rows) if last in nm) + 1
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for name, v in rows[lo:hi]:
+        if any(name.startswith(p) for p in skip_prefixes):
+            continue
+        agg[name][0] += 1
+        agg[name][1] += v
     return dict(agg)
 
 
@@ -109,6 +124,9 @@ def main(argv=None):
     s.add_argument("--skip", action="append", default=[], help="kernel-name prefix to leave out")
     s.add_argument("--skip-first", type=int, default=0, help="leave out the first launches (set-up)")
     s.add_argument("--metric", default="gpu__time_duration.sum")
+    s.add_argument("--first", help="window starts at the first launch whose name contains this")
+    s.add_argument("--back", type=int, default=0, help="... and this many launches before it")
+    s.add_argument("--last", help="window ends at the last launch whose name contains this")
     a = ap.parse_args(argv)
     if a.cmd == "case":
         blk, si = run_case(a.m, a.k, a.n, a.repeat, not a.full_c0)
@@ -117,7 +135,7 @@ def main(argv=None):
         run_share_case(a.m, a.k, a.n, a.repeat)
         print("ok")
     else:
-        agg = summarize_launches(a.csv, tuple(a.skip), a.skip_first, a.metric)
+        agg = summarize_launches(a.csv, tuple(a.skip), a.skip_first, a.metric, a.first, a.back, a.last)
         tot = sum(v[1] for v in agg.values()) or 1.0
         print(f"| kernel | launches | total {a.metric} | per launch | share |\n|---|---|---|---|---|")
         for name, (cnt, x) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
