@@ -13,6 +13,7 @@
 #include "../../include/he_gb300.h"
 #include "kernels.h"
 #include "multi.h"
+#include "ntt.cuh"
 
 using he::u32;
 using he::u64;
@@ -779,7 +780,7 @@ namespace {
 struct MultiPlan {
   he::MultiTable T;
   u64 fwd = 0, mac = 0, inv = 0, c0 = 0, ws_bytes = 0;
-  u32 max_nc = 0;
+  u32 max_nc = 0;  // shared-memory words of the largest c0 transform
 };
 
 // Validates the products and lays out the table; workspace may be NULL (size query).
@@ -821,7 +822,7 @@ int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* w
       off = (off + 255) & ~(u64)255;
       it.c0_ntt = workspace ? (u64*)(workspace + off) : nullptr;
       off += out_cts * L * N * 8;
-      P->max_nc = std::max<u32>(P->max_nc, (u32)(N >> it.logkb));
+      P->max_nc = std::max<u32>(P->max_nc, he::c0_smem_words((u32)N, it.logkb));
     }
     it.fwd_begin = P->fwd;
     it.mac_begin = P->mac;

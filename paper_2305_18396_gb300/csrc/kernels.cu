@@ -730,7 +730,7 @@ cudaError_t launch_intt_c0_targets(const Consts& C, const u64* src, u64* dst, u6
                                    u32 logkb, u64 seed, cudaStream_t st) {
   const u64 polys = out_cts * batch * C.L;
   if (!polys) return cudaGetLastError();
-  const size_t smem = (size_t)(C.N + (C.N >> logkb)) * sizeof(u64);
+  const size_t smem = (size_t)c0_smem_words(C.N, logkb) * sizeof(u64);
   k_intt_c0_targets<<<(unsigned)polys, kNttThreads, smem, st>>>(src, dst, ct_stride, out_cts, logkb, seed, C);
   return cudaGetLastError();
 }

@@ -227,9 +227,8 @@ cudaError_t launch_inv_multi(const Consts& C, const MultiTable& T, u64 blocks, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_c0_multi(const Consts& C, const MultiTable& T, u64 blocks, u32 max_nc, cudaStream_t st) {
-  if (blocks)
-    k_c0_multi<<<(unsigned)blocks, kThreadsSmall, (size_t)(C.N + max_nc) * sizeof(u64), st>>>(T, C);
+cudaError_t launch_c0_multi(const Consts& C, const MultiTable& T, u64 blocks, u32 c0_words, cudaStream_t st) {
+  if (blocks) k_c0_multi<<<(unsigned)blocks, kThreadsSmall, (size_t)c0_words * sizeof(u64), st>>>(T, C);
   return cudaGetLastError();
 }
 

@@ -32,6 +32,6 @@ u32 mac_tile_cols();
 cudaError_t launch_fwd_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
 cudaError_t launch_mac_multi(const Consts& C, const MultiTable& T, u64 blocks, int* err, cudaStream_t st);
 cudaError_t launch_inv_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
-cudaError_t launch_c0_multi(const Consts& C, const MultiTable& T, u64 blocks, u32 max_nc, cudaStream_t st);
+cudaError_t launch_c0_multi(const Consts& C, const MultiTable& T, u64 blocks, u32 c0_words, cudaStream_t st);
 
 }  // namespace he

@@ -275,29 +275,87 @@ __device__ __forceinline__ void ntt_inverse_block(u64* sm, const PrimeConsts& P,
 
 // Compact-output mode, one c0 polynomial (prime l) of output ciphertext o: inverse NTT kept
 // only at the coefficients e = g k_b + k_b - 1, then c0_e - round(q s_e / t) for the mask
-// s of output o under `seed`.  src: N NTT-domain words; dst: N / k_b words.  sm: N + N/k_b
-// words of shared memory.  All threads of the block call it.
+// s of output o under `seed`.  src: N NTT-domain words in [0, q); dst: N / k_b words.
+// sm: c0_smem_words(N, log2 k_b) words of shared memory.  All threads of the block call it.
+//
+// The first log2 k_b Gentleman-Sande stages pair elements inside aligned groups of k_b
+// consecutive slots, and the kept position of group g (its last element) depends on that
+// group alone: for k_b <= 16 each thread loads whole groups (16-byte loads), runs the
+// pruned stages in registers (k_b - 1 Shoup products: stage s keeps the positions whose
+// low s + 1 bits are all ones) and writes one value to a compact array.  The remaining
+// log2(N / k_b) stages are an inverse transform of length N / k_b on that array: the
+// index of stage s's twiddle, N / 2^(s+1) + group, falls below N / k_b, where the table
+// entries are exactly the twiddles of that shorter transform (psi^{k_b} as its root).
+__host__ __device__ constexpr u32 c0_smem_words(u32 N, u32 logkb) {
+  return logkb <= 4 ? (N >> logkb) : N + (N >> logkb);
+}
+
+template <int LOGKB>
+__device__ __forceinline__ u64 c0_pruned_group(const u64* __restrict__ src, u32 g, u32 N, bool vec,
+                                               const PrimeConsts& P) {
+  constexpr int KB = 1 << LOGKB;
+  u64 v[KB];
+  const u64* p = src + (u64)g * KB;
+  if (vec) {  // 16-byte aligned group start (KB even, src 16-byte aligned)
+#pragma unroll
+    for (int i = 0; i < KB; i += 2) {
+      const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(p + i);
+      v[i] = t.x;
+      v[i + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < KB; ++i) v[i] = p[i];
+  }
+#pragma unroll
+  for (int s = 0; s < LOGKB; ++s) {
+    const int span = 1 << s;
+#pragma unroll
+    for (int i = (2 << s) - 1; i < KB; i += (2 << s)) {
+      const u32 widx = (N >> (s + 1)) + ((g * KB + i) >> (s + 1));
+      v[i] = mul_shoup(v[i - span] - v[i] + P.two_q, __ldg(P.ipsi + widx), __ldg(P.ipsi_sh + widx), P.q);
+    }
+  }
+  return v[KB - 1];
+}
+
 __device__ __forceinline__ void ntt_inverse_c0_targets(const u64* src, u64* dst, u32 logkb, u64 seed, u32 o, u32 l,
                                                        const Consts& C, u64* sm) {
   const PrimeConsts& P = C.p[l];
   const u32 N = C.N, logN = C.logN, Nc = N >> logkb;
   const u64 q = P.q, two_q = P.two_q;
-  u64* z = sm + N;  // compact values
-  for (u32 i = threadIdx.x; i < N; i += blockDim.x) sm[i] = src[i];
-  __syncthreads();
-  // pruned stages s < log2 k_b: keep positions whose low s+1 bits are all ones
-  for (u32 s = 0; s < logkb; ++s) {
-    const u32 span = 1u << s, ones = (2u << s) - 1;
-    for (u32 t = threadIdx.x; t < (N >> (s + 1)); t += blockDim.x) {
-      const u32 p = (t << (s + 1)) | ones;
-      const u32 widx = (N >> (s + 1)) + (p >> (s + 1));
-      const u64 U = sm[p - span], V = sm[p];
-      sm[p] = mul_shoup(U - V + two_q, __ldg(P.ipsi + widx), __ldg(P.ipsi_sh + widx), q);
+  u64* z;  // compact values
+  if (logkb <= 4) {
+    z = sm;
+    const bool vec = logkb >= 1 && ((reinterpret_cast<uintptr_t>(src) & 15) == 0);
+    for (u32 g = threadIdx.x; g < Nc; g += blockDim.x) {
+      u64 zv;
+      switch (logkb) {
+        case 0: zv = src[g]; break;
+        case 1: zv = c0_pruned_group<1>(src, g, N, vec, P); break;
+        case 2: zv = c0_pruned_group<2>(src, g, N, vec, P); break;
+        case 3: zv = c0_pruned_group<3>(src, g, N, vec, P); break;
+        default: zv = c0_pruned_group<4>(src, g, N, vec, P); break;
+      }
+      z[g] = zv;
     }
+  } else {  // long groups: stage the whole polynomial in shared memory
+    z = sm + N;
+    for (u32 i = threadIdx.x; i < N; i += blockDim.x) sm[i] = src[i];
     __syncthreads();
+    for (u32 s = 0; s < logkb; ++s) {
+      const u32 span = 1u << s, ones = (2u << s) - 1;
+      for (u32 t = threadIdx.x; t < (N >> (s + 1)); t += blockDim.x) {
+        const u32 p = (t << (s + 1)) | ones;
+        const u32 widx = (N >> (s + 1)) + (p >> (s + 1));
+        const u64 U = sm[p - span], V = sm[p];
+        sm[p] = mul_shoup(U - V + two_q, __ldg(P.ipsi + widx), __ldg(P.ipsi_sh + widx), q);
+      }
+      __syncthreads();
+    }
+    const u32 kb = 1u << logkb;
+    for (u32 g = threadIdx.x; g < Nc; g += blockDim.x) z[g] = sm[g * kb + kb - 1];
   }
-  const u32 kb = 1u << logkb;
-  for (u32 g = threadIdx.x; g < Nc; g += blockDim.x) z[g] = sm[g * kb + kb - 1];
   __syncthreads();
   // remaining stages on the compact array (span 2^(s - log2 k_b) there)
   for (u32 s = logkb; s < logN; ++s) {
@@ -312,6 +370,7 @@ __device__ __forceinline__ void ntt_inverse_c0_targets(const u64* src, u64* dst,
     }
     __syncthreads();
   }
+  const u32 kb = 1u << logkb;
   for (u32 g = threadIdx.x; g < Nc; g += blockDim.x) {
     u64 v = csub(mul_shoup(z[g], P.ninv, P.ninv_sh, q), q);
     const u32 e = g * kb + kb - 1;

@@ -318,6 +318,9 @@ def test_matmul_batch_equals_single_calls_and_oracle(B, N, L, m, k, n, blk):
     (8192, 3, 7, 33, 20, (8, 32, 32), 1),
     (4096, 2, 3, 5, 2, (1, 1, 1), 1),
     (4096, 2, 2, 300, 3, (1, 256, 16), 1),
+    (4096, 2, 12, 40, 30, (4, 16, 8), 2),
+    (4096, 2, 10, 9, 50, (8, 2, 64), 1),
+    (8192, 3, 20, 50, 40, (16, 16, 32), 1),
 ])
 def test_matmul_compact_c0(B, N, L, m, k, n, blk, batch):
     """With HE_DROP_C0 the output keeps c1 and c0 only at the decoded coefficients
