@@ -310,6 +310,14 @@ HE_API int he_unmask(he_ctx* ctx, uint64_t mask_seed, uint32_t m, uint32_t n, co
 HE_API int he_share_matmul(he_ctx* ctx, const uint64_t* X, const uint64_t* W, const uint64_t* bias,
                            const uint64_t* acc, uint32_t m, uint32_t k, uint32_t n, uint64_t* out, void* stream);
 
+/* he_share_matmul over `batch` same-shape items in one launch (e.g. the per-head
+ * <X>_1 <Y>_1 products of an attention layer): item b reads X + b m k, W + b k n,
+ * bias + b n, acc + b m n and writes out + b m n.  batch <= 65535; batch = 0 does
+ * nothing.  Errors as for he_share_matmul. */
+HE_API int he_share_matmul_batch(he_ctx* ctx, const uint64_t* X, const uint64_t* W, const uint64_t* bias,
+                                 const uint64_t* acc, uint32_t m, uint32_t k, uint32_t n, uint32_t batch,
+                                 uint64_t* out, void* stream);
+
 /* he_unmask into an existing share: with HE_UNMASK_ACCUMULATE the mask share of the
  * Pi_MatMul of an (m x k) . (k x n) product (blocking blk, mask_seed) is added mod t to
  * out instead of overwriting it; with HE_UNMASK_TRANSPOSE it goes to out as its

@@ -95,6 +95,7 @@ def _load():
         "he_autotune_blocking": (ctypes.c_int, [P, u32, u32, u32, u32, u32, u32, u32, P, sz, ctypes.POINTER(sz), pB,
                                                 ctypes.POINTER(ctypes.c_float), P]),
         "he_share_matmul": (ctypes.c_int, [P, P, P, P, P, u32, u32, u32, P, P]),
+        "he_share_matmul_batch": (ctypes.c_int, [P, P, P, P, P, u32, u32, u32, u32, P, P]),
         "he_expand_compact": (ctypes.c_int, [P, P, u32, u32, P, P]),
         "he_ntt_forward": (ctypes.c_int, [P, P, u32, P]),
         "he_ntt_inverse": (ctypes.c_int, [P, P, u32, P]),
@@ -415,19 +416,24 @@ def he_unmask_acc(ctx, mask_seed, m, n, blk, out, flags=HE_UNMASK_ACCUMULATE, st
 
 def he_share_matmul(ctx, X, W, m, k, n, bias=None, acc=None, out=None, stream=None):
     """Server-local share product: out = (acc + X W + bias) mod t, row-major device tensors."""
-    out = ctx.empty(m * n) if out is None else ctx._dev(out, m * n, "out")
-    if not m or not n:
+    return he_share_matmul_batch(ctx, X, W, m, k, n, 1, bias, acc, out, stream)
+
+
+def he_share_matmul_batch(ctx, X, W, m, k, n, batch, bias=None, acc=None, out=None, stream=None):
+    """`batch` same-shape share products laid back to back (item b at b m k, b k n, b n, b m n)."""
+    out = ctx.empty(batch * m * n) if out is None else ctx._dev(out, batch * m * n, "out")
+    if not m or not n or not batch:
         return out
     if k:
-        ctx._dev(X, m * k, "X")
-        ctx._dev(W, k * n, "W")
+        ctx._dev(X, batch * m * k, "X")
+        ctx._dev(W, batch * k * n, "W")
     if bias is not None:
-        ctx._dev(bias, n, "bias")
+        ctx._dev(bias, batch * n, "bias")
     if acc is not None:
-        ctx._dev(acc, m * n, "acc")
-    _check(lib.he_share_matmul(ctx.h, _ptr(X) if k else None, _ptr(W) if k else None,
-                               None if bias is None else _ptr(bias), None if acc is None else _ptr(acc),
-                               m, k, n, _ptr(out), _stream(stream)))
+        ctx._dev(acc, batch * m * n, "acc")
+    _check(lib.he_share_matmul_batch(ctx.h, _ptr(X) if k else None, _ptr(W) if k else None,
+                                     None if bias is None else _ptr(bias), None if acc is None else _ptr(acc),
+                                     m, k, n, batch, _ptr(out), _stream(stream)))
     return out
 
 

@@ -516,20 +516,26 @@ int he_unmask_acc(he_ctx* c, uint64_t mask_seed, uint32_t m, uint32_t n, const h
   });
 }
 
-int he_share_matmul(he_ctx* c, const uint64_t* X, const uint64_t* W, const uint64_t* bias, const uint64_t* acc,
-                    uint32_t m, uint32_t k, uint32_t n, uint64_t* out, void* stream) {
+int he_share_matmul_batch(he_ctx* c, const uint64_t* X, const uint64_t* W, const uint64_t* bias, const uint64_t* acc,
+                          uint32_t m, uint32_t k, uint32_t n, uint32_t batch, uint64_t* out, void* stream) {
   if (!c) return fail(HE_EINVAL, "ctx is NULL");
-  if (!m || !n) return HE_OK;
+  if (!m || !n || !batch) return HE_OK;
+  if (batch > 65535) return fail(HE_EINVAL, "batch must be <= 65535");
   if (!out || (k && (!X || !W))) return fail(HE_EINVAL, "NULL buffer");
   if (int r = set_device(c)) return r;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const u32 splits = k ? he::share_matmul_splits(m, k, n, sms > 0 ? sms : 1) : 1;
+  const u32 splits = k ? he::share_matmul_splits(m, k, n, batch, sms > 0 ? sms : 1) : 1;
   int r = launch(c, KShare, (cudaStream_t)stream, "share_matmul", [&] {
-    return he::launch_share_matmul(c->C, X, W, bias, acc, m, k, n, splits, out, (cudaStream_t)stream);
+    return he::launch_share_matmul(c->C, X, W, bias, acc, m, k, n, batch, splits, out, (cudaStream_t)stream);
   });
   if (r == HE_OK && splits > 1) c->launches.fetch_add(2, std::memory_order_relaxed);  // set-up + finishing pass
   return r;
+}
+
+int he_share_matmul(he_ctx* c, const uint64_t* X, const uint64_t* W, const uint64_t* bias, const uint64_t* acc,
+                    uint32_t m, uint32_t k, uint32_t n, uint64_t* out, void* stream) {
+  return he_share_matmul_batch(c, X, W, bias, acc, m, k, n, 1, out, stream);
 }
 
 int he_encode_weights_batch(he_ctx* c, const uint64_t* W, uint32_t k, uint32_t n, const he_blocking* blk,

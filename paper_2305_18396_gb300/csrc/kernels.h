@@ -29,9 +29,9 @@ cudaError_t launch_unpack(const Consts& C, const u64* dec, u32 m, u32 n, Blk b, 
 cudaError_t launch_unmask(const Consts& C, u64 seed, u32 m, u32 n, Blk b, u32 nI, u64* share, cudaStream_t st);
 cudaError_t launch_fill_random(const Consts& C, u64* dst, u64 words, u64 seed, int mode, cudaStream_t st);
 // share.cu: server-local share products and mask-share accumulation
-u32 share_matmul_splits(u32 m, u32 k, u32 n, int sms);
+u32 share_matmul_splits(u32 m, u32 k, u32 n, u32 batch, int sms);
 cudaError_t launch_share_matmul(const Consts& C, const u64* X, const u64* W, const u64* bias, const u64* acc, u32 m,
-                                u32 k, u32 n, u32 splits, u64* out, cudaStream_t st);
+                                u32 k, u32 n, u32 batch, u32 splits, u64* out, cudaStream_t st);
 cudaError_t launch_unmask_acc(const Consts& C, u64 seed, u32 m, u32 n, Blk b, u32 nI, int accumulate, int transpose,
                               u64* out, cudaStream_t st);
 

@@ -114,3 +114,41 @@ def test_attention_server_share(env):
     B.he_unmask_acc(ctx, 82, n, m, blk2, z, flags=B.HE_UNMASK_ACCUMULATE | B.HE_UNMASK_TRANSPOSE)
     want = (O.share_matmul(X1, Y1) + O.unmask(P, 81, m, n, blk1) + O.unmask(P, 82, n, m, blk2).T) % T
     assert np.array_equal(to_np(z, (m, n)), want)
+
+
+def test_share_matmul_batch_equals_items(env):
+    """A batch of per-head sized products in one launch equals each item alone and the oracle."""
+    B, ctx, P = env
+    batch, m, k, n = 12, 128, 64, 128
+    Xs = [S.uniform_share((m, k), 300 + b) for b in range(batch)]
+    Ws = [S.uniform_share((k, n), 400 + b) for b in range(batch)]
+    acc = S.uniform_share((batch * m, n), 500)
+    got = B.he_share_matmul_batch(ctx, to_dev(np.stack(Xs)), to_dev(np.stack(Ws)), m, k, n, batch,
+                                  acc=to_dev(acc))
+    got = to_np(got, (batch, m, n))
+    for b in range(batch):
+        assert np.array_equal(got[b], O.share_matmul(Xs[b], Ws[b], None, acc[b * m:(b + 1) * m]))
+    # split k across a batch (short outputs, long k), with a per-item bias
+    batch, m, k, n = 3, 8, 2000, 16
+    Xs = [S.uniform_share((m, k), 600 + b) for b in range(batch)]
+    Ws = [S.uniform_share((k, n), 700 + b) for b in range(batch)]
+    bias = S.uniform_share((batch, n), 800)
+    got = to_np(B.he_share_matmul_batch(ctx, to_dev(np.stack(Xs)), to_dev(np.stack(Ws)), m, k, n, batch,
+                                        bias=to_dev(bias)), (batch, m, n))
+    for b in range(batch):
+        assert np.array_equal(got[b], O.share_matmul(Xs[b], Ws[b], bias[b]))
+
+
+@pytest.mark.parametrize("log2t", [20, 37, 40])
+def test_share_matmul_other_plaintext_moduli(env, log2t):
+    """t = 2^20 and 2^37 take the packed cross term, t = 2^40 the general one: both exact."""
+    B, _, _ = env
+    ctx = B.Context(1024, 2, log2t=log2t)
+    t = 1 << log2t
+    rng = np.random.default_rng(log2t)
+    for m, k, n in [(33, 70, 65), (16, 1500, 8)]:
+        X = rng.integers(0, t, size=(m, k), dtype=np.uint64)
+        W = rng.integers(0, t, size=(k, n), dtype=np.uint64)
+        X[0, :] = t - 1
+        got = B.he_share_matmul(ctx, to_dev(X), to_dev(W), m, k, n)
+        assert np.array_equal(to_np(got, (m, n)), O.share_matmul(X, W, log2t=log2t))
