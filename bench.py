@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--launch", default="multi", choices=["multi", "groups"],
                     help="multi: the whole layer as one multi-product launch per step; groups: one batched "
                          "launch per product shape")
+    ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
+                    help="1: replay each step as a captured CUDA graph (multi launch; mask seeds read from device "
+                         "memory, fresh every step)")
     ap.add_argument("--blocking", default="tuned", choices=["tuned", "model"],
                     help="tuned: he_autotune_blocking per product at set-up; model: the cost model's choice")
     ap.add_argument("--full-c0", action="store_true",
@@ -139,7 +142,7 @@ class Layer:
     """Device state of one layer's products: resident weights, input ciphertexts, outputs.
     Products that occur once per head run as one same-shape batch (he_matmul_batch)."""
 
-    def __init__(self, B, ctx, prods, rank, want_host, flags, tune=True, multi=True):
+    def __init__(self, B, ctx, prods, rank, want_host, flags, tune=True, multi=True, graph=False):
         import numpy as np
         import torch
 
@@ -206,6 +209,14 @@ class Layer:
             self.items = items
             self.prods = B.make_products(items)
             self.multi_ws = ctx.empty(B.he_multi_workspace_bytes(ctx, self.prods) // 8 + 1)
+            # seed of item b of launch group c on step s: (s << 20) + idx_c + b
+            self.seed_offs = np.array([c["idx"] + b for c in self.calls for b in range(c["cnt"])], dtype=np.int64)
+        self.graph, self.graph_kernels = None, 0
+        if multi and graph:  # the replayed graph reads every product's mask seed from device memory
+            self.seeds_dev = torch.zeros(len(self.prods), dtype=torch.int64, device=dev)
+            for i, a in enumerate(self.prods):
+                a.flags |= B.HE_SEED_DEVICE
+                a.mask_seed = self.seeds_dev.data_ptr() + 8 * i
         self.host_ws = [ctx.empty(max_hostws), ctx.empty(max_hostws)] if want_host else None
         self.host_streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)] if want_host else None
         self.enc_done = torch.cuda.Event()
@@ -214,19 +225,46 @@ class Layer:
         self.products = sum(c["cnt"] for c in self.calls)
         torch.cuda.synchronize()
 
-    def step(self, step_idx, host=False):
+    def _multi_body(self):
+        B, ctx = self.B, self.ctx
+        for c in self.calls:
+            if "pt_step" in c:
+                p = c["p"]
+                B.he_encode_weights_batch(ctx, c["W"], p.k, p.n, c["blk"], c["cnt"], pt=c["pt_step"])
+        B.he_matmul_multi(ctx, self.prods, self.multi_ws)
+
+    def capture(self):
+        """Capture one step (per-step encodings + the whole-layer launch) as a CUDA graph."""
+        torch, B = self.torch, self.B
+        self.seeds_dev.copy_(torch.from_numpy(self.seed_offs))
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self._multi_body()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        l0 = B.he_launch_count(self.ctx)
+        with torch.cuda.graph(self.graph):
+            self._multi_body()
+        self.graph_kernels = B.he_launch_count(self.ctx) - l0
+        torch.cuda.synchronize()
+
+    def step(self, step_idx, host=False, eager=False):
         B, ctx = self.B, self.ctx
         if self.multi and not host:
-            i = 0
-            for c in self.calls:
-                p, cnt = c["p"], c["cnt"]
-                if "pt_step" in c:
-                    B.he_encode_weights_batch(ctx, c["W"], p.k, p.n, c["blk"], cnt, pt=c["pt_step"])
-                seed = (step_idx << 20) | c["idx"]
-                for b in range(cnt):
-                    self.prods[i].mask_seed = seed + b
-                    i += 1
-            B.he_matmul_multi(ctx, self.prods, self.multi_ws)
+            seeds = (step_idx << 20) + self.seed_offs
+            if self.graph is not None and not eager:
+                # this step's seeds into the device words the graph reads, then replay
+                self.seeds_dev.copy_(self.torch.from_numpy(seeds).pin_memory(), non_blocking=True)
+                self.graph.replay()
+                return
+            if self.graph is None:
+                for i, a in enumerate(self.prods):
+                    a.mask_seed = int(seeds[i])
+            else:  # eager pass of a graph-mode layer: the products read device seeds
+                self.seeds_dev.copy_(self.torch.from_numpy(seeds).pin_memory(), non_blocking=True)
+            self._multi_body()
             return
         k = 0
         for c in self.calls:
@@ -483,10 +521,14 @@ def gpu_arm(args, world, rank, local):
     prods = workloads.bert_layer_products(**workloads.BERT_BASE)
     want_host = not args.no_e2e
     flags = B.HE_FLAGS_NONE if args.full_c0 else B.HE_DROP_C0
-    layer = Layer(B, ctx, prods, rank, want_host, flags, tune=args.blocking == "tuned", multi=args.launch == "multi")
+    use_graph = args.graph and args.launch == "multi"
+    layer = Layer(B, ctx, prods, rank, want_host, flags, tune=args.blocking == "tuned", multi=args.launch == "multi",
+                  graph=use_graph)
     stream = torch.cuda.current_stream()
 
     mad_peak, mad_per_sm_clk = B.he_probe_mad_wide(ctx)
+    if use_graph:
+        layer.capture()
     for w in range(max(args.warmup, 3) if args.warmup else 0):
         layer.step(w)
     torch.cuda.synchronize()
@@ -507,7 +549,7 @@ def gpu_arm(args, world, rank, local):
         t_end.record(stream)
         torch.cuda.synchronize()
     barrier(world)
-    launches = B.he_launch_count(ctx) - l0
+    launches = B.he_launch_count(ctx) - l0 + layer.graph_kernels * args.steps  # graph replays: captured kernels
     total_ms = max_over_ranks(t_start.elapsed_time(t_end), world, device=f"cuda:{local}")
     per = [a.elapsed_time(b) for a, b in evs]
     ms_per_step = total_ms / args.steps
@@ -517,7 +559,7 @@ def gpu_arm(args, world, rank, local):
     B.he_profile_enable(ctx, True)
     steps_prof = max(3, min(args.steps, 10))
     for k in range(steps_prof):
-        layer.step(5000 + k)
+        layer.step(5000 + k, eager=True)
     stats = B.he_profile_read(ctx)
     B.he_profile_enable(ctx, False)
     alg = layer.algorithmic_bytes()
@@ -593,7 +635,8 @@ def gpu_arm(args, world, rank, local):
                    "plain_macs_per_step": layer.macs,
                    "output": "full ciphertexts" if args.full_c0 else
                    "c1 + c0 at the decoded coefficients only (Sec. 3.1.3, HE_DROP_C0)",
-                   "blockings_mkn": blks, "blocking_choice": args.blocking, "launch": args.launch, "kernel_source_hash": kernel_source_hash(), "parallelism": f"replicas x{world} (independent layers, no collective)",
+                   "blockings_mkn": blks, "blocking_choice": args.blocking, "launch": args.launch,
+                   "cuda_graph": bool(use_graph), "kernel_source_hash": kernel_source_hash(), "parallelism": f"replicas x{world} (independent layers, no collective)",
                    "l2": "inputs larger than L2: one step reads/writes ~3 GB of ciphertexts/weights"},
         "latency_ms": {"p50": statistics.median(per), "p99": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))]},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "share_products": share,

@@ -241,6 +241,13 @@ HE_API int he_matmul_batch(he_ctx* ctx, const uint64_t* ct_in, const uint64_t* p
                            const he_blocking* blk, uint32_t batch, uint64_t mask_seed, uint32_t flags,
                            uint64_t* ct_out, void* workspace, size_t workspace_bytes, void* stream);
 
+/* he_matmul_multi only (a product's flags): the product's mask_seed field holds the
+ * address of a device uint64_t, and the kernels read the seed from there when they run.
+ * A CUDA graph that captured the launch then re-masks with whatever seed the word holds
+ * at each replay (write it on the replay's stream before the replay).  The word must
+ * stay valid until the launch completes. */
+#define HE_SEED_DEVICE 16u
+
 /* One product of a multi-product launch. */
 typedef struct {
   const uint64_t* ct_in; /* device, in_words                                   */
@@ -248,15 +255,17 @@ typedef struct {
   uint64_t* ct_out;      /* device, out_words (out_words_compact with DROP_C0)  */
   uint32_t m, k, n;
   he_blocking blk;
-  uint32_t flags;        /* HE_FLAGS_NONE or HE_DROP_C0                          */
-  uint64_t mask_seed;
+  uint32_t flags;        /* HE_FLAGS_NONE, HE_DROP_C0, HE_SEED_DEVICE (or'ed)   */
+  uint64_t mask_seed;    /* the seed, or with HE_SEED_DEVICE its device address */
 } he_product;
 
 /* Up to 64 products of any shapes, blockings and output modes (e.g. the requests a
  * serving loop has admitted) in one set of launches: one forward-NTT grid, one
  * multiply-accumulate grid and one or two inverse-NTT grids over the union of the
  * products' work.  Each product's output is bit-identical to its own he_matmul call.
- * workspace: device, >= he_multi_workspace_bytes(ctx, count, items). */
+ * workspace: device, >= he_multi_workspace_bytes(ctx, count, items).  The call only
+ * enqueues kernels (no allocation, copy or synchronization), so it can be captured in
+ * a CUDA graph; with HE_SEED_DEVICE products the graph takes fresh seeds per replay. */
 HE_API int he_matmul_multi(he_ctx* ctx, uint32_t count, const he_product* items, void* workspace,
                            size_t workspace_bytes, void* stream);
 HE_API int he_multi_workspace_bytes(const he_ctx* ctx, uint32_t count, const he_product* items, size_t* bytes);

@@ -403,6 +403,7 @@ def he_unmask(ctx, mask_seed, m, n, blk, share=None, stream=None):
     return share
 
 
+HE_SEED_DEVICE = 16
 HE_UNMASK_ACCUMULATE = 4
 HE_UNMASK_TRANSPOSE = 8
 

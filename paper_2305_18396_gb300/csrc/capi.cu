@@ -800,7 +800,8 @@ int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* w
   for (u32 i = 0; i < count; ++i) {
     const he_product& x = items[i];
     if (int r = check_blk(c, &x.blk)) return r;
-    if (x.flags & ~(uint32_t)HE_DROP_C0) return fail(HE_EINVAL, "unknown flags");
+    if (x.flags & ~(uint32_t)(HE_DROP_C0 | HE_SEED_DEVICE)) return fail(HE_EINVAL, "unknown flags");
+    if ((x.flags & HE_SEED_DEVICE) && !x.mask_seed) return fail(HE_EINVAL, "HE_SEED_DEVICE with a NULL seed address");
     const bool compact = x.flags & HE_DROP_C0;
     if (compact && !pow2(x.blk.k_b)) return fail(HE_EINVAL, "HE_DROP_C0 needs a power-of-two k_b");
     if (!x.m || !x.k || !x.n) continue;
@@ -813,6 +814,7 @@ int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* w
     it.pt = x.pt;
     it.out = x.ct_out;
     it.mask_seed = x.mask_seed;
+    it.seed_dev = (x.flags & HE_SEED_DEVICE) ? reinterpret_cast<const u64*>((uintptr_t)x.mask_seed) : nullptr;
     it.nI = s.nI;
     it.nJ = s.nJ;
     it.nLb = s.nLb;

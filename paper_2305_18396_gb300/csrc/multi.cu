@@ -28,6 +28,10 @@ __device__ __forceinline__ u32 find_item(const MultiTable& T, u64 b, F begin) {
   return lo;
 }
 
+// The item's mask seed: its value, or the word it points to (a seed that a replayed CUDA
+// graph takes fresh on every replay).
+__device__ __forceinline__ u64 item_seed(const MultiItem& it) { return it.seed_dev ? *it.seed_dev : it.mask_seed; }
+
 template <int LOGN>
 __global__ void __launch_bounds__(NttShape<LOGN>::T) k_fwd_multi_t(const __grid_constant__ MultiTable T,
                                                                    const __grid_constant__ Consts C) {
@@ -111,9 +115,10 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_inv_multi_t(const __grid_
     const u32 o = (u32)(local / (2 * L));
     const PrimeConsts& P = C.p[l];
     u64* d = it.out + local * N;
+    const u64 seed = item_seed(it);
     ntt_inverse_block<S>(sm, P, [&](u32 e) { return d[e]; }, [&](u32 e, u64 v) {
       if (c == 0) {
-        const u64 sv = lo64(draw(it.mask_seed, e, o, kDomainMask, 0)) & C.tmask;
+        const u64 sv = lo64(draw(seed, e, o, kDomainMask, 0)) & C.tmask;
         v = sub_mod(v, delta_residue(sv, C, P), P.q);
       }
       d[e] = v;
@@ -140,13 +145,14 @@ __global__ void __launch_bounds__(kThreadsSmall) k_inv_multi_small(const __grid_
     o = (u32)(local / (2 * L));
     d = it.out + local * N;
   }
+  const u64 seed = item_seed(it);
   for (u32 e = threadIdx.x; e < N; e += blockDim.x) sm[e] = d[e];
   __syncthreads();
   ntt_inverse_smem(sm, C.logN, P);
   for (u32 e = threadIdx.x; e < N; e += blockDim.x) {
     u64 v = sm[e];
     if (c == 0) {
-      const u64 sv = lo64(draw(it.mask_seed, e, o, kDomainMask, 0)) & C.tmask;
+      const u64 sv = lo64(draw(seed, e, o, kDomainMask, 0)) & C.tmask;
       v = sub_mod(v, delta_residue(sv, C, P), P.q);
     }
     d[e] = v;
@@ -163,7 +169,7 @@ __global__ void __launch_bounds__(kThreadsSmall) k_c0_multi(const __grid_constan
   const u64 N = C.N, L = C.L, Nc = N >> it.logkb;
   const u32 l = local % L;
   const u32 o = (u32)(local / L);
-  ntt_inverse_c0_targets(it.c0_ntt + local * N, it.out + (u64)o * L * (Nc + N) + l * Nc, it.logkb, it.mask_seed, o, l,
+  ntt_inverse_c0_targets(it.c0_ntt + local * N, it.out + (u64)o * L * (Nc + N) + l * Nc, it.logkb, item_seed(it), o, l,
                          C, sm);
 }
 

@@ -16,6 +16,7 @@ struct MultiItem {
   u64* ctN;          // workspace: NTT of the inputs (slot-chunked)
   u64* c0_ntt;       // workspace (compact output only): NTT-domain c0 of every output
   u64 mask_seed;
+  const u64* seed_dev;  // HE_SEED_DEVICE: the seed is read from here when the kernels run
   u64 fwd_begin, mac_begin, inv_begin, c0_begin;
   u32 nI, nJ, nLb, logkb;
   u32 compact, tilesR, tilesC, pad;
