@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--launch", default="multi", choices=["multi", "groups"],
                     help="multi: the whole layer as one multi-product launch per step; groups: one batched "
                          "launch per product shape")
+    ap.add_argument("--host-depth", type=int, default=4,
+                    help="end-to-end leg: host-buffer steps in flight (streams with their own buffers)")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="1: replay each step as a captured CUDA graph (multi launch; mask seeds read from device "
                          "memory, fresh every step)")
@@ -142,7 +144,7 @@ class Layer:
     """Device state of one layer's products: resident weights, input ciphertexts, outputs.
     Products that occur once per head run as one same-shape batch (he_matmul_batch)."""
 
-    def __init__(self, B, ctx, prods, rank, want_host, flags, tune=True, multi=True, graph=False):
+    def __init__(self, B, ctx, prods, rank, want_host, flags, tune=True, multi=True, graph=False, host_depth=4):
         import numpy as np
         import torch
 
@@ -211,6 +213,28 @@ class Layer:
             self.multi_ws = ctx.empty(B.he_multi_workspace_bytes(ctx, self.prods) // 8 + 1)
             # seed of item b of launch group c on step s: (s << 20) + idx_c + b
             self.seed_offs = np.array([c["idx"] + b for c in self.calls for b in range(c["cnt"])], dtype=np.int64)
+        # host-buffer steps of the whole-layer launch: `host_depth` streams, each with its own
+        # device workspace, per-step share encodings and pinned output buffers (inputs are
+        # shared, read-only); consecutive steps rotate over the streams so one step's uploads
+        # and downloads overlap the others' kernels
+        self.host_sets, self.host_k = [], 0
+        if multi and want_host:
+            for sidx in range(host_depth):
+                items, pt_bufs = [], {}
+                for c in self.calls:
+                    p, si, cnt = c["p"], c["si"], c["cnt"]
+                    pt_all = c.get("pt")
+                    if pt_all is None:
+                        pt_all = pt_bufs[c["idx"]] = ctx.empty(cnt * si["pt_words"])
+                    out_h = torch.empty(cnt * si["out"], dtype=torch.int64).pin_memory()
+                    for b in range(cnt):
+                        items.append(dict(ct_in=c["in_host"][b * si["in_words"]:(b + 1) * si["in_words"]],
+                                          pt=pt_all[b * si["pt_words"]:(b + 1) * si["pt_words"]],
+                                          ct_out=out_h[b * si["out"]:(b + 1) * si["out"]], m=p.m, k=p.k, n=p.n,
+                                          blk=c["blk"], flags=flags, mask_seed=0, keep=out_h))
+                prods_h = B.make_products(items)
+                ws_h = ctx.empty(B.he_multi_host_workspace_bytes(ctx, prods_h) // 8 + 1)
+                self.host_sets.append((prods_h, ws_h, pt_bufs, items))
         self.graph, self.graph_kernels = None, 0
         if multi and graph:  # the replayed graph reads every product's mask seed from device memory
             self.seeds_dev = torch.zeros(len(self.prods), dtype=torch.int64, device=dev)
@@ -218,7 +242,7 @@ class Layer:
                 a.flags |= B.HE_SEED_DEVICE
                 a.mask_seed = self.seeds_dev.data_ptr() + 8 * i
         self.host_ws = [ctx.empty(max_hostws), ctx.empty(max_hostws)] if want_host else None
-        self.host_streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)] if want_host else None
+        self.host_streams = [torch.cuda.Stream(device=dev) for _ in range(max(2, host_depth))] if want_host else None
         self.enc_done = torch.cuda.Event()
         self.torch = torch
         self.macs = sum(c["p"].m * c["p"].k * c["p"].n * c["cnt"] for c in self.calls)
@@ -252,6 +276,21 @@ class Layer:
 
     def step(self, step_idx, host=False, eager=False):
         B, ctx = self.B, self.ctx
+        if self.multi and host:
+            k = self.host_k
+            self.host_k = (k + 1) % len(self.host_sets)
+            prods_h, ws_h, pt_bufs, _ = self.host_sets[k]
+            st = self.host_streams[k]
+            for c in self.calls:
+                if c["idx"] in pt_bufs:
+                    p = c["p"]
+                    B.he_encode_weights_batch(ctx, c["W"], p.k, p.n, c["blk"], c["cnt"], pt=pt_bufs[c["idx"]],
+                                              stream=st)
+            seeds = (step_idx << 20) + self.seed_offs
+            for i, a in enumerate(prods_h):
+                a.mask_seed = int(seeds[i])
+            B.he_matmul_multi_host(ctx, prods_h, ws_h, flags=B.HE_ASYNC, stream=st)
+            return
         if self.multi and not host:
             seeds = (step_idx << 20) + self.seed_offs
             if self.graph is not None and not eager:
@@ -523,7 +562,7 @@ def gpu_arm(args, world, rank, local):
     flags = B.HE_FLAGS_NONE if args.full_c0 else B.HE_DROP_C0
     use_graph = args.graph and args.launch == "multi"
     layer = Layer(B, ctx, prods, rank, want_host, flags, tune=args.blocking == "tuned", multi=args.launch == "multi",
-                  graph=use_graph)
+                  graph=use_graph, host_depth=args.host_depth)
     stream = torch.cuda.current_stream()
 
     mad_peak, mad_per_sm_clk = B.he_probe_mad_wide(ctx)
@@ -604,12 +643,13 @@ def gpu_arm(args, world, rank, local):
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ksteps = max(1, min(args.steps, 5))
+        ksteps = max(1, min(args.steps, 40))
         for k in range(ksteps):
             layer.step(9100 + k, host=True)
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, world, device=f"cuda:{local}")
         e2e = {"value": world * layer.macs * ksteps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "steps_in_flight": len(layer.host_sets) if layer.multi else 2,
                "d2h_bytes_per_step": d2h, "steps": ksteps, "ms_per_step": dt * 1e3 / ksteps}
 
     share = share_products_leg(B, ctx, prods, mad_peak)

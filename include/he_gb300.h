@@ -270,6 +270,18 @@ HE_API int he_matmul_multi(he_ctx* ctx, uint32_t count, const he_product* items,
                            size_t workspace_bytes, void* stream);
 HE_API int he_multi_workspace_bytes(const he_ctx* ctx, uint32_t count, const he_product* items, size_t* bytes);
 
+/* he_matmul_multi from HOST buffers: each product's ct_in and ct_out are host pointers
+ * (pinned memory lets the copies overlap other streams' work).  Enqueues on `stream` one
+ * host-to-device copy per input, the multi-product launch and one device-to-host copy
+ * per output, staging them in the workspace, then waits for the stream unless flags has
+ * HE_ASYNC (the caller then synchronizes before reading ct_out and keeps the host
+ * buffers and the workspace alive until then).  Calls on two streams with their own
+ * workspaces overlap one call's transfers with the other's kernels.
+ * workspace: device, >= he_multi_host_workspace_bytes(ctx, count, items). */
+HE_API int he_matmul_multi_host(he_ctx* ctx, uint32_t count, const he_product* items, uint32_t flags, void* workspace,
+                                size_t workspace_bytes, void* stream);
+HE_API int he_multi_host_workspace_bytes(const he_ctx* ctx, uint32_t count, const he_product* items, size_t* bytes);
+
 /* he_matmul for callers that cannot allocate device memory.  Some callers have no
  * way to obtain a workspace: a serving process whose device memory is already
  * reserved by another allocator (where cudaMalloc would fail, or would stall the

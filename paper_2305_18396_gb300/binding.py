@@ -96,6 +96,8 @@ def _load():
                                                 ctypes.POINTER(ctypes.c_float), P]),
         "he_share_matmul": (ctypes.c_int, [P, P, P, P, P, u32, u32, u32, P, P]),
         "he_share_matmul_batch": (ctypes.c_int, [P, P, P, P, P, u32, u32, u32, u32, P, P]),
+        "he_matmul_multi_host": (ctypes.c_int, [P, u32, ctypes.POINTER(Product), u32, P, sz, P]),
+        "he_multi_host_workspace_bytes": (ctypes.c_int, [P, u32, ctypes.POINTER(Product), ctypes.POINTER(sz)]),
         "he_expand_compact": (ctypes.c_int, [P, P, u32, u32, P, P]),
         "he_ntt_forward": (ctypes.c_int, [P, P, u32, P]),
         "he_ntt_inverse": (ctypes.c_int, [P, P, u32, P]),
@@ -322,6 +324,18 @@ def he_matmul_multi(ctx, products, workspace, stream=None):
     """products: from make_products (keeps the descriptor array alive for the call)."""
     _check(lib.he_matmul_multi(ctx.h, len(products), products, _ptr(workspace), workspace.numel() * 8,
                                _stream(stream)))
+
+
+def he_multi_host_workspace_bytes(ctx, products):
+    out = ctypes.c_size_t()
+    _check(lib.he_multi_host_workspace_bytes(ctx.h, len(products), products, ctypes.byref(out)))
+    return out.value
+
+
+def he_matmul_multi_host(ctx, products, workspace, flags=HE_FLAGS_NONE, stream=None):
+    """products: from make_products with HOST (preferably pinned) ct_in / ct_out tensors."""
+    _check(lib.he_matmul_multi_host(ctx.h, len(products), products, flags, _ptr(workspace), workspace.numel() * 8,
+                                    _stream(stream)))
 
 
 def he_matmul(ctx, ct_in, pt, m, k, n, blk, mask_seed, ct_out=None, workspace=None, flags=HE_FLAGS_NONE,

@@ -878,6 +878,80 @@ int he_matmul_multi(he_ctx* c, uint32_t count, const he_product* items, void* wo
   return r;
 }
 
+namespace {
+
+// Device words of one product's input and output ciphertexts (output compact with DROP_C0).
+void product_io_words(const he_ctx* c, const he_product& x, u64* in_w, u64* out_w) {
+  he_size_info si;
+  he_sizes(c, x.m, x.k, x.n, &x.blk, &si);
+  const bool empty = !x.m || !x.k || !x.n;
+  *in_w = empty ? 0 : si.in_words;
+  *out_w = empty ? 0 : ((x.flags & HE_DROP_C0) ? si.out_words_compact : si.out_words);
+}
+
+u64 up256(u64 b) { return (b + 255) & ~(u64)255; }
+
+}  // namespace
+
+int he_multi_host_workspace_bytes(const he_ctx* c, uint32_t count, const he_product* items, size_t* bytes) {
+  if (!c || !bytes) return fail(HE_EINVAL, "NULL argument");
+  MultiPlan P;
+  if (int r = plan_multi(c, count, items, nullptr, &P)) return r;
+  u64 need = up256(P.ws_bytes);
+  for (u32 i = 0; i < count; ++i) {
+    u64 in_w, out_w;
+    product_io_words(c, items[i], &in_w, &out_w);
+    need += up256(8 * in_w) + up256(8 * out_w);
+  }
+  *bytes = need;
+  return HE_OK;
+}
+
+int he_matmul_multi_host(he_ctx* c, uint32_t count, const he_product* items, uint32_t flags, void* workspace,
+                         size_t workspace_bytes, void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (flags & ~(uint32_t)HE_ASYNC) return fail(HE_EINVAL, "flags other than HE_ASYNC");
+  size_t need = 0;
+  if (int r = he_multi_host_workspace_bytes(c, count, items, &need)) return r;
+  if (!count) return HE_OK;
+  if (!workspace) return fail(HE_EINVAL, "workspace is NULL");
+  if (workspace_bytes < need) return fail(HE_ENOMEM, "workspace smaller than he_multi_host_workspace_bytes()");
+  MultiPlan P;
+  if (int r = plan_multi(c, count, items, nullptr, &P)) return r;
+  if (int r = set_device(c)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  // [multi-product workspace][inputs][outputs]: the items' host buffers staged on the device
+  std::vector<he_product> dev(items, items + count);
+  char* base = (char*)workspace;
+  u64 off = up256(P.ws_bytes);
+  for (u32 i = 0; i < count; ++i) {
+    u64 in_w, out_w;
+    product_io_words(c, items[i], &in_w, &out_w);
+    if (in_w && (!items[i].ct_in || !items[i].ct_out)) return fail(HE_EINVAL, "NULL host buffer");
+    dev[i].ct_in = (const uint64_t*)(base + off);
+    off += up256(8 * in_w);
+    dev[i].ct_out = (uint64_t*)(base + off);
+    off += up256(8 * out_w);
+    if (in_w) {
+      cudaError_t e = cudaMemcpyAsync((void*)dev[i].ct_in, items[i].ct_in, 8 * in_w, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "matmul_multi_host: upload");
+    }
+  }
+  if (int r = he_matmul_multi(c, count, dev.data(), workspace, P.ws_bytes, stream)) return r;
+  for (u32 i = 0; i < count; ++i) {
+    u64 in_w, out_w;
+    product_io_words(c, items[i], &in_w, &out_w);
+    if (!out_w) continue;
+    cudaError_t e = cudaMemcpyAsync(items[i].ct_out, dev[i].ct_out, 8 * out_w, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "matmul_multi_host: download");
+  }
+  if (!(flags & HE_ASYNC)) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "matmul_multi_host: synchronize");
+  }
+  return HE_OK;
+}
+
 int he_expand_compact(he_ctx* c, const uint64_t* ct_compact, uint32_t cnt, uint32_t k_b, uint64_t* ct_full,
                       void* stream) {
   if (!c) return fail(HE_EINVAL, "ctx is NULL");

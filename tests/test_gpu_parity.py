@@ -440,3 +440,47 @@ def test_matmul_host_async_two_streams(B):
         s_.synchronize()
     for o, r in zip(outs, refs):
         assert np.array_equal(o.numpy().view(np.uint64), r)
+
+
+def test_matmul_multi_host_buffers(B):
+    """he_matmul_multi_host (host ct_in / ct_out, pinned) equals he_matmul_multi on device
+    buffers, synchronously and with HE_ASYNC calls on two streams."""
+    ctx, P = ctx_for(B, 4096, 2)
+    sk = B.he_keygen(ctx, 3)
+    shapes = [(16, 64, 64, 0), (40, 96, 48, B.HE_DROP_C0), (9, 70, 37, B.HE_DROP_C0), (0, 5, 5, 0)]
+    dev_items, host_items = [], []
+    for i, (m, k, n, flags) in enumerate(shapes):
+        blk = ctx.default_blocking(max(m, 1), k, n)
+        si = ctx.sizes(m, k, n, blk)
+        ow = si["out_words_compact"] if flags else si["out_words"]
+        X = S.uniform_share((m, k), 40 + i)
+        W = S.fixed_point_weights((k, n), 50 + i)
+        ct = B.he_encrypt(ctx, sk, B.he_pack_input(ctx, to_dev(X), m, k, blk), 60 + i) if m else ctx.empty(1)
+        pt = B.he_encode_weights(ctx, to_dev(W), k, n, blk)
+        dev_items.append(dict(ct_in=ct, pt=pt, ct_out=ctx.empty(max(ow, 1)), m=m, k=k, n=n, blk=blk, flags=flags,
+                              mask_seed=70 + i))
+        host_items.append(dict(dev_items[-1], ct_in=ct.cpu().pin_memory(),
+                               ct_out=torch.zeros(max(ow, 1), dtype=torch.int64).pin_memory()))
+    prods = B.make_products(dev_items)
+    B.he_matmul_multi(ctx, prods, ctx.empty(B.he_multi_workspace_bytes(ctx, prods) // 8 + 1))
+    hprods = B.make_products(host_items)
+    need = B.he_multi_host_workspace_bytes(ctx, hprods)
+    B.he_matmul_multi_host(ctx, hprods, ctx.empty(need // 8 + 1))
+    for d, h in zip(dev_items, host_items):
+        if d["m"]:  # an empty product writes nothing
+            assert np.array_equal(to_np(d["ct_out"]), h["ct_out"].numpy().view(np.uint64))
+    # two asynchronous calls in flight on two streams, each with its own workspace and outputs
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for st in streams:
+        items = [dict(h, ct_out=torch.zeros_like(h["ct_out"]).pin_memory()) for h in host_items]
+        pr = B.make_products(items)
+        ws = ctx.empty(need // 8 + 1)
+        B.he_matmul_multi_host(ctx, pr, ws, flags=B.HE_ASYNC, stream=st)
+        outs.append((items, pr, ws))
+    for st in streams:
+        st.synchronize()
+    for items, _, _ in outs:
+        for d, h in zip(dev_items, items):
+            if d["m"]:
+                assert np.array_equal(to_np(d["ct_out"]), h["ct_out"].numpy().view(np.uint64))
