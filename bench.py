@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--launch", default="multi", choices=["multi", "groups"],
                     help="multi: the whole layer as one multi-product launch per step; groups: one batched "
                          "launch per product shape")
-    ap.add_argument("--host-depth", type=int, default=4,
+    ap.add_argument("--host-depth", type=int, default=6,
                     help="end-to-end leg: host-buffer steps in flight (streams with their own buffers)")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="1: replay each step as a captured CUDA graph (multi launch; mask seeds read from device "
@@ -144,7 +144,7 @@ class Layer:
     """Device state of one layer's products: resident weights, input ciphertexts, outputs.
     Products that occur once per head run as one same-shape batch (he_matmul_batch)."""
 
-    def __init__(self, B, ctx, prods, rank, want_host, flags, tune=True, multi=True, graph=False, host_depth=4):
+    def __init__(self, B, ctx, prods, rank, want_host, flags, tune=True, multi=True, graph=False, host_depth=6):
         import numpy as np
         import torch
 
@@ -639,7 +639,8 @@ def gpu_arm(args, world, rank, local):
     if want_host:
         h2d = sum(8 * c["cnt"] * c["si"]["in_words"] for c in layer.calls)
         d2h = sum(8 * c["cnt"] * c["si"]["out"] for c in layer.calls)
-        layer.step(9000, host=True)
+        for w in range(max(2, len(layer.host_sets))):  # every stream's buffers once before timing
+            layer.step(9000 + w, host=True)
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
