@@ -31,6 +31,13 @@ METRIC = "HE-MatMul plaintext MACs/s"
 UNIT = "MAC/s"
 N_POLY, L_PRIMES = 4096, 2
 WORKLOAD = "bert-base layer linear products, seq 128 (QKV, attn-out, FFN1, FFN2 + 12 heads x 2 cross terms x {QK^T, PV})"
+# selectable with --workload; the default is the headline configuration
+WORKLOADS = {
+    "bert-base": dict(N=N_POLY, L=L_PRIMES, model="BERT_BASE", desc=WORKLOAD, baseline_fc=("attn_out", "qkv")),
+    "bert-large-n8192": dict(N=8192, L=3, model="BERT_LARGE", baseline_fc=(),
+                             desc="bert-large layer linear products, seq 512, N=8192, L=3 (QKV, attn-out, FFN1, FFN2 "
+                                  "+ 16 heads x 2 cross terms x {QK^T, PV})"),
+}
 
 
 def parse():
@@ -47,6 +54,9 @@ def parse():
     ap.add_argument("--launch", default="multi", choices=["multi", "groups"],
                     help="multi: the whole layer as one multi-product launch per step; groups: one batched "
                          "launch per product shape")
+    ap.add_argument("--workload", default="bert-base", choices=sorted(WORKLOADS),
+                    help="bert-base: the headline layer (N=4096, L=2); bert-large-n8192: a BERT-large layer at seq "
+                         "512 with N=8192, L=3")
     ap.add_argument("--host-depth", type=int, default=6,
                     help="end-to-end leg: host-buffer steps in flight (streams with their own buffers)")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
@@ -209,8 +219,11 @@ class Layer:
                                       ct_out=c["out"][b * si["out"]:(b + 1) * si["out"]], m=p.m, k=p.k, n=p.n,
                                       blk=c["blk"], flags=flags, mask_seed=0))
             self.items = items
-            self.prods = B.make_products(items)
-            self.multi_ws = ctx.empty(B.he_multi_workspace_bytes(ctx, self.prods) // 8 + 1)
+            # at most 64 products per multi-product launch: larger layers run as consecutive
+            # launches on one stream, sharing one workspace
+            self.prod_chunks = [B.make_products(items[i:i + 64]) for i in range(0, len(items), 64)]
+            self.prods = [a for arr in self.prod_chunks for a in arr]
+            self.multi_ws = ctx.empty(max(B.he_multi_workspace_bytes(ctx, arr) for arr in self.prod_chunks) // 8 + 1)
             # seed of item b of launch group c on step s: (s << 20) + idx_c + b
             self.seed_offs = np.array([c["idx"] + b for c in self.calls for b in range(c["cnt"])], dtype=np.int64)
         # host-buffer steps of the whole-layer launch: `host_depth` streams, each with its own
@@ -232,9 +245,9 @@ class Layer:
                                           pt=pt_all[b * si["pt_words"]:(b + 1) * si["pt_words"]],
                                           ct_out=out_h[b * si["out"]:(b + 1) * si["out"]], m=p.m, k=p.k, n=p.n,
                                           blk=c["blk"], flags=flags, mask_seed=0, keep=out_h))
-                prods_h = B.make_products(items)
-                ws_h = ctx.empty(B.he_multi_host_workspace_bytes(ctx, prods_h) // 8 + 1)
-                self.host_sets.append((prods_h, ws_h, pt_bufs, items))
+                chunks_h = [B.make_products(items[i:i + 64]) for i in range(0, len(items), 64)]
+                ws_h = ctx.empty(max(B.he_multi_host_workspace_bytes(ctx, arr) for arr in chunks_h) // 8 + 1)
+                self.host_sets.append((chunks_h, ws_h, pt_bufs, items))
         self.graph, self.graph_kernels = None, 0
         if multi and graph:  # the replayed graph reads every product's mask seed from device memory
             self.seeds_dev = torch.zeros(len(self.prods), dtype=torch.int64, device=dev)
@@ -255,7 +268,8 @@ class Layer:
             if "pt_step" in c:
                 p = c["p"]
                 B.he_encode_weights_batch(ctx, c["W"], p.k, p.n, c["blk"], c["cnt"], pt=c["pt_step"])
-        B.he_matmul_multi(ctx, self.prods, self.multi_ws)
+        for arr in self.prod_chunks:
+            B.he_matmul_multi(ctx, arr, self.multi_ws)
 
     def capture(self):
         """Capture one step (per-step encodings + the whole-layer launch) as a CUDA graph."""
@@ -279,7 +293,7 @@ class Layer:
         if self.multi and host:
             k = self.host_k
             self.host_k = (k + 1) % len(self.host_sets)
-            prods_h, ws_h, pt_bufs, _ = self.host_sets[k]
+            chunks_h, ws_h, pt_bufs, _ = self.host_sets[k]
             st = self.host_streams[k]
             for c in self.calls:
                 if c["idx"] in pt_bufs:
@@ -287,9 +301,12 @@ class Layer:
                     B.he_encode_weights_batch(ctx, c["W"], p.k, p.n, c["blk"], c["cnt"], pt=pt_bufs[c["idx"]],
                                               stream=st)
             seeds = (step_idx << 20) + self.seed_offs
-            for i, a in enumerate(prods_h):
-                a.mask_seed = int(seeds[i])
-            B.he_matmul_multi_host(ctx, prods_h, ws_h, flags=B.HE_ASYNC, stream=st)
+            i = 0
+            for arr in chunks_h:
+                for a in arr:
+                    a.mask_seed = int(seeds[i])
+                    i += 1
+                B.he_matmul_multi_host(ctx, arr, ws_h, flags=B.HE_ASYNC, stream=st)
             return
         if self.multi and not host:
             seeds = (step_idx << 20) + self.seed_offs
@@ -393,9 +410,10 @@ def peaks():
 # ------------------------------------------------------------------ CPU oracle legs
 
 
-def oracle_sample(kind="baseline"):
+def oracle_sample(kind="baseline", workload="bert-base"):
     """The oracle as it stands on a bounded sample of the layer: one head's four
-    attention cross products (+ the whole attention-output product for the baseline)."""
+    attention cross products (+ the QKV and attention-output products for the baseline of
+    the default workload)."""
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
     import numpy as np  # noqa: F401
 
@@ -404,19 +422,21 @@ def oracle_sample(kind="baseline"):
     from paper_2305_18396_gb300 import workloads
     from paper_2305_18396_gb300.binding import he_choose_blocking
 
-    prods = [p for p in workloads.bert_layer_products(distinct_heads=1, **workloads.BERT_BASE)]
+    wl = WORKLOADS[workload]
+    n_poly, l_primes = wl["N"], wl["L"]
+    prods = [p for p in workloads.bert_layer_products(distinct_heads=1, **getattr(workloads, wl["model"]))]
     heads = [p for p in prods if p.share_weights]
     heads = heads + [heads[0]]  # qk_x1 has the shape of qk_x0
     if kind == "baseline":
-        heads = heads + [p for p in prods if p.name in ("attn_out", "qkv")]
-    P = O.Params(N_POLY, L_PRIMES)
+        heads = heads + [p for p in prods if p.name in wl["baseline_fc"]]
+    P = O.Params(n_poly, l_primes)
     s = O.keygen(P, S.SEED_KEY)
     jobs = []
     for i, p in enumerate(heads):
-        blk = he_choose_blocking(N_POLY, L_PRIMES, p.m, p.k, p.n, p.share_weights)
+        blk = he_choose_blocking(n_poly, l_primes, p.m, p.k, p.n, p.share_weights)
         X = S.uniform_share((p.m, p.k), 100 + i)
         W = S.uniform_share((p.k, p.n), 200 + i) if p.share_weights else S.fixed_point_weights((p.k, p.n), 200 + i)
-        ct = O.encrypt(P, s, O.pack_input(X, blk, N_POLY), 300 + i)
+        ct = O.encrypt(P, s, O.pack_input(X, blk, n_poly), 300 + i)
         jobs.append((p, blk, ct, W))
     return P, jobs, O
 
@@ -430,19 +450,20 @@ def run_oracle(P, jobs, O, seed):
     return macs, time.perf_counter() - t0
 
 
-def cpu_baseline():
-    P, jobs, O = oracle_sample("baseline")
+def cpu_baseline(workload="bert-base"):
+    P, jobs, O = oracle_sample("baseline", workload)
     macs, dt = run_oracle(P, jobs, O, 12345)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": macs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one head's 4 attention cross products + the QKV and attn-out products ({macs} plain MACs, "
+            "sample": f"one head's 4 attention cross products"
+                      f"{' + the QKV and attn-out products' if WORKLOADS[workload]['baseline_fc'] else ''} ({macs} plain MACs, "
                       f"{dt:.1f} s), full Pi_MatMul (encode, NTT, MAC, INTT, mask) on the host cores"}
 
 
 def reference_arm(args, world, rank):
     if rank != 0:
         return
-    P, jobs, O = oracle_sample("reference")
+    P, jobs, O = oracle_sample("reference", args.workload)
     for w in range(args.warmup):
         run_oracle(P, jobs, O, w)
     tot_macs, tot_t, per = 0, 0.0, []
@@ -456,7 +477,8 @@ def reference_arm(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " -- CPU oracle sample", "N": N_POLY, "L": L_PRIMES, "log2_t": 37},
+            "config": {"workload": WORKLOADS[args.workload]["desc"] + " -- CPU oracle sample",
+                       "N": WORKLOADS[args.workload]["N"], "L": WORKLOADS[args.workload]["L"], "log2_t": 37},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"per step: one head's 4 attention cross products ({tot_macs // args.steps} "
                                        "plain MACs), full Pi_MatMul on the host cores"},
@@ -556,8 +578,9 @@ def gpu_arm(args, world, rank, local):
     from paper_2305_18396_gb300 import workloads
 
     torch.cuda.set_device(local)
-    ctx = B.Context(N_POLY, L_PRIMES, device=local)
-    prods = workloads.bert_layer_products(**workloads.BERT_BASE)
+    wl = WORKLOADS[args.workload]
+    ctx = B.Context(wl["N"], wl["L"], device=local)
+    prods = workloads.bert_layer_products(**getattr(workloads, wl["model"]))
     want_host = not args.no_e2e
     flags = B.HE_FLAGS_NONE if args.full_c0 else B.HE_DROP_C0
     use_graph = args.graph and args.launch == "multi"
@@ -662,7 +685,7 @@ def gpu_arm(args, world, rank, local):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(args.workload)
     blks = {}
     for c in layer.calls:
         blks.setdefault(c["p"].name, list(c["blk"]))
@@ -670,7 +693,7 @@ def gpu_arm(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N_POLY, "L": L_PRIMES, "log2_t": 37,
+        "config": {"workload": wl["desc"], "N": wl["N"], "L": wl["L"], "log2_t": 37,
                    "products_per_step": layer.products,
                    "launch_groups_per_step": 1 if layer.multi else len(layer.calls),
                    "plain_macs_per_step": layer.macs,

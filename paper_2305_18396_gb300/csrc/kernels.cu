@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kNttThreads) k_poly_mul(const u64* a, const u6
   for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) c[poly * C.N + i] = sa[i];
 }
 
-// Forward NTT of matmul inputs for N < 512 into the slot-chunked layout (see k_mac_t).
+// Forward NTT of matmul inputs for N < 512 into the slot-chunked layout (see mac.cuh).
 
 
 __global__ void __launch_bounds__(kNttThreads) k_ntt_forward_mm_small(const u64* src, u64* ctN, u32 nJ, u32 nLb,
@@ -392,26 +392,6 @@ cudaError_t launch_mac_ws_cfg(const Consts& C, const u64* ctN, const u64* pt, Ou
   return cudaGetLastError();
 }
 
-// Slot-wise multiply-accumulate of one product or a same-shape batch: the block body is
-// mac_tile (mac.cuh); grid x = (chunk group, output tile), grid y = (batch item, prime).
-template <class M, int MINB>
-__global__ void __launch_bounds__(M::kThreads, MINB) k_mac_t(const u64* __restrict__ ctN, const u64* __restrict__ pt,
-                                                             OutPlace out, u32 nI, u32 nJ, u32 nLb,
-                                                             u32 tilesR, int* err, const __grid_constant__ Consts C) {
-  extern __shared__ __align__(128) u64 sm[];
-  constexpr int CPB = M::kChunksPerBlock;
-  const u32 chunks = C.N >> 5;
-  const u32 groups = (chunks + CPB - 1) / CPB;
-  const u32 chunk0 = (blockIdx.x % groups) * CPB;
-  const u32 nch = min((u32)CPB, chunks - chunk0);
-  const u32 tile = blockIdx.x / groups;
-  const u32 r0 = (tile % tilesR) * M::kRows, c0 = (tile / tilesR) * M::kCols;
-  const u32 l = blockIdx.y % C.L;
-  const u64 item = blockIdx.y / C.L;  // batch item
-  const u64 per_in = (u64)nLb * nJ * 2 * C.L * C.N, per_pt = (u64)nI * nJ * C.L * C.N;
-  mac_tile<M>(ctN + item * per_in, pt + item * per_pt, out, item * ((u64)nLb * nI), nI, nJ, nLb, r0, c0, chunk0, nch,
-              l, err, C, sm);
-}
 
 
 // Forward NTT of the input ciphertexts of a product into the slot-chunked operand layout.
@@ -554,7 +534,6 @@ cudaError_t configure_kernels(const Consts&) {
   set((const void*)k_decrypt, all);
   set((const void*)k_encode_weights, one);
   set((const void*)k_intt_mask, one);
-  set((const void*)k_mac_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
   set((const void*)k_mac_ws_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
 #define HE_SET_T(LOGN)                                                                             \
   set((const void*)k_ntt_forward_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
@@ -667,16 +646,6 @@ cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, B
   return cudaGetLastError();
 }
 
-template <class M, int MINB>
-cudaError_t launch_mac_cfg(const Consts& C, const u64* ctN, const u64* pt, OutPlace out, u32 nI, u32 nJ, u32 nLb,
-                           u32 batch, int* err, cudaStream_t st) {
-  const u32 tilesR = (2 * nLb + M::kRows - 1) / M::kRows, tilesC = (nI + M::kCols - 1) / M::kCols;
-  if ((u64)tilesR * tilesC * nJ * batch == 0) return cudaGetLastError();
-  const u64 groups = ((C.N >> 5) + M::kChunksPerBlock - 1) / M::kChunksPerBlock;
-  dim3 grid((unsigned)(groups * tilesR * tilesC), C.L * batch);
-  k_mac_t<M, MINB><<<grid, M::kThreads, M::kSmemBytes, st>>>(ctN, pt, out, nI, nJ, nLb, tilesR, err, C);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out0, u64 stride0, u64* out1, u64 stride1,
                        u32 nI, u32 nJ, u32 nLb, u32 batch, int* err, cudaStream_t st) {

@@ -12,9 +12,7 @@ namespace he {
 // v mod 2^25 in the low half and floor(v / 2^25) in the high half.
 __device__ __forceinline__ u64 split_word(u64 v) { return (v & ((1ull << 25) - 1)) | ((v >> 25) << 32); }
 
-// Slot-wise multiply-accumulate (Algorithm 1 step 3 in the NTT domain).  The library
-// launches the warp-specialized form (mac_tile_ws, below); mac_tile is the form in which
-// every thread both computes and, in warp 0, streams the stages.  For each
+// Slot-wise multiply-accumulate (Algorithm 1 step 3 in the NTT domain).  For each
 // prime l and slot s the outputs form a small matrix product over the k-blocks J:
 //   out[r][I] = sum_J ct[r][J] * pt[I][J],   r = (Lb, component c) rows, I columns.
 //
@@ -23,10 +21,10 @@ __device__ __forceinline__ u64 split_word(u64 v) { return (v & ((1ull << 25) - 1
 // 32-slot vectors of all nJ k-blocks contiguously:
 //   word ((row * L + l) * (N / 32) + s / 32) * nJ * 32 + J * 32 + s % 32.
 // A block owns one 32-slot chunk of one prime and a (kRows x kCols) output tile.  Per
-// stage, warp 0 streams JB consecutive k-blocks of every operand row of the tile into
-// shared memory -- one 1-D bulk copy (TMA) of JB * 256 contiguous bytes per row --
-// completing on the stage's mbarrier; STAGES stages are in flight.  Each thread owns one
-// slot and a TM x TN register tile.  Operands < 2^50 are stored split, x = x0 + 2^25 x1
+// stage, a producer warp streams JB consecutive k-blocks of every operand row of the tile
+// into shared memory -- one 1-D bulk copy (TMA) of JB * 256 contiguous bytes per row --
+// completing on the stage's mbarrier; STAGES stages are in flight.  Each consumer thread
+// owns one slot and a TM x TN register tile.  Operands < 2^50 are stored split, x = x0 + 2^25 x1
 // (split_word), and multiplied Karatsuba-style: three mad.wide.u32 per slot product into lo / mid / hi
 // 64-bit columns (no carries for nJ <= 4096), reduced once per output at the end.
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: a copy that never lands is an error
@@ -54,143 +52,20 @@ __host__ __device__ constexpr u64 chunked_index(u64 row, u32 J, u32 l, u32 s, u3
   return ((row * L + l) * (N >> 5) + (s >> 5)) * (u64)nJ * 32 + (u64)J * 32 + (s & 31);
 }
 
-template <int TM, int TN, int WR, int WC, int JB, int STAGES, int CPB = 1>
+template <int TM, int TN, int WR, int WC, int JB, int STAGES>
 struct MacCfg {
   static constexpr int kTM = TM, kTN = TN, kWR = WR, kWC = WC, kJB = JB, kStages = STAGES;
-  static constexpr int kChunksPerBlock = CPB;  // 32-slot chunks one block streams back to back
   static constexpr int kRows = TM * WR, kCols = TN * WC;
   static constexpr int kThreads = 32 * WR * WC;
   static constexpr int kStageWords = (kRows + kCols) * JB * 32;
   static constexpr size_t kSmemBytes = (size_t)STAGES * kStageWords * sizeof(u64);
 };
 
-// One block's share of a product: the 32-slot chunks [chunk0, chunk0 + nch) of prime l and
-// the output tile with first row r0 and first column c0.  ct0 = global index of the
-// product's first output ciphertext (for the output placement).  Shared memory: the
-// caller's dynamic buffer of M::kSmemBytes bytes.
-template <class M>
-__device__ __forceinline__ void mac_tile(const u64* __restrict__ ctN, const u64* __restrict__ pt, const OutPlace& out,
-                                         u64 ct0, u32 nI, u32 nJ, u32 nLb, u32 r0, u32 c0, u32 chunk0, u32 nch,
-                                         u32 l, int* err, const Consts& C, u64* sm) {
-  __shared__ __align__(8) uint64_t bars[M::kStages];
-  __shared__ int abort_flag;
-  constexpr int TM = M::kTM, TN = M::kTN, JB = M::kJB, ST = M::kStages;
-
-  const u32 N = C.N, L = C.L;
-  const PrimeConsts& P = C.p[l];
-  const u32 rows = 2 * nLb;
-  const u32 nrows = min((u32)M::kRows, rows - r0), ncols = min((u32)M::kCols, nI - c0);
-  const u32 nsp = (nJ + JB - 1) / JB;  // stages per chunk
-  const u32 nstages = nch * nsp;
-  const u32 warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const u32 wr = warp % M::kWR, wc = warp / M::kWR;
-
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < ST; ++st) mbar_init(&bars[st], 1);
-    mbar_init_fence();
-    abort_flag = 0;
-  }
-  __syncthreads();
-
-  // warp 0: stream k-blocks [JB k, JB k + jb) of chunk chunk0 + i / nsp (k = i % nsp) of
-  // every operand row of the tile into stage st
-  auto issue = [&](u32 i, u32 st) {
-    const u32 chunk = chunk0 + i / nsp, k = i % nsp;
-    const u32 J0 = k * JB, jb = min((u32)JB, nJ - J0);
-    const u32 bytes = jb * 32 * sizeof(u64);
-    if (lane == 0) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&bars[st], (nrows + ncols) * bytes);
-    }
-    __syncwarp();
-    u64* stage = sm + st * M::kStageWords;
-    for (u32 t = lane; t < nrows + ncols; t += 32) {
-      const bool is_row = t < nrows;
-      const u64* src = is_row ? ctN + chunked_index(r0 + t, J0, l, chunk << 5, nJ, L, N)
-                              : pt + chunked_index(c0 + (t - nrows), J0, l, chunk << 5, nJ, L, N);
-      u64* dst = stage + (is_row ? t : M::kRows + (t - nrows)) * (JB * 32);
-      bulk_copy_g2s(dst, src, bytes, &bars[st]);
-    }
-  };
-
-  if (warp == 0)
-    for (u32 i = 0; i < (u32)ST && i < nstages; ++i) issue(i, i);
-
-  u64 lo[TM][TN], mid[TM][TN], hi[TM][TN];
-#pragma unroll
-  for (int a = 0; a < TM; ++a)
-#pragma unroll
-    for (int b = 0; b < TN; ++b) lo[a][b] = mid[a][b] = hi[a][b] = 0;
-
-  for (u32 i = 0; i < nstages; ++i) {
-    const u32 st = i % ST;
-    if (threadIdx.x == 0) {
-      if (!mbar_wait_bounded(&bars[st], (i / ST) & 1, kWaitLimitNs)) {
-        abort_flag = 1;
-        atomicExch(err, 1);
-        // let every other copy this block issued land (bounded) before the block exits
-        for (u32 i2 = i + 1; i2 < nstages && i2 < i + ST; ++i2)
-          mbar_wait_bounded(&bars[i2 % ST], (i2 / ST) & 1, kWaitLimitNs);
-      }
-    }
-    __syncthreads();
-    if (abort_flag) return;
-    const u64* stage = sm + st * M::kStageWords;
-    const u32 k = i % nsp;
-    const u32 jb = min((u32)JB, nJ - k * JB);
-    const u64* prow = stage + (M::kRows + wc * TN) * (JB * 32) + lane;  // this thread's column operands
-    const u64* crow = stage + (wr * TM) * (JB * 32) + lane;             // this thread's row operands
-    // one k-block: TN column and TM row operands (pre-split words), TM x TN x 3 mad.wide
-    auto kblock = [&](u32 jj) {
-      u32 p0[TN], p1[TN], ps[TN];
-#pragma unroll
-      for (int b = 0; b < TN; ++b) split25(prow[b * (JB * 32) + jj * 32], p0[b], p1[b], ps[b]);
-#pragma unroll
-      for (int a = 0; a < TM; ++a) {
-        u32 x0, x1, xs;
-        split25(crow[a * (JB * 32) + jj * 32], x0, x1, xs);
-#pragma unroll
-        for (int b = 0; b < TN; ++b) {
-          mad_wide(lo[a][b], x0, p0[b]);
-          mad_wide(hi[a][b], x1, p1[b]);
-          mad_wide(mid[a][b], xs, ps[b]);
-        }
-      }
-    };
-    if (jb == (u32)JB) {  // full stage: constant offsets, fully unrolled
-#pragma unroll
-      for (int jj = 0; jj < JB; ++jj) kblock(jj);
-    } else {
-      for (u32 jj = 0; jj < jb; ++jj) kblock(jj);
-    }
-    if (k == nsp - 1) {  // chunk complete: reduce, store, restart the accumulators
-      const u32 s = ((chunk0 + i / nsp) << 5) + lane;
-#pragma unroll
-      for (int a = 0; a < TM; ++a) {
-        const u32 r = r0 + wr * TM + a;
-#pragma unroll
-        for (int b = 0; b < TN; ++b) {
-          const u32 I = c0 + wc * TN + b;
-          if (r < rows && I < nI) {
-            const u64 cross = mid[a][b] - lo[a][b] - hi[a][b];  // sum of x0 y1 + x1 y0
-            u64 v = reduce_word(lo[a][b], P);
-            v = add_mod(v, csub(mul_shoup(cross, P.r25, P.r25_sh, P.q), P.q), P.q);
-            v = add_mod(v, csub(mul_shoup(hi[a][b], P.r50, P.r50_sh, P.q), P.q), P.q);
-            const u32 c = r & 1;
-            out.base[c][(ct0 + (u64)(r >> 1) * nI + I) * out.ct_stride[c] + (u64)l * N + s] = v;
-          }
-          lo[a][b] = mid[a][b] = hi[a][b] = 0;
-        }
-      }
-    }
-    __syncthreads();
-    if (warp == 0 && i + ST < nstages) issue(i + ST, st);
-  }
-}
-
-
-// Warp-specialized variant of mac_tile: the block has M::kThreads consumer threads plus one
-// producer warp (the last).  The producer streams the stages (waiting on a stage's "empty"
+// One block's share of a product: the 32-slot chunk `chunk` of prime l and the output
+// tile with first row r0 and first column c0 (ct0 = global index of the product's first
+// output ciphertext, for the output placement; shared memory: the caller's dynamic
+// buffer of M::kSmemBytes bytes).  Warp-specialized: the block has M::kThreads consumer
+// threads plus one producer warp (the last).  The producer streams the stages (waiting on a stage's "empty"
 // barrier before refilling it); each consumer warp waits on the stage's "full" barrier
 // itself, computes, and releases the stage by arriving on "empty" (count = consumer warps).
 // No block-wide barrier after set-up.  Every wait is bounded and warp-uniform; a warp that
@@ -314,7 +189,7 @@ __device__ __forceinline__ void mac_tile_ws(const u64* __restrict__ ctN, const u
 }
 
 // The configuration the library launches.
-using MacProd = MacCfg<4, 2, 2, 4, 8, 2, 1>;
+using MacProd = MacCfg<4, 2, 2, 4, 8, 2>;
 constexpr int kMacMinBlocks = 2;
 
 }  // namespace he
