@@ -73,11 +73,15 @@ __device__ __forceinline__ void ntt_inverse_smem(u64* a, u32 logN, const PrimeCo
 
 // ------------------------------------------------------------------ register-blocked form
 
+
 template <int LOGN>
 struct NttShape {
   static constexpr int kLogN = LOGN;
   static constexpr int N = 1 << LOGN;
-  static constexpr int LOGR = LOGN >= 13 ? 5 : 4;  // values per thread: 16, or 32 for N = 8192
+  // 2^LOGR values per thread.  Measured on GB300 (whole BERT layers): 16 beats 8 and 32 at
+  // N = 4096 (3.28 ms vs 3.47 / 3.65 ms per layer) and 32 at N = 8192 (40.3 vs 45.0 ms per
+  // BERT-large layer: 128 instead of 242 registers, twice the resident warps)
+  static constexpr int LOGR = 4;
   static constexpr int R = 1 << LOGR;
   static constexpr int T = N / R;                   // threads per block
   static constexpr int P = (LOGN + LOGR - 1) / LOGR;  // passes
