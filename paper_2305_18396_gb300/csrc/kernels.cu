@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_forward_mm_small(const u64*
 
 // Register-blocked versions for N >= 512 (blockDim = NttShape<LOGN>::T).
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_forward_t(const u64* src, u64* dst,
+__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocksFwd) k_ntt_forward_t(const u64* src, u64* dst,
                                                                      const __grid_constant__ Consts C) {
   using S = NttShape<LOGN>;
   extern __shared__ u64 sm[];
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_forward_t(const u64* 
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_inverse_t(const u64* src, u64* dst,
+__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_ntt_inverse_t(const u64* src, u64* dst,
                                                                      const __grid_constant__ Consts C) {
   using S = NttShape<LOGN>;
   extern __shared__ u64 sm[];
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kNttThreads) k_encode_weights(const u64* W, u3
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T) k_encode_weights_t(const u64* W, u32 k, u32 n, Blk b, u32 nI,
+__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_encode_weights_t(const u64* W, u32 k, u32 n, Blk b, u32 nI,
                                                                         u32 nJ, u64* pt, const __grid_constant__ Consts C) {
   using S = NttShape<LOGN>;
   extern __shared__ u64 sm[];
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_encode_weights_t(const u6
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T) k_intt_mask_t(u64* out, u64 out_cts, u64 seed,
+__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_intt_mask_t(u64* out, u64 out_cts, u64 seed,
                                                                    const __grid_constant__ Consts C) {
   using S = NttShape<LOGN>;
   extern __shared__ u64 sm[];
@@ -397,7 +397,7 @@ cudaError_t launch_mac_ws_cfg(const Consts& C, const u64* ctN, const u64* pt, Ou
 // Forward NTT of the input ciphertexts of a product into the slot-chunked operand layout.
 // Input poly p = ((Lb nJ + J) 2 + c) L + l of the wire format [Lb nJ + J][2][L][N].
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_forward_mm_t(const u64* src, u64* ctN, u32 nJ, u32 nLb,
+__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocksFwd) k_ntt_forward_mm_t(const u64* src, u64* ctN, u32 nJ, u32 nLb,
                                                                         const __grid_constant__ Consts C) {
   using S = NttShape<LOGN>;
   extern __shared__ u64 sm[];
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_forward_mm_t(const u6
 // Compact-output mode: inverse NTT of the c1 polynomials only, in place.  Ciphertext g's
 // c1 for prime l sits at base + g * ct_stride + l * N.
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T) k_intt_c1_t(u64* base, u64 ct_stride,
+__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_intt_c1_t(u64* base, u64 ct_stride,
                                                                  const __grid_constant__ Consts C) {
   using S = NttShape<LOGN>;
   extern __shared__ u64 sm[];
