@@ -62,6 +62,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // completed phase), the warp leaves together once all lanes saw it, or together with
 // `false` once any lane's clock passes the limit.  Call with all 32 lanes.
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;  // already complete: no clock read
   const uint64_t t0 = global_timer_ns();
   while (true) {
     const bool ok = mbar_try_wait(bar, parity);
