@@ -54,6 +54,18 @@ __device__ __forceinline__ u64 mul_shoup(u64 x, u64 w, u64 w_sh, u64 q) {
   return x * w - qh * q;
 }
 
+// Shoup product with an estimated quotient, for the lazily reduced forward transforms:
+// x < 2^56, w < q < 2^50, w_sh = floor(w 2^64 / q).  With x = x1 2^32 + x0 and
+// w_sh = s1 2^32 + s0, the quotient floor(x w_sh / 2^64) is x1 s1 + floor(x1 s0 / 2^32)
+// + floor(x0 s1 / 2^32) + (at most 2: the three dropped fractions, x0 s0 / 2^64 among
+// them, sum to less than 3).  Taking the estimate leaves the result x w - qh q in
+// [0, 4q) instead of Shoup's [0, 2q).
+__device__ __forceinline__ u64 mul_shoup_lazy(u64 x, u64 w, u64 w_sh, u64 q) {
+  const u32 x0 = (u32)x, x1 = (u32)(x >> 32), s0 = (u32)w_sh, s1 = (u32)(w_sh >> 32);
+  const u64 qh = (u64)x1 * s1 + __umulhi(x1, s0) + __umulhi(x0, s1);
+  return x * w - qh * q;
+}
+
 __device__ __forceinline__ u64 csub(u64 x, u64 b) { return x >= b ? x - b : x; }
 
 // x mod q for any 64-bit x.

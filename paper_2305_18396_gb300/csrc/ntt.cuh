@@ -12,8 +12,9 @@
 // instead of one per stage).  Shared memory is padded (one word every 2^LOGR) so the
 // contiguous groups of the innermost pass are free of bank conflicts.
 //
-// Lazy reduction: forward butterflies keep values in [0, q + 2 q s) after stage s (no
-// conditional subtraction; q < 2^50 keeps 13 stages below 2^55); the inverse keeps
+// Lazy reduction: forward butterflies use a Shoup product with an estimated quotient
+// (mul_shoup_lazy, result in [0, 4q)) and keep values in [0, q + 4 q s) after stage s (no
+// conditional subtraction; q < 2^50 keeps 13 stages below 2^56); the inverse keeps
 // [0, 2q).  Both produce fully reduced values in [0, q).
 #pragma once
 
@@ -105,7 +106,7 @@ template <class S, int S0, int RS>
 __device__ __forceinline__ void fwd_pass_regs(u64 (&x)[S::R], const PrimeConsts& P) {
   constexpr int G = S::R >> RS;
   constexpr int TLAST_LOG = S::kLogN - S0 - RS;
-  const u64 two_q = P.two_q, q = P.q;
+  const u64 four_q = 2 * P.two_q, q = P.q;
 #pragma unroll
   for (int h = 0; h < G; ++h) {
     const u32 g = threadIdx.x + S::T * h;
@@ -121,9 +122,9 @@ __device__ __forceinline__ void fwd_pass_regs(u64 (&x)[S::R], const PrimeConsts&
         u64& A = x[h * (1 << RS) + j];
         u64& Bv = x[h * (1 << RS) + j + span];
         const u64 U = A;
-        const u64 V = mul_shoup(Bv, w, wsh, q);
+        const u64 V = mul_shoup_lazy(Bv, w, wsh, q);  // [0, 4q)
         A = U + V;
-        Bv = U - V + two_q;
+        Bv = U - V + four_q;
       }
     }
   }
