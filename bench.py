@@ -504,7 +504,8 @@ def serving_leg(B, ctx, args):
     out = {"requests_per_rate": args.serving_requests,
            "mix": "BERT-base/large layer matrices (QKV, out, FFN1, FFN2), m log-uniform in [8, 512], Poisson arrivals",
            "resident_weight_gb": round(sum(m.pt.numel() for m in models) * 8 / 1e9, 2),
-           "policy": "2 launches in flight, each on a stream of lower CUDA priority than those running; a launch "
+           "policy": "up to 2 launches in flight, a second one only while the first is estimated to end within 2 "
+                     "ms; each on a stream of lower CUDA priority than those running; a launch "
                      "takes the oldest admitted request plus, in arrival order, requests whose estimated device "
                      "time fits 1.25 x the oldest's (at least 1 ms), up to 8; admission by a 32 GiB device "
                      "budget for outputs + workspace; outputs released on completion", "rates": {}}

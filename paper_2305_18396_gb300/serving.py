@@ -16,9 +16,14 @@ form; requests arrive over time and are
   that arrive while others are on the GPU join the next launch and their work overlaps
   on the device with the running one.  The cap keeps a long request from being delayed
   by the requests that arrived after it;
+* started only while the work still in flight is estimated to end within an overlap
+  window (2 ms): short launches overlap the next one, a long launch runs without a
+  second one taking SMs at its kernel boundaries (requests arriving meanwhile are
+  batched into the launch that follows it);
 * run on a stream whose CUDA priority is below that of every launch still in flight
   (the highest when the device is idle): the oldest launch keeps the SMs it can fill,
-  later launches take the SMs it leaves idle (its tail, its small grids);
+  later launches take the SMs it leaves idle (its tail, its small grids); each launch
+  stream keeps its workspace between launches;
 * completed when their launch's event fires (latency = completion - arrival).
 
 `run_per_request` is the plain path it is compared against: one he_matmul per request,
@@ -64,14 +69,15 @@ class Request:
 
 
 # Device-time estimate of one product inside a multi-product launch: a fixed part per
-# product plus its plaintext MACs at the rate the BERT-shaped products reach.
-EST_FIXED_S = 20e-6
-EST_MACS_PER_S = 2.5e11
+# product plus its plaintext MACs at the rate large BERT-shaped products reach alone.
+EST_FIXED_S = 100e-6
+EST_MACS_PER_S = 4.0e11
 
 
 @dataclass(order=True)
 class _InFlight:
     start: float
+    est: float = field(compare=False)  # estimated device seconds of the launch
     level: int = field(compare=False)
     event: object = field(compare=False)
     reqs: list = field(compare=False)
@@ -95,11 +101,13 @@ def priority_levels(n=4):
 
 class Server:
     def __init__(self, ctx, models, flags=B.HE_DROP_C0, hbm_budget=32 << 30, slots=2, max_batch=8,
-                 batch_work_factor=0.25, batch_floor_ms=1.0, priorities=True, keep_outputs=True):
+                 batch_work_factor=0.25, batch_floor_ms=1.0, priorities=True, keep_outputs=True,
+                 overlap_ms=2.0):
         self.ctx, self.models, self.flags = ctx, {mm.name: mm for mm in models}, flags
         self.budget, self.max_batch = hbm_budget, min(max_batch, 64)
         self.slots = slots
         self.work_factor, self.floor_s = batch_work_factor, batch_floor_ms * 1e-3
+        self.overlap_s = overlap_ms * 1e-3
         self.keep = keep_outputs
         levels = priority_levels() if priorities else [0]
         # a fixed set of streams, `slots` per priority level; buffers are allocated on the
@@ -110,6 +118,14 @@ class Server:
         self.queue, self.admitted, self.inflight, self.done = [], [], [], []
         self.in_use = 0
         self.launches = 0
+        self._sizes = {}  # (matrix, m) -> he_sizes
+        self._ws = {}     # launch stream -> workspace, grown as needed (a stream runs one launch at a time)
+
+    def _size(self, mm, m):
+        key = (mm.name, m)
+        if key not in self._sizes:
+            self._sizes[key] = self.ctx.sizes(m, mm.k, mm.n, mm.blk)
+        return self._sizes[key]
 
     def submit(self, req):
         mm = self.models[req.model]
@@ -139,8 +155,17 @@ class Server:
         self.admitted = rest
         return batch
 
-    def _launch(self, now):
+    def _may_launch(self, now):
+        """A launch slot is free and the work still in flight (estimated) ends within the
+        overlap window: a long launch is not slowed by a second one taking SMs at its kernel
+        boundaries, while short launches overlap the next."""
         if not self.admitted or len(self.inflight) >= self.slots:
+            return False
+        remaining = sum(max(0.0, f.est - (now - f.start)) for f in self.inflight)
+        return not self.inflight or remaining <= self.overlap_s
+
+    def _launch(self, now):
+        if not self._may_launch(now):
             return
         batch = self._take_batch()
         # below every launch in flight, so the oldest work keeps priority on the SMs
@@ -150,21 +175,33 @@ class Server:
         items = []
         for r in batch:
             mm = self.models[r.model]
-            si = self.ctx.sizes(r.m, mm.k, mm.n, mm.blk)
+            si = self._size(mm, r.m)
             ow = si["out_words_compact"] if self.flags else si["out_words"]
             r.out = self.ctx.empty(ow)
             r.out.record_stream(stream)
             items.append(dict(ct_in=mm.ct_pool, pt=mm.pt, ct_out=r.out, m=r.m, k=mm.k, n=mm.n, blk=mm.blk,
                               flags=self.flags, mask_seed=r.mask_seed))
             r.launched = now
-        prods = B.make_products(items)
-        ws = self.ctx.empty(max(B.he_multi_workspace_bytes(self.ctx, prods) // 8 + 1, 1))
-        ws.record_stream(stream)
+        if len(batch) == 1:  # one product: its own launch, no descriptor table to build
+            r, mm = batch[0], self.models[batch[0].model]
+            si = self._size(mm, r.m)
+            need = (si["workspace_bytes_compact"] if self.flags else si["workspace_bytes"]) // 8 + 1
+        else:
+            prods = B.make_products(items)
+            need = B.he_multi_workspace_bytes(self.ctx, prods) // 8 + 1
+        ws = self._ws.get(id(stream))
+        if ws is None or ws.numel() < need:  # the stream's previous launch has completed
+            ws = self._ws[id(stream)] = self.ctx.empty(need)
+            ws.record_stream(stream)
         stream.wait_stream(self.alloc_stream)  # the buffers' previous users are done
-        B.he_matmul_multi(self.ctx, prods, ws, stream=stream)
+        if len(batch) == 1:
+            B.he_matmul(self.ctx, mm.ct_pool, mm.pt, r.m, mm.k, mm.n, mm.blk, r.mask_seed, ct_out=r.out, workspace=ws,
+                        flags=self.flags, stream=stream)
+        else:
+            B.he_matmul_multi(self.ctx, prods, ws, stream=stream)
         ev = torch.cuda.Event()
         ev.record(stream)
-        heapq.heappush(self.inflight, _InFlight(now, level, ev, batch, ws, stream))
+        heapq.heappush(self.inflight, _InFlight(now, sum(r.est for r in batch), level, ev, batch, ws, stream))
         self.launches += 1
 
     def _poll(self, now):
@@ -184,7 +221,7 @@ class Server:
     def pump(self, now):
         self._poll(now)
         self._admit()
-        while self.admitted and len(self.inflight) < self.slots:
+        while self._may_launch(now):
             self._launch(now)
 
     def idle(self):
