@@ -263,11 +263,20 @@ class Layer:
         torch.cuda.synchronize()
 
     def _multi_body(self):
-        B, ctx = self.B, self.ctx
-        for c in self.calls:
-            if "pt_step" in c:
-                p = c["p"]
-                B.he_encode_weights_batch(ctx, c["W"], p.k, p.n, c["blk"], c["cnt"], pt=c["pt_step"])
+        """The per-step encodings of the server's shares, one per product shape, run side by
+        side on their own streams (their small grids overlap instead of each draining
+        alone), joined before the whole-layer launch; a captured graph keeps the fork."""
+        B, ctx, torch = self.B, self.ctx, self.torch
+        enc = [c for c in self.calls if "pt_step" in c]
+        main = torch.cuda.current_stream()
+        if not hasattr(self, "enc_streams"):
+            self.enc_streams = [torch.cuda.Stream(device=ctx.device) for _ in enc]
+        for c, st in zip(enc, self.enc_streams):
+            st.wait_stream(main)
+            p = c["p"]
+            B.he_encode_weights_batch(ctx, c["W"], p.k, p.n, c["blk"], c["cnt"], pt=c["pt_step"], stream=st)
+        for st in self.enc_streams:
+            main.wait_stream(st)
         for arr in self.prod_chunks:
             B.he_matmul_multi(ctx, arr, self.multi_ws)
 
