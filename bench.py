@@ -375,6 +375,7 @@ class Layer:
                 tot["intt_mask"] += cnt * 2 * full_b
             if p.share_weights:
                 tot["encode_weights"] += cnt * (8 * p.k * p.n + pt_b)
+        tot["intt_c1_c0"] = tot["intt_mask"] + tot.get("intt_c0_targets", 0)  # the whole-layer launch's fused grid
         return tot
 
     def slot_macs(self):

@@ -122,12 +122,12 @@ struct ProfRec {
 
 enum Kind {
   KNttFwd, KNttInv, KPolyMul, KKeygen, KEncrypt, KDecrypt, KPack, KUnpack, KUnmask, KEncode, KMac, KInttMask, KInttC0,
-  KExpand, KProbe, KShare, KCount
+  KExpand, KProbe, KShare, KInvC0, KCount
 };
 static const char* kKindNames[KCount] = {"ntt_forward", "ntt_inverse", "poly_mul", "keygen", "encrypt",
                                          "decrypt", "pack", "unpack", "unmask", "encode_weights",
                                          "mac", "intt_mask", "intt_c0_targets", "expand_compact", "probe",
-                                         "share_matmul"};
+                                         "share_matmul", "intt_c1_c0"};
 
 struct he_ctx {
   int device = 0;
@@ -871,10 +871,12 @@ int he_matmul_multi(he_ctx* c, uint32_t count, const he_product* items, void* wo
   if (!r)
     r = launch(c, KMac, st, "multi: multiply-accumulate",
                [&] { return he::launch_mac_multi(c->C, P.T, P.mac, c->d_err, st); });
-  if (!r) r = launch(c, KInttMask, st, "multi: inverse NTT", [&] { return he::launch_inv_multi(c->C, P.T, P.inv, st); });
-  if (!r && P.c0)
-    r = launch(c, KInttC0, st, "multi: pruned inverse NTT of c0",
-               [&] { return he::launch_c0_multi(c->C, P.T, P.c0, P.max_nc, st); });
+  if (!r && P.c0)  // compact products: c1 inverse NTTs and pruned c0 transforms in one grid
+    r = launch(c, KInvC0, st, "multi: inverse NTT of c1 + pruned inverse NTT of c0",
+               [&] { return he::launch_inv_c0_multi(c->C, P.T, P.inv, P.c0, P.max_nc, st); });
+  if (!r && P.c0 && !he::inv_c0_fused(c->C)) c->launches.fetch_add(1, std::memory_order_relaxed);  // two grids
+  else if (!r)
+    r = launch(c, KInttMask, st, "multi: inverse NTT", [&] { return he::launch_inv_multi(c->C, P.T, P.inv, st); });
   return r;
 }
 

@@ -94,16 +94,13 @@ __global__ void __launch_bounds__(M::kThreads + 32, MINB) k_mac_multi_t(const __
   mac_tile_ws<M>(it.ctN, it.pt, out, 0, it.nI, it.nJ, it.nLb, r0, c0, chunk, l, err, C, sm);
 }
 
-// Inverse NTT: compact products transform their c1 polynomials in place; full products
-// transform every output polynomial and re-mask c0.
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_inv_multi_t(const __grid_constant__ MultiTable T,
-                                                                   const __grid_constant__ Consts C) {
-  using S = NttShape<LOGN>;
-  extern __shared__ u64 sm[];
-  const u32 i = find_item(T, blockIdx.x, [](const MultiItem& x) { return x.inv_begin; });
+// Inverse NTT of block b of the inverse grid: compact products transform their c1
+// polynomials in place; full products transform every output polynomial and re-mask c0.
+template <class S>
+__device__ __forceinline__ void inv_block(const MultiTable& T, const Consts& C, u64 b, u64* sm) {
+  const u32 i = find_item(T, b, [](const MultiItem& x) { return x.inv_begin; });
   const MultiItem& it = T.it[i];
-  const u64 local = blockIdx.x - it.inv_begin;
+  const u64 local = b - it.inv_begin;
   const u64 N = S::N, L = C.L;
   const u32 l = local % L;
   if (it.compact) {
@@ -124,6 +121,36 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks)
       d[e] = v;
     });
   }
+}
+
+// Pruned inverse NTT + mask of c0 for block b of the c0 grid (one block per (o, l) of the
+// compact products).
+__device__ __forceinline__ void c0_block(const MultiTable& T, const Consts& C, u64 b, u64* sm) {
+  const u32 i = find_item(T, b, [](const MultiItem& x) { return x.c0_begin; });
+  const MultiItem& it = T.it[i];
+  const u64 local = b - it.c0_begin;
+  const u64 N = C.N, L = C.L, Nc = N >> it.logkb;
+  const u32 l = local % L;
+  const u32 o = (u32)(local / L);
+  ntt_inverse_c0_targets(it.c0_ntt + local * N, it.out + (u64)o * L * (Nc + N) + l * Nc, it.logkb, item_seed(it), o, l,
+                         C, sm);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_inv_multi_t(const __grid_constant__ MultiTable T,
+                                                                   const __grid_constant__ Consts C) {
+  extern __shared__ u64 sm[];
+  inv_block<NttShape<LOGN>>(T, C, blockIdx.x, sm);
+}
+
+// The c1 inverse NTTs and the pruned c0 transforms are independent: one grid runs both,
+// blocks [0, inv_blocks) the former and the rest the latter, so neither drains alone.
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_inv_c0_multi_t(
+    const __grid_constant__ MultiTable T, const __grid_constant__ Consts C, u64 inv_blocks) {
+  extern __shared__ u64 sm[];
+  if (blockIdx.x < inv_blocks) inv_block<NttShape<LOGN>>(T, C, blockIdx.x, sm);
+  else c0_block(T, C, blockIdx.x - inv_blocks, sm);
 }
 
 __global__ void __launch_bounds__(kThreadsSmall) k_inv_multi_small(const __grid_constant__ MultiTable T,
@@ -163,14 +190,7 @@ __global__ void __launch_bounds__(kThreadsSmall) k_inv_multi_small(const __grid_
 __global__ void __launch_bounds__(kThreadsSmall) k_c0_multi(const __grid_constant__ MultiTable T,
                                                             const __grid_constant__ Consts C) {
   extern __shared__ u64 sm[];
-  const u32 i = find_item(T, blockIdx.x, [](const MultiItem& x) { return x.c0_begin; });
-  const MultiItem& it = T.it[i];
-  const u64 local = blockIdx.x - it.c0_begin;
-  const u64 N = C.N, L = C.L, Nc = N >> it.logkb;
-  const u32 l = local % L;
-  const u32 o = (u32)(local / L);
-  ntt_inverse_c0_targets(it.c0_ntt + local * N, it.out + (u64)o * L * (Nc + N) + l * Nc, it.logkb, item_seed(it), o, l,
-                         C, sm);
+  c0_block(T, C, blockIdx.x, sm);
 }
 
 #define HE_MULTI_DISPATCH(KERNEL, GRID, ST, ...)                                                                   \
@@ -197,7 +217,8 @@ cudaError_t configure_multi_kernels() {
   set((const void*)k_mac_multi_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
 #define HE_SET_MULTI(LOGN)                                                                        \
   set((const void*)k_fwd_multi_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
-  set((const void*)k_inv_multi_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));
+  set((const void*)k_inv_multi_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
+  set((const void*)k_inv_c0_multi_t<LOGN>, 2 * (1 << LOGN) * (int)sizeof(u64));
   HE_SET_MULTI(9) HE_SET_MULTI(10) HE_SET_MULTI(11) HE_SET_MULTI(12) HE_SET_MULTI(13)
 #undef HE_SET_MULTI
   return e;
@@ -230,6 +251,31 @@ cudaError_t launch_inv_multi(const Consts& C, const MultiTable& T, u64 blocks, c
   } else {
     k_inv_multi_small<<<(unsigned)blocks, kThreadsSmall, C.N * sizeof(u64), st>>>(T, C);
   }
+  return cudaGetLastError();
+}
+
+// One grid where both kinds of block have the same shape (256 threads, N <= 4096); at
+// N = 8192 the inverse transform's 512-thread, 68 KB blocks would starve the c0 blocks
+// (measured: 19% slower than two grids), and small rings use the simple kernels.
+bool inv_c0_fused(const Consts& C) { return C.logN >= 9 && C.logN <= 12; }
+
+cudaError_t launch_inv_c0_multi(const Consts& C, const MultiTable& T, u64 inv_blocks, u64 c0_blocks, u32 c0_words,
+                                cudaStream_t st) {
+  if (!inv_c0_fused(C)) {
+    cudaError_t e = launch_inv_multi(C, T, inv_blocks, st);
+    return e == cudaSuccess ? launch_c0_multi(C, T, c0_blocks, c0_words, st) : e;
+  }
+  const u64 blocks = inv_blocks + c0_blocks;
+  if (!blocks) return cudaGetLastError();
+#define HE_INV_C0(LOGN)                                                                                      \
+  case LOGN: {                                                                                               \
+    const u32 words = (u32)NttShape<LOGN>::kSmemWords > c0_words ? (u32)NttShape<LOGN>::kSmemWords : c0_words; \
+    const size_t smem = (size_t)words * sizeof(u64);                                                         \
+    k_inv_c0_multi_t<LOGN><<<(unsigned)blocks, NttShape<LOGN>::T, smem, st>>>(T, C, inv_blocks);            \
+    break;                                                                                                   \
+  }
+  switch (C.logN) { HE_INV_C0(9) HE_INV_C0(10) HE_INV_C0(11) HE_INV_C0(12) HE_INV_C0(13) default: break; }
+#undef HE_INV_C0
   return cudaGetLastError();
 }
 

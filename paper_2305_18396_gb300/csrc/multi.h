@@ -34,5 +34,9 @@ cudaError_t launch_fwd_multi(const Consts& C, const MultiTable& T, u64 blocks, c
 cudaError_t launch_mac_multi(const Consts& C, const MultiTable& T, u64 blocks, int* err, cudaStream_t st);
 cudaError_t launch_inv_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
 cudaError_t launch_c0_multi(const Consts& C, const MultiTable& T, u64 blocks, u32 c0_words, cudaStream_t st);
+// The inverse-NTT grid and the c0 grid as one launch where inv_c0_fused(C), else two.
+bool inv_c0_fused(const Consts& C);
+cudaError_t launch_inv_c0_multi(const Consts& C, const MultiTable& T, u64 inv_blocks, u64 c0_blocks, u32 c0_words,
+                                cudaStream_t st);
 
 }  // namespace he

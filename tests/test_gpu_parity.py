@@ -373,7 +373,7 @@ def test_bounded_wait_reports_timeout_and_context_survives(B):
 # ------------------------------------------------------------------ multi-product launch
 
 
-@pytest.mark.parametrize("N,L", [(4096, 2), (256, 2)])
+@pytest.mark.parametrize("N,L", [(4096, 2), (256, 2), (8192, 3)])
 def test_matmul_multi_equals_single_calls(B, N, L):
     """Products of different shapes, blockings and output modes in one multi-product launch
     give exactly what their own he_matmul calls give (and one matches the oracle)."""
