@@ -871,12 +871,13 @@ int he_matmul_multi(he_ctx* c, uint32_t count, const he_product* items, void* wo
   if (!r)
     r = launch(c, KMac, st, "multi: multiply-accumulate",
                [&] { return he::launch_mac_multi(c->C, P.T, P.mac, c->d_err, st); });
-  if (!r && P.c0)  // compact products: c1 inverse NTTs and pruned c0 transforms in one grid
+  if (!r && P.c0) {  // compact products: c1 inverse NTTs and pruned c0 transforms in one grid
     r = launch(c, KInvC0, st, "multi: inverse NTT of c1 + pruned inverse NTT of c0",
                [&] { return he::launch_inv_c0_multi(c->C, P.T, P.inv, P.c0, P.max_nc, st); });
-  if (!r && P.c0 && !he::inv_c0_fused(c->C)) c->launches.fetch_add(1, std::memory_order_relaxed);  // two grids
-  else if (!r)
+    if (!r && !he::inv_c0_fused(c->C)) c->launches.fetch_add(1, std::memory_order_relaxed);  // two grids there
+  } else if (!r) {
     r = launch(c, KInttMask, st, "multi: inverse NTT", [&] { return he::launch_inv_multi(c->C, P.T, P.inv, st); });
+  }
   return r;
 }
 
