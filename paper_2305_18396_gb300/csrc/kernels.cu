@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks)
     return w >= half_t ? P.q - (C.tmask + 1 - w) : w;  // centred lift [-t/2, t/2)
   };
   ntt_forward_block<S>(sm, P, load,
-                       [&](u32 e, u64 v) { pt[chunked_index(I, J, l, e, nJ, C.L, S::N)] = split_word(v); });
+                       [&](u32 e, u64 v) { pt[chunked_index(I, J, l, e, nJ, C.L, S::N)] = split_word(v); }, nk);
 }
 
 template <int LOGN>

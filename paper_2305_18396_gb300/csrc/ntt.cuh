@@ -172,15 +172,32 @@ __device__ __forceinline__ void fwd_rest(u64 (&x)[S::R], u64* sm, const PrimeCon
 //                   coalesced across the warp);
 //   store(e, v)  <- slot e, fully reduced (called for every e in increasing-e order per
 //                   thread stride, coalesced);
+//   prefix       -- the coefficients at and above `prefix` are zero (default: none);
 //   sm: S::kSmemWords words of shared memory.  Synchronizes internally.
+// The first pass pairs element e with e + N/2, e + N/4, ..., i.e. each thread's group is
+// e = g + j N / 2^RS0 (j < 2^RS0).  With prefix <= N / 2^RS0 only j = 0 can be nonzero,
+// every butterfly of the pass has V = 0 and passes U through, so the pass reduces to
+// copying that element to the whole group (the skipped "+ 4q" offsets change nothing mod
+// q, and the final reduction is exact): a weight block of Algorithm 1's encoding pi_A
+// fills only its lowest n_b k_b = N / m_b coefficients.
 template <class S, class Load, class Store>
-__device__ __forceinline__ void ntt_forward_block(u64* sm, const PrimeConsts& P, Load&& load, Store&& store) {
+__device__ __forceinline__ void ntt_forward_block(u64* sm, const PrimeConsts& P, Load&& load, Store&& store,
+                                                  u32 prefix = S::N) {
   u64 x[S::R];
+  if (prefix <= (u32)(S::N >> S::RS0)) {
 #pragma unroll
-  for (int h = 0; h < (S::R >> S::RS0); ++h)
+    for (int h = 0; h < (S::R >> S::RS0); ++h) {
+      const u64 v = load(fwd_elem<S, 0, S::RS0>(h, 0));
 #pragma unroll
-    for (int j = 0; j < (1 << S::RS0); ++j) x[h * (1 << S::RS0) + j] = load(fwd_elem<S, 0, S::RS0>(h, j));
-  fwd_pass_regs<S, 0, S::RS0>(x, P);
+      for (int j = 0; j < (1 << S::RS0); ++j) x[h * (1 << S::RS0) + j] = v;
+    }
+  } else {
+#pragma unroll
+    for (int h = 0; h < (S::R >> S::RS0); ++h)
+#pragma unroll
+      for (int j = 0; j < (1 << S::RS0); ++j) x[h * (1 << S::RS0) + j] = load(fwd_elem<S, 0, S::RS0>(h, j));
+    fwd_pass_regs<S, 0, S::RS0>(x, P);
+  }
   fwd_store_smem<S, 0, S::RS0>(x, sm);
   __syncthreads();
   fwd_rest<S, S::RS0>(x, sm, P);
