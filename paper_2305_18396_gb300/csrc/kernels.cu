@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_forward_mm_small(const u64*
 
 // Register-blocked versions for N >= 512 (blockDim = NttShape<LOGN>::T).
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocksFwd) k_ntt_forward_t(const u64* src, u64* dst,
+__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_ntt_forward_t(const u64* src, u64* dst,
                                                                      const __grid_constant__ Consts C) {
   using S = NttShape<LOGN>;
   extern __shared__ u64 sm[];
@@ -397,7 +397,7 @@ cudaError_t launch_mac_ws_cfg(const Consts& C, const u64* ctN, const u64* pt, Ou
 // Forward NTT of the input ciphertexts of a product into the slot-chunked operand layout.
 // Input poly p = ((Lb nJ + J) 2 + c) L + l of the wire format [Lb nJ + J][2][L][N].
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocksFwd) k_ntt_forward_mm_t(const u64* src, u64* ctN, u32 nJ, u32 nLb,
+__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_ntt_forward_mm_t(const u64* src, u64* ctN, u32 nJ, u32 nLb,
                                                                         const __grid_constant__ Consts C) {
   using S = NttShape<LOGN>;
   extern __shared__ u64 sm[];

@@ -33,7 +33,7 @@ __device__ __forceinline__ u32 find_item(const MultiTable& T, u64 b, F begin) {
 __device__ __forceinline__ u64 item_seed(const MultiItem& it) { return it.seed_dev ? *it.seed_dev : it.mask_seed; }
 
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocksFwd) k_fwd_multi_t(const __grid_constant__ MultiTable T,
+__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_fwd_multi_t(const __grid_constant__ MultiTable T,
                                                                    const __grid_constant__ Consts C) {
   using S = NttShape<LOGN>;
   extern __shared__ u64 sm[];

@@ -88,11 +88,11 @@ struct NttShape {
   // Minimum resident blocks per SM asked of the compiler, which caps registers per thread.
   // Measured on the BERT-base layer (N = 4096, 256 threads): with no cap the whole-layer
   // transforms take up to 170 registers and run one block per SM; three blocks (80
-  // registers) make the step 3.178 ms against 3.555 with none, and the forward transforms
-  // gain further at four blocks (64 registers, no spill) where the inverse ones start to
-  // spill.  At 512 threads (N = 8192) 128 registers already allow one block of 16 warps.
+  // registers) make the step 3.178 ms against 3.555 with none and 3.217 with four (64
+  // registers, where the transforms spill); with the estimated-quotient forward product
+  // three blocks also beat four for the forward transforms alone (3.069 vs 3.091 ms).
+  // At 512 threads (N = 8192) 128 registers already allow one block of 16 warps.
   static constexpr int kMinBlocks = T <= 256 ? 3 : 1;
-  static constexpr int kMinBlocksFwd = T <= 256 ? 4 : 1;
   static constexpr int P = (LOGN + LOGR - 1) / LOGR;  // passes
   static constexpr int RS0 = LOGN - LOGR * (P - 1);   // stages of the outermost pass
   static constexpr int kSmemWords = N + (N >> LOGR);  // padded
