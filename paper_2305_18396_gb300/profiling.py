@@ -64,7 +64,9 @@ def run_share_case(m, k, n, repeat=3):
 
 
 def _short(name):
-    return re.sub(r"^.*?unnamed>::", "", name.split("(")[0].replace("void ", "")).strip()
+    """Kernel name without return type, parameters and anonymous-namespace prefix."""
+    name = name.replace("(anonymous namespace)::", "").replace("void ", "")
+    return re.sub(r"^.*?unnamed>::", "", name.split("(")[0]).strip()
 
 
 def summarize_launches(path, skip_prefixes=(), skip_first=0, metric="gpu__time_duration.sum", first=None, back=0,

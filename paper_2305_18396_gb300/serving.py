@@ -99,6 +99,34 @@ def priority_levels(n=4):
     return [p for p in range(greatest, least + 1)][:n] or [0]
 
 
+def take_batch(admitted, max_batch, work_factor, floor_s):
+    """Batch formation: the oldest admitted request plus, in arrival order, the requests
+    whose estimated device time keeps the batch within max(floor_s, (1 + work_factor) x
+    the oldest's estimate) (no cap with work_factor None), at most max_batch in all.
+    Returns (batch, the requests left admitted)."""
+    first = admitted[0]
+    cap = max(floor_s, first.est * (1.0 + work_factor)) if work_factor is not None else math.inf
+    batch, rest, total = [first], [], first.est
+    for r in admitted[1:]:
+        if len(batch) < max_batch and total + r.est <= cap:
+            batch.append(r)
+            total += r.est
+        else:
+            rest.append(r)
+    return batch, rest
+
+
+def launch_allowed(inflight, now, slots, overlap_s):
+    """inflight: (start, estimated seconds) of the launches running.  A new launch may start
+    when a slot is free and the work in flight is estimated to end within overlap_s: a long
+    launch is not slowed by a second one taking SMs at its kernel boundaries, while short
+    launches overlap the next."""
+    if len(inflight) >= slots:
+        return False
+    remaining = sum(max(0.0, est - (now - start)) for start, est in inflight)
+    return not inflight or remaining <= overlap_s
+
+
 class Server:
     def __init__(self, ctx, models, flags=B.HE_DROP_C0, hbm_budget=32 << 30, slots=2, max_batch=8,
                  batch_work_factor=0.25, batch_floor_ms=1.0, priorities=True, keep_outputs=True,
@@ -142,27 +170,12 @@ class Server:
             self.admitted.append(r)
 
     def _take_batch(self):
-        """The oldest admitted request plus, in arrival order, those that fit the work cap."""
-        first = self.admitted[0]
-        cap = max(self.floor_s, first.est * (1.0 + self.work_factor)) if self.work_factor is not None else math.inf
-        batch, rest, total = [first], [], first.est
-        for r in self.admitted[1:]:
-            if len(batch) < self.max_batch and total + r.est <= cap:
-                batch.append(r)
-                total += r.est
-            else:
-                rest.append(r)
-        self.admitted = rest
+        batch, self.admitted = take_batch(self.admitted, self.max_batch, self.work_factor, self.floor_s)
         return batch
 
     def _may_launch(self, now):
-        """A launch slot is free and the work still in flight (estimated) ends within the
-        overlap window: a long launch is not slowed by a second one taking SMs at its kernel
-        boundaries, while short launches overlap the next."""
-        if not self.admitted or len(self.inflight) >= self.slots:
-            return False
-        remaining = sum(max(0.0, f.est - (now - f.start)) for f in self.inflight)
-        return not self.inflight or remaining <= self.overlap_s
+        return bool(self.admitted) and launch_allowed([(f.start, f.est) for f in self.inflight], now, self.slots,
+                                                      self.overlap_s)
 
     def _launch(self, now):
         if not self._may_launch(now):

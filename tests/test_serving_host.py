@@ -1,0 +1,61 @@
+"""Host logic of the serving loop and the profiling summariser, on the CPU."""
+import math
+
+from paper_2305_18396_gb300 import serving as SV
+from paper_2305_18396_gb300.profiling import summarize_launches
+
+
+def reqs(*ests):
+    return [SV.Request(rid=i, model="x", m=1, arrival=float(i), mask_seed=i, est=e) for i, e in enumerate(ests)]
+
+
+def test_take_batch_work_cap_keeps_arrival_order_and_skips_what_does_not_fit():
+    admitted = reqs(1e-3, 0.2e-3, 5e-3, 0.1e-3, 0.3e-3)
+    batch, rest = SV.take_batch(admitted, max_batch=8, work_factor=0.25, floor_s=1e-3)
+    # cap = max(1 ms, 1.25 ms) = 1.25 ms: 1.0 + 0.2 fits, 5.0 does not, 0.1 would overflow 1.3
+    assert [r.rid for r in batch] == [0, 1]
+    assert [r.rid for r in rest] == [2, 3, 4]
+    # the floor admits several small requests behind a small first one
+    batch, rest = SV.take_batch(reqs(0.1e-3, 0.2e-3, 0.3e-3, 0.5e-3), 8, 0.25, 1e-3)
+    assert [r.rid for r in batch] == [0, 1, 2] and [r.rid for r in rest] == [3]
+    # a long first request takes no company beyond 25% of its own estimate
+    batch, rest = SV.take_batch(reqs(8e-3, 1e-3, 1.5e-3, 0.4e-3), 8, 0.25, 1e-3)
+    assert [r.rid for r in batch] == [0, 1, 3] and [r.rid for r in rest] == [2]
+
+
+def test_take_batch_limits_and_no_cap():
+    batch, rest = SV.take_batch(reqs(*[1e-4] * 10), max_batch=4, work_factor=None, floor_s=0.0)
+    assert len(batch) == 4 and len(rest) == 6
+    batch, rest = SV.take_batch(reqs(1.0, 5.0, 9.0), max_batch=8, work_factor=None, floor_s=0.0)
+    assert len(batch) == 3 and not rest
+
+
+def test_launch_allowed_overlap_gate():
+    assert SV.launch_allowed([], now=0.0, slots=2, overlap_s=2e-3)
+    # one long launch just started: 5 ms left > 2 ms window
+    assert not SV.launch_allowed([(0.0, 5e-3)], now=0.0, slots=2, overlap_s=2e-3)
+    # the same launch near its end: 1 ms left
+    assert SV.launch_allowed([(0.0, 5e-3)], now=4e-3, slots=2, overlap_s=2e-3)
+    # estimates that have run out count as zero, but the slots still bound concurrency
+    assert SV.launch_allowed([(0.0, 1e-3)], now=5e-3, slots=2, overlap_s=0.0)
+    assert not SV.launch_allowed([(0.0, 1e-3), (0.0, 1e-3)], now=5e-3, slots=2, overlap_s=math.inf)
+
+
+def test_summarize_launches_window_and_units(tmp_path):
+    rows = [
+        ('"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"'),
+        ('"0","k_setup(int)","gpu__time_duration.sum","usecond","5"'),
+        ('"1","void k_fwd_multi_t<12>(T)","gpu__time_duration.sum","usecond","10"'),
+        ('"2","void (anonymous namespace)::k_mac(int)","gpu__time_duration.sum","msecond","2"'),
+        ('"3","at::fill(float)","gpu__time_duration.sum","nsecond","500"'),
+        ('"4","void k_fwd_multi_t<12>(T)","gpu__time_duration.sum","usecond","30"'),
+        ('"5","k_tail(int)","gpu__time_duration.sum","usecond","7"'),
+    ]
+    f = tmp_path / "launches.csv"
+    f.write_text("\n".join(rows) + "\n")
+    agg = summarize_launches(str(f), skip_prefixes=("at::",), first="k_fwd_multi", last="k_fwd_multi")
+    assert agg == {"k_fwd_multi_t<12>": [2, 40.0], "k_mac": [1, 2000.0]}
+    agg = summarize_launches(str(f), skip_first=5)
+    assert agg == {"k_tail": [1, 7.0]}
+    agg = summarize_launches(str(f), back=1, first="k_mac")
+    assert set(agg) == {"k_fwd_multi_t<12>", "k_mac", "at::fill", "k_tail"}
