@@ -99,18 +99,22 @@ def priority_levels(n=4):
     return [p for p in range(greatest, least + 1)][:n] or [0]
 
 
-def take_batch(admitted, max_batch, work_factor, floor_s):
+def take_batch(admitted, max_batch, work_factor, floor_s, fifo=False):
     """Batch formation: the oldest admitted request plus, in arrival order, the requests
     whose estimated device time keeps the batch within max(floor_s, (1 + work_factor) x
-    the oldest's estimate) (no cap with work_factor None), at most max_batch in all.
-    Returns (batch, the requests left admitted)."""
+    the oldest's estimate) (no cap with work_factor None), at most max_batch in all.  With
+    fifo the batch ends at the first request that does not fit (none is overtaken), else
+    later requests that fit are still taken.  Returns (batch, the requests left admitted)."""
     first = admitted[0]
     cap = max(floor_s, first.est * (1.0 + work_factor)) if work_factor is not None else math.inf
     batch, rest, total = [first], [], first.est
-    for r in admitted[1:]:
+    for i, r in enumerate(admitted[1:], 1):
         if len(batch) < max_batch and total + r.est <= cap:
             batch.append(r)
             total += r.est
+        elif fifo:
+            rest = list(admitted[i:])
+            break
         else:
             rest.append(r)
     return batch, rest
@@ -130,12 +134,13 @@ def launch_allowed(inflight, now, slots, overlap_s):
 class Server:
     def __init__(self, ctx, models, flags=B.HE_DROP_C0, hbm_budget=32 << 30, slots=2, max_batch=8,
                  batch_work_factor=0.25, batch_floor_ms=1.0, priorities=True, keep_outputs=True,
-                 overlap_ms=2.0):
+                 overlap_ms=2.0, fifo=False):
         self.ctx, self.models, self.flags = ctx, {mm.name: mm for mm in models}, flags
         self.budget, self.max_batch = hbm_budget, min(max_batch, 64)
         self.slots = slots
         self.work_factor, self.floor_s = batch_work_factor, batch_floor_ms * 1e-3
         self.overlap_s = overlap_ms * 1e-3
+        self.fifo = fifo
         self.keep = keep_outputs
         levels = priority_levels() if priorities else [0]
         # a fixed set of streams, `slots` per priority level; buffers are allocated on the
@@ -170,7 +175,7 @@ class Server:
             self.admitted.append(r)
 
     def _take_batch(self):
-        batch, self.admitted = take_batch(self.admitted, self.max_batch, self.work_factor, self.floor_s)
+        batch, self.admitted = take_batch(self.admitted, self.max_batch, self.work_factor, self.floor_s, self.fifo)
         return batch
 
     def _may_launch(self, now):

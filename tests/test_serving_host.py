@@ -59,3 +59,14 @@ def test_summarize_launches_window_and_units(tmp_path):
     assert agg == {"k_tail": [1, 7.0]}
     agg = summarize_launches(str(f), back=1, first="k_mac")
     assert set(agg) == {"k_fwd_multi_t<12>", "k_mac", "at::fill", "k_tail"}
+
+
+def test_take_batch_fifo_stops_at_first_misfit():
+    admitted = reqs(1e-3, 0.2e-3, 5e-3, 0.1e-3, 0.3e-3)
+    batch, rest = SV.take_batch(admitted, max_batch=8, work_factor=0.25, floor_s=1e-3, fifo=True)
+    assert [r.rid for r in batch] == [0, 1]
+    assert [r.rid for r in rest] == [2, 3, 4]
+    batch, rest = SV.take_batch(reqs(0.1e-3, 2e-3, 0.1e-3), 8, 0.25, 1e-3, fifo=True)
+    assert [r.rid for r in batch] == [0] and [r.rid for r in rest] == [1, 2]
+    batch, rest = SV.take_batch(reqs(0.1e-3, 2e-3, 0.1e-3), 8, 0.25, 1e-3, fifo=False)
+    assert [r.rid for r in batch] == [0, 2] and [r.rid for r in rest] == [1]
