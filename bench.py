@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-rates", default="100,400,800", help="Poisson arrival rates (requests/s)")
-    ap.add_argument("--serving-requests", type=int, default=1000)
+    ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--launch", default="multi", choices=["multi", "groups"],
                     help="multi: the whole layer as one multi-product launch per step; groups: one batched "
                          "launch per product shape")
