@@ -385,11 +385,12 @@ class Layer:
 
 
 def kernel_source_hash():
-    """Fingerprint of the multiply-accumulate kernel's source: its configuration, body and the
-    headers it includes (a DRAM-traffic figure recorded for an older fingerprint is stale)."""
+    """Fingerprint of the multiply-accumulate kernel's source: its configuration and body, the
+    headers it includes and the whole-layer launch's kernels (grid order) -- a DRAM-traffic
+    figure recorded for an older fingerprint is stale."""
     csrc = ROOT / "paper_2305_18396_gb300" / "csrc"
     h = hashlib.sha256((csrc / "mac.cuh").read_bytes())
-    for f in ("async.cuh", "he_common.cuh"):
+    for f in ("async.cuh", "he_common.cuh", "multi.cu"):
         h.update((csrc / f).read_bytes())
     return h.hexdigest()[:16]
 
