@@ -484,3 +484,40 @@ def test_matmul_multi_host_buffers(B):
         for d, h in zip(dev_items, items):
             if d["m"]:
                 assert np.array_equal(to_np(d["ct_out"]), h["ct_out"].numpy().view(np.uint64))
+
+
+def test_multi_launch_keeps_each_clients_key(B):
+    """Requests of three clients, each with its own secret key, in one multi-product launch
+    (Sec. 3.1.1: the server's product needs no key): each client decrypts its own output
+    with its own key, and with the server's mask share gets its X W mod t; another client's
+    key does not."""
+    ctx, P = ctx_for(B, 4096, 2)
+    t = np.uint64(P.t)
+    items, clients = [], []
+    for c, (m, k, n, flags) in enumerate([(16, 64, 64, 0), (40, 96, 48, B.HE_DROP_C0), (9, 70, 37, 0)]):
+        blk = ctx.default_blocking(m, k, n)
+        sk = B.he_keygen(ctx, 1000 + c)
+        X = S.uniform_share((m, k), 1100 + c)
+        W = S.fixed_point_weights((k, n), 1200 + c)
+        ct = B.he_encrypt(ctx, sk, B.he_pack_input(ctx, to_dev(X), m, k, blk), 1300 + c)
+        pt = B.he_encode_weights(ctx, to_dev(W), k, n, blk)
+        si = ctx.sizes(m, k, n, blk)
+        items.append(dict(ct_in=ct, pt=pt, ct_out=ctx.empty(si["out_words_compact"] if flags else si["out_words"]),
+                          m=m, k=k, n=n, blk=blk, flags=flags, mask_seed=1400 + c))
+        clients.append((sk, X, W, blk, si, flags))
+    prods = B.make_products(items)
+    B.he_matmul_multi(ctx, prods, ctx.empty(B.he_multi_workspace_bytes(ctx, prods) // 8 + 1))
+    for c, (it, (sk, X, W, blk, si, flags)) in enumerate(zip(items, clients)):
+        m, n = it["m"], it["n"]
+        out = it["ct_out"]
+        if flags:
+            out = B.he_expand_compact(ctx, out, si["out_cts"], blk[1])
+        server = to_np(B.he_unmask(ctx, 1400 + c, m, n, blk), (m, n))
+        want = O.plain_matmul_mod_t(X, W, P.t)
+        dec, _ = B.he_decrypt(ctx, sk, out)
+        client = to_np(B.he_unpack_output(ctx, dec, m, n, blk), (m, n))
+        assert np.array_equal((client + server) % t, want), c
+        other = clients[(c + 1) % len(clients)][0]
+        dec_o, _ = B.he_decrypt(ctx, other, out)
+        client_o = to_np(B.he_unpack_output(ctx, dec_o, m, n, blk), (m, n))
+        assert not np.array_equal((client_o + server) % t, want), c
