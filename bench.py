@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the mixed-request leg (one multi-product launch vs one call per request)")
     ap.add_argument("--serving-rates", default="100,400,800", help="Poisson arrival rates (requests/s)")
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--launch", default="multi", choices=["multi", "groups"],
@@ -534,6 +536,86 @@ def serving_leg(B, ctx, args):
     return out
 
 
+# ------------------------------------------------------------------ batched requests (one launch vs one per request)
+
+BATCHED_MATRICES = [("base.qkv", 768, 2304), ("base.ffn2", 3072, 768), ("large.out", 1024, 1024),
+                    ("large.ffn1", 1024, 4096)]
+
+
+def batched_leg(B, ctx, flags, reps=5):
+    """Mixed requests of resident BERT-base / BERT-large layer matrices, sequence lengths
+    uniform in [16, 512]: 64 requests at N=4096 (32 at N=8192, the launch's product limit
+    halved for the larger ciphertexts), device-resident.  Times the whole set as one
+    he_matmul_multi launch against one he_matmul call per request on the same stream, and
+    checks that every request's output is the same bit for bit both ways."""
+    import numpy as np
+    import torch
+
+    from paper_2305_18396_gb300 import synthetic as S
+
+    count = 64 if ctx.N == 4096 else 32
+    rng = np.random.default_rng(31 + ctx.N)
+    sk = B.he_keygen(ctx, S.SEED_KEY)
+    weights = {}
+    for idx, (name, k, n) in enumerate(BATCHED_MATRICES):
+        blk = ctx.default_blocking(128, k, n)  # the blocking is fixed per weight matrix
+        W = torch.from_numpy(S.fixed_point_weights((k, n), 800 + idx).view(np.int64).reshape(-1)).to(ctx.device)
+        weights[name] = (k, n, blk, B.he_encode_weights(ctx, W, k, n, blk))
+    items, alone, macs, ws_words = [], [], 0, 1
+    for r in range(count):
+        name = BATCHED_MATRICES[int(rng.integers(0, len(BATCHED_MATRICES)))][0]
+        k, n, blk, pt = weights[name]
+        m = int(rng.integers(16, 513))
+        X = torch.from_numpy(S.uniform_share((m, k), 8000 + r).view(np.int64).reshape(-1)).to(ctx.device)
+        ct = B.he_encrypt(ctx, sk, B.he_pack_input(ctx, X, m, k, blk), 8500 + r)
+        del X
+        si = ctx.sizes(m, k, n, blk)
+        ow, wb = B._out_ws(si, flags)
+        ws_words = max(ws_words, (wb + 7) // 8)
+        items.append(dict(ct_in=ct, pt=pt, ct_out=ctx.empty(ow), m=m, k=k, n=n, blk=blk, flags=flags,
+                          mask_seed=9000 + r))
+        alone.append(ctx.empty(ow))
+        macs += m * k * n
+    prods = B.make_products(items)
+    ws_multi = ctx.empty(B.he_multi_workspace_bytes(ctx, prods) // 8 + 1)
+    ws_one = ctx.empty(ws_words)
+    stream = torch.cuda.current_stream()
+
+    def multi():
+        B.he_matmul_multi(ctx, prods, ws_multi)
+
+    def separate():
+        for it, out in zip(items, alone):
+            B.he_matmul(ctx, it["ct_in"], it["pt"], it["m"], it["k"], it["n"], it["blk"], it["mask_seed"],
+                        ct_out=out, workspace=ws_one, flags=flags)
+
+    res = {}
+    for name, fn in (("one_launch", multi), ("per_request", separate)):
+        for _ in range(2):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms": round(ms, 3), "value": macs / (ms / 1e3), "unit": UNIT}
+    B.he_device_status(ctx)
+    same = all(torch.equal(it["ct_out"], out) for it, out in zip(items, alone))
+    ms_ = [it["m"] for it in items]
+    out = {"what": f"{count} requests of mixed BERT-base/large layer matrices (QKV, FFN2, large attn-out, large "
+                   "FFN1), m uniform in [16, 512], inputs resident: one he_matmul_multi launch vs one he_matmul "
+                   "call per request",
+           "requests": count, "plain_macs": macs, "m_min": min(ms_), "m_max": max(ms_),
+           "speedup": round(res["per_request"]["ms"] / res["one_launch"]["ms"], 3),
+           "outputs_identical": bool(same), **res}
+    del items, alone, prods, ws_multi, ws_one, weights
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ server-local share products
 
 
@@ -689,6 +771,7 @@ def gpu_arm(args, world, rank, local):
                "d2h_bytes_per_step": d2h, "steps": ksteps, "ms_per_step": dt * 1e3 / ksteps}
 
     share = share_products_leg(B, ctx, prods, mad_peak)
+    batched = None if args.no_batched else batched_leg(B, ctx, flags)
 
     serving = None
     if world == 1 and not args.no_serving:
@@ -716,6 +799,7 @@ def gpu_arm(args, world, rank, local):
                    "l2": "inputs larger than L2: one step reads/writes ~3 GB of ciphertexts/weights"},
         "latency_ms": {"p50": statistics.median(per), "p99": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))]},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "share_products": share,
+        "batched_requests": batched,
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }

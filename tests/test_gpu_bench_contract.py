@@ -41,3 +41,6 @@ def test_bench_line_has_the_contract_fields():
     assert e["unit"] == "MAC/s" and e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] >= d["steps"]
     assert d["clocks"] is None or {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
+    bt = d["batched_requests"]  # mixed requests: one launch and one call per request agree bit for bit
+    assert bt["outputs_identical"] and bt["requests"] == 64 and 16 <= bt["m_min"] <= bt["m_max"] <= 512
+    assert bt["one_launch"]["ms"] > 0 and bt["per_request"]["ms"] > 0
