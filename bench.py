@@ -66,6 +66,8 @@ def parse():
                          "memory, fresh every step)")
     ap.add_argument("--blocking", default="tuned", choices=["tuned", "model"],
                     help="tuned: he_autotune_blocking per product at set-up; model: the cost model's choice")
+    ap.add_argument("--ntt-radix", default="tuned", choices=["tuned", "3", "4", "5"],
+                    help="log2 of the values per thread of the transforms: tuned = he_autotune_ntt_radix at set-up")
     ap.add_argument("--full-c0", action="store_true",
                     help="return all of c0 instead of only the decoded coefficients (Sec. 3.1.3)")
     return ap.parse_args()
@@ -674,6 +676,11 @@ def gpu_arm(args, world, rank, local):
     torch.cuda.set_device(local)
     wl = WORKLOADS[args.workload]
     ctx = B.Context(wl["N"], wl["L"], device=local)
+    if args.ntt_radix == "tuned":  # before the blocking tuner, which times whole products at this radix
+        radix_ms = {str(r): round(v, 4) for r, v in ctx.autotune_ntt_radix()[1].items()}
+    else:
+        ctx.set_ntt_radix(int(args.ntt_radix))
+        radix_ms = None
     prods = workloads.bert_layer_products(**getattr(workloads, wl["model"]))
     want_host = not args.no_e2e
     flags = B.HE_FLAGS_NONE if args.full_c0 else B.HE_DROP_C0
@@ -795,6 +802,8 @@ def gpu_arm(args, world, rank, local):
                    "output": "full ciphertexts" if args.full_c0 else
                    "c1 + c0 at the decoded coefficients only (Sec. 3.1.3, HE_DROP_C0)",
                    "blockings_mkn": blks, "blocking_choice": args.blocking, "launch": args.launch,
+                   "ntt_values_per_thread": 1 << ctx.ntt_radix, "ntt_radix_choice": args.ntt_radix,
+                   "ntt_radix_round_trip_ms": radix_ms,
                    "cuda_graph": bool(use_graph), "kernel_source_hash": kernel_source_hash(), "parallelism": f"replicas x{world} (independent layers, no collective)",
                    "l2": "inputs larger than L2: one step reads/writes ~3 GB of ciphertexts/weights"},
         "latency_ms": {"p50": statistics.median(per), "p99": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))]},

@@ -148,6 +148,30 @@ HE_API int he_autotune_blocking(he_ctx* ctx, uint32_t m, uint32_t k, uint32_t n,
                                 size_t scratch_bytes, size_t* scratch_needed, he_blocking* out, float* best_ms,
                                 void* stream);
 
+/* Radix of the number-theoretic transforms (the polynomial products of Sec. 3.1.3's
+ * footnote, done as NTT, slot-wise product, inverse NTT): each thread of a transform
+ * holds 2^log2_values coefficients and runs log2_values butterfly stages in registers
+ * per pass.  Built: 4 (16 values, the default) for 512 <= N <= 8192, and 3 and 5 as well
+ * for N = 4096 and 8192.  Outputs are bit-identical for every radix (transforms end fully
+ * reduced); only speed differs.  The setting applies to launches enqueued afterwards (a
+ * CUDA graph keeps the radix it captured) and must not change while another thread
+ * uses the context.  N < 512 accepts only 4.  Errors: HE_EINVAL (not built for N). */
+HE_API int he_set_ntt_radix(he_ctx* ctx, uint32_t log2_values);
+HE_API int he_get_ntt_radix(const he_ctx* ctx, uint32_t* log2_values);
+
+/* Measured choice of that radix (an autotuner; the paper has no counterpart): for every
+ * radix built for N, times forward and inverse transforms of cnt ciphertext components
+ * (cnt * L polynomials of pseudo-random residues, in place; cnt = 0 means enough for 256
+ * MB, larger than L2), one warm-up and three timed round trips, and selects the fastest
+ * for the context.  ms (may be NULL): 3 floats, the best round trip in milliseconds for
+ * log2_values 3, 4, 5, -1 where not built.  *chosen (may be NULL) receives the selected
+ * log2_values.  scratch: caller-owned device memory; with scratch == NULL nothing runs
+ * and *scratch_needed (may be NULL) receives cnt * L * N * 8.  Synchronizes `stream`.
+ * N < 512: nothing runs, *chosen = 4, *scratch_needed = 0.  Errors: HE_ENOMEM (scratch too small), HE_ECUDA;
+ * on an error the radix in force before the call is kept. */
+HE_API int he_autotune_ntt_radix(he_ctx* ctx, uint32_t cnt, void* scratch, size_t scratch_bytes,
+                                 size_t* scratch_needed, float* ms, uint32_t* chosen, void* stream);
+
 /* ---- test client (Sec. 2.2 BFV; encrypt/decrypt are the client's side) -- */
 
 /* Secret key s with ternary coefficients, coefficient i = (u mod 3) - 1 for the

@@ -94,6 +94,10 @@ def _load():
         "he_unmask_acc": (ctypes.c_int, [P, u64, u32, u32, pB, u32, P, P]),
         "he_autotune_blocking": (ctypes.c_int, [P, u32, u32, u32, u32, u32, u32, u32, P, sz, ctypes.POINTER(sz), pB,
                                                 ctypes.POINTER(ctypes.c_float), P]),
+        "he_set_ntt_radix": (ctypes.c_int, [P, u32]),
+        "he_get_ntt_radix": (ctypes.c_int, [P, pu32]),
+        "he_autotune_ntt_radix": (ctypes.c_int, [P, u32, P, sz, ctypes.POINTER(sz), ctypes.POINTER(ctypes.c_float),
+                                                 pu32, P]),
         "he_share_matmul": (ctypes.c_int, [P, P, P, P, P, u32, u32, u32, P, P]),
         "he_share_matmul_batch": (ctypes.c_int, [P, P, P, P, P, u32, u32, u32, u32, P, P]),
         "he_matmul_multi_host": (ctypes.c_int, [P, u32, ctypes.POINTER(Product), u32, P, sz, P]),
@@ -196,6 +200,30 @@ class Context:
                                             _stream(stream)))
             del scratch
         return b.as_tuple(), ms.value
+
+    @property
+    def ntt_radix(self):
+        """log2 of the values per thread of the register-blocked transforms (he_get_ntt_radix)."""
+        v = ctypes.c_uint32(0)
+        _check(lib.he_get_ntt_radix(self.h, ctypes.byref(v)))
+        return v.value
+
+    def set_ntt_radix(self, log2_values):
+        _check(lib.he_set_ntt_radix(self.h, log2_values))
+
+    def autotune_ntt_radix(self, cnt=0, stream=None):
+        """Measured transform radix (he_autotune_ntt_radix), selected for this context.
+        Returns (log2 values per thread, {log2 values: ms per forward + inverse round trip})."""
+        need = ctypes.c_size_t(0)
+        ms = (ctypes.c_float * 3)()
+        chosen = ctypes.c_uint32(0)
+        _check(lib.he_autotune_ntt_radix(self.h, cnt, None, 0, ctypes.byref(need), ms, ctypes.byref(chosen),
+                                         _stream(stream)))
+        scratch = self.empty(max(need.value // 8, 1))
+        _check(lib.he_autotune_ntt_radix(self.h, cnt, _ptr(scratch), scratch.numel() * 8, None, ms,
+                                         ctypes.byref(chosen), _stream(stream)))
+        del scratch
+        return chosen.value, {r: ms[r - 3] for r in (3, 4, 5) if ms[r - 3] >= 0}
 
     # ---- allocation helpers (device memory comes from torch)
     def empty(self, words):

@@ -228,6 +228,7 @@ int he_params_init(he_ctx** out, uint32_t N, uint32_t L, const uint64_t* q, uint
   while ((1u << C.logN) < N) ++C.logN;
   C.L = L;
   C.log2t = log2_t;
+  C.logR = he::kNttLogRDefault;
   C.tmask = (1ull << log2_t) - 1;
   u64 qmt = 1;
   for (u32 l = 0; l < L; ++l) qmt = (u64)(((u128)qmt * (q[l] & C.tmask)) & C.tmask);
@@ -725,6 +726,82 @@ int he_autotune_blocking(he_ctx* c, uint32_t m, uint32_t k, uint32_t n, uint32_t
   if (int r = he_device_status(c, stream)) return r;
   if (best_ms) *best_ms = best;
   return HE_OK;
+}
+
+int he_set_ntt_radix(he_ctx* c, uint32_t log2_values) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (c->C.logN < 9) {  // small rings run the shared-memory transforms, which have no radix
+    if (log2_values != (uint32_t)he::kNttLogRDefault) return fail(HE_EINVAL, "N < 512 has only the default radix");
+    return HE_OK;
+  }
+  if (!he::ntt_radix_built(c->C.logN, log2_values)) return fail(HE_EINVAL, "radix not built for this N");
+  c->C.logR = log2_values;
+  return HE_OK;
+}
+
+int he_get_ntt_radix(const he_ctx* c, uint32_t* log2_values) {
+  if (!c || !log2_values) return fail(HE_EINVAL, "NULL argument");
+  *log2_values = c->C.logR;
+  return HE_OK;
+}
+
+int he_autotune_ntt_radix(he_ctx* c, uint32_t cnt, void* scratch, size_t scratch_bytes, size_t* scratch_needed,
+                          float* ms, uint32_t* chosen, void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (ms)
+    for (int i = 0; i < 3; ++i) ms[i] = -1.f;
+  if (chosen) *chosen = c->C.logR;
+  if (c->C.logN < 9) {  // shared-memory transforms only: nothing to choose
+    if (scratch_needed) *scratch_needed = 0;
+    return HE_OK;
+  }
+  const u64 poly_bytes = 8ull * c->C.L * c->C.N;
+  if (!cnt) cnt = (uint32_t)std::max<u64>(1, (256ull << 20) / poly_bytes);  // larger than L2
+  const u64 need = (u64)cnt * poly_bytes;
+  if (scratch_needed) *scratch_needed = need;
+  if (!scratch) return HE_OK;
+  if (scratch_bytes < need) return fail(HE_ENOMEM, "scratch smaller than *scratch_needed");
+  if (int r = set_device(c)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  u64* polys = (u64*)scratch;
+  const u64 npolys = (u64)cnt * c->C.L;
+  int rc = launch(c, KProbe, st, "autotune radix: fill",
+                  [&] { return he::launch_fill_random(c->C, polys, npolys * c->C.N, 0x7adull, 0, st); });
+  if (rc) return rc;
+  const u32 keep = c->C.logR;
+  cudaEvent_t e0 = get_event(c), e1 = get_event(c);
+  float best = -1.f;
+  u32 best_r = keep;
+  for (u32 r = 3; r <= 5 && rc == HE_OK; ++r) {
+    if (!he::ntt_radix_built(c->C.logN, r)) continue;
+    c->C.logR = r;
+    float rbest = -1.f;
+    for (int rep = 0; rep < 4 && rc == HE_OK; ++rep) {  // one warm-up, three timed round trips
+      cudaEventRecord(e0, st);
+      rc = launch(c, KNttFwd, st, "autotune radix: forward",
+                  [&] { return he::launch_ntt_forward(c->C, polys, polys, npolys, st); });
+      if (rc == HE_OK)
+        rc = launch(c, KNttInv, st, "autotune radix: inverse",
+                    [&] { return he::launch_ntt_inverse(c->C, polys, polys, npolys, st); });
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep && (rbest < 0 || t < rbest)) rbest = t;
+    }
+    if (rc != HE_OK) break;
+    if (ms) ms[r - 3] = rbest;
+    if (best < 0 || rbest < best) {
+      best = rbest;
+      best_r = r;
+    }
+  }
+  c->pool.push_back(e0);
+  c->pool.push_back(e1);
+  c->C.logR = rc == HE_OK ? best_r : keep;
+  if (rc != HE_OK) return rc;
+  if (chosen) *chosen = best_r;
+  return he_device_status(c, stream);
 }
 
 int he_matmul_batch_host(he_ctx* c, const uint64_t* ct_in_host, const uint64_t* pt, uint32_t m, uint32_t k,

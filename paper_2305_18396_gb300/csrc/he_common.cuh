@@ -41,6 +41,7 @@ struct PrimeConsts {
 
 struct Consts {
   u32 N, logN, L, log2t;
+  u32 logR;     // log2 of the values per thread of the register-blocked transforms (N >= 512)
   u64 tmask;    // t - 1
   u64 q_mod_t;  // (q_0 ... q_{L-1}) mod t
   PrimeConsts p[kMaxPrimes];

@@ -103,11 +103,11 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_forward_mm_small(const u64*
     dst[chunked_index((u64)Lb * 2 + c, J, l, i, nJ, C.L, C.N)] = split_word(sm[i]);
 }
 
-// Register-blocked versions for N >= 512 (blockDim = NttShape<LOGN>::T).
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_ntt_forward_t(const u64* src, u64* dst,
+// Register-blocked versions for N >= 512 (blockDim = NttShape<LOGN, LOGR>::T).
+template <int LOGN, int LOGR>
+__global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>::kMinBlocks) k_ntt_forward_t(const u64* src, u64* dst,
                                                                      const __grid_constant__ Consts C) {
-  using S = NttShape<LOGN>;
+  using S = NttShape<LOGN, LOGR>;
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
   const PrimeConsts& P = C.p[poly % C.L];
@@ -116,10 +116,10 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks)
   ntt_forward_block<S>(sm, P, [&](u32 e) { return s[e]; }, [&](u32 e, u64 v) { d[e] = v; });
 }
 
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_ntt_inverse_t(const u64* src, u64* dst,
+template <int LOGN, int LOGR>
+__global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>::kMinBlocks) k_ntt_inverse_t(const u64* src, u64* dst,
                                                                      const __grid_constant__ Consts C) {
-  using S = NttShape<LOGN>;
+  using S = NttShape<LOGN, LOGR>;
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
   const PrimeConsts& P = C.p[poly % C.L];
@@ -313,10 +313,10 @@ __global__ void __launch_bounds__(kNttThreads) k_encode_weights(const u64* W, u3
   for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) pt[chunked_index(I, J, l, i, nJ, C.L, C.N)] = split_word(sm[i]);
 }
 
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_encode_weights_t(const u64* W, u32 k, u32 n, Blk b, u32 nI,
+template <int LOGN, int LOGR>
+__global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>::kMinBlocks) k_encode_weights_t(const u64* W, u32 k, u32 n, Blk b, u32 nI,
                                                                         u32 nJ, u64* pt, const __grid_constant__ Consts C) {
-  using S = NttShape<LOGN>;
+  using S = NttShape<LOGN, LOGR>;
   extern __shared__ u64 sm[];
   const u64 item_polys = (u64)nI * nJ * C.L;
   const u64 item = blockIdx.x / item_polys, poly = blockIdx.x % item_polys;
@@ -340,10 +340,10 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks)
                        [&](u32 e, u64 v) { pt[chunked_index(I, J, l, e, nJ, C.L, S::N)] = split_word(v); }, nk);
 }
 
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_intt_mask_t(u64* out, u64 out_cts, u64 seed,
+template <int LOGN, int LOGR>
+__global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>::kMinBlocks) k_intt_mask_t(u64* out, u64 out_cts, u64 seed,
                                                                    const __grid_constant__ Consts C) {
-  using S = NttShape<LOGN>;
+  using S = NttShape<LOGN, LOGR>;
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
   const u64 item = poly / (out_cts * 2 * C.L);  // batch item: re-masked with seed + item
@@ -396,10 +396,10 @@ cudaError_t launch_mac_ws_cfg(const Consts& C, const u64* ctN, const u64* pt, Ou
 
 // Forward NTT of the input ciphertexts of a product into the slot-chunked operand layout.
 // Input poly p = ((Lb nJ + J) 2 + c) L + l of the wire format [Lb nJ + J][2][L][N].
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_ntt_forward_mm_t(const u64* src, u64* ctN, u32 nJ, u32 nLb,
+template <int LOGN, int LOGR>
+__global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>::kMinBlocks) k_ntt_forward_mm_t(const u64* src, u64* ctN, u32 nJ, u32 nLb,
                                                                         const __grid_constant__ Consts C) {
-  using S = NttShape<LOGN>;
+  using S = NttShape<LOGN, LOGR>;
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
   const u64 item_polys = (u64)nLb * nJ * 2 * C.L;
@@ -418,10 +418,10 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks)
 
 // Compact-output mode: inverse NTT of the c1 polynomials only, in place.  Ciphertext g's
 // c1 for prime l sits at base + g * ct_stride + l * N.
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_intt_c1_t(u64* base, u64 ct_stride,
+template <int LOGN, int LOGR>
+__global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>::kMinBlocks) k_intt_c1_t(u64* base, u64 ct_stride,
                                                                  const __grid_constant__ Consts C) {
-  using S = NttShape<LOGN>;
+  using S = NttShape<LOGN, LOGR>;
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
   u64* d = base + (poly / C.L) * ct_stride + (poly % C.L) * (u64)S::N;
@@ -535,27 +535,31 @@ cudaError_t configure_kernels(const Consts&) {
   set((const void*)k_encode_weights, one);
   set((const void*)k_intt_mask, one);
   set((const void*)k_mac_ws_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
-#define HE_SET_T(LOGN)                                                                             \
-  set((const void*)k_ntt_forward_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
-  set((const void*)k_ntt_inverse_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
-  set((const void*)k_encode_weights_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));       \
-  set((const void*)k_ntt_forward_mm_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));       \
-  set((const void*)k_intt_mask_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
-  set((const void*)k_intt_c1_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));
-  HE_SET_T(9) HE_SET_T(10) HE_SET_T(11) HE_SET_T(12) HE_SET_T(13)
+#define HE_SET_T(LN, LR, unused)                                                                    \
+  {                                                                                                  \
+    const int bytes = NttShape<LN, LR>::kSmemWords * (int)sizeof(u64);                               \
+    set((const void*)k_ntt_forward_t<LN, LR>, bytes);                                                \
+    set((const void*)k_ntt_inverse_t<LN, LR>, bytes);                                                \
+    set((const void*)k_encode_weights_t<LN, LR>, bytes);                                             \
+    set((const void*)k_ntt_forward_mm_t<LN, LR>, bytes);                                             \
+    set((const void*)k_intt_mask_t<LN, LR>, bytes);                                                  \
+    set((const void*)k_intt_c1_t<LN, LR>, bytes);                                                    \
+  }
+  HE_NTT_SHAPES(HE_SET_T, 0)
 #undef HE_SET_T
   return e;
 }
 
-// Launch KERNEL<LOGN> with NttShape<LOGN> threads / shared memory when N >= 512.
+// Launch KERNEL<LOGN, LOGR> for the context's (log N, radix) with NttShape<LOGN, LOGR>
+// threads and shared memory when N >= 512; a pair that is not built is an error.
+#define HE_T_CASE(LN, LR, KERNEL, GRID, ST, ...)                                                          \
+  case HE_NTT_KEY(LN, LR):                                                                                \
+    KERNEL<LN, LR><<<GRID, NttShape<LN, LR>::T, NttShape<LN, LR>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); \
+    break;
 #define HE_DISPATCH_T(KERNEL, GRID, ST, ...)                                                              \
-  switch (C.logN) {                                                                                       \
-    case 9: KERNEL<9><<<GRID, NttShape<9>::T, NttShape<9>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break;     \
-    case 10: KERNEL<10><<<GRID, NttShape<10>::T, NttShape<10>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
-    case 11: KERNEL<11><<<GRID, NttShape<11>::T, NttShape<11>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
-    case 12: KERNEL<12><<<GRID, NttShape<12>::T, NttShape<12>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
-    case 13: KERNEL<13><<<GRID, NttShape<13>::T, NttShape<13>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
-    default: break;                                                                                       \
+  switch (HE_NTT_KEY(C.logN, C.logR)) {                                                                   \
+    HE_NTT_SHAPES(HE_T_CASE, KERNEL, GRID, ST, __VA_ARGS__)                                               \
+    default: return cudaErrorInvalidValue;                                                                \
   }
 
 cudaError_t launch_ntt_forward(const Consts& C, const u64* src, u64* dst, u64 npolys, cudaStream_t st) {

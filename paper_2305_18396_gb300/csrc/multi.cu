@@ -32,10 +32,10 @@ __device__ __forceinline__ u32 find_item(const MultiTable& T, u64 b, F begin) {
 // graph takes fresh on every replay).
 __device__ __forceinline__ u64 item_seed(const MultiItem& it) { return it.seed_dev ? *it.seed_dev : it.mask_seed; }
 
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_fwd_multi_t(const __grid_constant__ MultiTable T,
+template <int LOGN, int LOGR>
+__global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>::kMinBlocks) k_fwd_multi_t(const __grid_constant__ MultiTable T,
                                                                    const __grid_constant__ Consts C) {
-  using S = NttShape<LOGN>;
+  using S = NttShape<LOGN, LOGR>;
   extern __shared__ u64 sm[];
   const u32 i = find_item(T, blockIdx.x, [](const MultiItem& x) { return x.fwd_begin; });
   const MultiItem& it = T.it[i];
@@ -136,20 +136,20 @@ __device__ __forceinline__ void c0_block(const MultiTable& T, const Consts& C, u
                          C, sm);
 }
 
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_inv_multi_t(const __grid_constant__ MultiTable T,
+template <int LOGN, int LOGR>
+__global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>::kMinBlocks) k_inv_multi_t(const __grid_constant__ MultiTable T,
                                                                    const __grid_constant__ Consts C) {
   extern __shared__ u64 sm[];
-  inv_block<NttShape<LOGN>>(T, C, blockIdx.x, sm);
+  inv_block<NttShape<LOGN, LOGR>>(T, C, blockIdx.x, sm);
 }
 
 // The c1 inverse NTTs and the pruned c0 transforms are independent: one grid runs both,
 // blocks [0, inv_blocks) the former and the rest the latter, so neither drains alone.
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, NttShape<LOGN>::kMinBlocks) k_inv_c0_multi_t(
+template <int LOGN, int LOGR>
+__global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>::kMinBlocks) k_inv_c0_multi_t(
     const __grid_constant__ MultiTable T, const __grid_constant__ Consts C, u64 inv_blocks) {
   extern __shared__ u64 sm[];
-  if (blockIdx.x < inv_blocks) inv_block<NttShape<LOGN>>(T, C, blockIdx.x, sm);
+  if (blockIdx.x < inv_blocks) inv_block<NttShape<LOGN, LOGR>>(T, C, blockIdx.x, sm);
   else c0_block(T, C, blockIdx.x - inv_blocks, sm);
 }
 
@@ -193,14 +193,15 @@ __global__ void __launch_bounds__(kThreadsSmall) k_c0_multi(const __grid_constan
   c0_block(T, C, blockIdx.x, sm);
 }
 
+// KERNEL<LOGN, LOGR> for the context's (log N, radix); a pair that is not built is an error.
+#define HE_MULTI_CASE(LN, LR, KERNEL, GRID, ST, ...)                                                               \
+  case HE_NTT_KEY(LN, LR):                                                                                         \
+    KERNEL<LN, LR><<<GRID, NttShape<LN, LR>::T, NttShape<LN, LR>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__);    \
+    break;
 #define HE_MULTI_DISPATCH(KERNEL, GRID, ST, ...)                                                                   \
-  switch (C.logN) {                                                                                                \
-    case 9: KERNEL<9><<<GRID, NttShape<9>::T, NttShape<9>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break;     \
-    case 10: KERNEL<10><<<GRID, NttShape<10>::T, NttShape<10>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
-    case 11: KERNEL<11><<<GRID, NttShape<11>::T, NttShape<11>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
-    case 12: KERNEL<12><<<GRID, NttShape<12>::T, NttShape<12>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
-    case 13: KERNEL<13><<<GRID, NttShape<13>::T, NttShape<13>::kSmemWords * sizeof(u64), ST>>>(__VA_ARGS__); break; \
-    default: break;                                                                                                \
+  switch (HE_NTT_KEY(C.logN, C.logR)) {                                                                            \
+    HE_NTT_SHAPES(HE_MULTI_CASE, KERNEL, GRID, ST, __VA_ARGS__)                                                    \
+    default: return cudaErrorInvalidValue;                                                                         \
   }
 
 }  // namespace
@@ -215,11 +216,11 @@ cudaError_t configure_multi_kernels() {
   set((const void*)k_inv_multi_small, one);
   set((const void*)k_c0_multi, 2 * one);
   set((const void*)k_mac_multi_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
-#define HE_SET_MULTI(LOGN)                                                                        \
-  set((const void*)k_fwd_multi_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
-  set((const void*)k_inv_multi_t<LOGN>, NttShape<LOGN>::kSmemWords * (int)sizeof(u64));          \
-  set((const void*)k_inv_c0_multi_t<LOGN>, 2 * (1 << LOGN) * (int)sizeof(u64));
-  HE_SET_MULTI(9) HE_SET_MULTI(10) HE_SET_MULTI(11) HE_SET_MULTI(12) HE_SET_MULTI(13)
+#define HE_SET_MULTI(LN, LR, unused)                                                                   \
+  set((const void*)k_fwd_multi_t<LN, LR>, NttShape<LN, LR>::kSmemWords * (int)sizeof(u64));            \
+  set((const void*)k_inv_multi_t<LN, LR>, NttShape<LN, LR>::kSmemWords * (int)sizeof(u64));            \
+  set((const void*)k_inv_c0_multi_t<LN, LR>, 2 * (1 << LN) * (int)sizeof(u64));
+  HE_NTT_SHAPES(HE_SET_MULTI, 0)
 #undef HE_SET_MULTI
   return e;
 }
@@ -254,10 +255,10 @@ cudaError_t launch_inv_multi(const Consts& C, const MultiTable& T, u64 blocks, c
   return cudaGetLastError();
 }
 
-// One grid where both kinds of block have the same shape (256 threads, N <= 4096); at
-// N = 8192 the inverse transform's 512-thread, 68 KB blocks would starve the c0 blocks
+// One grid where the inverse transform's blocks are small (at most 256 threads, N <= 4096);
+// at N = 8192 the inverse transform's 512-thread, 68 KB blocks would starve the c0 blocks
 // (measured: 19% slower than two grids), and small rings use the simple kernels.
-bool inv_c0_fused(const Consts& C) { return C.logN >= 9 && C.logN <= 12; }
+bool inv_c0_fused(const Consts& C) { return C.logN >= 9 && C.logN <= 12 && C.logN - C.logR <= 8; }
 
 cudaError_t launch_inv_c0_multi(const Consts& C, const MultiTable& T, u64 inv_blocks, u64 c0_blocks, u32 c0_words,
                                 cudaStream_t st) {
@@ -267,14 +268,17 @@ cudaError_t launch_inv_c0_multi(const Consts& C, const MultiTable& T, u64 inv_bl
   }
   const u64 blocks = inv_blocks + c0_blocks;
   if (!blocks) return cudaGetLastError();
-#define HE_INV_C0(LOGN)                                                                                      \
-  case LOGN: {                                                                                               \
-    const u32 words = (u32)NttShape<LOGN>::kSmemWords > c0_words ? (u32)NttShape<LOGN>::kSmemWords : c0_words; \
-    const size_t smem = (size_t)words * sizeof(u64);                                                         \
-    k_inv_c0_multi_t<LOGN><<<(unsigned)blocks, NttShape<LOGN>::T, smem, st>>>(T, C, inv_blocks);            \
-    break;                                                                                                   \
+#define HE_INV_C0(LN, LR, unused)                                                                    \
+  case HE_NTT_KEY(LN, LR): {                                                                         \
+    using S = NttShape<LN, LR>;                                                                      \
+    const u32 words = (u32)S::kSmemWords > c0_words ? (u32)S::kSmemWords : c0_words;                 \
+    k_inv_c0_multi_t<LN, LR><<<(unsigned)blocks, S::T, (size_t)words * sizeof(u64), st>>>(T, C, inv_blocks); \
+    break;                                                                                           \
   }
-  switch (C.logN) { HE_INV_C0(9) HE_INV_C0(10) HE_INV_C0(11) HE_INV_C0(12) HE_INV_C0(13) default: break; }
+  switch (HE_NTT_KEY(C.logN, C.logR)) {
+    HE_NTT_SHAPES(HE_INV_C0, 0)
+    default: return cudaErrorInvalidValue;
+  }
 #undef HE_INV_C0
   return cudaGetLastError();
 }

@@ -75,14 +75,29 @@ __device__ __forceinline__ void ntt_inverse_smem(u64* a, u32 logN, const PrimeCo
 // ------------------------------------------------------------------ register-blocked form
 
 
-template <int LOGN>
+// The radices built: 2^LOGR values per thread.  16 (LOGR = 4) everywhere; 8 and 32 as well
+// at N = 4096 and 8192, where a context may select them (he_set_ntt_radix) or have them
+// measured (he_autotune_ntt_radix).  Measured on GB300 (whole BERT layers, before the
+// register caps below): 16 beats 8 and 32 at N = 4096 (3.28 ms vs 3.47 / 3.65 ms per
+// layer) and 32 at N = 8192 (40.3 vs 45.0 ms per BERT-large layer: 128 instead of 242
+// registers, twice the resident warps).
+constexpr int kNttLogRDefault = 4;
+__host__ __device__ constexpr bool ntt_radix_built(u32 logN, u32 logR) {
+  return logN >= 9 && logN <= 13 && (logR == 4 || ((logN == 12 || logN == 13) && (logR == 3 || logR == 5)));
+}
+// X(LOGN, LOGR, ...) for every built pair (instantiation and dispatch lists).
+#define HE_NTT_SHAPES(X, ...)                                                                          \
+  X(9, 4, __VA_ARGS__) X(10, 4, __VA_ARGS__) X(11, 4, __VA_ARGS__) X(12, 3, __VA_ARGS__)             \
+  X(12, 4, __VA_ARGS__) X(12, 5, __VA_ARGS__) X(13, 3, __VA_ARGS__) X(13, 4, __VA_ARGS__)           \
+  X(13, 5, __VA_ARGS__)
+// Dispatch key of a (log N, LOGR) pair.
+#define HE_NTT_KEY(LOGN, LOGR) ((LOGN) * 8 + (LOGR))
+
+template <int LOGN, int LOGR_ = kNttLogRDefault>
 struct NttShape {
   static constexpr int kLogN = LOGN;
   static constexpr int N = 1 << LOGN;
-  // 2^LOGR values per thread.  Measured on GB300 (whole BERT layers): 16 beats 8 and 32 at
-  // N = 4096 (3.28 ms vs 3.47 / 3.65 ms per layer) and 32 at N = 8192 (40.3 vs 45.0 ms per
-  // BERT-large layer: 128 instead of 242 registers, twice the resident warps)
-  static constexpr int LOGR = 4;
+  static constexpr int LOGR = LOGR_;
   static constexpr int R = 1 << LOGR;
   static constexpr int T = N / R;                   // threads per block
   // Minimum resident blocks per SM asked of the compiler, which caps registers per thread.
@@ -91,8 +106,9 @@ struct NttShape {
   // registers) make the step 3.178 ms against 3.555 with none and 3.217 with four (64
   // registers, where the transforms spill); with the estimated-quotient forward product
   // three blocks also beat four for the forward transforms alone (3.069 vs 3.091 ms).
-  // At 512 threads (N = 8192) 128 registers already allow one block of 16 warps.
-  static constexpr int kMinBlocks = T <= 256 ? 3 : 1;
+  // At 512 threads (N = 8192) 128 registers already allow one block of 16 warps; 32 values
+  // per thread need their registers (no cap).
+  static constexpr int kMinBlocks = (LOGR <= 4 && T <= 256) ? 3 : 1;
   static constexpr int P = (LOGN + LOGR - 1) / LOGR;  // passes
   static constexpr int RS0 = LOGN - LOGR * (P - 1);   // stages of the outermost pass
   static constexpr int kSmemWords = N + (N >> LOGR);  // padded
