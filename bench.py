@@ -778,7 +778,7 @@ def gpu_arm(args, world, rank, local):
                "d2h_bytes_per_step": d2h, "steps": ksteps, "ms_per_step": dt * 1e3 / ksteps}
 
     share = share_products_leg(B, ctx, prods, mad_peak)
-    batched = None if args.no_batched else batched_leg(B, ctx, flags)
+    batched = batched_leg(B, ctx, flags) if world == 1 and not args.no_batched else None
 
     serving = None
     if world == 1 and not args.no_serving:
