@@ -163,7 +163,8 @@ HE_API int he_get_ntt_radix(const he_ctx* ctx, uint32_t* log2_values);
  * radix built for N, times forward and inverse transforms of cnt ciphertext components
  * (cnt * L polynomials of pseudo-random residues, in place; cnt = 0 means enough for 256
  * MB, larger than L2), one warm-up and three timed round trips, and selects the fastest
- * for the context.  ms (may be NULL): 3 floats, the best round trip in milliseconds for
+ * for the context -- another radix than the default 4 only when it is at least 5% faster
+ * (the transforms timed alone are not the layer).  ms (may be NULL): 3 floats, the best round trip in milliseconds for
  * log2_values 3, 4, 5, -1 where not built.  *chosen (may be NULL) receives the selected
  * log2_values.  scratch: caller-owned device memory; with scratch == NULL nothing runs
  * and *scratch_needed (may be NULL) receives cnt * L * N * 8.  Synchronizes `stream`.

@@ -113,7 +113,9 @@ def test_radix_tuner_selects_a_built_radix(B):
         chosen, ms = ctx.autotune_ntt_radix()
         assert chosen in (3, 4, 5) and ctx.ntt_radix == chosen
         assert set(ms) == {3, 4, 5} and all(v > 0 for v in ms.values())
-        assert ms[chosen] == min(ms.values())
+        best = min(ms, key=ms.get)  # the fastest, unless the default is within 5% of it
+        assert chosen == best or (chosen == 4 and ms[best] > 0.95 * ms[4])
+        assert chosen == 4 or ms[chosen] <= 0.95 * ms[4]
         m, k, n, blk, compact, W, ct, seed, want = cases[0]
         out = B.he_matmul(ctx, to_dev(ct), B.he_encode_weights(ctx, to_dev(W), k, n, blk), m, k, n, blk, seed)
         check_output(B, P, to_np(out), want, blk, compact, ctx.sizes(m, k, n, blk)["out_cts"])
