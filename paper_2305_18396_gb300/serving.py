@@ -24,7 +24,10 @@ form; requests arrive over time and are
   (the highest when the device is idle): the oldest launch keeps the SMs it can fill,
   later launches take the SMs it leaves idle (its tail, its small grids); each launch
   stream keeps its workspace between launches;
-* completed when their launch's event fires (latency = completion - arrival).
+* completed when their launch's event fires (latency = completion - arrival);
+* withdrawn by `Server.cancel` (a client that went away): a queued or admitted request
+  leaves at once and frees its share of the budget; one already launched cannot be
+  taken back from the GPU, so its output is dropped when its launch completes.
 
 `run_per_request` is the plain path it is compared against: one he_matmul per request,
 in arrival order, on one stream.
@@ -66,6 +69,7 @@ class Request:
     done: float = math.nan
     footprint: int = 0
     est: float = 0.0  # estimated device seconds inside a multi-product launch
+    cancelled: bool = False
 
 
 # Device-time estimate of one product inside a multi-product launch: a fixed part per
@@ -131,6 +135,18 @@ def launch_allowed(inflight, now, slots, overlap_s):
     return not inflight or remaining <= overlap_s
 
 
+def withdraw(queue, admitted, rid):
+    """Takes request `rid` out of the waiting lists.  Returns (queue, admitted, request,
+    where) with where "queued" or "admitted", or (queue, admitted, None, None) when it
+    is in neither (launched, finished or unknown)."""
+    for where, lst in (("queued", queue), ("admitted", admitted)):
+        for i, r in enumerate(lst):
+            if r.rid == rid:
+                rest = lst[:i] + lst[i + 1:]
+                return (rest, admitted, r, where) if where == "queued" else (queue, rest, r, where)
+    return queue, admitted, None, None
+
+
 class Server:
     def __init__(self, ctx, models, flags=B.HE_DROP_C0, hbm_budget=32 << 30, slots=2, max_batch=8,
                  batch_work_factor=0.25, batch_floor_ms=1.0, priorities=True, keep_outputs=True,
@@ -148,7 +164,7 @@ class Server:
         # the caching allocator keeps one pool instead of one per launch stream
         self.streams = [[torch.cuda.Stream(device=ctx.device, priority=p) for _ in range(slots)] for p in levels]
         self.alloc_stream = torch.cuda.current_stream(ctx.device)
-        self.queue, self.admitted, self.inflight, self.done = [], [], [], []
+        self.queue, self.admitted, self.inflight, self.done, self.cancelled = [], [], [], [], []
         self.in_use = 0
         self.launches = 0
         self._sizes = {}  # (matrix, m) -> he_sizes
@@ -167,6 +183,24 @@ class Server:
         if req.footprint > self.budget:
             raise ValueError(f"request {req.rid} needs {req.footprint} bytes, more than the whole budget")
         self.queue.append(req)
+
+    def cancel(self, rid):
+        """Withdraws request `rid`: "queued" / "admitted" (gone at once; an admitted one
+        frees its budget), "in_flight" (launched: its output is dropped when the launch
+        completes), or None (finished or unknown)."""
+        self.queue, self.admitted, r, where = withdraw(self.queue, self.admitted, rid)
+        if r is not None:
+            r.cancelled = True
+            if where == "admitted":
+                self.in_use -= r.footprint
+            self.cancelled.append(r)
+            return where
+        for f in self.inflight:
+            for r in f.reqs:
+                if r.rid == rid and not r.cancelled:
+                    r.cancelled = True
+                    return "in_flight"
+        return None
 
     def _admit(self):
         while self.queue and self.in_use + self.queue[0].footprint <= self.budget:
@@ -229,9 +263,9 @@ class Server:
                 for r in f.reqs:
                     r.done = now
                     self.in_use -= r.footprint
-                    if not self.keep:
+                    if not self.keep or r.cancelled:
                         r.out = None
-                    self.done.append(r)
+                    (self.cancelled if r.cancelled else self.done).append(r)
             else:
                 still.append(f)
         self.inflight = still

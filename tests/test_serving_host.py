@@ -70,3 +70,52 @@ def test_take_batch_fifo_stops_at_first_misfit():
     assert [r.rid for r in batch] == [0] and [r.rid for r in rest] == [1, 2]
     batch, rest = SV.take_batch(reqs(0.1e-3, 2e-3, 0.1e-3), 8, 0.25, 1e-3, fifo=False)
     assert [r.rid for r in batch] == [0, 2] and [r.rid for r in rest] == [1]
+
+
+def test_withdraw_from_queue_or_admitted():
+    queue, admitted = reqs(1e-3, 2e-3), reqs(3e-3, 4e-3, 5e-3)
+    for r in admitted:
+        r.rid += 10
+    q, a, r, where = SV.withdraw(queue, admitted, 11)
+    assert where == "admitted" and r.rid == 11 and [x.rid for x in a] == [10, 12] and q == queue
+    q, a, r, where = SV.withdraw(queue, admitted, 1)
+    assert where == "queued" and r.rid == 1 and [x.rid for x in q] == [0] and a == admitted
+    assert SV.withdraw(queue, admitted, 99) == (queue, admitted, None, None)
+
+
+class _Event:
+    def __init__(self, done):
+        self.done = done
+
+    def query(self):
+        return self.done
+
+
+def _server_state():
+    """A Server's host state without a device: two queued, two admitted, one launch in flight."""
+    srv = object.__new__(SV.Server)
+    srv.queue, srv.admitted = reqs(1e-3, 1e-3), reqs(1e-3, 1e-3)
+    for i, r in enumerate(srv.admitted):
+        r.rid, r.footprint = 10 + i, 100
+    running = reqs(1e-3, 1e-3)
+    for i, r in enumerate(running):
+        r.rid, r.footprint, r.out = 20 + i, 100, object()
+    srv.inflight = [SV._InFlight(0.0, 1e-3, 0, _Event(False), running, None, None)]
+    srv.done, srv.cancelled, srv.in_use, srv.keep = [], [], 400, True
+    return srv
+
+
+def test_cancel_queued_admitted_and_launched_requests():
+    srv = _server_state()
+    assert srv.cancel(1) == "queued" and [r.rid for r in srv.queue] == [0] and srv.in_use == 400
+    assert srv.cancel(11) == "admitted" and [r.rid for r in srv.admitted] == [10] and srv.in_use == 300
+    assert srv.cancel(21) == "in_flight" and srv.cancel(21) is None  # already withdrawn
+    assert srv.cancel(99) is None
+    assert [r.rid for r in srv.cancelled] == [1, 11]
+    srv._poll(1.0)  # launch still running: nothing completes
+    assert srv.inflight and not srv.done
+    srv.inflight[0].event.done = True
+    srv._poll(2.0)  # the launch completes: the cancelled request's output is dropped
+    assert not srv.inflight and srv.in_use == 100
+    assert [r.rid for r in srv.done] == [20] and srv.done[0].out is not None
+    assert [r.rid for r in srv.cancelled] == [1, 11, 21] and srv.cancelled[-1].out is None
