@@ -45,3 +45,21 @@ def test_peaks_fall_back_without_measured_file(tmp_path, monkeypatch):
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6749.7, "bf16_tflops": 1901.0}')
     pk, src = bench.peaks()
     assert src == "measured" and pk["hbm_gbs"] == 6749.7
+
+
+def test_clock_summary_parses_nvidia_smi_rows():
+    s = bench.ClockSampler(0)
+    s.out = "\n".join([
+        "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2062, 2070, 1210.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 345, 2070, 120.0, 0x0000000000000001, Not Active, Not Active, Not Active, Not Active",  # idle
+        "garbage line",
+    ])
+    c = s.summary()
+    assert c["samples"] == 3 and c["sm_max_mhz"] == 2070.0
+    assert c["sm_mhz"] == 2066.0  # median over the loaded samples (idle ones dropped)
+    assert c["reasons"] == ["sw_power_cap"]
+    s.out = "0, 1800, 2070, 1300.0, 0x48, Active, Not Active, Active, Not Active"
+    assert s.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    s.out = ""
+    assert s.summary() is None
