@@ -1,6 +1,6 @@
 """bench.py's JSON line on a GPU: one line with every field of the contract, consistent.
 
-Runs a short bench (two timed steps, no serving leg, no CPU baseline) as a subprocess
+Runs a short bench (four timed steps, no serving leg, no CPU baseline) as a subprocess
 and checks the keys, the units and the relations between them.
 """
 import json
