@@ -45,6 +45,7 @@ def _load():
         "or_sample_ternary": (None, [u64, u32, _i64p]),
         "or_sample_uniform": (None, [u64, u32, u32, u64, u32, _u64p]),
         "or_sample_gauss": (None, [u64, u32, u32, _i64p]),
+        "or_gauss_from_draw": (ctypes.c_int64, [u64]),
         "or_sample_mask": (None, [u64, u32, u32, u32, _u64p]),
         "or_gauss_cdt": (None, [_u64p]),
         "or_gauss_bound": (u32, []),

@@ -271,16 +271,17 @@ void or_sample_uniform(u64 seed, u32 obj, u32 prime_index, u64 q, u32 N, u64* a)
   }
 }
 
-/* Discrete Gaussian (sigma = 3.2, |e| <= 19) by inversion of its CDT:
- * e = -B + #{ j : u >= T_j }. */
+/* Discrete Gaussian (sigma = 3.2, |e| <= 19) by inversion of its CDT: the value of
+ * one 64-bit draw u is e = -B + #{ j : u >= T_j }. */
+i64 or_gauss_from_draw(u64 u) {
+  i64 v = -(i64)OR_GAUSS_BOUND;
+  for (u32 j = 0; j < 2 * OR_GAUSS_BOUND; j++)
+    if (u >= OR_GAUSS_CDT[j]) v++;
+  return v;
+}
+
 void or_sample_gauss(u64 seed, u32 obj, u32 N, i64* e) {
-  for (u32 i = 0; i < N; i++) {
-    u64 u = draw64(seed, i, obj, OR_DOMAIN_ERROR, 0);
-    i64 v = -(i64)OR_GAUSS_BOUND;
-    for (u32 j = 0; j < 2 * OR_GAUSS_BOUND; j++)
-      if (u >= OR_GAUSS_CDT[j]) v++;
-    e[i] = v;
-  }
+  for (u32 i = 0; i < N; i++) e[i] = or_gauss_from_draw(draw64(seed, i, obj, OR_DOMAIN_ERROR, 0));
 }
 
 /* Server mask coefficients: uniform in Z_t, t = 2^log2t (low bits of a 64-bit draw). */

@@ -8,6 +8,7 @@ CDT, Python big-integer rounding of q*m/t, and brute-force integer matrix
 products.  A dropped term, a wrong sign, index or transposition anywhere in
 the oracle fails at least one of them.
 """
+import functools
 import math
 from pathlib import Path
 
@@ -144,19 +145,26 @@ def test_philox_known_answers():
         assert list(map(int, out)) == w[6:]
 
 
+@functools.lru_cache(maxsize=1)
+def _gauss_cdt_sympy(B=19):
+    """T_j = floor(2^64 P(e <= -B + j)), j < 2B, for the discrete Gaussian of sigma 3.2 on
+    [-B, B] (weights exp(-k^2 / (2 sigma^2))), evaluated by sympy at 60 digits."""
+    sigma = sympy.Rational(16, 5)
+    rho = [sympy.exp(-sympy.Rational(k * k) / (2 * sigma**2)) for k in range(-B, B + 1)]
+    total = sum(rho)
+    acc, out = 0, []
+    for j in range(2 * B):
+        acc += rho[j]
+        out.append(int(sympy.floor(sympy.N(acc / total * sympy.Integer(2) ** 64, 60))))
+    return tuple(out)
+
+
 def test_gauss_cdt_matches_sympy():
     B = lib.or_gauss_bound()
     assert B == 19
     table = np.zeros(2 * B, dtype=np.uint64)
     lib.or_gauss_cdt(p64(table))
-    sigma = sympy.Rational(16, 5)
-    rho = [sympy.exp(-sympy.Rational(k * k) / (2 * sigma**2)) for k in range(-B, B + 1)]
-    total = sum(rho)
-    acc = 0
-    for j in range(2 * B):
-        acc += rho[j]
-        v = sympy.N(acc / total * sympy.Integer(2) ** 64, 60)
-        assert int(sympy.floor(v)) == int(table[j]), j
+    assert [int(x) for x in table] == list(_gauss_cdt_sympy(B))
 
 
 def test_gauss_sampler_moments():
@@ -186,6 +194,110 @@ def test_ternary_and_mask_and_uniform_samplers():
     out = np.zeros(4, dtype=np.uint32)
     lib.or_philox4x32_10(p32(ctr), p32(key), p32(out))
     assert int(m[17]) == (int(out[0]) | (int(out[1]) << 32)) & (2**37 - 1)
+
+
+# ------------------------------------------------------------------ sampler draw -> value maps
+#
+# The paper fixes no distributions or generator (Sec. 2.2 only names the BFV scheme), so the
+# oracle's samplers follow stated readings: Philox4x32-10 with counter (coefficient, object,
+# domain, lane) and key = seed; secret coefficient (u mod 3) - 1 of the low 64-bit word u;
+# uniform residue = the little-endian 128-bit block mod q_l, lane = prime index; error
+# -19 + #{j : u >= T_j} with T the sigma = 3.2 CDT.  The tests below recompute each map in
+# Python from a Philox written here from its published definition (pinned to the authors'
+# known answers) and the CDT from sympy, and compare element by element, so a different
+# word order, reduction width, modulus or comparison in the oracle fails.
+
+_PHILOX_M = (0xD2511F53, 0xCD9E8D57)  # round multipliers (SC'11, Philox4x32)
+_PHILOX_W = (0x9E3779B9, 0xBB67AE85)  # key schedule increments
+_M32 = 0xFFFFFFFF
+
+
+def _philox_py(ctr, key, rounds=10):
+    x0, x1, x2, x3 = (int(c) & _M32 for c in ctr)
+    k0, k1 = (int(k) & _M32 for k in key)
+    for r in range(rounds):
+        if r:
+            k0, k1 = (k0 + _PHILOX_W[0]) & _M32, (k1 + _PHILOX_W[1]) & _M32
+        a = _PHILOX_M[0] * x0
+        b = _PHILOX_M[1] * x2
+        x0, x1, x2, x3 = (b >> 32) ^ x1 ^ k0, b & _M32, (a >> 32) ^ x3 ^ k1, a & _M32
+    return x0, x1, x2, x3
+
+
+def _draw_py(seed, coef, obj, domain, lane):
+    return _philox_py((coef, obj, domain, lane), (seed & _M32, seed >> 32))
+
+
+def test_python_philox_matches_known_answers():
+    for w in _read_kat():
+        assert list(_philox_py(w[:4], w[4:6])) == w[6:]
+
+
+@pytest.mark.parametrize("seed", [3, (1 << 40) + 5])
+def test_ternary_sampler_is_low_word_mod_3(seed):
+    N = 512
+    s = np.zeros(N, dtype=np.int64)
+    lib.or_sample_ternary(seed, N, pi64(s))
+    want = []
+    for i in range(N):
+        w = _draw_py(seed, i, 0, 1, 0)
+        want.append((w[0] | (w[1] << 32)) % 3 - 1)
+    assert [int(x) for x in s] == want
+    # keygen is that sampler
+    P = O.Params(64, 1)
+    assert [int(x) for x in O.keygen(P, seed)] == want[:64]
+
+
+@pytest.mark.parametrize("seed,obj", [(4, 2), ((7 << 33) + 1, 0)])
+def test_uniform_sampler_is_128_bit_block_mod_q(seed, obj):
+    N = 256
+    for li, q in enumerate(O.DEFAULT_PRIMES):
+        a = np.zeros(N, dtype=np.uint64)
+        lib.or_sample_uniform(seed, obj, li, q, N, p64(a))
+        want = []
+        for i in range(N):
+            w = _draw_py(seed, i, obj, 2, li)
+            want.append((w[0] | (w[1] << 32) | (w[2] << 64) | (w[3] << 96)) % q)
+        assert [int(x) for x in a] == want, li
+
+
+def test_gauss_inversion_at_every_table_boundary():
+    T = _gauss_cdt_sympy()
+    assert lib.or_gauss_from_draw(0) == -19
+    assert lib.or_gauss_from_draw((1 << 64) - 1) == 19
+    for j, tj in enumerate(T):
+        assert lib.or_gauss_from_draw(tj - 1) == -19 + j, j
+        assert lib.or_gauss_from_draw(tj) == -19 + j + 1, j
+
+
+@pytest.mark.parametrize("seed,obj", [(7, 0), (3, 5)])
+def test_gauss_sampler_is_cdt_inversion_of_low_word(seed, obj):
+    T = _gauss_cdt_sympy()
+    N = 512
+    e = np.zeros(N, dtype=np.int64)
+    lib.or_sample_gauss(seed, obj, N, pi64(e))
+    want = []
+    for i in range(N):
+        w = _draw_py(seed, i, obj, 3, 0)
+        u = w[0] | (w[1] << 32)
+        want.append(-19 + sum(1 for t in T if u >= t))
+    assert [int(x) for x in e] == want
+
+
+def test_encryption_draws_follow_the_sampler_readings():
+    """c1 of ciphertext j, prime l is the uniform map at counter (i, obj0 + j, 2, l)."""
+    N, L = 64, 3
+    P = O.Params(N, L)
+    s = O.keygen(P, 1)
+    m = S.uniform_plaintexts(2, N, 2)
+    ct = O.encrypt(P, s, m, 9, obj0=4)
+    for j in range(2):
+        for li, q in enumerate(P.q):
+            want = []
+            for i in range(N):
+                w = _draw_py(9, i, 4 + j, 2, li)
+                want.append((w[0] | (w[1] << 32) | (w[2] << 64) | (w[3] << 96)) % q)
+            assert [int(x) for x in ct[j, 1, li]] == want
 
 
 # ------------------------------------------------------------------ BFV scaling
@@ -305,8 +417,11 @@ def test_encryption_structure_small_n():
     s = O.keygen(P, 1)
     m = S.uniform_plaintexts(1, N, 2)
     ct = O.encrypt(P, s, m, 3)
-    e_ref = np.zeros(N, dtype=np.int64)
-    lib.or_sample_gauss(3, 0, N, pi64(e_ref))
+    T = _gauss_cdt_sympy()
+    e_ref = []
+    for i in range(N):
+        w = _draw_py(3, i, 0, 3, 0)
+        e_ref.append(-19 + sum(1 for t in T if (w[0] | (w[1] << 32)) >= t))
     for li, q in enumerate(P.q):
         c0 = ct[0, 0, li].astype(object)
         c1 = ct[0, 1, li].astype(object)
