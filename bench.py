@@ -1,12 +1,15 @@
-"""Benchmark: homomorphic matrix products (Algorithm 1) of one BERT-base layer.
+"""Benchmark: homomorphic matrix products (Algorithm 1) of one transformer encoder layer.
 
-One step = every linear product of one BERT-base encoder layer at sequence
-length 128 (Sec. 3.1.1): the four fully connected layers against resident
-NTT-form weights and, for each of the 12 heads, the two cross terms of Q K^T
-and of P V against the server's shares (encoded per step).  BFV N = 4096, two
-~50-bit primes, t = 2^37.  52 server-side Pi_MatMul calls, 956,301,312 plain
-multiply-accumulates per step.  Input ciphertexts are encrypted (GPU test
-client) before timing and stay resident; every call re-masks with a fresh seed.
+One step = every linear product of one encoder layer (Sec. 3.1.1): the four fully
+connected layers against resident NTT-form weights and, for each head, the two cross
+terms of Q K^T and of P V against the server's shares (encoded per step).  The default
+(headline) workload is one BERT-large layer at sequence length 512 with BFV N = 8192,
+three ~50-bit primes, t = 2^37: 68 server-side Pi_MatMul calls, 7,516,192,768 plain
+multiply-accumulates per step.  `--workload bert-base` runs one BERT-base layer at
+sequence 128 with N = 4096 and two primes instead (52 calls, 956,301,312 MACs); the
+default run also times that layer and reports it under "bert_base_layer".  Input
+ciphertexts are encrypted (GPU test client) before timing and stay resident; every
+call re-masks with a fresh seed.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -29,14 +32,24 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "HE-MatMul plaintext MACs/s"
 UNIT = "MAC/s"
-N_POLY, L_PRIMES = 4096, 2
-WORKLOAD = "bert-base layer linear products, seq 128 (QKV, attn-out, FFN1, FFN2 + 12 heads x 2 cross terms x {QK^T, PV})"
-# selectable with --workload; the default is the headline configuration
+# selectable with --workload; the default is the headline configuration (the largest that
+# fits one GPU)
 WORKLOADS = {
-    "bert-base": dict(N=N_POLY, L=L_PRIMES, model="BERT_BASE", desc=WORKLOAD, baseline_fc=("attn_out", "qkv")),
-    "bert-large-n8192": dict(N=8192, L=3, model="BERT_LARGE", baseline_fc=(),
+    "bert-large-n8192": dict(N=8192, L=3, model="BERT_LARGE", host_depth=3,
                              desc="bert-large layer linear products, seq 512, N=8192, L=3 (QKV, attn-out, FFN1, FFN2 "
                                   "+ 16 heads x 2 cross terms x {QK^T, PV})"),
+    "bert-base": dict(N=4096, L=2, model="BERT_BASE", host_depth=6,
+                      desc="bert-base layer linear products, seq 128 (QKV, attn-out, FFN1, FFN2 + 12 heads x 2 cross "
+                           "terms x {QK^T, PV})"),
+}
+DEFAULT_WORKLOAD = "bert-large-n8192"
+
+# Blockings (m_b, k_b, n_b) of the products the CPU oracle legs sample, keyed by (N, m, k, n):
+# the library cost model's choice for these shapes, written out so that the oracle legs
+# load no part of the CUDA library.
+ORACLE_BLOCKINGS = {
+    (4096, 128, 64, 128): (32, 8, 16), (4096, 128, 128, 64): (32, 16, 8), (4096, 64, 128, 128): (16, 16, 16),
+    (8192, 512, 64, 512): (64, 4, 32), (8192, 512, 512, 64): (64, 32, 4), (8192, 64, 512, 512): (8, 32, 32),
 }
 
 
@@ -51,16 +64,21 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the mixed-request leg (one multi-product launch vs one call per request)")
-    ap.add_argument("--serving-rates", default="100,400,800", help="Poisson arrival rates (requests/s)")
-    ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--serving-rates", default="50,100,400,800,1600,3200",
+                    help="Poisson arrival rates (requests/s); the highest saturate the per-request path")
+    ap.add_argument("--serving-requests", type=int, default=2000,
+                    help="requests per rate (at most 10 s of arrivals per rate)")
     ap.add_argument("--launch", default="multi", choices=["multi", "groups"],
                     help="multi: the whole layer as one multi-product launch per step; groups: one batched "
                          "launch per product shape")
-    ap.add_argument("--workload", default="bert-base", choices=sorted(WORKLOADS),
-                    help="bert-base: the headline layer (N=4096, L=2); bert-large-n8192: a BERT-large layer at seq "
-                         "512 with N=8192, L=3")
-    ap.add_argument("--host-depth", type=int, default=6,
-                    help="end-to-end leg: host-buffer steps in flight (streams with their own buffers)")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
+                    help="bert-large-n8192: the headline, one BERT-large layer at seq 512 with N=8192, L=3; "
+                         "bert-base: one BERT-base layer at seq 128 with N=4096, L=2")
+    ap.add_argument("--no-bert-base", action="store_true",
+                    help="skip the extra BERT-base layer (N=4096) timed beside the headline workload")
+    ap.add_argument("--host-depth", type=int, default=None,
+                    help="end-to-end leg: host-buffer steps in flight (streams with their own buffers); default 3 "
+                         "for the BERT-large layer, 6 for the BERT-base layer")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="1: replay each step as a captured CUDA graph (multi launch; mask seeds read from device "
                          "memory, fresh every step)")
@@ -389,19 +407,22 @@ class Layer:
 
 
 def kernel_source_hash():
-    """Fingerprint of the multiply-accumulate kernel's source: its configuration and body, the
-    headers it includes and the whole-layer launch's kernels (grid order) -- a DRAM-traffic
+    """Fingerprint of what sets the multiply-accumulate kernel's DRAM traffic: its
+    configuration and body, the headers it includes, the whole-layer launch's kernels (grid
+    order), the blocking choice and autotuner (capi.cu) and the workload shapes -- a traffic
     figure recorded for an older fingerprint is stale."""
     csrc = ROOT / "paper_2305_18396_gb300" / "csrc"
     h = hashlib.sha256((csrc / "mac.cuh").read_bytes())
-    for f in ("async.cuh", "he_common.cuh", "multi.cu"):
+    for f in ("async.cuh", "he_common.cuh", "multi.cu", "capi.cu"):
         h.update((csrc / f).read_bytes())
+    h.update((ROOT / "paper_2305_18396_gb300" / "workloads.py").read_bytes())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, launch):
-    """DRAM traffic per launch from the committed ncu summary, if it was taken on this source
-    and in this launch mode (per-group launches and the whole-layer launch differ in size)."""
+def recorded_traffic(kernel, launch, workload=DEFAULT_WORKLOAD):
+    """DRAM traffic per launch from the committed ncu summary, if it was taken on this source,
+    in this launch mode (per-group launches and the whole-layer launch differ in size) and on
+    this workload."""
     for f in (ROOT / "profiles").glob("*.md"):
         txt = f.read_text()
         m = re.search(r"^traffic_kernel:\s*(\S+)\s*$", txt, re.M)
@@ -409,8 +430,10 @@ def recorded_traffic(kernel, launch):
             continue
         src = re.search(r"^source_hash:\s*(\S+)\s*$", txt, re.M)
         mode = re.search(r"^traffic_launch:\s*(\S+)\s*$", txt, re.M)
+        wl = re.search(r"^traffic_workload:\s*(\S+)\s*$", txt, re.M)
         val = re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*$", txt, re.M)
-        if src and val and mode and src.group(1) == kernel_source_hash() and mode.group(1) == launch:
+        if src and val and mode and wl and src.group(1) == kernel_source_hash() and mode.group(1) == launch \
+                and wl.group(1) == workload:
             return float(val.group(1))
     return None
 
@@ -422,35 +445,48 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+# ------------------------------------------------------------------ workload identity
+
+
+def workload_config(args):
+    """The `config` object of the JSON line: what the workload is, identical for the GPU arm
+    and the reference arm (how the GPU arm ran it goes under "run")."""
+    from paper_2305_18396_gb300 import workloads
+
+    wl = WORKLOADS[args.workload]
+    prods = workloads.bert_layer_products(**getattr(workloads, wl["model"]))
+    return {"workload": wl["desc"], "N": wl["N"], "L": wl["L"], "log2_t": 37,
+            "products_per_step": sum(p.count for p in prods), "plain_macs_per_step": workloads.layer_macs(prods),
+            "output": "full ciphertexts" if args.full_c0 else
+            "c1 + c0 at the decoded coefficients only (Sec. 3.1.3, HE_DROP_C0)",
+            "l2": "inputs larger than L2: one step reads and writes several GB of ciphertexts and weights"}
+
+
 # ------------------------------------------------------------------ CPU oracle legs
 
 
-def oracle_sample(kind="baseline", workload="bert-base"):
-    """The oracle as it stands on a bounded sample of the layer: one head's four
-    attention cross products (+ the QKV and attention-output products for the baseline of
-    the default workload)."""
+def oracle_sample(workload):
+    """The oracle as it stands on a bounded sample of the layer: one head's four attention
+    cross products (Q K^T's two cross terms, P V's two), full Pi_MatMul each (encode, NTT,
+    multiply-accumulate, inverse NTT, mask).  Imports the oracle and the input generators
+    only: nothing of the CUDA library."""
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
-    import numpy as np  # noqa: F401
-
     import oracle as O
     from paper_2305_18396_gb300 import synthetic as S
     from paper_2305_18396_gb300 import workloads
-    from paper_2305_18396_gb300.binding import he_choose_blocking
 
     wl = WORKLOADS[workload]
     n_poly, l_primes = wl["N"], wl["L"]
     prods = [p for p in workloads.bert_layer_products(distinct_heads=1, **getattr(workloads, wl["model"]))]
     heads = [p for p in prods if p.share_weights]
     heads = heads + [heads[0]]  # qk_x1 has the shape of qk_x0
-    if kind == "baseline":
-        heads = heads + [p for p in prods if p.name in wl["baseline_fc"]]
     P = O.Params(n_poly, l_primes)
     s = O.keygen(P, S.SEED_KEY)
     jobs = []
     for i, p in enumerate(heads):
-        blk = he_choose_blocking(n_poly, l_primes, p.m, p.k, p.n, p.share_weights)
+        blk = ORACLE_BLOCKINGS[(n_poly, p.m, p.k, p.n)]
         X = S.uniform_share((p.m, p.k), 100 + i)
-        W = S.uniform_share((p.k, p.n), 200 + i) if p.share_weights else S.fixed_point_weights((p.k, p.n), 200 + i)
+        W = S.uniform_share((p.k, p.n), 200 + i)
         ct = O.encrypt(P, s, O.pack_input(X, blk, n_poly), 300 + i)
         jobs.append((p, blk, ct, W))
     return P, jobs, O
@@ -465,20 +501,25 @@ def run_oracle(P, jobs, O, seed):
     return macs, time.perf_counter() - t0
 
 
-def cpu_baseline(workload="bert-base"):
-    P, jobs, O = oracle_sample("baseline", workload)
-    macs, dt = run_oracle(P, jobs, O, 12345)
+SAMPLE_DESC = "one head's 4 attention cross products ({macs} plain MACs), full Pi_MatMul each on the host cores"
+
+
+def cpu_baseline(workload, min_s=10.0, max_reps=20):
+    """The same sample as the reference arm's step, repeated until at least min_s of CPU work."""
+    P, jobs, O = oracle_sample(workload)
+    macs, dt, reps = 0, 0.0, 0
+    while (dt < min_s and reps < max_reps) or reps == 0:
+        m, d = run_oracle(P, jobs, O, 12345 + reps)
+        macs, dt, reps = macs + m, dt + d, reps + 1
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": macs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one head's 4 attention cross products"
-                      f"{' + the QKV and attn-out products' if WORKLOADS[workload]['baseline_fc'] else ''} ({macs} plain MACs, "
-                      f"{dt:.1f} s), full Pi_MatMul (encode, NTT, MAC, INTT, mask) on the host cores"}
+            "sample": SAMPLE_DESC.format(macs=macs // reps) + f", {reps} passes in {dt:.1f} s"}
 
 
 def reference_arm(args, world, rank):
     if rank != 0:
         return
-    P, jobs, O = oracle_sample("reference", args.workload)
+    P, jobs, O = oracle_sample(args.workload)
     for w in range(args.warmup):
         run_oracle(P, jobs, O, w)
     tot_macs, tot_t, per = 0, 0.0, []
@@ -492,11 +533,9 @@ def reference_arm(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload]["desc"] + " -- CPU oracle sample",
-                       "N": WORKLOADS[args.workload]["N"], "L": WORKLOADS[args.workload]["L"], "log2_t": 37},
+            "config": workload_config(args),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"per step: one head's 4 attention cross products ({tot_macs // args.steps} "
-                                       "plain MACs), full Pi_MatMul on the host cores"},
+                             "sample": "per step: " + SAMPLE_DESC.format(macs=tot_macs // args.steps)},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "latency_ms": {"p50": statistics.median(per), "p99": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))]}}
     print(json.dumps(line), flush=True)
@@ -516,7 +555,7 @@ def serving_leg(B, ctx, args):
              ("base.ffn2", 3072, 768, 512), ("large.qkv", 1024, 3072, 512), ("large.out", 1024, 1024, 512),
              ("large.ffn1", 1024, 4096, 512), ("large.ffn2", 4096, 1024, 512)]
     models = SV.make_models(ctx, specs)
-    out = {"requests_per_rate": args.serving_requests,
+    out = {"requests_per_rate": f"min({args.serving_requests}, 10 s of arrivals), at least 100", "N": ctx.N,
            "mix": "BERT-base/large layer matrices (QKV, out, FFN1, FFN2), m log-uniform in [8, 512], Poisson arrivals",
            "resident_weight_gb": round(sum(m.pt.numel() for m in models) * 8 / 1e9, 2),
            "policy": "up to 2 launches in flight, a second one only while the first is estimated to end within 2 "
@@ -526,10 +565,11 @@ def serving_leg(B, ctx, args):
                      "budget for outputs + workspace; outputs released on completion", "rates": {}}
     for rate in [float(x) for x in args.serving_rates.split(",") if x]:
         res = {}
+        count = max(100, min(args.serving_requests, int(rate * 10)))  # at most ~10 s of arrivals per path
         for name, fn, kw in (("per_request", SV.run_per_request, {"keep_outputs": False}),
                              ("continuous_batching", SV.run_served,
                               {"slots": 2, "max_batch": 8, "keep_outputs": False})):
-            reqs = SV.make_requests(models, args.serving_requests, rate)
+            reqs = SV.make_requests(models, count, rate)
             st, _ = fn(ctx, models, reqs, **kw)
             res[name] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
         out["rates"][str(int(rate))] = res
@@ -544,18 +584,17 @@ BATCHED_MATRICES = [("base.qkv", 768, 2304), ("base.ffn2", 3072, 768), ("large.o
                     ("large.ffn1", 1024, 4096)]
 
 
-def batched_leg(B, ctx, flags, reps=5):
+def batched_leg(B, ctx, flags, reps=5, count=64):
     """Mixed requests of resident BERT-base / BERT-large layer matrices, sequence lengths
-    uniform in [16, 512]: 64 requests at N=4096 (32 at N=8192, the launch's product limit
-    halved for the larger ciphertexts), device-resident.  Times the whole set as one
-    he_matmul_multi launch against one he_matmul call per request on the same stream, and
-    checks that every request's output is the same bit for bit both ways."""
+    uniform in [16, 512]: 64 requests at the context's N, device-resident.  Times the whole
+    set as he_matmul_multi launches of at most 64 products against one he_matmul call per
+    request on the same stream, and checks that every request's output is the same bit for
+    bit both ways."""
     import numpy as np
     import torch
 
     from paper_2305_18396_gb300 import synthetic as S
 
-    count = 64 if ctx.N == 4096 else 32
     rng = np.random.default_rng(31 + ctx.N)
     sk = B.he_keygen(ctx, S.SEED_KEY)
     weights = {}
@@ -578,13 +617,14 @@ def batched_leg(B, ctx, flags, reps=5):
                           mask_seed=9000 + r))
         alone.append(ctx.empty(ow))
         macs += m * k * n
-    prods = B.make_products(items)
-    ws_multi = ctx.empty(B.he_multi_workspace_bytes(ctx, prods) // 8 + 1)
+    chunks = [B.make_products(items[i:i + 64]) for i in range(0, len(items), 64)]
+    ws_multi = ctx.empty(max(B.he_multi_workspace_bytes(ctx, arr) for arr in chunks) // 8 + 1)
     ws_one = ctx.empty(ws_words)
     stream = torch.cuda.current_stream()
 
     def multi():
-        B.he_matmul_multi(ctx, prods, ws_multi)
+        for arr in chunks:
+            B.he_matmul_multi(ctx, arr, ws_multi)
 
     def separate():
         for it, out in zip(items, alone):
@@ -608,12 +648,13 @@ def batched_leg(B, ctx, flags, reps=5):
     same = all(torch.equal(it["ct_out"], out) for it, out in zip(items, alone))
     ms_ = [it["m"] for it in items]
     out = {"what": f"{count} requests of mixed BERT-base/large layer matrices (QKV, FFN2, large attn-out, large "
-                   "FFN1), m uniform in [16, 512], inputs resident: one he_matmul_multi launch vs one he_matmul "
-                   "call per request",
+                   f"FFN1), m uniform in [16, 512], N={ctx.N}, inputs resident: {len(chunks)} he_matmul_multi "
+                   "launch(es) of at most 64 products vs one he_matmul call per request",
+           "N": ctx.N, "launches": len(chunks),
            "requests": count, "plain_macs": macs, "m_min": min(ms_), "m_max": max(ms_),
            "speedup": round(res["per_request"]["ms"] / res["one_launch"]["ms"], 3),
            "outputs_identical": bool(same), **res}
-    del items, alone, prods, ws_multi, ws_one, weights
+    del items, alone, chunks, ws_multi, ws_one, weights
     torch.cuda.empty_cache()
     return out
 
@@ -667,6 +708,46 @@ def share_products_leg(B, ctx, prods, mad_peak, reps=20):
 # ------------------------------------------------------------------ GPU arm
 
 
+def bert_base_leg(B, args, local, flags, steps=20):
+    """The BERT-base layer (seq 128, N=4096, L=2) timed beside the headline workload: same
+    launch mode (whole layer in one multi-product launch, CUDA-graph replay, tuned blockings
+    and radix), device-resident inputs, CUDA events over `steps` steps."""
+    import torch
+
+    from paper_2305_18396_gb300 import workloads
+
+    ctx = B.Context(4096, 2, device=local)
+    if args.ntt_radix == "tuned":
+        ctx.autotune_ntt_radix()
+    else:
+        ctx.set_ntt_radix(int(args.ntt_radix))
+    prods = workloads.bert_layer_products(**workloads.BERT_BASE)
+    use_graph = args.graph and args.launch == "multi"
+    layer = Layer(B, ctx, prods, 0, False, flags, tune=args.blocking == "tuned", multi=args.launch == "multi",
+                  graph=use_graph)
+    if use_graph:
+        layer.capture()
+    for w in range(3):
+        layer.step(w)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(steps):
+        layer.step(1000 + k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    B.he_device_status(ctx)
+    ms = e0.elapsed_time(e1) / steps
+    out = {"workload": WORKLOADS["bert-base"]["desc"], "N": 4096, "L": 2, "steps": steps,
+           "plain_macs_per_step": layer.macs, "ms_per_step": round(ms, 4), "value": layer.macs / (ms / 1e3),
+           "unit": UNIT}
+    del layer
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def gpu_arm(args, world, rank, local):
     import torch
 
@@ -685,8 +766,9 @@ def gpu_arm(args, world, rank, local):
     want_host = not args.no_e2e
     flags = B.HE_FLAGS_NONE if args.full_c0 else B.HE_DROP_C0
     use_graph = args.graph and args.launch == "multi"
+    host_depth = args.host_depth or wl["host_depth"]
     layer = Layer(B, ctx, prods, rank, want_host, flags, tune=args.blocking == "tuned", multi=args.launch == "multi",
-                  graph=use_graph, host_depth=args.host_depth)
+                  graph=use_graph, host_depth=host_depth)
     stream = torch.cuda.current_stream()
 
     mad_peak, mad_per_sm_clk = B.he_probe_mad_wide(ctx)
@@ -753,7 +835,7 @@ def gpu_arm(args, world, rank, local):
     else:
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(hbm_gbs, 1), "peak": pk["hbm_gbs"],
                     "unit": "GB/s", "frac": round(hbm_gbs / pk["hbm_gbs"], 4), "peak_source": pk_src}
-    roofline.update({"algorithmic_bytes_per_launch": bytes_per_launch, "traffic": recorded_traffic(dom, args.launch),
+    roofline.update({"algorithmic_bytes_per_launch": bytes_per_launch, "traffic": recorded_traffic(dom, args.launch, args.workload),
                      "kernels": kern,
                      "slot_macs_per_s": layer.slot_macs() * steps_prof / (stats["mac"]["total_ms"] / 1e3)
                      if "mac" in stats else None})
@@ -778,37 +860,39 @@ def gpu_arm(args, world, rank, local):
                "d2h_bytes_per_step": d2h, "steps": ksteps, "ms_per_step": dt * 1e3 / ksteps}
 
     share = share_products_leg(B, ctx, prods, mad_peak)
+    blks = {}
+    for c in layer.calls:
+        blks.setdefault(c["p"].name, list(c["blk"]))
+    layer_multi, n_calls = layer.multi, len(layer.calls)
     batched = batched_leg(B, ctx, flags) if world == 1 and not args.no_batched else None
 
     serving = None
     if world == 1 and not args.no_serving:
         serving = serving_leg(B, ctx, args)
+    base_layer = None
+    if world == 1 and args.workload != "bert-base" and not args.no_bert_base:
+        del layer
+        torch.cuda.empty_cache()
+        base_layer = bert_base_leg(B, args, local, flags)
     if rank != 0:
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
-    blks = {}
-    for c in layer.calls:
-        blks.setdefault(c["p"].name, list(c["blk"]))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": wl["desc"], "N": wl["N"], "L": wl["L"], "log2_t": 37,
-                   "products_per_step": layer.products,
-                   "launch_groups_per_step": 1 if layer.multi else len(layer.calls),
-                   "plain_macs_per_step": layer.macs,
-                   "output": "full ciphertexts" if args.full_c0 else
-                   "c1 + c0 at the decoded coefficients only (Sec. 3.1.3, HE_DROP_C0)",
-                   "blockings_mkn": blks, "blocking_choice": args.blocking, "launch": args.launch,
-                   "ntt_values_per_thread": 1 << ctx.ntt_radix, "ntt_radix_choice": args.ntt_radix,
-                   "ntt_radix_round_trip_ms": radix_ms,
-                   "cuda_graph": bool(use_graph), "kernel_source_hash": kernel_source_hash(), "parallelism": f"replicas x{world} (independent layers, no collective)",
-                   "l2": "inputs larger than L2: one step reads/writes ~3 GB of ciphertexts/weights"},
+        "config": workload_config(args),
+        "run": {"blockings_mkn": blks, "blocking_choice": args.blocking, "launch": args.launch,
+                "launch_groups_per_step": 1 if layer_multi else n_calls,
+                "ntt_values_per_thread": 1 << ctx.ntt_radix, "ntt_radix_choice": args.ntt_radix,
+                "ntt_radix_round_trip_ms": radix_ms, "cuda_graph": bool(use_graph),
+                "kernel_source_hash": kernel_source_hash(),
+                "parallelism": f"replicas x{world} (independent layers, no collective)"},
         "latency_ms": {"p50": statistics.median(per), "p99": sorted(per)[min(len(per) - 1, int(0.99 * len(per)))]},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "share_products": share,
-        "batched_requests": batched,
+        "batched_requests": batched, "bert_base_layer": base_layer,
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }

@@ -312,11 +312,14 @@ HE_API int he_multi_host_workspace_bytes(const he_ctx* ctx, uint32_t count, cons
  * reserved by another allocator (where cudaMalloc would fail, or would stall the
  * device while requests are in flight), or a host program that is not permitted to
  * manage device memory.  This entry point computes exactly what he_matmul computes
- * and allocates nothing: its scratch (the NTT of the input ciphertexts) is a fixed
- * device array of HE_NOALLOC_SCRATCH_BYTES inside the library, which every GPU
- * that loads the library keeps until the process exits.
- * - Products whose he_sizes().workspace_bytes exceeds HE_NOALLOC_SCRATCH_BYTES are
- *   rejected with HE_EINVAL before any GPU work.
+ * with the same flags (HE_FLAGS_NONE or HE_DROP_C0; ct_out then holds out_words or
+ * out_words_compact words) and allocates nothing: its scratch (the NTT of the input
+ * ciphertexts, and with HE_DROP_C0 the NTT-domain c0 of the outputs) is a fixed
+ * device array of HE_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that
+ * loads the library keeps until the process exits.
+ * - Products whose he_sizes().workspace_bytes (workspace_bytes_compact with
+ *   HE_DROP_C0) exceeds HE_NOALLOC_SCRATCH_BYTES are rejected with HE_EINVAL before
+ *   any GPU work; so is HE_ASYNC or any other flag.
  * - The first call on a device looks up the array's device address (with that
  *   device current); make that first call before any stream capture.
  * - All calls share the one array and it keeps the last call's contents (every word
@@ -334,6 +337,30 @@ HE_API int he_matmul_noalloc(he_ctx* ctx, const uint64_t* ct_in, const uint64_t*
  * coefficients, for he_decrypt (whose other coefficients are then meaningless). */
 HE_API int he_expand_compact(he_ctx* ctx, const uint64_t* ct_compact, uint32_t cnt, uint32_t k_b, uint64_t* ct_full,
                              void* stream);
+
+/* Ciphertexts on the wire between client and server (Algorithm 1: the client sends its
+ * encrypted share, the server returns the re-masked product; Sec. 3.1.3, "Reducing the
+ * communication cost": only c1 and the decoded c0 coefficients need to travel).  The
+ * wire format is the library's ciphertext layout in coefficient form, little-endian u64
+ * words: with k_b = 0, full ciphertexts [cnt][2][L][N]; with a power-of-two k_b (at most
+ * N), compact ciphertexts as written by HE_DROP_C0 for a product of that k_b, each
+ * [c0 at the decoded coefficients: L x N / k_b][c1: L x N].
+ *
+ * he_ct_export copies cnt ciphertexts from device memory `ct` (caller-owned) to
+ * host_buf (caller-owned, cnt x words per ciphertext) and returns once host_buf holds
+ * them (synchronizes `stream`).
+ *
+ * he_ct_import copies host_buf to device memory `ct` (caller-owned) and checks on the
+ * GPU that every word is a residue of its prime (below q_l); it synchronizes `stream`
+ * and returns HE_EINVAL naming the count and the first offending word (ciphertext,
+ * component, prime) if not -- `ct` then holds the rejected words and must not be used.
+ *
+ * Errors: HE_EINVAL (NULL ctx or buffer with cnt > 0, k_b neither 0 nor a power of two
+ * <= N, residue out of range), HE_ECUDA.  cnt = 0 does nothing. */
+HE_API int he_ct_export(he_ctx* ctx, const uint64_t* ct, uint32_t cnt, uint32_t k_b, uint64_t* host_buf,
+                        void* stream);
+HE_API int he_ct_import(he_ctx* ctx, const uint64_t* host_buf, uint32_t cnt, uint32_t k_b, uint64_t* ct,
+                        void* stream);
 
 /* Server's share pi_C^{-1}(s) of X W for the masks of he_matmul(mask_seed):
  * share[Lb m_b + l][I n_b + i] = s_{Lb nI + I}[l n_b k_b + i k_b + k_b - 1].

@@ -103,6 +103,8 @@ def _load():
         "he_matmul_multi_host": (ctypes.c_int, [P, u32, ctypes.POINTER(Product), u32, P, sz, P]),
         "he_multi_host_workspace_bytes": (ctypes.c_int, [P, u32, ctypes.POINTER(Product), ctypes.POINTER(sz)]),
         "he_expand_compact": (ctypes.c_int, [P, P, u32, u32, P, P]),
+        "he_ct_export": (ctypes.c_int, [P, P, u32, u32, P, P]),
+        "he_ct_import": (ctypes.c_int, [P, P, u32, u32, P, P]),
         "he_ntt_forward": (ctypes.c_int, [P, P, u32, P]),
         "he_ntt_inverse": (ctypes.c_int, [P, P, u32, P]),
         "he_poly_mul": (ctypes.c_int, [P, P, P, P, u32, P]),
@@ -385,11 +387,13 @@ HE_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 def he_matmul_noalloc(ctx, ct_in, pt, m, k, n, blk, mask_seed, ct_out, flags=HE_FLAGS_NONE, stream=None):
     """he_matmul without a workspace: for callers that cannot allocate device memory.
-    ct_out must be provided by the caller; the library's fixed scratch is used instead."""
+    ct_out (out_words, or out_words_compact with HE_DROP_C0) must be provided by the
+    caller; the library's fixed scratch is used instead."""
     si = ctx.sizes(m, k, n, blk)
+    ow, _ = _out_ws(si, flags)
     ctx._dev(ct_in, si["in_words"], "ct_in")
     ctx._dev(pt, si["pt_words"], "pt")
-    ctx._dev(ct_out, si["out_words"], "ct_out")
+    ctx._dev(ct_out, ow, "ct_out")
     _check(lib.he_matmul_noalloc(ctx.h, _ptr(ct_in), _ptr(pt), m, k, n, _blk(blk), mask_seed, flags, _ptr(ct_out),
                                  _stream(stream)))
     return ct_out
@@ -422,6 +426,39 @@ def he_expand_compact(ctx, ct_compact, cnt, k_b, ct_full=None, stream=None):
     ct_full = ctx.empty(words) if ct_full is None else ctx._dev(ct_full, words, "ct_full")
     _check(lib.he_expand_compact(ctx.h, _ptr(ct_compact), cnt, k_b, _ptr(ct_full), _stream(stream)))
     return ct_full
+
+
+def wire_words(ctx, cnt, k_b=0):
+    """Words of cnt ciphertexts in the wire format: full (k_b = 0) or compact (HE_DROP_C0 of a
+    product with this k_b)."""
+    return cnt * ctx.L * ((ctx.N // k_b if k_b else ctx.N) + ctx.N)
+
+
+def _host(t, words, name):
+    if t.device.type != "cpu" or not t.is_contiguous() or t.dtype not in (torch.int64, torch.uint64):
+        raise ValueError(f"{name} must be a contiguous int64/uint64 CPU tensor")
+    if t.numel() < words:
+        raise ValueError(f"{name} needs at least {words} words, has {t.numel()}")
+    return t
+
+
+def he_ct_export(ctx, ct, cnt, k_b=0, host_buf=None, stream=None):
+    """Device ciphertexts -> host wire format (a CPU tensor; pinned if host_buf is None)."""
+    words = wire_words(ctx, cnt, k_b)
+    ctx._dev(ct, words, "ct")
+    host_buf = torch.empty(words, dtype=torch.int64).pin_memory() if host_buf is None else \
+        _host(host_buf, words, "host_buf")
+    _check(lib.he_ct_export(ctx.h, _ptr(ct), cnt, k_b, _ptr(host_buf), _stream(stream)))
+    return host_buf
+
+
+def he_ct_import(ctx, host_buf, cnt, k_b=0, ct=None, stream=None):
+    """Host wire format -> device ciphertexts, every word checked to be below its prime."""
+    words = wire_words(ctx, cnt, k_b)
+    _host(host_buf, words, "host_buf")
+    ct = ctx.empty(words) if ct is None else ctx._dev(ct, words, "ct")
+    _check(lib.he_ct_import(ctx.h, _ptr(host_buf), cnt, k_b, _ptr(ct), _stream(stream)))
+    return ct
 
 
 def he_matmul_batch_host(ctx, ct_in_host, pt, m, k, n, blk, batch, mask_seed, ct_out_host, workspace,

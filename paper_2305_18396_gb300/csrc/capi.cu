@@ -122,12 +122,12 @@ struct ProfRec {
 
 enum Kind {
   KNttFwd, KNttInv, KPolyMul, KKeygen, KEncrypt, KDecrypt, KPack, KUnpack, KUnmask, KEncode, KMac, KInttMask, KInttC0,
-  KExpand, KProbe, KShare, KInvC0, KCount
+  KExpand, KProbe, KShare, KInvC0, KCheck, KCount
 };
 static const char* kKindNames[KCount] = {"ntt_forward", "ntt_inverse", "poly_mul", "keygen", "encrypt",
                                          "decrypt", "pack", "unpack", "unmask", "encode_weights",
                                          "mac", "intt_mask", "intt_c0_targets", "expand_compact", "probe",
-                                         "share_matmul", "intt_c1_c0"};
+                                         "share_matmul", "intt_c1_c0", "check_residues"};
 
 struct he_ctx {
   int device = 0;
@@ -135,6 +135,7 @@ struct he_ctx {
   u64 psi[he::kMaxPrimes] = {};
   u64* d_tables = nullptr;
   int* d_err = nullptr;  // set by kernels whose bounded waits expired
+  u64* d_bad = nullptr;  // he_ct_import: count and first index of residues out of range
   std::atomic<uint64_t> launches{0};
   bool prof = false;
   std::vector<ProfRec> recs;
@@ -283,8 +284,10 @@ int he_params_init(he_ctx** out, uint32_t N, uint32_t L, const uint64_t* q, uint
   }
   e = cudaMalloc(&c->d_tables, host.size() * sizeof(u64));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_bad, 2 * sizeof(u64));
   if (e != cudaSuccess) {
     if (c->d_tables) cudaFree(c->d_tables);
+    if (c->d_err) cudaFree(c->d_err);
     delete c;
     return fail(HE_ENOMEM, "cudaMalloc of context tables failed");
   }
@@ -295,6 +298,7 @@ int he_params_init(he_ctx** out, uint32_t N, uint32_t L, const uint64_t* q, uint
   if (e != cudaSuccess) {
     cudaFree(c->d_tables);
     cudaFree(c->d_err);
+    cudaFree(c->d_bad);
     delete c;
     return cuda_fail(e, "table upload / kernel configuration");
   }
@@ -319,6 +323,7 @@ int he_ctx_free(he_ctx* c) {
   for (auto e : c->pool) cudaEventDestroy(e);
   if (c->d_tables) cudaFree(c->d_tables);
   if (c->d_err) cudaFree(c->d_err);
+  if (c->d_bad) cudaFree(c->d_bad);
   delete c;
   return HE_OK;
 }
@@ -850,10 +855,10 @@ int he_matmul_noalloc(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint
   if (int r = matmul_checks(c, m, k, n, blk, flags, &si)) return r;
   if (!m || !k || !n) return HE_OK;
   if (!ct_in || !pt || !ct_out) return fail(HE_EINVAL, "NULL buffer");
-  if (flags != HE_FLAGS_NONE) return fail(HE_EINVAL, "he_matmul_noalloc takes no flags");
-  if (si.workspace_bytes > HE_NOALLOC_SCRATCH_BYTES)
-    return fail(HE_EINVAL, "product needs " + std::to_string(si.workspace_bytes) +
-                               " bytes of scratch; he_matmul_noalloc has " +
+  if (flags & HE_ASYNC) return fail(HE_EINVAL, "HE_ASYNC applies to he_matmul_host only");
+  const u64 need = (flags & HE_DROP_C0) ? si.workspace_bytes_compact : si.workspace_bytes;
+  if (need > HE_NOALLOC_SCRATCH_BYTES)
+    return fail(HE_EINVAL, "product needs " + std::to_string(need) + " bytes of scratch; he_matmul_noalloc has " +
                                std::to_string((size_t)HE_NOALLOC_SCRATCH_BYTES) + " (use he_matmul)");
   if (int r = set_device(c)) return r;
   void* scratch = nullptr;
@@ -1048,6 +1053,60 @@ int he_expand_compact(he_ctx* c, const uint64_t* ct_compact, uint32_t cnt, uint3
   return launch(c, KExpand, (cudaStream_t)stream, "expand_compact", [&] {
     return he::launch_expand_compact(c->C, ct_compact, cnt, log2u(k_b), ct_full, (cudaStream_t)stream);
   });
+}
+
+// Words of cnt wire-format ciphertexts: full (k_b = 0) or compact (HE_DROP_C0 output of
+// a product with this power-of-two k_b); logkb receives log2 k_b (0 for full).
+static int wire_words(const he_ctx* c, uint32_t cnt, uint32_t k_b, u64* words, u32* logkb) {
+  if (k_b && !pow2(k_b)) return fail(HE_EINVAL, "k_b must be 0 (full ciphertexts) or a power of two");
+  if (k_b > c->C.N) return fail(HE_EINVAL, "k_b must be at most N");
+  *logkb = k_b ? log2u(k_b) : 0;
+  *words = (u64)cnt * c->C.L * ((u64)(c->C.N >> *logkb) + c->C.N);
+  return HE_OK;
+}
+
+int he_ct_export(he_ctx* c, const uint64_t* ct, uint32_t cnt, uint32_t k_b, uint64_t* host_buf, void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  u64 words;
+  u32 logkb;
+  if (int r = wire_words(c, cnt, k_b, &words, &logkb)) return r;
+  if (!words) return HE_OK;
+  if (!ct || !host_buf) return fail(HE_EINVAL, "NULL buffer");
+  if (int r = set_device(c)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(host_buf, ct, words * sizeof(u64), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? HE_OK : cuda_fail(e, "ct_export: copy to host");
+}
+
+int he_ct_import(he_ctx* c, const uint64_t* host_buf, uint32_t cnt, uint32_t k_b, uint64_t* ct, void* stream) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  u64 words;
+  u32 logkb;
+  if (int r = wire_words(c, cnt, k_b, &words, &logkb)) return r;
+  if (!words) return HE_OK;
+  if (!ct || !host_buf) return fail(HE_EINVAL, "NULL buffer");
+  if (int r = set_device(c)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  u64 bad[2] = {0, ~0ull};
+  cudaError_t e = cudaMemcpyAsync(ct, host_buf, words * sizeof(u64), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_bad, bad, sizeof(bad), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ct_import: copy to device");
+  int r = launch(c, KCheck, st, "ct_import: residue check",
+                 [&] { return he::launch_check_residues(c->C, ct, cnt, logkb, c->d_bad, st); });
+  if (r) return r;
+  e = cudaMemcpyAsync(bad, c->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "ct_import: residue check readback");
+  if (bad[0]) {
+    const u64 N = c->C.N, L = c->C.L, Nc = N >> logkb, per = L * (Nc + N), w = bad[1] % per;
+    const bool c0 = w < L * Nc;
+    const u64 l = c0 ? w / Nc : (w - L * Nc) / N;
+    return fail(HE_EINVAL, std::to_string(bad[0]) + " word(s) not below their prime; first at word " +
+                               std::to_string(bad[1]) + " (ciphertext " + std::to_string(bad[1] / per) +
+                               (c0 ? ", c0" : ", c1") + ", prime " + std::to_string(l) + ")");
+  }
+  return HE_OK;
 }
 
 int he_ntt_forward(he_ctx* c, uint64_t* polys, uint32_t cnt, void* stream) {

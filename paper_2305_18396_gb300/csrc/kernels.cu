@@ -8,6 +8,7 @@
 // plus the test client (keygen / encrypt / decrypt / pack / unpack) and the
 // server's unmask.  The polynomial product is NTT + slot-wise product + inverse
 // NTT (footnote of Sec. 3.1.3).
+#include <algorithm>
 #include <mutex>
 
 #include "async.cuh"
@@ -730,6 +731,31 @@ __global__ void k_expand_compact(const u64* src, u64 cnt, u32 logkb, u64* dst, c
 cudaError_t launch_expand_compact(const Consts& C, const u64* src, u64 cnt, u32 logkb, u64* dst, cudaStream_t st) {
   const u64 total = cnt * 2 * C.L * C.N;
   if (total) k_expand_compact<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(src, cnt, logkb, dst, C);
+  return cudaGetLastError();
+}
+
+// Wire-format check of he_ct_import: counts the words of cnt ciphertexts that are not
+// below their prime and keeps the index of the first one (bad[0], bad[1]).  Per
+// ciphertext: c0 with N >> logkb words per prime (all N for full ciphertexts, logkb = 0),
+// then c1 with N words per prime.
+__global__ void k_check_residues(const u64* ct, u64 cnt, u32 logkb, u64* bad, const __grid_constant__ Consts C) {
+  const u64 N = C.N, L = C.L, Nc = N >> logkb, per = L * (Nc + N), total = cnt * per;
+  for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (u64)gridDim.x * blockDim.x) {
+    const u64 w = idx % per;
+    const u32 l = (u32)(w < L * Nc ? w / Nc : (w - L * Nc) / N);
+    if (ct[idx] >= C.p[l].q) {
+      atomicAdd((unsigned long long*)bad, 1ull);
+      atomicMin((unsigned long long*)bad + 1, (unsigned long long)idx);
+    }
+  }
+}
+
+cudaError_t launch_check_residues(const Consts& C, const u64* ct, u64 cnt, u32 logkb, u64* bad, cudaStream_t st) {
+  const u64 total = cnt * C.L * ((u64)(C.N >> logkb) + C.N);
+  if (total) {
+    const u64 blocks = std::min<u64>((total + 255) / 256, 152ull * 16);
+    k_check_residues<<<(unsigned)blocks, 256, 0, st>>>(ct, cnt, logkb, bad, C);
+  }
   return cudaGetLastError();
 }
 

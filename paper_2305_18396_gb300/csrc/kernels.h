@@ -52,6 +52,10 @@ cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out0
 // base + g * ct_stride), and the pruned inverse NTT + mask of c0 at the coefficients
 // e = i k_b + k_b - 1 only (NTT-domain c0 of ciphertext g at src + g L N).
 cudaError_t launch_intt_c1(const Consts& C, u64* base, u64 ct_stride, u64 cts, cudaStream_t st);
+// Counts the words of cnt wire-format ciphertexts (c0 with N >> logkb words per prime, then
+// c1) not below their prime into bad[0] and the first such index into bad[1] (the caller
+// sets bad[0] = 0 and bad[1] = ~0 first).
+cudaError_t launch_check_residues(const Consts& C, const u64* ct, u64 cnt, u32 logkb, u64* bad, cudaStream_t st);
 // Compact ciphertexts -> full ciphertexts with zero c0 outside the kept coefficients.
 cudaError_t launch_expand_compact(const Consts& C, const u64* src, u64 cnt, u32 logkb, u64* dst, cudaStream_t st);
 cudaError_t launch_intt_c0_targets(const Consts& C, const u64* src, u64* dst, u64 ct_stride, u64 out_cts, u32 batch,

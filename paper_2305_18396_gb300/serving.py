@@ -24,7 +24,12 @@ form; requests arrive over time and are
   (the highest when the device is idle): the oldest launch keeps the SMs it can fill,
   later launches take the SMs it leaves idle (its tail, its small grids); each launch
   stream keeps its workspace between launches;
-* completed when their launch's event fires (latency = completion - arrival);
+* completed when their launch's event fires (latency = completion - arrival), after
+  the context's error flag is read: a kernel whose bounded wait for its data expired
+  leaves invalid outputs, and the flag (one per context) cannot tell which launch set
+  it, so every launch that may have set it -- the ones that completed and the ones
+  still in flight -- is marked failed and its requests are reported as failed, not
+  done;
 * withdrawn by `Server.cancel` (a client that went away): a queued or admitted request
   leaves at once and frees its share of the budget; one already launched cannot be
   taken back from the GPU, so its output is dropped when its launch completes.
@@ -70,12 +75,18 @@ class Request:
     footprint: int = 0
     est: float = 0.0  # estimated device seconds inside a multi-product launch
     cancelled: bool = False
+    failed: bool = False  # its launch hit a device error: no valid output
 
 
 # Device-time estimate of one product inside a multi-product launch: a fixed part per
-# product plus its plaintext MACs at the rate large BERT-shaped products reach alone.
+# product plus its plaintext MACs at the rate large BERT-shaped products reach alone at
+# the ring dimension (N = 8192 carries three primes and twice the slots per ciphertext).
 EST_FIXED_S = 100e-6
-EST_MACS_PER_S = 4.0e11
+EST_MACS_PER_S = {4096: 4.0e11, 8192: 2.0e11}
+
+
+def est_rate(N):
+    return EST_MACS_PER_S.get(N, 4.0e11 * 4096 / max(N, 1))
 
 
 @dataclass(order=True)
@@ -87,6 +98,28 @@ class _InFlight:
     reqs: list = field(compare=False)
     ws: torch.Tensor = field(compare=False)
     stream: object = field(compare=False)
+    failed: bool = field(default=False, compare=False)
+
+
+def mark_failed(finished, inflight, device_error):
+    """After reading the context's error flag at the completion of `finished` launches:
+    with an error, every launch that may have set it -- those finished and those still
+    `inflight` -- is marked failed (the flag is one per context)."""
+    if device_error:
+        for f in list(finished) + list(inflight):
+            f.failed = True
+
+
+def device_error(ctx, stream):
+    """True if a kernel of the context gave up a bounded wait since the last check
+    (he_device_status reads and clears the flag; `stream` has completed its work)."""
+    try:
+        B.he_device_status(ctx, stream)
+    except B.HEError as e:
+        if e.code == B.HE_ETIMEOUT:
+            return True
+        raise
+    return False
 
 
 def request_footprint(ctx, model, m, flags):
@@ -165,6 +198,7 @@ class Server:
         self.streams = [[torch.cuda.Stream(device=ctx.device, priority=p) for _ in range(slots)] for p in levels]
         self.alloc_stream = torch.cuda.current_stream(ctx.device)
         self.queue, self.admitted, self.inflight, self.done, self.cancelled = [], [], [], [], []
+        self.failed = []
         self.in_use = 0
         self.launches = 0
         self._sizes = {}  # (matrix, m) -> he_sizes
@@ -179,7 +213,7 @@ class Server:
     def submit(self, req):
         mm = self.models[req.model]
         req.footprint = request_footprint(self.ctx, mm, req.m, self.flags)
-        req.est = EST_FIXED_S + req.m * mm.k * mm.n / EST_MACS_PER_S
+        req.est = EST_FIXED_S + req.m * mm.k * mm.n / est_rate(self.ctx.N)
         if req.footprint > self.budget:
             raise ValueError(f"request {req.rid} needs {req.footprint} bytes, more than the whole budget")
         self.queue.append(req)
@@ -257,18 +291,22 @@ class Server:
         self.launches += 1
 
     def _poll(self, now):
-        still = []
+        finished, still = [], []
         for f in self.inflight:
-            if f.event.query():
-                for r in f.reqs:
-                    r.done = now
-                    self.in_use -= r.footprint
-                    if not self.keep or r.cancelled:
-                        r.out = None
-                    (self.cancelled if r.cancelled else self.done).append(r)
-            else:
-                still.append(f)
+            (finished if f.event.query() else still).append(f)
         self.inflight = still
+        if not finished:
+            return
+        mark_failed(finished, still, device_error(self.ctx, finished[0].stream))
+        for f in finished:
+            for r in f.reqs:
+                r.done = now
+                self.in_use -= r.footprint
+                if f.failed:
+                    r.failed = True
+                if not self.keep or r.cancelled or r.failed:
+                    r.out = None
+                (self.cancelled if r.cancelled else self.failed if r.failed else self.done).append(r)
 
     def pump(self, now):
         self._poll(now)
@@ -309,6 +347,9 @@ def make_requests(models, count, rate, seed=6, m_lo=8, m_hi=512):
 
 
 def _stats(reqs, models, wall):
+    if not reqs:
+        return {"requests": 0, "throughput_req_s": 0.0, "plain_macs_per_s": 0.0, "p50_ms": math.nan,
+                "p99_ms": math.nan, "mean_ms": math.nan}
     lat = np.array([(r.done - r.arrival) * 1e3 for r in reqs])
     macs = sum(r.m * models[r.model].k * models[r.model].n for r in reqs)
     return {"requests": len(reqs), "throughput_req_s": len(reqs) / wall, "plain_macs_per_s": macs / wall,
@@ -334,6 +375,7 @@ def run_served(ctx, models, requests, **kw):
     wall = time.perf_counter() - t0
     st = _stats(srv.done, {mm.name: mm for mm in models}, wall)
     st["launches"] = srv.launches
+    st["failed"] = len(srv.failed)
     return st, srv.done
 
 
@@ -354,9 +396,12 @@ def run_per_request(ctx, models, requests, flags=B.HE_DROP_C0, keep_outputs=True
                                 stream=stream)
         stream.synchronize()
         r.done = time.perf_counter() - t0
-        if not keep_outputs:
+        r.failed = device_error(ctx, stream)
+        if not keep_outputs or r.failed:
             r.out = None
     wall = time.perf_counter() - t0
-    st = _stats(pending, by, wall)
+    ok = [r for r in pending if not r.failed]
+    st = _stats(ok, by, wall)
     st["launches"] = len(pending)
-    return st, pending
+    st["failed"] = len(pending) - len(ok)
+    return st, ok

@@ -14,10 +14,11 @@ def test_recorded_traffic_needs_matching_source_and_launch(tmp_path, monkeypatch
     monkeypatch.setattr(bench, "ROOT", tmp_path)
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc123")
     _write(tmp_path, "a.md", "notes\n\ntraffic_kernel: mac\ntraffic_launch: multi\nsource_hash: abc123\n"
-                             "traffic_bytes_per_launch: 4699534194\n")
+                             "traffic_workload: bert-large-n8192\ntraffic_bytes_per_launch: 4699534194\n")
     _write(tmp_path, "b.md", "traffic_kernel: mac\ntraffic_launch: groups\nsource_hash: old999\n"
-                             "traffic_bytes_per_launch: 1\n")
+                             "traffic_workload: bert-large-n8192\ntraffic_bytes_per_launch: 1\n")
     assert bench.recorded_traffic("mac", "multi") == 4699534194.0
+    assert bench.recorded_traffic("mac", "multi", "bert-base") is None  # captured on another workload
     assert bench.recorded_traffic("mac", "groups") is None  # captured on another source
     assert bench.recorded_traffic("ntt", "multi") is None   # no record for that kernel
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "changed")
@@ -25,8 +26,8 @@ def test_recorded_traffic_needs_matching_source_and_launch(tmp_path, monkeypatch
 
 
 def test_committed_traffic_record_is_well_formed():
-    """The committed summary names a kernel, a launch mode, a 16-hex-digit fingerprint and a
-    byte count (whether it matches the current source is the bench's business)."""
+    """A committed summary names a kernel, a launch mode, a workload, a 16-hex-digit fingerprint
+    and a byte count (whether it matches the current source is the bench's business)."""
     import re
 
     recs = [p for p in (bench.ROOT / "profiles").glob("*.md") if "traffic_kernel:" in p.read_text()]
@@ -35,6 +36,7 @@ def test_committed_traffic_record_is_well_formed():
         t = p.read_text()
         assert re.search(r"^source_hash: [0-9a-f]{16}$", t, re.M), p
         assert re.search(r"^traffic_launch: (multi|groups)$", t, re.M), p
+        assert re.search(r"^traffic_workload: (%s)$" % "|".join(bench.WORKLOADS), t, re.M), p
         assert float(re.search(r"^traffic_bytes_per_launch: ([0-9.eE+]+)$", t, re.M).group(1)) > 0
 
 

@@ -100,3 +100,12 @@ def test_binding_refuses_missing_library(tmp_path, monkeypatch):
         sys.modules.pop("paper_2305_18396_gb300.binding", None)
         if saved is not None:
             sys.modules["paper_2305_18396_gb300.binding"] = saved
+
+
+def test_wire_format_calls_reject_a_null_context_without_gpu(B):
+    import ctypes
+
+    buf = (ctypes.c_uint64 * 4)()
+    for fn in (B.lib.he_ct_export, B.lib.he_ct_import):
+        assert fn(None, buf, 1, 0, buf, None) == B.HE_EINVAL
+        assert "ctx" in B.lib.he_last_error().decode()

@@ -63,6 +63,12 @@ def check_sampled(P, s, X, W, m, k, n, blk, mask_seed, rows, sel, got):
     """got: [len(sel)][2][L][N] from the device.  Bit-exact vs the oracle, then decrypt."""
     want = O.matmul(P, rows, W, m, k, n, blk, mask_seed, sel=sel)
     assert np.array_equal(got, want)
+    check_decrypts(P, s, X, W, n, blk, mask_seed, sel, want)
+
+
+def check_decrypts(P, s, X, W, n, blk, mask_seed, sel, want):
+    """The oracle's outputs `want` of ciphertexts `sel` decrypt with a positive noise budget,
+    and with the server's mask give the blocks of X W mod t."""
     dec, budget = O.decrypt(P, s, want)
     assert (budget > 0).all()
     m_b, k_b, n_b = blk

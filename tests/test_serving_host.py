@@ -101,11 +101,12 @@ def _server_state():
     for i, r in enumerate(running):
         r.rid, r.footprint, r.out = 20 + i, 100, object()
     srv.inflight = [SV._InFlight(0.0, 1e-3, 0, _Event(False), running, None, None)]
-    srv.done, srv.cancelled, srv.in_use, srv.keep = [], [], 400, True
+    srv.done, srv.cancelled, srv.failed, srv.in_use, srv.keep, srv.ctx = [], [], [], 400, True, None
     return srv
 
 
-def test_cancel_queued_admitted_and_launched_requests():
+def test_cancel_queued_admitted_and_launched_requests(monkeypatch):
+    monkeypatch.setattr(SV.B, "he_device_status", lambda ctx, stream=None: None)  # no device error
     srv = _server_state()
     assert srv.cancel(1) == "queued" and [r.rid for r in srv.queue] == [0] and srv.in_use == 400
     assert srv.cancel(11) == "admitted" and [r.rid for r in srv.admitted] == [10] and srv.in_use == 300
@@ -119,3 +120,51 @@ def test_cancel_queued_admitted_and_launched_requests():
     assert not srv.inflight and srv.in_use == 100
     assert [r.rid for r in srv.done] == [20] and srv.done[0].out is not None
     assert [r.rid for r in srv.cancelled] == [1, 11, 21] and srv.cancelled[-1].out is None
+
+
+
+def _launch(start, rids, done):
+    reqs_ = [SV.Request(rid=i, model="x", m=1, arrival=0.0, mask_seed=i, footprint=10) for i in rids]
+    return SV._InFlight(start, 1e-3, 0, _Event(done), reqs_, None, None)
+
+
+def _bare_server(inflight):
+    srv = object.__new__(SV.Server)  # only the completion logic: no device, no streams
+    srv.ctx, srv.keep = None, True
+    srv.inflight, srv.done, srv.cancelled, srv.failed = inflight, [], [], []
+    srv.in_use = sum(r.footprint for f in inflight for r in f.reqs)
+    return srv
+
+
+def test_poll_reports_requests_of_a_launch_with_a_device_error_as_failed(monkeypatch):
+    """The bounded wait of a kernel expired (the context's flag is set): the finished launch and
+    the one still in flight (either may have set the flag) report failed requests, none done."""
+    calls = []
+
+    def status(ctx, stream=None):
+        calls.append(stream)
+        if len(calls) == 1:
+            raise SV.B.HEError(SV.B.HE_ETIMEOUT, "bounded wait expired")
+
+    monkeypatch.setattr(SV.B, "he_device_status", status)
+    a, b = _launch(0.0, [0, 1], True), _launch(0.1, [2], False)
+    srv = _bare_server([a, b])
+    srv._poll(1.0)
+    assert [r.rid for r in srv.failed] == [0, 1] and not srv.done and srv.inflight == [b]
+    assert all(r.out is None and r.failed for r in a.reqs) and b.failed
+    b.event.done = True
+    srv._poll(2.0)  # the flag is clear now, but b was in flight when it was set
+    assert [r.rid for r in srv.failed] == [0, 1, 2] and not srv.done and srv.in_use == 0
+    c = _launch(2.5, [3], True)
+    srv.inflight = [c]
+    srv.in_use += 10
+    srv._poll(3.0)
+    assert [r.rid for r in srv.done] == [3] and not c.failed
+
+
+def test_mark_failed_without_error_marks_nothing():
+    a, b = _launch(0.0, [0], True), _launch(0.0, [1], False)
+    SV.mark_failed([a], [b], False)
+    assert not a.failed and not b.failed
+    SV.mark_failed([a], [b], True)
+    assert a.failed and b.failed

@@ -60,6 +60,21 @@ def test_noalloc_matches_matmul_on_consecutive_calls(setup):
         assert np.array_equal(second, ref)
 
 
+def test_noalloc_compact_output_through_the_binding(setup):
+    """HE_DROP_C0 through the Python wrapper: the same words as he_matmul with that flag, on
+    two calls in a row."""
+    B, ctx, sk = setup
+    m, k, n = 64, 256, 192
+    blk, ct, pt = _inputs(B, ctx, sk, m, k, n, 70)
+    si = ctx.sizes(m, k, n, blk)
+    assert si["workspace_bytes_compact"] <= B.HE_NOALLOC_SCRATCH_BYTES
+    ref = to_np(B.he_matmul(ctx, ct, pt, m, k, n, blk, 7, flags=B.HE_DROP_C0))
+    for _ in range(2):
+        out = ctx.empty(si["out_words_compact"])
+        B.he_matmul_noalloc(ctx, ct, pt, m, k, n, blk, 7, out, flags=B.HE_DROP_C0)
+        assert np.array_equal(to_np(out), ref)
+
+
 def test_noalloc_rejects_products_beyond_its_scratch(setup):
     B, ctx, sk = setup
     m, k, n = 128, 768, 2304  # the QKV product needs ~50 MB of scratch
