@@ -84,6 +84,6 @@ def test_import_rejects_words_not_below_their_prime(B):
     with pytest.raises(B.HEError) as e:
         B.he_ct_import(ctx, _host(comp), 1, kb)
     assert "ciphertext 0, c0, prime 1" in str(e.value)
-    with pytest.raises(B.HEError):
-        B.he_ct_import(ctx, _host(comp), 1, 3)  # k_b not a power of two
+    rc = B.lib.he_ct_import(ctx.h, B._ptr(_host(comp)), 1, 3, B._ptr(ctx.empty(comp.size)), B._stream(None))
+    assert rc == B.HE_EINVAL and "power of two" in B.lib.he_last_error().decode()  # k_b = 3
     ctx.close()
