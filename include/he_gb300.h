@@ -448,6 +448,25 @@ HE_API int he_device_status(he_ctx* ctx, void* stream);
 HE_API int he_probe_mad_wide(he_ctx* ctx, uint64_t* scratch, size_t scratch_words, double* ops_per_s,
                              double* per_sm_per_clock, void* stream);
 
+/* Tensor-core rate probe for roofline reporting (the paper has no counterpart).  kind 0:
+ * dense tcgen05 MMAs with bf16 operands and f32 accumulation (kind::f16; M = 128, N = 256,
+ * K = 16, operands in shared memory, one issuing thread per block, two blocks per SM on
+ * every SM).  kind 1: warp-level mma.sync m16n8k32 with signed 8-bit operands and s32
+ * accumulation -- the only 8-bit integer tensor instruction sm_103a offers (tcgen05.mma
+ * kind::i8 is not supported for this target).  These are the two exact routes for
+ * splitting the slot-wise multiply-accumulate (Algorithm 1 step 3) into small integer
+ * limbs.  Returns the achieved rate in operations (2 per multiply-add) per second.
+ * scratch: device, >= 4 x (number of SMs) words.  Synchronizes the stream.  A bounded wait
+ * that expires is reported by he_device_status. */
+HE_API int he_probe_tensor(he_ctx* ctx, uint32_t kind, double* ops_per_s, uint32_t* scratch, size_t scratch_words,
+                           void* stream);
+
+/* Test hook: D = A B^T on the tcgen05 tensor cores through the library's shared-memory and
+ * instruction descriptor encodings.  A: device, 128 x k bf16; B: device, n x k bf16
+ * (row-major); D: device, 128 x n f32.  n a multiple of 16 in [16, 256]; k a positive
+ * multiple of 16 with (128 + n) x k x 2 <= 200 KB.  Errors: HE_EINVAL, HE_ECUDA. */
+HE_API int he_test_tc_gemm(he_ctx* ctx, uint32_t n, uint32_t k, const void* A, const void* B, void* D, void* stream);
+
 /* Number of kernels this context has launched since creation. */
 HE_API int he_launch_count(const he_ctx* ctx, uint64_t* out);
 

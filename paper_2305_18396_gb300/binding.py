@@ -115,6 +115,8 @@ def _load():
         "he_device_status": (ctypes.c_int, [P, P]),
         "he_test_wait_timeout": (ctypes.c_int, [P, u32, P]),
         "he_probe_mad_wide": (ctypes.c_int, [P, P, sz, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P]),
+        "he_probe_tensor": (ctypes.c_int, [P, u32, ctypes.POINTER(ctypes.c_double), P, sz, P]),
+        "he_test_tc_gemm": (ctypes.c_int, [P, u32, u32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(so, name)
@@ -572,6 +574,28 @@ def he_probe_mad_wide(ctx, stream=None):
     _check(lib.he_probe_mad_wide(ctx.h, _ptr(scratch), scratch.numel(), ctypes.byref(ops), ctypes.byref(per),
                                  _stream(stream)))
     return ops.value, per.value
+
+
+def he_probe_tensor(ctx, kind, stream=None):
+    """Dense tensor MMA rate (ops/s) on the context's GPU: kind 0 tcgen05 bf16 -> f32, kind 1
+    mma.sync s8 -> s32."""
+    sms = torch.cuda.get_device_properties(ctx.device).multi_processor_count
+    scratch = torch.empty(4 * sms, dtype=torch.int32, device=ctx.device)
+    ops = ctypes.c_double()
+    _check(lib.he_probe_tensor(ctx.h, kind, ctypes.byref(ops), _ptr(scratch), scratch.numel(), _stream(stream)))
+    return ops.value
+
+
+def he_test_tc_gemm(ctx, A, B, stream=None):
+    """A: (128, k), B: (n, k) torch.bfloat16 CUDA tensors; returns D = A B^T as (128, n)
+    float32, computed by tcgen05."""
+    assert A.is_cuda and B.is_cuda and A.is_contiguous() and B.is_contiguous()
+    assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16
+    n, k = B.shape
+    assert A.shape == (128, k)
+    D = torch.empty((128, n), dtype=torch.float32, device=A.device)
+    _check(lib.he_test_tc_gemm(ctx.h, n, k, _ptr(A), _ptr(B), _ptr(D), _stream(stream)))
+    return D
 
 
 def he_launch_count(ctx):

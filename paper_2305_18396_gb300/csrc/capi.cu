@@ -1206,6 +1206,35 @@ int he_device_status(he_ctx* c, void* stream) {
               : HE_OK;
 }
 
+int he_probe_tensor(he_ctx* c, uint32_t kind, double* ops_per_s, uint32_t* scratch, size_t scratch_words,
+                    void* stream) {
+  if (!c || !ops_per_s || !scratch) return fail(HE_EINVAL, "NULL argument");
+  if (kind > 1) return fail(HE_EINVAL, "kind must be 0 (tcgen05 bf16) or 1 (mma.sync s8)");
+  if (int r = set_device(c)) return r;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  if ((u64)4 * sms > scratch_words) return fail(HE_EINVAL, "scratch needs 4 x SMs words");
+  float ms = 0;
+  int iters = 0;
+  cudaError_t e = he::probe_tensor((int)kind, sms, c->d_err, scratch, &ms, &iters, (cudaStream_t)stream);
+  c->launches.fetch_add(3, std::memory_order_relaxed);
+  if (e != cudaSuccess) return cuda_fail(e, "probe_tensor");
+  const double ops = kind == 0 ? 2.0 * 128 * 256 * 16 * iters * 2.0 * sms            // per block: iters MMAs
+                               : 2.0 * 16 * 8 * 32 * 8.0 * iters * 8.0 * 4.0 * sms;  // 8 warps x 8 chains
+  *ops_per_s = ms > 0 ? ops / (ms * 1e-3) : 0.0;
+  return HE_OK;
+}
+
+int he_test_tc_gemm(he_ctx* c, uint32_t n, uint32_t k, const void* A, const void* B, void* D, void* stream) {
+  if (!c || !A || !B || !D) return fail(HE_EINVAL, "NULL argument");
+  if (n < 16 || n > 256 || n % 16) return fail(HE_EINVAL, "n must be a multiple of 16 in [16, 256]");
+  if (!k || k % 16) return fail(HE_EINVAL, "k must be a positive multiple of 16");
+  if ((u64)(128 + n) * k * 2 > 200 * 1024) return fail(HE_EINVAL, "operands exceed 200 KB of shared memory");
+  if (int r = set_device(c)) return r;
+  return launch(c, KProbe, (cudaStream_t)stream, "tc_gemm check",
+                [&] { return he::launch_tc_check(A, B, D, n, k, c->d_err, (cudaStream_t)stream); });
+}
+
 int he_probe_mad_wide(he_ctx* c, uint64_t* scratch, size_t scratch_words, double* ops_per_s, double* per_sm_per_clock,
                       void* stream) {
   if (!c || !scratch || !ops_per_s) return fail(HE_EINVAL, "NULL argument");

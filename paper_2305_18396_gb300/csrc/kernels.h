@@ -68,6 +68,15 @@ cudaError_t launch_intt_mask(const Consts& C, u64* out, u64 out_cts, u32 batch, 
 // (`out`: sms * 8 * 256 words of scratch).
 cudaError_t probe_mad_wide(int sms, u64* out, float* ms, cudaStream_t st);
 
+// Tensor-core rate probes (tc_probe.cu), timed with events (*ms): kind 0, 2 x sms blocks each
+// issuing *iters_used tcgen05 MMAs of M = 128, N = 256, K = 16 (bf16 -> f32); kind 1,
+// 4 x sms blocks of 256 threads issuing 8 x *iters_used warp-level mma.sync m16n8k32
+// (s8 -> s32) per warp.  *err set if a bounded wait expired; sink: 4 x sms words.
+cudaError_t probe_tensor(int kind, int sms, int* err, uint32_t* sink, float* ms, int* iters_used, cudaStream_t st);
+// D (128 x n f32 words) = A (128 x k bf16) . B (n x k bf16)^T through tcgen05; A, B
+// row-major; n in [16, 256] a multiple of 16; k a multiple of 16 with (128 + n) k 2 <= 200 KB.
+cudaError_t launch_tc_check(const void* A, const void* B, void* D, uint32_t n, uint32_t k, int* err, cudaStream_t st);
+
 // Runs one bounded wait on an mbarrier nothing completes (limit_ns), setting *err on expiry.
 cudaError_t launch_wait_timeout_check(uint64_t limit_ns, int* err, cudaStream_t st);
 

@@ -2,12 +2,13 @@
 and a reader for the per-launch CSV that `ncu --metrics gpu__time_duration.sum --csv`
 writes.
 
-    python -m paper_2305_18396_gb300.profiling case M K N [--repeat R] [--full-c0]
+    python -m paper_2305_18396_gb300.profiling case M K N [--repeat R] [--full-c0] [--logn 13 --L 3] [--multi]
     python -m paper_2305_18396_gb300.profiling share M K N [--repeat R]
     python -m paper_2305_18396_gb300.profiling launches launches.csv
 
 `case` runs one Pi_MatMul (Algorithm 1) of an M x K share against a K x N weight matrix
-at N=4096, L=2 through the public binding: key generation, packing, encryption and
+at N=4096, L=2 (or --logn / --L) through the public binding (he_matmul, or with --multi
+he_matmul_multi): key generation, packing, encryption and
 weight encoding once, then R products (compact output, Sec. 3.1.3, unless --full-c0),
 then a device status check.  The products are the launches worth capturing; everything
 before them is set-up.
@@ -23,7 +24,7 @@ import sys
 import numpy as np
 
 
-def run_case(m, k, n, repeat=3, compact=True, logN=12, L=2):
+def run_case(m, k, n, repeat=3, compact=True, logN=12, L=2, multi=False):
     import torch
 
     from . import binding as B
@@ -38,7 +39,15 @@ def run_case(m, k, n, repeat=3, compact=True, logN=12, L=2):
     pt = B.he_encode_weights(ctx, W, k, n, blk)
     flags = B.HE_DROP_C0 if compact else 0
     out = None
-    for i in range(repeat):
+    if multi:  # through the multi-product launch (one product): the kernels of a whole-layer step
+        si = ctx.sizes(m, k, n, blk)
+        out = ctx.empty(si["out_words_compact"] if compact else si["out_words"])
+        prods = B.make_products([dict(ct_in=ct, pt=pt, ct_out=out, m=m, k=k, n=n, blk=blk, flags=flags,
+                                      mask_seed=5)])
+        ws = ctx.empty(B.he_multi_workspace_bytes(ctx, prods) // 8 + 1)
+        for i in range(repeat):
+            B.he_matmul_multi(ctx, prods, ws)
+    for i in range(0 if multi else repeat):
         out = B.he_matmul(ctx, ct, pt, m, k, n, blk, 5 + i, ct_out=out, flags=flags)
     torch.cuda.synchronize()
     B.he_device_status(ctx)
@@ -116,6 +125,9 @@ def main(argv=None):
     c.add_argument("n", type=int)
     c.add_argument("--repeat", type=int, default=3)
     c.add_argument("--full-c0", action="store_true")
+    c.add_argument("--logn", type=int, default=12, help="log2 N (12 or 13)")
+    c.add_argument("--L", type=int, default=2, help="number of primes")
+    c.add_argument("--multi", action="store_true", help="run through he_matmul_multi")
     sh = sub.add_parser("share")
     sh.add_argument("m", type=int)
     sh.add_argument("k", type=int)
@@ -131,7 +143,7 @@ def main(argv=None):
     s.add_argument("--last", help="window ends at the last launch whose name contains this")
     a = ap.parse_args(argv)
     if a.cmd == "case":
-        blk, si = run_case(a.m, a.k, a.n, a.repeat, not a.full_c0)
+        blk, si = run_case(a.m, a.k, a.n, a.repeat, not a.full_c0, a.logn, a.L, a.multi)
         print("ok", blk, si)
     elif a.cmd == "share":
         run_share_case(a.m, a.k, a.n, a.repeat)
