@@ -173,6 +173,30 @@ HE_API int he_get_ntt_radix(const he_ctx* ctx, uint32_t* log2_values);
 HE_API int he_autotune_ntt_radix(he_ctx* ctx, uint32_t cnt, void* scratch, size_t scratch_bytes,
                                  size_t* scratch_needed, float* ms, uint32_t* chosen, void* stream);
 
+/* Which multiply-accumulate evaluates step 3 of Algorithm 1 in the NTT domain (the
+ * slot-wise sum over the k-blocks of ciphertext x plaintext products; footnote of Sec.
+ * 3.1.3).  Both are exact and give bit-identical outputs; they differ in speed and in the
+ * memory layout of the encoded weights and of the workspace.
+ *   HE_MAC_INTEGER: 64-bit residues split into 25-bit halves, three 32 x 32 -> 64-bit
+ *     integer multiply-adds per slot product (Karatsuba) on the CUDA cores.
+ *   HE_MAC_TENSOR: residues split into seven balanced 8-bit digits, exact in bf16; the
+ *     digit products summed on the tcgen05 tensor cores with f32 accumulation (every sum
+ *     stays an exact integer below 2^24) and recombined mod q_l.  Needs N >= 512.
+ *   HE_MAC_AUTO (the default): the tensor cores for products of at least 32 k-blocks
+ *     (k / k_b) when N >= 512, the integer path otherwise.
+ * The choice fixes the layout of he_encode_weights' output and of the workspace (he_sizes
+ * reports both for the engine in force), so set it before encoding weights and keep it
+ * while those weights are in use.  Must not change while another thread uses the
+ * context.  Errors: HE_EINVAL (unknown engine). */
+#define HE_MAC_AUTO 0u
+#define HE_MAC_INTEGER 1u
+#define HE_MAC_TENSOR 2u
+HE_API int he_set_mac_engine(he_ctx* ctx, uint32_t engine);
+HE_API int he_get_mac_engine(const he_ctx* ctx, uint32_t* engine);
+/* Host-side: *yes = 1 if products of inner dimension k under blk use the tensor cores on
+ * this context (engine and N as above), else 0. */
+HE_API int he_mac_uses_tensor_cores(const he_ctx* ctx, uint32_t k, const he_blocking* blk, uint32_t* yes);
+
 /* ---- test client (Sec. 2.2 BFV; encrypt/decrypt are the client's side) -- */
 
 /* Secret key s with ternary coefficients, coefficient i = (u mod 3) - 1 for the

@@ -20,6 +20,7 @@ HE_OK, HE_EINVAL, HE_ENOMEM, HE_ECUDA, HE_ETIMEOUT, HE_ENOISE = range(6)
 HE_FLAGS_NONE = 0
 HE_DROP_C0 = 1
 HE_ASYNC = 2
+HE_MAC_AUTO, HE_MAC_INTEGER, HE_MAC_TENSOR = 0, 1, 2
 _NAMES = {1: "HE_EINVAL", 2: "HE_ENOMEM", 3: "HE_ECUDA", 4: "HE_ETIMEOUT", 5: "HE_ENOISE"}
 
 
@@ -95,6 +96,9 @@ def _load():
         "he_autotune_blocking": (ctypes.c_int, [P, u32, u32, u32, u32, u32, u32, u32, P, sz, ctypes.POINTER(sz), pB,
                                                 ctypes.POINTER(ctypes.c_float), P]),
         "he_set_ntt_radix": (ctypes.c_int, [P, u32]),
+        "he_set_mac_engine": (ctypes.c_int, [P, u32]),
+        "he_get_mac_engine": (ctypes.c_int, [P, pu32]),
+        "he_mac_uses_tensor_cores": (ctypes.c_int, [P, u32, pB, pu32]),
         "he_get_ntt_radix": (ctypes.c_int, [P, pu32]),
         "he_autotune_ntt_radix": (ctypes.c_int, [P, u32, P, sz, ctypes.POINTER(sz), ctypes.POINTER(ctypes.c_float),
                                                  pu32, P]),
@@ -214,6 +218,22 @@ class Context:
 
     def set_ntt_radix(self, log2_values):
         _check(lib.he_set_ntt_radix(self.h, log2_values))
+
+    @property
+    def mac_engine(self):
+        """HE_MAC_AUTO, HE_MAC_INTEGER or HE_MAC_TENSOR (he_get_mac_engine)."""
+        v = ctypes.c_uint32(0)
+        _check(lib.he_get_mac_engine(self.h, ctypes.byref(v)))
+        return v.value
+
+    def set_mac_engine(self, engine):
+        """Set before encoding weights: the engine fixes their layout (he_set_mac_engine)."""
+        _check(lib.he_set_mac_engine(self.h, engine))
+
+    def uses_tensor_cores(self, k, blk):
+        v = ctypes.c_uint32(0)
+        _check(lib.he_mac_uses_tensor_cores(self.h, k, _blk(blk), ctypes.byref(v)))
+        return bool(v.value)
 
     def autotune_ntt_radix(self, cnt=0, stream=None):
         """Measured transform radix (he_autotune_ntt_radix), selected for this context.

@@ -12,6 +12,7 @@
 
 #include "../../include/he_gb300.h"
 #include "kernels.h"
+#include "mac_tc.cuh"
 #include "multi.h"
 #include "ntt.cuh"
 
@@ -122,12 +123,12 @@ struct ProfRec {
 
 enum Kind {
   KNttFwd, KNttInv, KPolyMul, KKeygen, KEncrypt, KDecrypt, KPack, KUnpack, KUnmask, KEncode, KMac, KInttMask, KInttC0,
-  KExpand, KProbe, KShare, KInvC0, KCheck, KCount
+  KExpand, KProbe, KShare, KInvC0, KCheck, KMacTc, KCount
 };
 static const char* kKindNames[KCount] = {"ntt_forward", "ntt_inverse", "poly_mul", "keygen", "encrypt",
                                          "decrypt", "pack", "unpack", "unmask", "encode_weights",
                                          "mac", "intt_mask", "intt_c0_targets", "expand_compact", "probe",
-                                         "share_matmul", "intt_c1_c0", "check_residues"};
+                                         "share_matmul", "intt_c1_c0", "check_residues", "mac_tc"};
 
 struct he_ctx {
   int device = 0;
@@ -135,6 +136,7 @@ struct he_ctx {
   u64 psi[he::kMaxPrimes] = {};
   u64* d_tables = nullptr;
   int* d_err = nullptr;  // set by kernels whose bounded waits expired
+  uint32_t mac_engine = HE_MAC_AUTO;  // which multiply-accumulate products use (he_set_mac_engine)
   u64* d_bad = nullptr;  // he_ct_import: count and first index of residues out of range
   std::atomic<uint64_t> launches{0};
   bool prof = false;
@@ -197,6 +199,19 @@ Shape shape_of(u32 m, u32 k, u32 n, const he_blocking* b) {
 }
 
 he::Blk to_blk(const he_blocking* b) { return {b->m_b, b->k_b, b->n_b}; }
+
+// Whether a product with nJ k-blocks uses the tensor-core multiply-accumulate (and its
+// slot-major operand layout) on this context: needs N >= 512; HE_MAC_AUTO takes it from
+// kTcMinKBlocks k-blocks on, where the exact limb split amortises its digit split and
+// epilogue; HE_MAC_TENSOR for every product; HE_MAC_INTEGER never.
+constexpr u32 kTcMinKBlocks = 32;
+bool use_tc(const he_ctx* c, u32 nJ) {
+  if (c->C.logN < 9 || c->mac_engine == HE_MAC_INTEGER) return false;
+  return c->mac_engine == HE_MAC_TENSOR || nJ >= kTcMinKBlocks;
+}
+
+// k-blocks per operand row in memory: the tensor-core layout pads rows to an even count.
+u32 nJ_stored(const he_ctx* c, u32 nJ) { return use_tc(c, nJ) ? he::tc_nJp(nJ) : nJ; }
 
 }  // namespace
 
@@ -263,6 +278,8 @@ int he_params_init(he_ctx** out, uint32_t N, uint32_t L, const uint64_t* q, uint
     P.tinv_sh = shoup(P.tinv, ql);
     P.r25 = (1ull << 25) % ql;
     P.r25_sh = shoup(P.r25, ql);
+    P.r32 = 1ull << 32;
+    P.r32_sh = shoup(P.r32, ql);
     P.r50 = (1ull << 50) % ql;
     P.r50_sh = shoup(P.r50, ql);
     P.r64 = (u64)(((u128)1 << 64) % ql);
@@ -354,12 +371,14 @@ int he_sizes(const he_ctx* c, uint32_t m, uint32_t k, uint32_t n, const he_block
   out->pts = (u64)s.nI * s.nJ;
   out->in_words = out->in_cts * 2 * L * N;
   out->out_words = out->out_cts * 2 * L * N;
-  out->pt_words = out->pts * L * N;
+  const u64 nJs = nJ_stored(c, s.nJ);
+  out->pt_words = (u64)s.nI * nJs * L * N;
   out->packed_words = out->in_cts * N;
-  out->workspace_bytes = out->in_words * sizeof(u64);  // NTT of the input ciphertexts
+  const u64 ntt_words = (u64)s.nLb * nJs * 2 * L * N;  // NTT of the input ciphertexts (MAC layout)
+  out->workspace_bytes = ntt_words * sizeof(u64);
   const u64 Nc = pow2(blk->k_b) ? N / blk->k_b : 0;
   out->out_words_compact = Nc ? out->out_cts * L * (Nc + N) : 0;
-  out->workspace_bytes_compact = (out->in_words + out->out_cts * L * N) * sizeof(u64);
+  out->workspace_bytes_compact = (ntt_words + out->out_cts * L * N) * sizeof(u64);
   return HE_OK;
 }
 
@@ -553,7 +572,8 @@ int he_encode_weights_batch(he_ctx* c, const uint64_t* W, uint32_t k, uint32_t n
   if (int r = set_device(c)) return r;
   Shape s = shape_of(1, k, n, blk);
   return launch(c, KEncode, (cudaStream_t)stream, "encode_weights", [&] {
-    return he::launch_encode_weights(c->C, W, k, n, to_blk(blk), s.nI, s.nJ, batch, pt, (cudaStream_t)stream);
+    return he::launch_encode_weights(c->C, W, k, n, to_blk(blk), s.nI, s.nJ, batch, use_tc(c, s.nJ), pt,
+                                     (cudaStream_t)stream);
   });
 }
 
@@ -575,14 +595,17 @@ static int matmul_device(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, u
   const u64 N = c->C.N, L = c->C.L;
   const u64 out_cts = (u64)s.nLb * s.nI;
   u64* ctN = (u64*)ws;
+  const bool tc = use_tc(c, s.nJ);
+  auto mac = [&](u64* o0, u64 st0, u64* o1, u64 st1) {
+    return tc ? he::launch_mac_tc(c->C, ctN, pt, o0, st0, o1, st1, s.nI, s.nJ, s.nLb, batch, c->d_err, st)
+              : he::launch_mac(c->C, ctN, pt, o0, st0, o1, st1, s.nI, s.nJ, s.nLb, batch, c->d_err, st);
+  };
   int r = launch(c, KNttFwd, st, "matmul: forward NTT",
-                 [&] { return he::launch_ntt_forward_mm(c->C, ct_in, ctN, s.nJ, s.nLb, batch, st); });
+                 [&] { return he::launch_ntt_forward_mm(c->C, ct_in, ctN, s.nJ, s.nLb, batch, tc, st); });
   if (r) return r;
   if (!(flags & HE_DROP_C0)) {
-    r = launch(c, KMac, st, "matmul: multiply-accumulate", [&] {
-      return he::launch_mac(c->C, ctN, pt, ct_out, 2 * L * N, ct_out + L * N, 2 * L * N, s.nI, s.nJ, s.nLb, batch,
-                            c->d_err, st);
-    });
+    r = launch(c, tc ? KMacTc : KMac, st, "matmul: multiply-accumulate",
+               [&] { return mac(ct_out, 2 * L * N, ct_out + L * N, 2 * L * N); });
     if (r) return r;
     return launch(c, KInttMask, st, "matmul: inverse NTT + mask",
                   [&] { return he::launch_intt_mask(c->C, ct_out, out_cts, batch, mask_seed, st); });
@@ -590,11 +613,9 @@ static int matmul_device(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, u
   // compact output: per ciphertext [c0 at the decoded coefficients: L x N/k_b][c1: L x N]
   const u32 logkb = log2u(blk->k_b);
   const u64 Nc = N >> logkb, ct_stride = L * (Nc + N);
-  u64* c0_ntt = ctN + (u64)batch * s.nLb * s.nJ * 2 * L * N;  // after the inputs' NTT in the workspace
-  r = launch(c, KMac, st, "matmul: multiply-accumulate", [&] {
-    return he::launch_mac(c->C, ctN, pt, c0_ntt, L * N, ct_out + L * Nc, ct_stride, s.nI, s.nJ, s.nLb, batch, c->d_err,
-                          st);
-  });
+  u64* c0_ntt = ctN + (u64)batch * s.nLb * nJ_stored(c, s.nJ) * 2 * L * N;  // after the inputs' NTT
+  r = launch(c, tc ? KMacTc : KMac, st, "matmul: multiply-accumulate",
+             [&] { return mac(c0_ntt, L * N, ct_out + L * Nc, ct_stride); });
   if (r) return r;
   r = launch(c, KInttMask, st, "matmul: inverse NTT of c1",
              [&] { return he::launch_intt_c1(c->C, ct_out + L * Nc, ct_stride, out_cts * batch, st); });
@@ -700,7 +721,7 @@ int he_autotune_blocking(he_ctx* c, uint32_t m, uint32_t k, uint32_t n, uint32_t
     Shape s = shape_of(m, k, n, &b);
     auto encode = [&] {
       return launch(c, KEncode, st, "autotune: encode", [&] {
-        return he::launch_encode_weights(c->C, W, k, n, to_blk(&b), s.nI, s.nJ, batch, pt, st);
+        return he::launch_encode_weights(c->C, W, k, n, to_blk(&b), s.nI, s.nJ, batch, use_tc(c, s.nJ), pt, st);
       });
     };
     if ((rc = launch(c, KProbe, st, "autotune: fill", [&] {
@@ -730,6 +751,26 @@ int he_autotune_blocking(he_ctx* c, uint32_t m, uint32_t k, uint32_t n, uint32_t
   if (rc != HE_OK) return rc;
   if (int r = he_device_status(c, stream)) return r;
   if (best_ms) *best_ms = best;
+  return HE_OK;
+}
+
+int he_set_mac_engine(he_ctx* c, uint32_t engine) {
+  if (!c) return fail(HE_EINVAL, "ctx is NULL");
+  if (engine > HE_MAC_TENSOR) return fail(HE_EINVAL, "engine must be HE_MAC_AUTO, HE_MAC_INTEGER or HE_MAC_TENSOR");
+  c->mac_engine = engine;
+  return HE_OK;
+}
+
+int he_get_mac_engine(const he_ctx* c, uint32_t* engine) {
+  if (!c || !engine) return fail(HE_EINVAL, "NULL argument");
+  *engine = c->mac_engine;
+  return HE_OK;
+}
+
+int he_mac_uses_tensor_cores(const he_ctx* c, uint32_t k, const he_blocking* blk, uint32_t* yes) {
+  if (!c || !yes) return fail(HE_EINVAL, "NULL argument");
+  if (int r = check_blk(c, blk)) return r;
+  *yes = use_tc(c, shape_of(1, k, 1, blk).nJ) ? 1 : 0;
   return HE_OK;
 }
 
@@ -873,7 +914,7 @@ namespace {
 
 struct MultiPlan {
   he::MultiTable T;
-  u64 fwd = 0, mac = 0, inv = 0, c0 = 0, ws_bytes = 0;
+  u64 fwd = 0, mac = 0, tc = 0, inv = 0, c0 = 0, ws_bytes = 0;
   u32 max_nc = 0;  // shared-memory words of the largest c0 transform
 };
 
@@ -910,7 +951,8 @@ int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* w
     it.logkb = compact ? log2u(x.blk.k_b) : 0;
     it.tilesR = (2 * s.nLb + rows_t - 1) / rows_t;
     it.tilesC = (s.nI + cols_t - 1) / cols_t;
-    const u64 in_words = (u64)s.nLb * s.nJ * 2 * L * N, out_cts = (u64)s.nLb * s.nI;
+    it.tc = use_tc(c, s.nJ);
+    const u64 in_words = (u64)s.nLb * nJ_stored(c, s.nJ) * 2 * L * N, out_cts = (u64)s.nLb * s.nI;
     off = (off + 255) & ~(u64)255;
     it.ctN = workspace ? (u64*)(workspace + off) : nullptr;
     off += in_words * 8;
@@ -924,13 +966,15 @@ int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* w
     it.mac_begin = P->mac;
     it.inv_begin = P->inv;
     it.c0_begin = P->c0;
+    it.tc_begin = P->tc;
     P->fwd += (u64)s.nLb * s.nJ * 2 * L;
-    P->mac += (N >> 5) * it.tilesR * it.tilesC * L;
+    if (it.tc) P->tc += he::tc_units((u32)N, (u32)L, s.nI, s.nLb);
+    else P->mac += (N >> 5) * it.tilesR * it.tilesC * L;
     P->inv += out_cts * (compact ? 1 : 2) * L;
     P->c0 += compact ? out_cts * L : 0;
   }
   P->ws_bytes = off;
-  if (P->fwd >= (1ull << 31) || P->mac >= (1ull << 31) || P->inv >= (1ull << 31))
+  if (P->fwd >= (1ull << 31) || P->mac >= (1ull << 31) || P->tc >= (1ull << 31) || P->inv >= (1ull << 31))
     return fail(HE_EINVAL, "multi-product launch too large");
   return HE_OK;
 }
@@ -956,9 +1000,12 @@ int he_matmul_multi(he_ctx* c, uint32_t count, const he_product* items, void* wo
   if (int r = set_device(c)) return r;
   cudaStream_t st = (cudaStream_t)stream;
   int r = launch(c, KNttFwd, st, "multi: forward NTT", [&] { return he::launch_fwd_multi(c->C, P.T, P.fwd, st); });
-  if (!r)
+  if (!r && P.mac)
     r = launch(c, KMac, st, "multi: multiply-accumulate",
                [&] { return he::launch_mac_multi(c->C, P.T, P.mac, c->d_err, st); });
+  if (!r && P.tc)
+    r = launch(c, KMacTc, st, "multi: tensor-core multiply-accumulate",
+               [&] { return he::launch_mac_tc_multi(c->C, P.T, P.tc, c->d_err, st); });
   if (!r && P.c0) {  // compact products: c1 inverse NTTs and pruned c0 transforms in one grid
     r = launch(c, KInvC0, st, "multi: inverse NTT of c1 + pruned inverse NTT of c0",
                [&] { return he::launch_inv_c0_multi(c->C, P.T, P.inv, P.c0, P.max_nc, st); });

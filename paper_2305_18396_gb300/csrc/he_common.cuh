@@ -29,6 +29,7 @@ struct PrimeConsts {
   u64 ninv, ninv_sh;   // N^{-1} mod q
   u64 tinv, tinv_sh;   // t^{-1} mod q
   u64 r25, r25_sh;     // 2^25 mod q
+  u64 r32, r32_sh;     // 2^32 (below q)
   u64 r50, r50_sh;     // 2^50 mod q
   u64 r64, r64_sh;     // 2^64 mod q
   u64 crt, crt_sh;     // ((Q / q)^{-1} mod q), for decryption

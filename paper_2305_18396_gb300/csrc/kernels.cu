@@ -14,6 +14,7 @@
 #include "async.cuh"
 #include "kernels.h"
 #include "mac.cuh"
+#include "mac_tc.cuh"
 #include "ntt.cuh"
 
 namespace he {
@@ -316,13 +317,14 @@ __global__ void __launch_bounds__(kNttThreads) k_encode_weights(const u64* W, u3
 
 template <int LOGN, int LOGR>
 __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>::kMinBlocks) k_encode_weights_t(const u64* W, u32 k, u32 n, Blk b, u32 nI,
-                                                                        u32 nJ, u64* pt, const __grid_constant__ Consts C) {
+                                                                        u32 nJ, u32 tc, u64* pt, const __grid_constant__ Consts C) {
   using S = NttShape<LOGN, LOGR>;
   extern __shared__ u64 sm[];
   const u64 item_polys = (u64)nI * nJ * C.L;
   const u64 item = blockIdx.x / item_polys, poly = blockIdx.x % item_polys;
+  const u32 nJp = tc_nJp(nJ);
   W += item * k * n;
-  pt += item * item_polys * S::N;
+  pt += item * (u64)nI * (tc ? nJp : nJ) * C.L * S::N;
   const u32 l = poly % C.L;
   const u32 IJ = (u32)(poly / C.L);
   const u32 I = IJ / nJ, J = IJ % nJ;
@@ -337,8 +339,11 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
     u64 w = W[(u64)row * n + col] & C.tmask;
     return w >= half_t ? P.q - (C.tmask + 1 - w) : w;  // centred lift [-t/2, t/2)
   };
-  ntt_forward_block<S>(sm, P, load,
-                       [&](u32 e, u64 v) { pt[chunked_index(I, J, l, e, nJ, C.L, S::N)] = split_word(v); }, nk);
+  if (tc)
+    ntt_forward_block<S>(sm, P, load, [&](u32 e, u64 v) { pt[tc_index(I, J, l, e, nJp, C.L, S::N)] = v; }, nk);
+  else
+    ntt_forward_block<S>(sm, P, load,
+                         [&](u32 e, u64 v) { pt[chunked_index(I, J, l, e, nJ, C.L, S::N)] = split_word(v); }, nk);
 }
 
 template <int LOGN, int LOGR>
@@ -399,7 +404,7 @@ cudaError_t launch_mac_ws_cfg(const Consts& C, const u64* ctN, const u64* pt, Ou
 // Input poly p = ((Lb nJ + J) 2 + c) L + l of the wire format [Lb nJ + J][2][L][N].
 template <int LOGN, int LOGR>
 __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>::kMinBlocks) k_ntt_forward_mm_t(const u64* src, u64* ctN, u32 nJ, u32 nLb,
-                                                                        const __grid_constant__ Consts C) {
+                                                                        u32 tc, const __grid_constant__ Consts C) {
   using S = NttShape<LOGN, LOGR>;
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
@@ -411,10 +416,30 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
   const u32 Lb = LbJ / nJ, J = LbJ % nJ;
   const PrimeConsts& P = C.p[l];
   const u64* sp = src + poly * S::N;
-  u64* dst = ctN + item * item_polys * S::N;
+  const u32 nJp = tc_nJp(nJ);
+  u64* dst = ctN + item * (u64)nLb * (tc ? nJp : nJ) * 2 * C.L * S::N;
   const u64 row = (u64)Lb * 2 + c;
-  ntt_forward_block<S>(sm, P, [&](u32 e) { return sp[e]; },
-                       [&](u32 e, u64 v) { dst[chunked_index(row, J, l, e, nJ, C.L, S::N)] = split_word(v); });
+  if (tc)
+    ntt_forward_block<S>(sm, P, [&](u32 e) { return sp[e]; },
+                         [&](u32 e, u64 v) { dst[tc_index(row, J, l, e, nJp, C.L, S::N)] = v; });
+  else
+    ntt_forward_block<S>(sm, P, [&](u32 e) { return sp[e]; },
+                         [&](u32 e, u64 v) { dst[chunked_index(row, J, l, e, nJ, C.L, S::N)] = split_word(v); });
+}
+
+// The tensor-core multiply-accumulate (mac_tc.cuh) of `batch` same-shape products:
+// blockIdx.x = work unit within a product, blockIdx.y = product.
+__global__ void __launch_bounds__(kTcThreads, 2) k_mac_tc(const u64* __restrict__ ctN, const u64* __restrict__ pt,
+                                                         OutPlace out, u32 nI, u32 nJ, u32 nLb, int* err,
+                                                         const __grid_constant__ Consts C) {
+  extern __shared__ __align__(128) uint8_t smem_tc[];
+  __shared__ TcShared sh;
+  const u64 item = blockIdx.y;
+  const u32 nJp = tc_nJp(nJ);
+  const u64 per_in = (u64)nLb * nJp * 2 * C.L * C.N, per_pt = (u64)nI * nJp * C.L * C.N;
+  const TcUnit u = tc_unit(blockIdx.x, C.N, nI, nLb);
+  mac_tc_block(ctN + item * per_in, pt + item * per_pt, out, item * ((u64)nLb * nI), nI, nJ, nLb, u.I0, u.r0, u.s0,
+               kTcSlots, u.l, err, C, smem_tc, sh);
 }
 
 // Compact-output mode: inverse NTT of the c1 polynomials only, in place.  Ciphertext g's
@@ -536,6 +561,7 @@ cudaError_t configure_kernels(const Consts&) {
   set((const void*)k_encode_weights, one);
   set((const void*)k_intt_mask, one);
   set((const void*)k_mac_ws_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
+  set((const void*)k_mac_tc, (int)kTcSmem);
 #define HE_SET_T(LN, LR, unused)                                                                    \
   {                                                                                                  \
     const int bytes = NttShape<LN, LR>::kSmemWords * (int)sizeof(u64);                               \
@@ -640,12 +666,13 @@ cudaError_t launch_unmask(const Consts& C, u64 seed, u32 m, u32 n, Blk b, u32 nI
 }
 
 cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u32 batch,
-                                  u64* pt, cudaStream_t st) {
+                                  u32 tc, u64* pt, cudaStream_t st) {
   u64 polys = (u64)nI * nJ * C.L * batch;
   if (!polys) return cudaGetLastError();
   if (C.logN >= 9) {
-    HE_DISPATCH_T(k_encode_weights_t, (unsigned)polys, st, W, k, n, b, nI, nJ, pt, C)
+    HE_DISPATCH_T(k_encode_weights_t, (unsigned)polys, st, W, k, n, b, nI, nJ, tc, pt, C)
   } else {
+    if (tc) return cudaErrorInvalidValue;  // the tensor-core layout needs N >= 512
     k_encode_weights<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(W, k, n, b, nI, nJ, pt, C);
   }
   return cudaGetLastError();
@@ -662,13 +689,28 @@ cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out0
   return launch_mac_ws_cfg<MacProd, kMacMinBlocks>(C, ctN, pt, o, nI, nJ, nLb, batch, err, st);
 }
 
-cudaError_t launch_ntt_forward_mm(const Consts& C, const u64* ct_in, u64* ctN, u32 nJ, u32 nLb, u32 batch,
+cudaError_t launch_mac_tc(const Consts& C, const u64* ctN, const u64* pt, u64* out0, u64 stride0, u64* out1,
+                          u64 stride1, u32 nI, u32 nJ, u32 nLb, u32 batch, int* err, cudaStream_t st) {
+  OutPlace o;
+  o.base[0] = out0;
+  o.base[1] = out1;
+  o.ct_stride[0] = stride0;
+  o.ct_stride[1] = stride1;
+  const u64 units = tc_units(C.N, C.L, nI, nLb);
+  if (!units || !nJ || !batch) return cudaGetLastError();
+  if (C.logN < 9 || units >= (1ull << 31) || batch > 65535) return cudaErrorInvalidValue;
+  k_mac_tc<<<dim3((unsigned)units, batch), kTcThreads, kTcSmem, st>>>(ctN, pt, o, nI, nJ, nLb, err, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ntt_forward_mm(const Consts& C, const u64* ct_in, u64* ctN, u32 nJ, u32 nLb, u32 batch, u32 tc,
                                   cudaStream_t st) {
   const u64 polys = (u64)nLb * nJ * 2 * C.L * batch;
   if (!polys) return cudaGetLastError();
   if (C.logN >= 9) {
-    HE_DISPATCH_T(k_ntt_forward_mm_t, (unsigned)polys, st, ct_in, ctN, nJ, nLb, C)
+    HE_DISPATCH_T(k_ntt_forward_mm_t, (unsigned)polys, st, ct_in, ctN, nJ, nLb, tc, C)
   } else {
+    if (tc) return cudaErrorInvalidValue;  // the tensor-core layout needs N >= 512
     k_ntt_forward_mm_small<<<(unsigned)polys, kNttThreads, poly_smem(C), st>>>(ct_in, ctN, nJ, nLb, C);
   }
   return cudaGetLastError();

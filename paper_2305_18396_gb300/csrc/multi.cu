@@ -7,6 +7,7 @@
 #include "async.cuh"
 #include "kernels.h"
 #include "mac.cuh"
+#include "mac_tc.cuh"
 #include "multi.h"
 #include "ntt.cuh"
 
@@ -45,8 +46,14 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
   const u32 Lb = LbJ / it.nJ, J = LbJ % it.nJ;
   const u64* sp = it.ct_in + local * S::N;
   const u64 row = (u64)Lb * 2 + c;
-  ntt_forward_block<S>(sm, C.p[l], [&](u32 e) { return sp[e]; },
-                       [&](u32 e, u64 v) { it.ctN[chunked_index(row, J, l, e, it.nJ, C.L, S::N)] = split_word(v); });
+  if (it.tc) {
+    const u32 nJp = tc_nJp(it.nJ);
+    ntt_forward_block<S>(sm, C.p[l], [&](u32 e) { return sp[e]; },
+                         [&](u32 e, u64 v) { it.ctN[tc_index(row, J, l, e, nJp, C.L, S::N)] = v; });
+  } else {
+    ntt_forward_block<S>(sm, C.p[l], [&](u32 e) { return sp[e]; },
+                         [&](u32 e, u64 v) { it.ctN[chunked_index(row, J, l, e, it.nJ, C.L, S::N)] = split_word(v); });
+  }
 }
 
 __global__ void __launch_bounds__(kThreadsSmall) k_fwd_multi_small(const __grid_constant__ MultiTable T,
@@ -92,6 +99,31 @@ __global__ void __launch_bounds__(M::kThreads + 32, MINB) k_mac_multi_t(const __
     out.ct_stride[0] = out.ct_stride[1] = 2 * L * N;
   }
   mac_tile_ws<M>(it.ctN, it.pt, out, 0, it.nI, it.nJ, it.nLb, r0, c0, chunk, l, err, C, sm);
+}
+
+// The tensor-core multiply-accumulate (mac_tc.cuh) over the products flagged tc: each block
+// finds its product and its work unit (prime, slot group, weight-row tile, row tile).
+__global__ void __launch_bounds__(kTcThreads, 2) k_mac_tc_multi(const __grid_constant__ MultiTable T, int* err,
+                                                               const __grid_constant__ Consts C) {
+  extern __shared__ __align__(128) uint8_t smem_tc[];
+  __shared__ TcShared sh;
+  const u32 i = find_item(T, blockIdx.x, [](const MultiItem& x) { return x.tc_begin; });
+  const MultiItem& it = T.it[i];
+  const TcUnit u = tc_unit(blockIdx.x - it.tc_begin, C.N, it.nI, it.nLb);
+  const u64 N = C.N, L = C.L;
+  OutPlace out;
+  if (it.compact) {
+    const u64 Nc = N >> it.logkb;
+    out.base[0] = it.c0_ntt;
+    out.ct_stride[0] = L * N;
+    out.base[1] = it.out + L * Nc;
+    out.ct_stride[1] = L * (Nc + N);
+  } else {
+    out.base[0] = it.out;
+    out.base[1] = it.out + L * N;
+    out.ct_stride[0] = out.ct_stride[1] = 2 * L * N;
+  }
+  mac_tc_block(it.ctN, it.pt, out, 0, it.nI, it.nJ, it.nLb, u.I0, u.r0, u.s0, kTcSlots, u.l, err, C, smem_tc, sh);
 }
 
 // Inverse NTT of block b of the inverse grid: compact products transform their c1
@@ -216,6 +248,7 @@ cudaError_t configure_multi_kernels() {
   set((const void*)k_inv_multi_small, one);
   set((const void*)k_c0_multi, 2 * one);
   set((const void*)k_mac_multi_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
+  set((const void*)k_mac_tc_multi, (int)kTcSmem);
 #define HE_SET_MULTI(LN, LR, unused)                                                                   \
   set((const void*)k_fwd_multi_t<LN, LR>, NttShape<LN, LR>::kSmemWords * (int)sizeof(u64));            \
   set((const void*)k_inv_multi_t<LN, LR>, NttShape<LN, LR>::kSmemWords * (int)sizeof(u64));            \
@@ -242,6 +275,11 @@ cudaError_t launch_mac_multi(const Consts& C, const MultiTable& T, u64 blocks, i
   if (blocks)
     k_mac_multi_t<MacProd, kMacMinBlocks><<<(unsigned)blocks, MacProd::kThreads + 32, MacProd::kSmemBytes, st>>>(
         T, err, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mac_tc_multi(const Consts& C, const MultiTable& T, u64 blocks, int* err, cudaStream_t st) {
+  if (blocks) k_mac_tc_multi<<<(unsigned)blocks, kTcThreads, kTcSmem, st>>>(T, err, C);
   return cudaGetLastError();
 }
 

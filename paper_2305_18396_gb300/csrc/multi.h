@@ -17,9 +17,9 @@ struct MultiItem {
   u64* c0_ntt;       // workspace (compact output only): NTT-domain c0 of every output
   u64 mask_seed;
   const u64* seed_dev;  // HE_SEED_DEVICE: the seed is read from here when the kernels run
-  u64 fwd_begin, mac_begin, inv_begin, c0_begin;
+  u64 fwd_begin, mac_begin, inv_begin, c0_begin, tc_begin;
   u32 nI, nJ, nLb, logkb;
-  u32 compact, tilesR, tilesC, pad;
+  u32 compact, tilesR, tilesC, tc;  // tc: operands in the slot-major layout, tensor-core MAC
 };
 
 struct MultiTable {
@@ -32,6 +32,8 @@ u32 mac_tile_rows();
 u32 mac_tile_cols();
 cudaError_t launch_fwd_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
 cudaError_t launch_mac_multi(const Consts& C, const MultiTable& T, u64 blocks, int* err, cudaStream_t st);
+// The tensor-core multiply-accumulate of the products flagged tc (blocks: their work units).
+cudaError_t launch_mac_tc_multi(const Consts& C, const MultiTable& T, u64 blocks, int* err, cudaStream_t st);
 cudaError_t launch_inv_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
 cudaError_t launch_c0_multi(const Consts& C, const MultiTable& T, u64 blocks, u32 c0_words, cudaStream_t st);
 // The inverse-NTT grid and the c0 grid as one launch where inv_c0_fused(C), else two.
