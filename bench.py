@@ -86,6 +86,8 @@ def parse():
                     help="tuned: he_autotune_blocking per product at set-up; model: the cost model's choice")
     ap.add_argument("--ntt-radix", default="tuned", choices=["tuned", "3", "4", "5"],
                     help="log2 of the values per thread of the transforms: tuned = he_autotune_ntt_radix at set-up")
+    ap.add_argument("--mac-engine", default="auto", choices=["auto", "integer", "tensor"],
+                    help="multiply-accumulate engine (he_set_mac_engine): auto = tensor cores from 32 k-blocks on")
     ap.add_argument("--full-c0", action="store_true",
                     help="return all of c0 instead of only the decoded coefficients (Sec. 3.1.3)")
     return ap.parse_args()
@@ -212,7 +214,8 @@ class Layer:
                 B.he_pack_input(ctx, Xd[b * p.m * p.k:(b + 1) * p.m * p.k], p.m, p.k, blk,
                                 polys=polys[b * si["packed_words"]:(b + 1) * si["packed_words"]])
             ct_in = B.he_encrypt(ctx, self.sk, polys, seed + 900_000)
-            call = dict(p=p, blk=blk, si=si, cnt=cnt, ct_in=ct_in, out=ctx.empty(cnt * si["out"]), idx=idx)
+            call = dict(p=p, blk=blk, si=si, cnt=cnt, ct_in=ct_in, out=ctx.empty(cnt * si["out"]), idx=idx,
+                        tc=ctx.uses_tensor_cores(p.k, blk))
             if p.share_weights:
                 call["W"] = Wd  # the server's shares, encoded on every step
                 max_pt = max(max_pt, cnt * si["pt_words"])
@@ -382,13 +385,13 @@ class Layer:
 
     def algorithmic_bytes(self):
         """Per kernel family: algorithmic HBM bytes of one step (reads + writes, 8-byte words)."""
-        tot = {"mac": 0, "ntt_forward": 0, "intt_mask": 0, "encode_weights": 0}
+        tot = {"mac": 0, "mac_tc": 0, "ntt_forward": 0, "intt_mask": 0, "encode_weights": 0}
         for c in self.calls:
             si, p, cnt = c["si"], c["p"], c["cnt"]
             pt_b, in_b = 8 * si["pt_words"], 8 * si["in_words"]
             full_b = 8 * si["out_words"]  # the multiply-accumulate writes both components in full (NTT domain)
             c1_b = full_b // 2
-            tot["mac"] += cnt * (pt_b + in_b + full_b)
+            tot["mac_tc" if c["tc"] else "mac"] += cnt * (pt_b + in_b + full_b)
             tot["ntt_forward"] += cnt * 2 * in_b
             if self.flags:  # c1: read + write; c0: read in full, write the kept coefficients
                 tot["intt_mask"] += cnt * 2 * c1_b
@@ -400,10 +403,12 @@ class Layer:
         tot["intt_c1_c0"] = tot["intt_mask"] + tot.get("intt_c0_targets", 0)  # the whole-layer launch's fused grid
         return tot
 
-    def slot_macs(self):
-        """Slot-wise modular multiply-accumulates of one step."""
+    def slot_macs(self, tc=None):
+        """Slot-wise modular multiply-accumulates of one step (tc: only the products on the tensor
+        cores (True) or on the integer pipe (False))."""
         L, N = self.ctx.L, self.ctx.N
-        return sum(c["cnt"] * c["si"]["nI"] * c["si"]["nJ"] * c["si"]["nLb"] * 2 * L * N for c in self.calls)
+        return sum(c["cnt"] * c["si"]["nI"] * c["si"]["nJ"] * c["si"]["nLb"] * 2 * L * N for c in self.calls
+                   if tc is None or c["tc"] == tc)
 
 
 def kernel_source_hash():
@@ -717,6 +722,7 @@ def bert_base_leg(B, args, local, flags, steps=20):
     from paper_2305_18396_gb300 import workloads
 
     ctx = B.Context(4096, 2, device=local)
+    ctx.set_mac_engine({"auto": B.HE_MAC_AUTO, "integer": B.HE_MAC_INTEGER, "tensor": B.HE_MAC_TENSOR}[args.mac_engine])
     if args.ntt_radix == "tuned":
         ctx.autotune_ntt_radix()
     else:
@@ -757,6 +763,8 @@ def gpu_arm(args, world, rank, local):
     torch.cuda.set_device(local)
     wl = WORKLOADS[args.workload]
     ctx = B.Context(wl["N"], wl["L"], device=local)
+    engine = {"auto": B.HE_MAC_AUTO, "integer": B.HE_MAC_INTEGER, "tensor": B.HE_MAC_TENSOR}[args.mac_engine]
+    ctx.set_mac_engine(engine)  # before any weights are encoded: it fixes their layout
     if args.ntt_radix == "tuned":  # before the blocking tuner, which times whole products at this radix
         radix_ms = {str(r): round(v, 4) for r, v in ctx.autotune_ntt_radix()[1].items()}
     else:
@@ -821,10 +829,30 @@ def gpu_arm(args, world, rank, local):
     launches_per_step = stats[dom]["launches"] / steps_prof
     bytes_per_launch = alg.get(dom, 0) / launches_per_step
     hbm_gbs = bytes_per_launch / per_launch_s / 1e9
-    if dom == "mac":
+    if dom == "mac_tc":
+        # tensor-core multiply-accumulate: 49 digit products (2 flops each) per slot product, bf16
+        # on tcgen05, against the measured dense bf16 rate (sustained: the kernel runs inside a
+        # long step), and its HBM bytes against the measured copy bandwidth; the bound named is
+        # the roof it runs closest to
+        tc_peak = 1e12 * pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))
+        flops_per_launch = 2 * 49 * layer.slot_macs(True) / launches_per_step
+        tflops = flops_per_launch / per_launch_s
+        fr_t, fr_h = tflops / tc_peak, hbm_gbs / pk["hbm_gbs"]
+        t_obj = {"achieved": round(tflops / 1e12, 2), "peak": round(tc_peak / 1e12, 1), "unit": "TFLOP/s",
+                 "frac": round(fr_t, 4), "peak_source": f"{pk_src}: bf16 dense, sustained",
+                 "tcgen05_probe_tflops": round(B.he_probe_tensor(ctx, 0) / 1e12, 1),
+                 "flops_per_launch": flops_per_launch}
+        h_obj = {"achieved": round(hbm_gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(fr_h, 4),
+                 "peak_source": pk_src}
+        main, other, bound = (h_obj, t_obj, "hbm") if fr_h >= fr_t else (t_obj, h_obj, "tensor")
+        roofline = {"bound": bound, "kernel": dom, **{k: main[k] for k in ("achieved", "peak", "unit", "frac",
+                                                                           "peak_source")},
+                    ("tensor" if bound == "hbm" else "hbm"): other,
+                    "slot_products_per_s": layer.slot_macs(True) * steps_prof / (stats[dom]["total_ms"] / 1e3)}
+    elif dom == "mac":
         # integer-pipe bound: three mad.wide.u32 per slot product (Karatsuba), peak measured by
         # he_probe_mad_wide on this GPU (per-SM rate x SMs x clock)
-        ops_per_launch = 3 * layer.slot_macs() / launches_per_step
+        ops_per_launch = 3 * layer.slot_macs(False) / launches_per_step
         achieved = ops_per_launch / per_launch_s
         roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved / 1e12, 3),
                     "peak": round(mad_peak / 1e12, 3), "unit": "T mad.wide.u32/s", "frac": round(achieved / mad_peak, 4),
@@ -837,8 +865,8 @@ def gpu_arm(args, world, rank, local):
                     "unit": "GB/s", "frac": round(hbm_gbs / pk["hbm_gbs"], 4), "peak_source": pk_src}
     roofline.update({"algorithmic_bytes_per_launch": bytes_per_launch, "traffic": recorded_traffic(dom, args.launch, args.workload),
                      "kernels": kern,
-                     "slot_macs_per_s": layer.slot_macs() * steps_prof / (stats["mac"]["total_ms"] / 1e3)
-                     if "mac" in stats else None})
+                     "slot_macs_per_s": layer.slot_macs(False) * steps_prof / (stats["mac"]["total_ms"] / 1e3)
+                     if "mac" in stats and layer.slot_macs(False) else None})
 
     # end to end: host buffers through he_matmul_host (H2D + compute + D2H inside the region)
     e2e = None
@@ -864,6 +892,7 @@ def gpu_arm(args, world, rank, local):
     for c in layer.calls:
         blks.setdefault(c["p"].name, list(c["blk"]))
     layer_multi, n_calls = layer.multi, len(layer.calls)
+    tc_calls = [c for c in layer.calls if ctx.uses_tensor_cores(c["p"].k, c["blk"])]
     batched = batched_leg(B, ctx, flags) if world == 1 and not args.no_batched else None
 
     serving = None
@@ -885,6 +914,8 @@ def gpu_arm(args, world, rank, local):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": workload_config(args),
         "run": {"blockings_mkn": blks, "blocking_choice": args.blocking, "launch": args.launch,
+                "mac_engine": args.mac_engine,
+                "tensor_core_products": sum(c["cnt"] for c in tc_calls), 
                 "launch_groups_per_step": 1 if layer_multi else n_calls,
                 "ntt_values_per_thread": 1 << ctx.ntt_radix, "ntt_radix_choice": args.ntt_radix,
                 "ntt_radix_round_trip_ms": radix_ms, "cuda_graph": bool(use_graph),

@@ -201,7 +201,7 @@ Shape shape_of(u32 m, u32 k, u32 n, const he_blocking* b) {
 he::Blk to_blk(const he_blocking* b) { return {b->m_b, b->k_b, b->n_b}; }
 
 // Whether a product with nJ k-blocks uses the tensor-core multiply-accumulate (and its
-// slot-major operand layout) on this context: needs N >= 512; HE_MAC_AUTO takes it from
+// stage-tiled operand layout) on this context: needs N >= 512; HE_MAC_AUTO takes it from
 // kTcMinKBlocks k-blocks on, where the exact limb split amortises its digit split and
 // epilogue; HE_MAC_TENSOR for every product; HE_MAC_INTEGER never.
 constexpr u32 kTcMinKBlocks = 32;
@@ -210,8 +210,11 @@ bool use_tc(const he_ctx* c, u32 nJ) {
   return c->mac_engine == HE_MAC_TENSOR || nJ >= kTcMinKBlocks;
 }
 
-// k-blocks per operand row in memory: the tensor-core layout pads rows to an even count.
-u32 nJ_stored(const he_ctx* c, u32 nJ) { return use_tc(c, nJ) ? he::tc_nJp(nJ) : nJ; }
+// Words of a product's encoded weights (nI rows) and of the NTT of its inputs (2 nLb rows) in
+// the layout of its multiply-accumulate: the tensor-core one pads k-blocks to stages of 16.
+u64 operand_words(const he_ctx* c, u32 rows, u32 nJ) {
+  return use_tc(c, nJ) ? he::tc_words(rows, nJ, c->C.L, c->C.N) : (u64)rows * nJ * c->C.L * c->C.N;
+}
 
 }  // namespace
 
@@ -371,10 +374,9 @@ int he_sizes(const he_ctx* c, uint32_t m, uint32_t k, uint32_t n, const he_block
   out->pts = (u64)s.nI * s.nJ;
   out->in_words = out->in_cts * 2 * L * N;
   out->out_words = out->out_cts * 2 * L * N;
-  const u64 nJs = nJ_stored(c, s.nJ);
-  out->pt_words = (u64)s.nI * nJs * L * N;
+  out->pt_words = operand_words(c, s.nI, s.nJ);
   out->packed_words = out->in_cts * N;
-  const u64 ntt_words = (u64)s.nLb * nJs * 2 * L * N;  // NTT of the input ciphertexts (MAC layout)
+  const u64 ntt_words = operand_words(c, 2 * s.nLb, s.nJ);  // NTT of the input ciphertexts (MAC layout)
   out->workspace_bytes = ntt_words * sizeof(u64);
   const u64 Nc = pow2(blk->k_b) ? N / blk->k_b : 0;
   out->out_words_compact = Nc ? out->out_cts * L * (Nc + N) : 0;
@@ -613,7 +615,7 @@ static int matmul_device(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, u
   // compact output: per ciphertext [c0 at the decoded coefficients: L x N/k_b][c1: L x N]
   const u32 logkb = log2u(blk->k_b);
   const u64 Nc = N >> logkb, ct_stride = L * (Nc + N);
-  u64* c0_ntt = ctN + (u64)batch * s.nLb * nJ_stored(c, s.nJ) * 2 * L * N;  // after the inputs' NTT
+  u64* c0_ntt = ctN + (u64)batch * operand_words(c, 2 * s.nLb, s.nJ);  // after the inputs' NTT
   r = launch(c, tc ? KMacTc : KMac, st, "matmul: multiply-accumulate",
              [&] { return mac(c0_ntt, L * N, ct_out + L * Nc, ct_stride); });
   if (r) return r;
@@ -952,7 +954,7 @@ int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* w
     it.tilesR = (2 * s.nLb + rows_t - 1) / rows_t;
     it.tilesC = (s.nI + cols_t - 1) / cols_t;
     it.tc = use_tc(c, s.nJ);
-    const u64 in_words = (u64)s.nLb * nJ_stored(c, s.nJ) * 2 * L * N, out_cts = (u64)s.nLb * s.nI;
+    const u64 in_words = operand_words(c, 2 * s.nLb, s.nJ), out_cts = (u64)s.nLb * s.nI;
     off = (off + 255) & ~(u64)255;
     it.ctN = workspace ? (u64*)(workspace + off) : nullptr;
     off += in_words * 8;

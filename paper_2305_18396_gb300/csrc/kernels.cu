@@ -322,9 +322,9 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
   extern __shared__ u64 sm[];
   const u64 item_polys = (u64)nI * nJ * C.L;
   const u64 item = blockIdx.x / item_polys, poly = blockIdx.x % item_polys;
-  const u32 nJp = tc_nJp(nJ);
+  const u32 nS = tc_stages(nJ);
   W += item * k * n;
-  pt += item * (u64)nI * (tc ? nJp : nJ) * C.L * S::N;
+  pt += item * (tc ? tc_words(nI, nJ, C.L, S::N) : (u64)nI * nJ * C.L * S::N);
   const u32 l = poly % C.L;
   const u32 IJ = (u32)(poly / C.L);
   const u32 I = IJ / nJ, J = IJ % nJ;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
     return w >= half_t ? P.q - (C.tmask + 1 - w) : w;  // centred lift [-t/2, t/2)
   };
   if (tc)
-    ntt_forward_block<S>(sm, P, load, [&](u32 e, u64 v) { pt[tc_index(I, J, l, e, nJp, C.L, S::N)] = v; }, nk);
+    ntt_forward_block<S>(sm, P, load, [&](u32 e, u64 v) { pt[tc_index(I, J, l, e, nI, nS, S::N)] = v; }, nk);
   else
     ntt_forward_block<S>(sm, P, load,
                          [&](u32 e, u64 v) { pt[chunked_index(I, J, l, e, nJ, C.L, S::N)] = split_word(v); }, nk);
@@ -416,12 +416,12 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
   const u32 Lb = LbJ / nJ, J = LbJ % nJ;
   const PrimeConsts& P = C.p[l];
   const u64* sp = src + poly * S::N;
-  const u32 nJp = tc_nJp(nJ);
-  u64* dst = ctN + item * (u64)nLb * (tc ? nJp : nJ) * 2 * C.L * S::N;
+  const u32 nS = tc_stages(nJ);
+  u64* dst = ctN + item * (tc ? tc_words(2 * nLb, nJ, C.L, S::N) : (u64)nLb * nJ * 2 * C.L * S::N);
   const u64 row = (u64)Lb * 2 + c;
   if (tc)
     ntt_forward_block<S>(sm, P, [&](u32 e) { return sp[e]; },
-                         [&](u32 e, u64 v) { dst[tc_index(row, J, l, e, nJp, C.L, S::N)] = v; });
+                         [&](u32 e, u64 v) { dst[tc_index((u32)row, J, l, e, 2 * nLb, nS, S::N)] = v; });
   else
     ntt_forward_block<S>(sm, P, [&](u32 e) { return sp[e]; },
                          [&](u32 e, u64 v) { dst[chunked_index(row, J, l, e, nJ, C.L, S::N)] = split_word(v); });
@@ -435,8 +435,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_mac_tc(const u64* __restrict_
   extern __shared__ __align__(128) uint8_t smem_tc[];
   __shared__ TcShared sh;
   const u64 item = blockIdx.y;
-  const u32 nJp = tc_nJp(nJ);
-  const u64 per_in = (u64)nLb * nJp * 2 * C.L * C.N, per_pt = (u64)nI * nJp * C.L * C.N;
+  const u64 per_in = tc_words(2 * nLb, nJ, C.L, C.N), per_pt = tc_words(nI, nJ, C.L, C.N);
   const TcUnit u = tc_unit(blockIdx.x, C.N, nI, nLb);
   mac_tc_block(ctN + item * per_in, pt + item * per_pt, out, item * ((u64)nLb * nI), nI, nJ, nLb, u.I0, u.r0, u.s0,
                kTcSlots, u.l, err, C, smem_tc, sh);

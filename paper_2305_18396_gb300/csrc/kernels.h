@@ -36,8 +36,8 @@ cudaError_t launch_unmask_acc(const Consts& C, u64 seed, u32 m, u32 n, Blk b, u3
                               u64* out, cudaStream_t st);
 
 // Products come in batches of identical shape laid out back to back (batch = 1 for one).
-// tc: write the slot-major layout of the tensor-core multiply-accumulate (mac_tc.cuh) instead
-// of the slot-chunked one (per product nI * tc_nJp(nJ) * L * N words instead of nI * nJ * L * N).
+// tc: write the stage-tiled layout of the tensor-core multiply-accumulate (mac_tc.cuh) instead
+// of the slot-chunked one (per product tc_words(nI, nJ, L, N) words instead of nI * nJ * L * N).
 cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u32 batch,
                                   u32 tc, u64* pt, cudaStream_t st);
 // Slot-wise sum_J pt[I][J] * ctN[Lb][J] for every output (Lb, I), both components, all primes.
@@ -50,7 +50,7 @@ cudaError_t launch_ntt_forward_mm(const Consts& C, const u64* ct_in, u64* ctN, u
 // out_c + g * stride_c + l * N (NTT domain).
 cudaError_t launch_mac(const Consts& C, const u64* ctN, const u64* pt, u64* out0, u64 stride0, u64* out1, u64 stride1,
                        u32 nI, u32 nJ, u32 nLb, u32 batch, int* err, cudaStream_t st);
-// The same on the tensor cores, operands in the slot-major layout (mac_tc.cuh); N >= 512.
+// The same on the tensor cores, operands in the stage-tiled layout (mac_tc.cuh); N >= 512.
 cudaError_t launch_mac_tc(const Consts& C, const u64* ctN, const u64* pt, u64* out0, u64 stride0, u64* out1,
                           u64 stride1, u32 nI, u32 nJ, u32 nLb, u32 batch, int* err, cudaStream_t st);
 // Compact-output mode: in-place inverse NTT of the c1 polynomials (c1 of ciphertext g at

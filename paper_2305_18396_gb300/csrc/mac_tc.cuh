@@ -23,14 +23,19 @@
 // k-blocks; the first stage of a round overwrites (diagonals 0-6 by plane 0, diagonals 7-12
 // by an MMA against a zero tile).
 //
-// Operand layout ("slot-major"): word ((row * L + l) * N + s) * nJp + J for operand row
-// `row` (weight block I, resp. input row (Lb, c)), prime l, slot s and k-block J, with
-// nJp = nJ rounded up to even (16-byte aligned rows); plain residues (no split).  A block
-// works on SLOTS consecutive slots of one prime, one tile of 128 weight rows and one tile of
-// 16 ciphertext rows; per stage a producer warp copies 16 k-blocks of each operand row
-// (one 1-D bulk copy per row) into shared memory, four warps split them into digit planes
-// (bf16, the K-major no-swizzle layout of tcgen05.cuh), one thread issues the MMAs, and the
-// same four warps read the accumulators back after each round.
+// Operand layout ("stage-tiled"): plain residues (no split); for prime l, slot s and stage
+// js (k-blocks 16 js .. 16 js + 15) the 16 words of every operand row (weight block I,
+// resp. input row (Lb, c)) are 128 contiguous bytes, rows back to back:
+//   word ((((l N + s) nS + js) rows + row) 16 + chunk 2 + (J & 1),
+//   chunk = ((J & 15) / 2 + row) mod 8   (the 16-byte chunks rotated by the row),
+// nS = ceil(nJ / 16) stages, `rows` = nI for the weights and 2 nLb for the inputs.  A stage
+// of a block's 128 weight rows (16 ciphertext rows) is then one contiguous 16 KB (2 KB)
+// bulk copy, and the rotation keeps the digit split's shared-memory reads free of bank
+// conflicts.  A block works on kTcSlots consecutive slots of one prime, one tile of 128
+// weight rows and one tile of 16 ciphertext rows; per stage a producer warp copies the two
+// tiles into shared memory, four warps split them into digit planes (bf16, the K-major
+// no-swizzle layout of tcgen05.cuh), one thread issues the MMAs, and the same four warps
+// read the accumulators back after each round.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -51,7 +56,7 @@ constexpr u32 kTcRound = 8;      // stages per exact accumulation round (128 k-b
 constexpr u32 kTcSlots = 4;      // consecutive slots per block
 constexpr u32 kTcThreads = 192;  // warp 0 producer, warp 1 MMA, warps 2-5 digits + epilogue
 constexpr u32 kTcCols = 256;     // TMEM columns per block (208 used); two blocks per SM
-constexpr u32 kTcRawRow = kTcJB * 8 + 16;                     // bytes per staged operand row (padded)
+constexpr u32 kTcRawRow = kTcJB * 8;                          // bytes per staged operand row
 constexpr u32 kTcRawBytes = (kTcM + kTcR) * kTcRawRow;        // one raw stage
 constexpr u32 kTcAKBytes = kTcPlanes * kTcJB * 2;             // K bytes per weight row (7 planes)
 constexpr u32 kTcABytes = kTcM * kTcAKBytes;                  // weight digit tile
@@ -59,10 +64,15 @@ constexpr u32 kTcBBytes = kTcPlanes * kTcR * kTcJB * 2;       // ciphertext digi
 constexpr u32 kTcZBytes = (kTcDiag - kTcPlanes) * kTcR * kTcJB * 2;  // zero tile (96 rows)
 constexpr u32 kTcSmem = 2 * kTcRawBytes + 2 * kTcABytes + 2 * kTcBBytes + kTcZBytes + 128;
 
-__host__ __device__ constexpr u32 tc_nJp(u32 nJ) { return (nJ + 1) & ~1u; }
+// Stages of 16 k-blocks per slot, and words of an operand with `rows` rows in the
+// stage-tiled layout (all primes and slots).
+__host__ __device__ constexpr u32 tc_stages(u32 nJ) { return (nJ + kTcJB - 1) / kTcJB; }
+__host__ __device__ constexpr u64 tc_words(u32 rows, u32 nJ, u32 L, u32 N) {
+  return (u64)L * N * tc_stages(nJ) * rows * kTcJB;
+}
 
-__host__ __device__ constexpr u64 tc_index(u64 row, u32 J, u32 l, u32 s, u32 nJp, u32 L, u32 N) {
-  return ((row * L + l) * N + s) * (u64)nJp + J;
+__host__ __device__ constexpr u64 tc_index(u32 row, u32 J, u32 l, u32 s, u32 rows, u32 nS, u32 N) {
+  return ((((u64)l * N + s) * nS + (J >> 4)) * rows + row) * kTcJB + ((((J & 15) >> 1) + row) & 7) * 2 + (J & 1);
 }
 
 // x mod q for a signed 64-bit x (|x| < 2^63).
@@ -117,8 +127,7 @@ __device__ __forceinline__ void mac_tc_block(const u64* __restrict__ ctN, const 
   const PrimeConsts& P = C.p[l];
   const u32 R = 2 * nLb;
   const u32 nw = min(kTcM, nI - I0), nc = min(kTcR, R - r0);
-  const u32 nJp = tc_nJp(nJ);
-  const u32 sps = (nJ + kTcJB - 1) / kTcJB;  // stages per slot
+  const u32 sps = tc_stages(nJ);  // stages per slot
   const u32 total = sps * nslots;
 
   if (threadIdx.x == 0) {
@@ -159,17 +168,15 @@ __device__ __forceinline__ void mac_tc_block(const u64* __restrict__ ctN, const 
         break;
       }
       const u32 s = s0 + i / sps, J0 = (i % sps) * kTcJB;
-      const u32 jb = min(kTcJB, nJ - J0), bytes = ((jb + 1) & ~1u) * 8;
-      if (lane == 0) {
+      if (lane == 0) {  // two bulk copies: the block's weight rows and its ciphertext rows of this stage
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&sh.raw_full[b], (nw + nc) * bytes);
+        mbar_arrive_expect_tx(&sh.raw_full[b], (nw + nc) * kTcRawRow);
+        bulk_copy_g2s(raw0 + b * kTcRawBytes, pt + tc_index(I0, J0, l, s, nI, sps, N), nw * kTcRawRow,
+                      &sh.raw_full[b]);
+        bulk_copy_g2s(raw0 + b * kTcRawBytes + kTcM * kTcRawRow, ctN + tc_index(r0, J0, l, s, R, sps, N),
+                      nc * kTcRawRow, &sh.raw_full[b]);
       }
       __syncwarp();
-      for (u32 t = lane; t < nw + nc; t += 32) {
-        const bool w = t < nw;
-        const u64* src = w ? pt + tc_index(I0 + t, J0, l, s, nJp, L, N) : ctN + tc_index(r0 + (t - nw), J0, l, s, nJp, L, N);
-        bulk_copy_g2s(raw0 + b * kTcRawBytes + (w ? t : kTcM + (t - nw)) * kTcRawRow, src, bytes, &sh.raw_full[b]);
-      }
       issued = i + 1;
     }
     // copies still in flight must land before the block's shared memory is released
@@ -234,11 +241,11 @@ __device__ __forceinline__ void mac_tc_block(const u64* __restrict__ ctN, const 
         const u32 row = wrow ? (t & (kTcM - 1)) : ((t - 2 * kTcM) & (kTcR - 1));
         const u32 o = wrow ? (t >> 7) : ((t - 2 * kTcM) >> 4);
         if (row >= (wrow ? nw : nc)) continue;  // padding rows only feed outputs nobody stores
-        const uint8_t* src = raw0 + b * kTcRawBytes + (wrow ? row : kTcM + row) * kTcRawRow + o * 64;
+        const uint8_t* src = raw0 + b * kTcRawBytes + (wrow ? row : kTcM + row) * kTcRawRow;
         u64 u[8];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const uint4 x = *reinterpret_cast<const uint4*>(src + 16 * h);
+        for (int h = 0; h < 4; ++h) {  // chunk 4 o + h of the row sits at position (4 o + h + row) mod 8
+          const uint4 x = *reinterpret_cast<const uint4*>(src + 16 * ((4 * o + h + row) & 7));
           u[2 * h] = (u64)x.x | ((u64)x.y << 32);
           u[2 * h + 1] = (u64)x.z | ((u64)x.w << 32);
         }

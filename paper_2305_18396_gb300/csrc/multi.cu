@@ -47,9 +47,9 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
   const u64* sp = it.ct_in + local * S::N;
   const u64 row = (u64)Lb * 2 + c;
   if (it.tc) {
-    const u32 nJp = tc_nJp(it.nJ);
+    const u32 nS = tc_stages(it.nJ), rows = 2 * it.nLb;
     ntt_forward_block<S>(sm, C.p[l], [&](u32 e) { return sp[e]; },
-                         [&](u32 e, u64 v) { it.ctN[tc_index(row, J, l, e, nJp, C.L, S::N)] = v; });
+                         [&](u32 e, u64 v) { it.ctN[tc_index((u32)row, J, l, e, rows, nS, S::N)] = v; });
   } else {
     ntt_forward_block<S>(sm, C.p[l], [&](u32 e) { return sp[e]; },
                          [&](u32 e, u64 v) { it.ctN[chunked_index(row, J, l, e, it.nJ, C.L, S::N)] = split_word(v); });

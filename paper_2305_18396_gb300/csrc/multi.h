@@ -19,7 +19,7 @@ struct MultiItem {
   const u64* seed_dev;  // HE_SEED_DEVICE: the seed is read from here when the kernels run
   u64 fwd_begin, mac_begin, inv_begin, c0_begin, tc_begin;
   u32 nI, nJ, nLb, logkb;
-  u32 compact, tilesR, tilesC, tc;  // tc: operands in the slot-major layout, tensor-core MAC
+  u32 compact, tilesR, tilesC, tc;  // tc: operands in the stage-tiled layout, tensor-core MAC
 };
 
 struct MultiTable {

@@ -24,13 +24,14 @@ import sys
 import numpy as np
 
 
-def run_case(m, k, n, repeat=3, compact=True, logN=12, L=2, multi=False):
+def run_case(m, k, n, repeat=3, compact=True, logN=12, L=2, multi=False, engine=0):
     import torch
 
     from . import binding as B
     from . import synthetic as S
 
     ctx = B.Context(1 << logN, L)
+    ctx.set_mac_engine(engine)
     blk = ctx.default_blocking(m, k, n)
     X = torch.from_numpy(S.uniform_share((m, k), 1).view(np.int64).reshape(-1)).to(ctx.device)
     W = torch.from_numpy(S.fixed_point_weights((k, n), 2).view(np.int64).reshape(-1)).to(ctx.device)
@@ -128,6 +129,7 @@ def main(argv=None):
     c.add_argument("--logn", type=int, default=12, help="log2 N (12 or 13)")
     c.add_argument("--L", type=int, default=2, help="number of primes")
     c.add_argument("--multi", action="store_true", help="run through he_matmul_multi")
+    c.add_argument("--engine", type=int, default=0, help="0 auto, 1 integer, 2 tensor (he_set_mac_engine)")
     sh = sub.add_parser("share")
     sh.add_argument("m", type=int)
     sh.add_argument("k", type=int)
@@ -143,7 +145,7 @@ def main(argv=None):
     s.add_argument("--last", help="window ends at the last launch whose name contains this")
     a = ap.parse_args(argv)
     if a.cmd == "case":
-        blk, si = run_case(a.m, a.k, a.n, a.repeat, not a.full_c0, a.logn, a.L, a.multi)
+        blk, si = run_case(a.m, a.k, a.n, a.repeat, not a.full_c0, a.logn, a.L, a.multi, a.engine)
         print("ok", blk, si)
     elif a.cmd == "share":
         run_share_case(a.m, a.k, a.n, a.repeat)
