@@ -561,6 +561,8 @@ cudaError_t configure_kernels(const Consts&) {
   set((const void*)k_intt_mask, one);
   set((const void*)k_mac_ws_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
   set((const void*)k_mac_tc, (int)kTcSmem);
+  if (e == cudaSuccess)  // two blocks per SM need the largest shared-memory carveout
+    e = cudaFuncSetAttribute((const void*)k_mac_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 #define HE_SET_T(LN, LR, unused)                                                                    \
   {                                                                                                  \
     const int bytes = NttShape<LN, LR>::kSmemWords * (int)sizeof(u64);                               \

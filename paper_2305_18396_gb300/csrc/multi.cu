@@ -249,6 +249,8 @@ cudaError_t configure_multi_kernels() {
   set((const void*)k_c0_multi, 2 * one);
   set((const void*)k_mac_multi_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
   set((const void*)k_mac_tc_multi, (int)kTcSmem);
+  if (e == cudaSuccess)  // two blocks per SM need the largest shared-memory carveout
+    e = cudaFuncSetAttribute((const void*)k_mac_tc_multi, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 #define HE_SET_MULTI(LN, LR, unused)                                                                   \
   set((const void*)k_fwd_multi_t<LN, LR>, NttShape<LN, LR>::kSmemWords * (int)sizeof(u64));            \
   set((const void*)k_inv_multi_t<LN, LR>, NttShape<LN, LR>::kSmemWords * (int)sizeof(u64));            \
