@@ -427,18 +427,26 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
                          [&](u32 e, u64 v) { dst[chunked_index(row, J, l, e, nJ, C.L, S::N)] = split_word(v); });
 }
 
-// The tensor-core multiply-accumulate (mac_tc.cuh) of `batch` same-shape products:
-// blockIdx.x = work unit within a product, blockIdx.y = product.
-__global__ void __launch_bounds__(kTcThreads, 2) k_mac_tc(const u64* __restrict__ ctN, const u64* __restrict__ pt,
-                                                         OutPlace out, u32 nI, u32 nJ, u32 nLb, int* err,
-                                                         const __grid_constant__ Consts C) {
+// The tensor-core multiply-accumulate (mac_tc.cuh) of `batch` same-shape products: one block
+// per SM works through units * batch work units (product-major).
+__global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc(const u64* __restrict__ ctN, const u64* __restrict__ pt,
+                                                         OutPlace out, u32 nI, u32 nJ, u32 nLb, u64 units, u64 total,
+                                                         int* err, const __grid_constant__ Consts C) {
   extern __shared__ __align__(128) uint8_t smem_tc[];
   __shared__ TcShared sh;
-  const u64 item = blockIdx.y;
   const u64 per_in = tc_words(2 * nLb, nJ, C.L, C.N), per_pt = tc_words(nI, nJ, C.L, C.N);
-  const TcUnit u = tc_unit(blockIdx.x, C.N, nI, nLb);
-  mac_tc_block(ctN + item * per_in, pt + item * per_pt, out, item * ((u64)nLb * nI), nI, nJ, nLb, u.I0, u.r0, u.s0,
-               kTcSlots, u.l, err, C, smem_tc, sh);
+  auto get = [&](u64 g, TcWork& w) {
+    const u64 item = g / units;
+    tc_unit(g % units, C.N, nI, nLb, w);
+    w.ctN = ctN + item * per_in;
+    w.pt = pt + item * per_pt;
+    w.out = out;
+    w.ct0 = item * ((u64)nLb * nI);
+    w.nI = nI;
+    w.nJ = nJ;
+    w.nLb = nLb;
+  };
+  mac_tc_run(get, total, err, C, smem_tc, sh);
 }
 
 // Compact-output mode: inverse NTT of the c1 polynomials only, in place.  Ciphertext g's
@@ -510,6 +518,20 @@ __global__ void __launch_bounds__(kNttThreads) k_intt_mask(u64* out, u64 out_cts
   } else {
     for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) d[i] = sm[i];
   }
+}
+
+// ------------------------------------------------------------------ SM count of the current device
+
+int device_sms() {
+  static int cached[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+  if (!cached[dev]) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = sms > 0 ? sms : 1;
+  }
+  return cached[dev];
 }
 
 // ------------------------------------------------------------------ fixed scratch for he_matmul_noalloc
@@ -699,8 +721,9 @@ cudaError_t launch_mac_tc(const Consts& C, const u64* ctN, const u64* pt, u64* o
   o.ct_stride[1] = stride1;
   const u64 units = tc_units(C.N, C.L, nI, nLb);
   if (!units || !nJ || !batch) return cudaGetLastError();
-  if (C.logN < 9 || units >= (1ull << 31) || batch > 65535) return cudaErrorInvalidValue;
-  k_mac_tc<<<dim3((unsigned)units, batch), kTcThreads, kTcSmem, st>>>(ctN, pt, o, nI, nJ, nLb, err, C);
+  if (C.logN < 9) return cudaErrorInvalidValue;
+  const u64 total = units * batch, grid = std::min<u64>(total, (u64)device_sms());
+  k_mac_tc<<<(unsigned)grid, kTcThreads, kTcSmem, st>>>(ctN, pt, o, nI, nJ, nLb, units, total, err, C);
   return cudaGetLastError();
 }
 

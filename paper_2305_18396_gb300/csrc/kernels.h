@@ -85,6 +85,9 @@ cudaError_t launch_tc_check(const void* A, const void* B, void* D, uint32_t n, u
 // Runs one bounded wait on an mbarrier nothing completes (limit_ns), setting *err on expiry.
 cudaError_t launch_wait_timeout_check(uint64_t limit_ns, int* err, cudaStream_t st);
 
+// Streaming multiprocessors of the current device (cached per device).
+int device_sms();
+
 // Fixed device scratch of he_matmul_noalloc (no allocation at call time).
 constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
 constexpr int kMaxDevices = 64;

@@ -4,6 +4,8 @@
 // single grid over the union of all products' work.  A product descriptor table travels
 // as a kernel parameter; each block finds its product by binary search over per-kernel
 // prefix sums of block counts.
+#include <algorithm>
+
 #include "async.cuh"
 #include "kernels.h"
 #include "mac.cuh"
@@ -101,29 +103,37 @@ __global__ void __launch_bounds__(M::kThreads + 32, MINB) k_mac_multi_t(const __
   mac_tile_ws<M>(it.ctN, it.pt, out, 0, it.nI, it.nJ, it.nLb, r0, c0, chunk, l, err, C, sm);
 }
 
-// The tensor-core multiply-accumulate (mac_tc.cuh) over the products flagged tc: each block
-// finds its product and its work unit (prime, slot group, weight-row tile, row tile).
-__global__ void __launch_bounds__(kTcThreads, 2) k_mac_tc_multi(const __grid_constant__ MultiTable T, int* err,
-                                                               const __grid_constant__ Consts C) {
+// The tensor-core multiply-accumulate (mac_tc.cuh) over the products flagged tc: one block
+// per SM works through the launch's work units (product, prime, slot group, weight-row tile,
+// row tile) back to back; each unit's product is found by its offset tc_begin.
+__global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc_multi(const __grid_constant__ MultiTable T, u64 total,
+                                                               int* err, const __grid_constant__ Consts C) {
   extern __shared__ __align__(128) uint8_t smem_tc[];
   __shared__ TcShared sh;
-  const u32 i = find_item(T, blockIdx.x, [](const MultiItem& x) { return x.tc_begin; });
-  const MultiItem& it = T.it[i];
-  const TcUnit u = tc_unit(blockIdx.x - it.tc_begin, C.N, it.nI, it.nLb);
-  const u64 N = C.N, L = C.L;
-  OutPlace out;
-  if (it.compact) {
-    const u64 Nc = N >> it.logkb;
-    out.base[0] = it.c0_ntt;
-    out.ct_stride[0] = L * N;
-    out.base[1] = it.out + L * Nc;
-    out.ct_stride[1] = L * (Nc + N);
-  } else {
-    out.base[0] = it.out;
-    out.base[1] = it.out + L * N;
-    out.ct_stride[0] = out.ct_stride[1] = 2 * L * N;
-  }
-  mac_tc_block(it.ctN, it.pt, out, 0, it.nI, it.nJ, it.nLb, u.I0, u.r0, u.s0, kTcSlots, u.l, err, C, smem_tc, sh);
+  auto get = [&](u64 g, TcWork& w) {
+    const u32 i = find_item(T, g, [](const MultiItem& x) { return x.tc_begin; });
+    const MultiItem& it = T.it[i];
+    tc_unit(g - it.tc_begin, C.N, it.nI, it.nLb, w);
+    const u64 N = C.N, L = C.L;
+    w.ctN = it.ctN;
+    w.pt = it.pt;
+    w.ct0 = 0;
+    w.nI = it.nI;
+    w.nJ = it.nJ;
+    w.nLb = it.nLb;
+    if (it.compact) {
+      const u64 Nc = N >> it.logkb;
+      w.out.base[0] = it.c0_ntt;
+      w.out.ct_stride[0] = L * N;
+      w.out.base[1] = it.out + L * Nc;
+      w.out.ct_stride[1] = L * (Nc + N);
+    } else {
+      w.out.base[0] = it.out;
+      w.out.base[1] = it.out + L * N;
+      w.out.ct_stride[0] = w.out.ct_stride[1] = 2 * L * N;
+    }
+  };
+  mac_tc_run(get, total, err, C, smem_tc, sh);
 }
 
 // Inverse NTT of block b of the inverse grid: compact products transform their c1
@@ -280,8 +290,11 @@ cudaError_t launch_mac_multi(const Consts& C, const MultiTable& T, u64 blocks, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_mac_tc_multi(const Consts& C, const MultiTable& T, u64 blocks, int* err, cudaStream_t st) {
-  if (blocks) k_mac_tc_multi<<<(unsigned)blocks, kTcThreads, kTcSmem, st>>>(T, err, C);
+cudaError_t launch_mac_tc_multi(const Consts& C, const MultiTable& T, u64 units, int* err, cudaStream_t st) {
+  if (units) {
+    const u64 grid = std::min<u64>(units, (u64)device_sms());
+    k_mac_tc_multi<<<(unsigned)grid, kTcThreads, kTcSmem, st>>>(T, units, err, C);
+  }
   return cudaGetLastError();
 }
 

@@ -32,7 +32,8 @@ u32 mac_tile_rows();
 u32 mac_tile_cols();
 cudaError_t launch_fwd_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
 cudaError_t launch_mac_multi(const Consts& C, const MultiTable& T, u64 blocks, int* err, cudaStream_t st);
-// The tensor-core multiply-accumulate of the products flagged tc (blocks: their work units).
+// The tensor-core multiply-accumulate of the products flagged tc (units: their work units,
+// spread over one block per SM).
 cudaError_t launch_mac_tc_multi(const Consts& C, const MultiTable& T, u64 blocks, int* err, cudaStream_t st);
 cudaError_t launch_inv_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
 cudaError_t launch_c0_multi(const Consts& C, const MultiTable& T, u64 blocks, u32 c0_words, cudaStream_t st);
