@@ -210,10 +210,14 @@ bool use_tc(const he_ctx* c, u32 nJ) {
   return c->mac_engine == HE_MAC_TENSOR || nJ >= kTcMinKBlocks;
 }
 
-// Words of a product's encoded weights (nI rows) and of the NTT of its inputs (2 nLb rows) in
-// the layout of its multiply-accumulate: the tensor-core one pads k-blocks to stages of 16.
+// Words of the NTT of a product's inputs (2 nLb rows) and of its encoded weights (nI rows) in
+// the layout of its multiply-accumulate: the tensor-core one pads k-blocks to stages of 16 and
+// stores the weights as bf16 digit tiles.
 u64 operand_words(const he_ctx* c, u32 rows, u32 nJ) {
   return use_tc(c, nJ) ? he::tc_words(rows, nJ, c->C.L, c->C.N) : (u64)rows * nJ * c->C.L * c->C.N;
+}
+u64 weight_words(const he_ctx* c, u32 nI, u32 nJ) {
+  return use_tc(c, nJ) ? he::tc_weight_words(nI, nJ, c->C.L, c->C.N) : (u64)nI * nJ * c->C.L * c->C.N;
 }
 
 }  // namespace
@@ -374,7 +378,7 @@ int he_sizes(const he_ctx* c, uint32_t m, uint32_t k, uint32_t n, const he_block
   out->pts = (u64)s.nI * s.nJ;
   out->in_words = out->in_cts * 2 * L * N;
   out->out_words = out->out_cts * 2 * L * N;
-  out->pt_words = operand_words(c, s.nI, s.nJ);
+  out->pt_words = weight_words(c, s.nI, s.nJ);
   out->packed_words = out->in_cts * N;
   const u64 ntt_words = operand_words(c, 2 * s.nLb, s.nJ);  // NTT of the input ciphertexts (MAC layout)
   out->workspace_bytes = ntt_words * sizeof(u64);

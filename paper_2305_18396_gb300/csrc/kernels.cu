@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
   const u64 item = blockIdx.x / item_polys, poly = blockIdx.x % item_polys;
   const u32 nS = tc_stages(nJ);
   W += item * k * n;
-  pt += item * (tc ? tc_words(nI, nJ, C.L, S::N) : (u64)nI * nJ * C.L * S::N);
+  pt += item * (tc ? tc_weight_words(nI, nJ, C.L, S::N) : (u64)nI * nJ * C.L * S::N);
   const u32 l = poly % C.L;
   const u32 IJ = (u32)(poly / C.L);
   const u32 I = IJ / nJ, J = IJ % nJ;
@@ -339,8 +339,17 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
     u64 w = W[(u64)row * n + col] & C.tmask;
     return w >= half_t ? P.q - (C.tmask + 1 - w) : w;  // centred lift [-t/2, t/2)
   };
-  if (tc)
-    ntt_forward_block<S>(sm, P, load, [&](u32 e, u64 v) { pt[tc_index(I, J, l, e, nI, nS, S::N)] = v; }, nk);
+  if (tc) {  // the weights' digit tiles (mac_tc.cuh): seven bf16 digits per residue
+    uint8_t* const ptd = reinterpret_cast<uint8_t*>(pt);
+    ntt_forward_block<S>(sm, P, load, [&](u32 e, u64 v) {
+      const u64 u = v + 0x0080808080808080ull;
+      uint8_t* grp = ptd + tc_weight_offset(I & ~7u, l, e, J >> 4, nI, nS, S::N);
+#pragma unroll
+      for (int p = 0; p < (int)kTcPlanes; ++p)
+        *reinterpret_cast<uint16_t*>(grp + tc::tile_offset(I & 7, kTcJB * p + (J & 15), kTcAKBytes, 2)) =
+            (uint16_t)(digit_f32_bits(u, p) >> 16);
+    }, nk);
+  }
   else
     ntt_forward_block<S>(sm, P, load,
                          [&](u32 e, u64 v) { pt[chunked_index(I, J, l, e, nJ, C.L, S::N)] = split_word(v); }, nk);
@@ -434,12 +443,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc(const u64* __restrict_
                                                          int* err, const __grid_constant__ Consts C) {
   extern __shared__ __align__(128) uint8_t smem_tc[];
   __shared__ TcShared sh;
-  const u64 per_in = tc_words(2 * nLb, nJ, C.L, C.N), per_pt = tc_words(nI, nJ, C.L, C.N);
+  const u64 per_in = tc_words(2 * nLb, nJ, C.L, C.N), per_pt = tc_weight_words(nI, nJ, C.L, C.N);
   auto get = [&](u64 g, TcWork& w) {
     const u64 item = g / units;
     tc_unit(g % units, C.N, nI, nLb, w);
     w.ctN = ctN + item * per_in;
-    w.pt = pt + item * per_pt;
+    w.ptd = reinterpret_cast<const uint8_t*>(pt + item * per_pt);
     w.out = out;
     w.ct0 = item * ((u64)nLb * nI);
     w.nI = nI;
@@ -693,6 +702,10 @@ cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, B
   u64 polys = (u64)nI * nJ * C.L * batch;
   if (!polys) return cudaGetLastError();
   if (C.logN >= 9) {
+    if (tc) {  // digit tiles: k-blocks past the last and rows past nI must read as zero digits
+      cudaError_t e = cudaMemsetAsync(pt, 0, 8 * batch * tc_weight_words(nI, nJ, C.L, C.N), st);
+      if (e != cudaSuccess) return e;
+    }
     HE_DISPATCH_T(k_encode_weights_t, (unsigned)polys, st, W, k, n, b, nI, nJ, tc, pt, C)
   } else {
     if (tc) return cudaErrorInvalidValue;  // the tensor-core layout needs N >= 512

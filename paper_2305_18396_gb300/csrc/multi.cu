@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc_multi(const __grid_con
     tc_unit(g - it.tc_begin, C.N, it.nI, it.nLb, w);
     const u64 N = C.N, L = C.L;
     w.ctN = it.ctN;
-    w.pt = it.pt;
+    w.ptd = reinterpret_cast<const uint8_t*>(it.pt);
     w.ct0 = 0;
     w.nI = it.nI;
     w.nJ = it.nJ;
