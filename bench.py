@@ -287,15 +287,24 @@ class Layer:
         self.products = sum(c["cnt"] for c in self.calls)
         torch.cuda.synchronize()
 
-    def _multi_body(self):
+    def _multi_body(self, serial=False):
         """The per-step encodings of the server's shares, one per product shape, run side by
         side on their own streams (their small grids overlap instead of each draining
-        alone), joined before the whole-layer launch; a captured graph keeps the fork."""
+        alone), joined before the whole-layer launch; a captured graph keeps the fork.
+        serial: all on the current stream (the per-kernel timing pass, whose events on one
+        stream then time each kernel alone)."""
         B, ctx, torch = self.B, self.ctx, self.torch
         enc = [c for c in self.calls if "pt_step" in c]
         main = torch.cuda.current_stream()
         if not hasattr(self, "enc_streams"):
             self.enc_streams = [torch.cuda.Stream(device=ctx.device) for _ in enc]
+        if serial:
+            for c in enc:
+                p = c["p"]
+                B.he_encode_weights_batch(ctx, c["W"], p.k, p.n, c["blk"], c["cnt"], pt=c["pt_step"], stream=main)
+            for arr in self.prod_chunks:
+                B.he_matmul_multi(ctx, arr, self.multi_ws)
+            return
         for c, st in zip(enc, self.enc_streams):
             st.wait_stream(main)
             p = c["p"]
@@ -354,7 +363,7 @@ class Layer:
                     a.mask_seed = int(seeds[i])
             else:  # eager pass of a graph-mode layer: the products read device seeds
                 self.seeds_dev.copy_(self.torch.from_numpy(seeds).pin_memory(), non_blocking=True)
-            self._multi_body()
+            self._multi_body(serial=eager)
             return
         k = 0
         for c in self.calls:
@@ -808,7 +817,7 @@ def gpu_arm(args, world, rank, local):
     ms_per_step = total_ms / args.steps
     value = world * layer.macs * args.steps / (total_ms / 1e3)
 
-    # roofline: per-kernel event timing (separate pass, same steps)
+    # roofline: per-kernel event timing (separate pass, same steps, every kernel on one stream)
     B.he_profile_enable(ctx, True)
     steps_prof = max(3, min(args.steps, 10))
     for k in range(steps_prof):

@@ -122,12 +122,14 @@ HE_API int he_sizes(const he_ctx* ctx, uint32_t m, uint32_t k, uint32_t n, const
  * transform work (NTT of the input polynomials, inverse NTT of the outputs and, if
  * weights_per_call is non-zero -- weights encoded on every call, e.g. the server's
  * share in an attention product -- the NTT of the weights), multiply-accumulate
- * work divided by its output-tile fill, and algorithmic HBM bytes.  Ties go to the
- * larger m_b, then k_b. */
+ * work divided by its tile fill on the engine the context's setting (he_set_mac_engine)
+ * gives a blocking, and algorithmic HBM bytes (the tensor-core engine's weights in their
+ * 14-byte digit form).  Ties go to the larger m_b, then k_b. */
 HE_API int he_default_blocking(const he_ctx* ctx, uint32_t m, uint32_t k, uint32_t n, uint32_t weights_per_call,
                                he_blocking* out);
 
-/* The same choice without a context (no GPU needed): N a power of two, L >= 1. */
+/* The same choice without a context (no GPU needed), for the default engine
+ * (HE_MAC_AUTO): N a power of two, L >= 1. */
 HE_API int he_choose_blocking(uint32_t N, uint32_t L, uint32_t m, uint32_t k, uint32_t n, uint32_t weights_per_call,
                               he_blocking* out);
 

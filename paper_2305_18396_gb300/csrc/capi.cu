@@ -401,14 +401,19 @@ struct Candidate {
 //   transforms: 45 ns per length-4096 residue polynomial (scaled by N log N), counting the
 //     NTT of every input polynomial, the inverse NTT of every output polynomial and, when
 //     the weights are encoded per call, the NTT of every weight polynomial;
-//   multiply-accumulate: 0.8 ps per slot product, divided by the fill of the kernel's
-//     8-row x 8-column output tiles;
+//   multiply-accumulate on the integer pipe: 0.8 ps per slot product, divided by the fill of
+//     the kernel's 8-row x 8-column output tiles;
+//   multiply-accumulate on the tensor cores (where the engine puts the product there): 0.07
+//     ps per slot product divided by the fill of its 128-weight-row x 16-row work units,
+//     plus the weights' digit form (14 instead of 8 bytes per residue; when encoded per
+//     call also cleared and written in that form);
 //   memory: algorithmic bytes at 6.75 TB/s.
 // Ties go to the larger m_b, then the larger k_b.
-std::vector<Candidate> blocking_candidates(u32 Nw, u32 Lw, u32 m, u32 k, u32 n, u32 weights_per_call) {
+std::vector<Candidate> blocking_candidates(u32 Nw, u32 Lw, u32 m, u32 k, u32 n, u32 weights_per_call,
+                                           u32 engine = HE_MAC_AUTO) {
   const double N = Nw, L = Lw;
   const double t_poly = 45e-9 * (N * std::log2(N)) / (4096.0 * 12.0);
-  const double t_slot = 0.8e-12, hbm = 6.75e12;
+  const double t_slot = 0.8e-12, t_slot_tc = 0.07e-12, hbm = 6.75e12;
   auto cap = [&](u32 d) {
     u64 p = 1;
     while (p < d && p < Nw) p <<= 1;
@@ -424,10 +429,18 @@ std::vector<Candidate> blocking_candidates(u32 Nw, u32 Lw, u32 m, u32 k, u32 n, 
         if (nJ > 4096) continue;
         const double pts = nI * nJ, in = nLb * nJ, outc = nLb * nI;
         const double polys = 2 * L * in + 2 * L * outc + (weights_per_call ? L * pts : 0);
-        const double rows = 2 * nLb, fill = (rows / (8 * std::ceil(rows / 8))) * (nI / (8 * std::ceil(nI / 8)));
-        const double slots = nI * nJ * nLb * 2 * L * N;
-        const double bytes = 8 * N * L * (pts * (weights_per_call ? 3 : 1) + 6 * in + 4 * outc);
-        out.push_back({{(u32)mb, (u32)kb, (u32)nb}, polys * t_poly + slots * t_slot / fill + bytes / hbm});
+        const double rows = 2 * nLb, slots = nI * nJ * nLb * 2 * L * N;
+        const bool tc = Nw >= 512 && engine != HE_MAC_INTEGER && (engine == HE_MAC_TENSOR || nJ >= 32);
+        double bytes = 8 * N * L * (pts * (weights_per_call ? 3 : 1) + 6 * in + 4 * outc), mac;
+        if (tc) {
+          const double fill = (rows / (16 * std::ceil(rows / 16))) * (nI / (128 * std::ceil(nI / 128)));
+          mac = slots * t_slot_tc / fill;
+          bytes += N * L * pts * (weights_per_call ? 34 : 6);
+        } else {
+          const double fill = (rows / (8 * std::ceil(rows / 8))) * (nI / (8 * std::ceil(nI / 8)));
+          mac = slots * t_slot / fill;
+        }
+        out.push_back({{(u32)mb, (u32)kb, (u32)nb}, polys * t_poly + mac + bytes / hbm});
       }
   std::stable_sort(out.begin(), out.end(), [](const Candidate& a, const Candidate& b) {
     if (a.cost < b.cost * (1 - 1e-9)) return true;
@@ -450,8 +463,12 @@ int he_choose_blocking(uint32_t Nw, uint32_t Lw, uint32_t m, uint32_t k, uint32_
 
 int he_default_blocking(const he_ctx* c, uint32_t m, uint32_t k, uint32_t n, uint32_t weights_per_call,
                         he_blocking* out) {
-  if (!c) return fail(HE_EINVAL, "ctx is NULL");
-  return he_choose_blocking(c->C.N, c->C.L, m, k, n, weights_per_call, out);
+  if (!c || !out) return fail(HE_EINVAL, "NULL argument");
+  if (!pow2(c->C.N)) return fail(HE_EINVAL, "N must be a power of two");
+  const std::vector<Candidate> cand = blocking_candidates(c->C.N, c->C.L, m, k, n, weights_per_call, c->mac_engine);
+  if (cand.empty()) return fail(HE_EINVAL, "no blocking fits");
+  *out = cand.front().b;
+  return HE_OK;
 }
 
 int he_keygen(he_ctx* c, uint64_t seed, uint64_t* sk, void* stream) {
@@ -680,7 +697,7 @@ int he_autotune_blocking(he_ctx* c, uint32_t m, uint32_t k, uint32_t n, uint32_t
   if ((u64)(batch ? batch : 1) * c->C.L > 65535) return fail(HE_EINVAL, "batch * L must be <= 65535");
   batch = batch ? batch : 1;
   candidates = candidates ? std::min(candidates, 16u) : 6u;
-  std::vector<Candidate> all = blocking_candidates(c->C.N, c->C.L, m, k, n, weights_per_call);
+  std::vector<Candidate> all = blocking_candidates(c->C.N, c->C.L, m, k, n, weights_per_call, c->mac_engine);
   std::vector<he_blocking> cand;
   for (const Candidate& x : all) {
     if ((flags & HE_DROP_C0) && !pow2(x.b.k_b)) continue;
