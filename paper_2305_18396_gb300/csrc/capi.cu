@@ -212,7 +212,7 @@ bool use_tc(const he_ctx* c, u32 nJ) {
 
 // Words of the NTT of a product's inputs (2 nLb rows) and of its encoded weights (nI rows) in
 // the layout of its multiply-accumulate: the tensor-core one pads k-blocks to stages of 16 and
-// stores the weights as digit tiles (7 bytes per residue).
+// stores the weights as bf16 digit tiles.
 u64 operand_words(const he_ctx* c, u32 rows, u32 nJ) {
   return use_tc(c, nJ) ? he::tc_words(rows, nJ, c->C.L, c->C.N) : (u64)rows * nJ * c->C.L * c->C.N;
 }
@@ -405,8 +405,8 @@ struct Candidate {
 //     the kernel's 8-row x 8-column output tiles;
 //   multiply-accumulate on the tensor cores (where the engine puts the product there): 0.07
 //     ps per slot product divided by the fill of its 128-weight-row x 16-row work units,
-//     the weights in their digit form (7 instead of 8 bytes per residue; when encoded per
-//     call also filled and written in that form);
+//     plus the weights' digit form (14 instead of 8 bytes per residue; when encoded per
+//     call also cleared and written in that form);
 //   memory: algorithmic bytes at 6.75 TB/s.
 // Ties go to the larger m_b, then the larger k_b.
 std::vector<Candidate> blocking_candidates(u32 Nw, u32 Lw, u32 m, u32 k, u32 n, u32 weights_per_call,
@@ -435,7 +435,7 @@ std::vector<Candidate> blocking_candidates(u32 Nw, u32 Lw, u32 m, u32 k, u32 n, 
         if (tc) {
           const double fill = (rows / (16 * std::ceil(rows / 16))) * (nI / (128 * std::ceil(nI / 128)));
           mac = slots * t_slot_tc / fill;
-          bytes += N * L * pts * (weights_per_call ? 6 : -1);
+          bytes += N * L * pts * (weights_per_call ? 34 : 6);
         } else {
           const double fill = (rows / (8 * std::ceil(rows / 8))) * (nI / (8 * std::ceil(nI / 8)));
           mac = slots * t_slot / fill;

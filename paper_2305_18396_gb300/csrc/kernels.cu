@@ -339,13 +339,15 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
     u64 w = W[(u64)row * n + col] & C.tmask;
     return w >= half_t ? P.q - (C.tmask + 1 - w) : w;  // centred lift [-t/2, t/2)
   };
-  if (tc) {  // the weights' digit tiles (mac_tc.cuh): seven digit bytes (digit + 128) per residue
+  if (tc) {  // the weights' digit tiles (mac_tc.cuh): seven bf16 digits per residue
     uint8_t* const ptd = reinterpret_cast<uint8_t*>(pt);
     ntt_forward_block<S>(sm, P, load, [&](u32 e, u64 v) {
       const u64 u = v + 0x0080808080808080ull;
-      uint8_t* dst = ptd + tc_weight_offset(I & ~7u, l, e, J >> 4, nI, nS, S::N) + 16 * (I & 7) + (J & 15);
+      uint8_t* grp = ptd + tc_weight_offset(I & ~7u, l, e, J >> 4, nI, nS, S::N);
 #pragma unroll
-      for (int p = 0; p < (int)kTcPlanes; ++p) dst[128 * p] = (uint8_t)(u >> (8 * p));
+      for (int p = 0; p < (int)kTcPlanes; ++p)
+        *reinterpret_cast<uint16_t*>(grp + tc::tile_offset(I & 7, kTcJB * p + (J & 15), kTcAKBytes, 2)) =
+            (uint16_t)(digit_f32_bits(u, p) >> 16);
     }, nk);
   }
   else
@@ -700,8 +702,8 @@ cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, B
   u64 polys = (u64)nI * nJ * C.L * batch;
   if (!polys) return cudaGetLastError();
   if (C.logN >= 9) {
-    if (tc) {  // digit tiles: k-blocks past the last and rows past nI hold digit 0 (byte 128)
-      cudaError_t e = cudaMemsetAsync(pt, 0x80, 8 * batch * tc_weight_words(nI, nJ, C.L, C.N), st);
+    if (tc) {  // digit tiles: k-blocks past the last and rows past nI must read as zero digits
+      cudaError_t e = cudaMemsetAsync(pt, 0, 8 * batch * tc_weight_words(nI, nJ, C.L, C.N), st);
       if (e != cudaSuccess) return e;
     }
     HE_DISPATCH_T(k_encode_weights_t, (unsigned)polys, st, W, k, n, b, nI, nJ, tc, pt, C)

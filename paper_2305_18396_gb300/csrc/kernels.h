@@ -38,7 +38,7 @@ cudaError_t launch_unmask_acc(const Consts& C, u64 seed, u32 m, u32 n, Blk b, u3
 // Products come in batches of identical shape laid out back to back (batch = 1 for one).
 // tc: write the digit tiles of the tensor-core multiply-accumulate (mac_tc.cuh) instead of the
 // slot-chunked layout (per product tc_weight_words(nI, nJ, L, N) words instead of nI nJ L N;
-// the buffer is first filled with digit 0).
+// the buffer is cleared first).
 cudaError_t launch_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u32 batch,
                                   u32 tc, u64* pt, cudaStream_t st);
 // Slot-wise sum_J pt[I][J] * ctN[Lb][J] for every output (Lb, I), both components, all primes.

@@ -23,27 +23,26 @@
 // k-blocks; the first stage of a round overwrites (diagonals 0-6 by plane 0, diagonals 7-12
 // by an MMA against a zero tile).
 //
-// Operand layouts.  The encoded weights are stored already split, one byte per digit
-// ("digit tiles"): for prime l, slot s and stage js (k-blocks 16 js .. 16 js + 15), groups
-// of 8 weight rows of 7 x 16 bytes, byte (I, p, j) = digit p of k-block j + 128 at
-// (I / 8) 896 + 128 p + 16 (I mod 8) + j of the stage's tile (tiles back to back in (l, s, js)
-// order; k-blocks past the product's last and rows past nI hold 128, digit 0).  That is 7
-// bytes per residue (the integer engine's layout takes 8).  A work unit's 128 weight rows of
-// a stage are one contiguous bulk copy; on the SM each 16-byte chunk (16 k-blocks of one
-// digit plane of one row) widens to the 32 bytes of bf16 the MMA reads, in the K-major
-// no-swizzle layout of tcgen05.cuh.  The NTT of the input ciphertexts keeps plain residues
-// ("stage-tiled"): for prime l, slot s and stage js the 16 words of every input row (Lb, c)
-// are 128 contiguous bytes, rows back to back,
+// Operand layouts.  The encoded weights are stored split, as the bf16 digit planes the MMAs
+// read ("digit tiles"): for prime l, slot s and stage js (k-blocks 16 js .. 16 js + 15) all
+// weight rows I form one K-major no-swizzle tile of K = 7 planes x 16 k-blocks (element
+// (I, 16 p + j) at tc::tile_offset(I, 16 p + j, 224, 2)), tiles back to back in (l, s, js)
+// order, k-blocks past the product's last zero.  A work unit's 128 weight rows of a stage
+// are then one contiguous bulk copy straight into the MMA's operand buffer, with no split
+// on the SM (the weights are resident and encoded once; their digit form costs 14 bytes
+// per residue instead of 8).  The NTT of the input ciphertexts keeps plain residues
+// ("stage-tiled"): for prime l, slot s and stage js the 16 words of every input row
+// (Lb, c) are 128 contiguous bytes, rows back to back,
 //   word ((((l N + s) nS + js) rows + row) 16 + chunk 2 + (J & 1),
 //   chunk = ((J & 15) / 2 + row) mod 8   (the 16-byte chunks rotated by the row),
-// nS = ceil(nJ / 16), rows = 2 nLb, and the same warps split them into digit planes (the
-// rotation keeps those shared-memory reads free of bank conflicts).  A work unit is
-// kTcSlots consecutive slots of one prime, one tile of 128 weight rows and one tile of 16
-// input rows; per stage a producer warp issues the two bulk copies, eight warps widen and
-// split, one thread issues the MMAs, and four warps read the accumulators back after each
-// round while the MMAs of the next round fill the other of two accumulator sets.  One
-// block per SM works through its share of the launch's work units back to back, so the
-// pipeline never drains between units.
+// nS = ceil(nJ / 16), rows = 2 nLb; one warp splits a unit's 16 input rows into digit
+// planes per stage (the rotation keeps its shared-memory reads free of bank conflicts).
+// A work unit is kTcSlots consecutive slots of one prime, one tile of 128 weight rows and
+// one tile of 16 input rows; per stage a producer warp issues the two bulk copies, one
+// warp splits the input rows, one thread issues the MMAs, and four warps read the
+// accumulators back after each round while the MMAs of the next round fill the other of
+// two accumulator sets.  One block per SM works through its share of the launch's work
+// units back to back, so the pipeline never drains between units.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -62,25 +61,21 @@ constexpr u32 kTcDiag = 13;        // diagonals a + b
 constexpr u32 kTcJB = 16;          // k-blocks per stage (one MMA K step)
 constexpr u32 kTcRound = 8;        // stages per exact accumulation round (128 k-blocks)
 constexpr u32 kTcSlots = 8;        // consecutive slots per work unit
-constexpr u32 kTcRawStages = 4;    // bulk-copied stages in flight
-constexpr u32 kTcLimbStages = 2;   // widened / split stages (read by the MMAs)
-constexpr u32 kTcConvWarps = 8;    // widen the weight digits, split the input rows
+constexpr u32 kTcStages = 4;       // stages in flight
 constexpr u32 kTcEpiWarps = 4;     // epilogue: one per TMEM lane quadrant
-constexpr u32 kTcThreads = 32 * (2 + kTcConvWarps + kTcEpiWarps);  // + producer and MMA warps: 448
+constexpr u32 kTcThreads = 32 * (3 + kTcEpiWarps);  // producer, MMA, digit split, epilogue: 224
 constexpr u32 kTcCols = 512;       // TMEM: two accumulator sets of 13 x 16 columns, at 0 and 256
 constexpr u32 kTcSetCols = 256;
-constexpr u32 kTcWGroupBytes = 8 * kTcPlanes * kTcJB;         // 8 weight rows of byte digits
-constexpr u32 kTcWRawBytes = kTcM * kTcPlanes * kTcJB;        // a unit's weight digits of a stage
 constexpr u32 kTcRawRow = kTcJB * 8;                          // bytes per staged input row
-constexpr u32 kTcRawBytes = kTcWRawBytes + kTcR * kTcRawRow;  // one bulk-copied stage
-constexpr u32 kTcAKBytes = kTcPlanes * kTcJB * 2;             // K bytes per weight row (7 bf16 planes)
-constexpr u32 kTcGroupBytes = 8 * kTcAKBytes;                 // one 8-row group of the bf16 tile
-constexpr u32 kTcABytes = kTcM * kTcAKBytes;                  // weight bf16 tile of a unit
+constexpr u32 kTcRawBytes = kTcR * kTcRawRow;                 // one stage of input rows
+constexpr u32 kTcAKBytes = kTcPlanes * kTcJB * 2;             // K bytes per weight row (7 planes)
+constexpr u32 kTcGroupBytes = 8 * kTcAKBytes;                 // one 8-row group of a digit tile
+constexpr u32 kTcABytes = kTcM * kTcAKBytes;                  // weight digit tile of a unit
 constexpr u32 kTcBBytes = kTcPlanes * kTcR * kTcJB * 2;       // input digit tile (112 rows)
 constexpr u32 kTcZBytes = (kTcDiag - kTcPlanes) * kTcR * kTcJB * 2;  // zero tile (96 rows)
 constexpr u32 kTcAccBytes = kTcR * 32 * kTcEpiWarps * 8;     // the epilogue's running sums mod q
-constexpr u32 kTcSmem = kTcRawStages * kTcRawBytes + kTcLimbStages * (kTcABytes + kTcBBytes) + kTcZBytes +
-                        kTcAccBytes + 128;
+constexpr u32 kTcStageBytes = kTcABytes + kTcRawBytes + kTcBBytes;
+constexpr u32 kTcSmem = kTcStages * kTcStageBytes + kTcZBytes + kTcAccBytes + 128;
 
 // Stages of 16 k-blocks per slot; words of the inputs' NTT (`rows` rows, stage-tiled) and of
 // the weights' digit tiles (nI rows) for all primes and slots.
@@ -89,7 +84,7 @@ __host__ __device__ constexpr u64 tc_words(u32 rows, u32 nJ, u32 L, u32 N) {
   return (u64)L * N * tc_stages(nJ) * rows * kTcJB;
 }
 __host__ __device__ constexpr u64 tc_weight_words(u32 nI, u32 nJ, u32 L, u32 N) {
-  return (u64)L * N * tc_stages(nJ) * ((nI + 7) / 8) * kTcWGroupBytes / 8;
+  return (u64)L * N * tc_stages(nJ) * ((nI + 7) / 8) * kTcGroupBytes / 8;
 }
 
 __host__ __device__ constexpr u64 tc_index(u32 row, u32 J, u32 l, u32 s, u32 rows, u32 nS, u32 N) {
@@ -98,9 +93,9 @@ __host__ __device__ constexpr u64 tc_index(u32 row, u32 J, u32 l, u32 s, u32 row
 
 // Byte offset of the digit-tile group (8 weight rows from I0, a multiple of 8) of prime l,
 // slot s and stage js; digit p of k-block j of row I0 + i sits at that offset plus
-// 128 p + 16 i + j.
+// tc::tile_offset(i, 16 p + j, 224, 2).
 __host__ __device__ constexpr u64 tc_weight_offset(u32 I0, u32 l, u32 s, u32 js, u32 nI, u32 nS, u32 N) {
-  return ((((u64)l * N + s) * nS + js) * ((nI + 7) / 8) + (I0 >> 3)) * kTcWGroupBytes;
+  return ((((u64)l * N + s) * nS + js) * ((nI + 7) / 8) + (I0 >> 3)) * kTcGroupBytes;
 }
 
 // x mod q for a signed 64-bit x (|x| < 2^63).
@@ -115,33 +110,24 @@ __device__ __forceinline__ int f32_to_s32(uint32_t bits) {
   return r;
 }
 
-// The exact f32 bits of (byte k of x) - 128: the byte placed into the float 2^23 + byte
-// (one byte permute), minus 2^23 + 128.  Its bf16 is the high half of those bits (at most
-// 8 significant bits).
-__device__ __forceinline__ uint32_t digit_bits(uint32_t x, uint32_t k) {
-  return __float_as_uint(__uint_as_float(__byte_perm(x, 0x4B000000u, 0x7440u | k)) - 8388736.0f);
+// Digit p of u = v + 0x0080808080808080 (v < 2^50) as the bits of an exact f32: byte p of u
+// placed into the float 2^23 + byte (one byte permute), minus 2^23 + 128.  Its bf16 is the
+// high half of those bits (the digit has at most 8 significant bits).
+__device__ __forceinline__ uint32_t digit_f32_bits(u64 u, int p) {
+  const uint32_t src = p < 4 ? (uint32_t)u : (uint32_t)(u >> 32);
+  return __float_as_uint(__uint_as_float(__byte_perm(src, 0x4B000000u, 0x7440u | (uint32_t)(p & 3))) - 8388736.0f);
 }
 
-// Digit plane p of the 8 offset residues u[0..7] (u = v + 0x0080808080808080) as 8 bf16.
+// Digit plane p of the 8 offset residues u[0..7] as 8 bf16 (16 bytes).
 __device__ __forceinline__ uint4 digit_plane(const u64 (&u)[8], int p) {
   uint32_t h[4];
 #pragma unroll
-  for (int j = 0; j < 8; j += 2) {
-    const uint32_t a = p < 4 ? (uint32_t)u[j] : (uint32_t)(u[j] >> 32);
-    const uint32_t b = p < 4 ? (uint32_t)u[j + 1] : (uint32_t)(u[j + 1] >> 32);
-    h[j >> 1] = __byte_perm(digit_bits(a, p & 3), digit_bits(b, p & 3), 0x7632u);
-  }
+  for (int j = 0; j < 8; j += 2) h[j >> 1] = __byte_perm(digit_f32_bits(u[j], p), digit_f32_bits(u[j + 1], p), 0x7632u);
   return make_uint4(h[0], h[1], h[2], h[3]);
 }
 
-// 4 digit bytes (each digit + 128) -> 4 bf16 (8 bytes).
-__device__ __forceinline__ uint2 widen4(uint32_t x) {
-  return make_uint2(__byte_perm(digit_bits(x, 0), digit_bits(x, 1), 0x7632u),
-                    __byte_perm(digit_bits(x, 2), digit_bits(x, 3), 0x7632u));
-}
-
 struct TcShared {
-  uint64_t raw_full[kTcRawStages], raw_empty[kTcRawStages], limb_full[kTcLimbStages], limb_empty[kTcLimbStages];
+  uint64_t full[kTcStages], conv[kTcStages], empty[kTcStages];
   uint64_t acc_full[2], acc_empty[2], done;
   uint32_t tmem;
   int abort;
@@ -183,24 +169,19 @@ __device__ __forceinline__ void tc_unit(u64 u, u32 N, u32 nI, u32 nLb, TcWork& w
 template <class GetWork>
 __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* err, const Consts& C, uint8_t* smem,
                                            TcShared& sh) {
-  // raw stage b at raw0 + b kTcRawBytes (weight digit bytes, then the input rows); widened /
-  // split stage b: weight bf16 tile at At0 + b kTcABytes, input digit tile at Bt0 + b kTcBBytes
-  uint8_t* const raw0 = smem;
-  uint8_t* const At0 = raw0 + kTcRawStages * kTcRawBytes;
-  uint8_t* const Bt0 = At0 + kTcLimbStages * kTcABytes;
-  uint8_t* const Zt = Bt0 + kTcLimbStages * kTcBBytes;
+  // stage b: weight digit tile at st0 + b kTcStageBytes, then the raw input rows, then the
+  // input digit tile
+  uint8_t* const st0 = smem;
+  uint8_t* const Zt = smem + kTcStages * kTcStageBytes;
   u64* const accs = reinterpret_cast<u64*>(Zt + kTcZBytes);  // [output row r][epilogue thread]
   const u32 warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const u32 N = C.N;
 
   if (threadIdx.x == 0) {
-    for (u32 b = 0; b < kTcRawStages; ++b) {
-      mbar_init(&sh.raw_full[b], 1);
-      mbar_init(&sh.raw_empty[b], kTcConvWarps);
-    }
-    for (u32 b = 0; b < kTcLimbStages; ++b) {
-      mbar_init(&sh.limb_full[b], kTcConvWarps);
-      mbar_init(&sh.limb_empty[b], 1);
+    for (u32 b = 0; b < kTcStages; ++b) {
+      mbar_init(&sh.full[b], 1);
+      mbar_init(&sh.conv[b], 1);
+      mbar_init(&sh.empty[b], 1);
     }
     for (u32 b = 0; b < 2; ++b) {
       mbar_init(&sh.acc_full[b], 1);
@@ -234,29 +215,29 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
       get(g, w);
       const u32 sps = tc_stages(w.nJ), R = 2 * w.nLb;
       const u32 nw = min(kTcM, w.nI - w.I0), nc = min(kTcR, R - w.r0);
-      const u32 wbytes = ((nw + 7) / 8) * kTcWGroupBytes;
       for (u32 st = 0; st < kTcSlots * sps; ++st, ++i) {
-        const u32 b = i % kTcRawStages;
-        if (i >= kTcRawStages && !mbar_wait_warp(&sh.raw_empty[b], ((i / kTcRawStages) - 1) & 1, kWaitLimitNs)) {
+        const u32 b = i % kTcStages;
+        if (i >= kTcStages && !mbar_wait_warp(&sh.empty[b], ((i / kTcStages) - 1) & 1, kWaitLimitNs)) {
           give_up();
           ok = false;
           break;
         }
         const u32 s = w.s0 + st / sps, js = st % sps;
-        if (lane == 0) {  // two bulk copies: the unit's weight digit bytes and its raw input rows
-          uint8_t* dst = raw0 + b * kTcRawBytes;
+        if (lane == 0) {  // two bulk copies: the unit's weight digit rows and its raw input rows
+          uint8_t* dst = st0 + b * kTcStageBytes;
+          const u32 abytes = ((nw + 7) / 8) * kTcGroupBytes;
           fence_proxy_async_smem();
-          mbar_arrive_expect_tx(&sh.raw_full[b], wbytes + nc * kTcRawRow);
-          bulk_copy_g2s(dst, w.ptd + tc_weight_offset(w.I0, w.l, s, js, w.nI, sps, N), wbytes, &sh.raw_full[b]);
-          bulk_copy_g2s(dst + kTcWRawBytes, w.ctN + tc_index(w.r0, js * kTcJB, w.l, s, R, sps, N), nc * kTcRawRow,
-                        &sh.raw_full[b]);
+          mbar_arrive_expect_tx(&sh.full[b], abytes + nc * kTcRawRow);
+          bulk_copy_g2s(dst, w.ptd + tc_weight_offset(w.I0, w.l, s, js, w.nI, sps, N), abytes, &sh.full[b]);
+          bulk_copy_g2s(dst + kTcABytes, w.ctN + tc_index(w.r0, js * kTcJB, w.l, s, R, sps, N), nc * kTcRawRow,
+                        &sh.full[b]);
         }
         __syncwarp();
       }
     }
     // copies still in flight must land before the block's shared memory is released
-    for (u32 k = i > kTcRawStages ? i - kTcRawStages : 0; k < i; ++k)
-      mbar_wait_warp(&sh.raw_full[k % kTcRawStages], (k / kTcRawStages) & 1, kWaitLimitNs);
+    for (u32 k = i > kTcStages ? i - kTcStages : 0; k < i; ++k)
+      mbar_wait_warp(&sh.full[k % kTcStages], (k / kTcStages) & 1, kWaitLimitNs);
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issue
     const uint32_t id_main = tc::idesc_bf16_f32(kTcM, kTcPlanes * kTcR);
@@ -268,25 +249,27 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
       get(g, w);
       const u32 sps = tc_stages(w.nJ);
       for (u32 st = 0; st < kTcSlots * sps; ++st, ++i) {
-        const u32 j = st % sps, set = round & 1, b = i % kTcLimbStages;
+        const u32 j = st % sps, set = round & 1, b = i % kTcStages;
         const bool first = (j % kTcRound) == 0, last = (j == sps - 1) || ((j + 1) % kTcRound == 0);
         if ((first && round >= 2 && !mbar_wait_warp(&sh.acc_empty[set], ((round >> 1) - 1) & 1, kWaitLimitNs)) ||
-            !mbar_wait_warp(&sh.limb_full[b], (i / kTcLimbStages) & 1, kWaitLimitNs)) {
+            !mbar_wait_warp(&sh.full[b], (i / kTcStages) & 1, kWaitLimitNs) ||  // the weight tile landed
+            !mbar_wait_warp(&sh.conv[b], (i / kTcStages) & 1, kWaitLimitNs)) {  // the input tile is split
           give_up();
           ok = false;
           break;
         }
         tc::fence_after_sync();
         if (lane == 0) {
+          uint8_t* stage = st0 + b * kTcStageBytes;
           const uint32_t d = tmem + set * kTcSetCols;
-          const uint64_t bdesc = tc::smem_desc(Bt0 + b * kTcBBytes, 128, 256);
+          const uint64_t bdesc = tc::smem_desc(stage + kTcABytes + kTcRawBytes, 128, 256);
 #pragma unroll
           for (u32 a = 0; a < kTcPlanes; ++a) {
-            const uint64_t adesc = tc::smem_desc(At0 + b * kTcABytes + a * 256, 128, kTcGroupBytes);
+            const uint64_t adesc = tc::smem_desc(stage + a * 256, 128, kTcGroupBytes);
             tc::mma_bf16(d + a * kTcR, adesc, bdesc, id_main, (a > 0 || !first) ? 1u : 0u);
             if (a == 0 && first) tc::mma_bf16(d + kTcPlanes * kTcR, adesc, tc::smem_desc(Zt, 128, 256), id_zero, 0u);
           }
-          tc::commit(&sh.limb_empty[b]);
+          tc::commit(&sh.empty[b]);
           if (last) tc::commit(&sh.acc_full[set]);
         }
         __syncwarp();
@@ -296,74 +279,52 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
     if (lane == 0) tc::commit(&sh.done);  // every MMA issued has completed once this arrives
     __syncwarp();
     mbar_wait_warp(&sh.done, 0, kWaitLimitNs);
-  } else if (warp < 2 + kTcConvWarps) {
-    // ---------------------------------------------------------------- widen + split
-    const u32 e = threadIdx.x - 64;  // 0 .. 255
+  } else if (warp == 2) {
+    // ---------------------------------------------------------------- input digit planes
     u32 i = 0;
     bool ok = true;
     for (u64 g = blockIdx.x; ok && g < total && !*abort_flag; g += gridDim.x) {
       TcWork w;
       get(g, w);
-      const u32 sps = tc_stages(w.nJ), nw = min(kTcM, w.nI - w.I0), nc = min(kTcR, 2 * w.nLb - w.r0);
+      const u32 sps = tc_stages(w.nJ), nc = min(kTcR, 2 * w.nLb - w.r0);
       for (u32 st = 0; st < kTcSlots * sps; ++st, ++i) {
-        const u32 rb = i % kTcRawStages, lb = i % kTcLimbStages;
-        if (!mbar_wait_warp(&sh.raw_full[rb], (i / kTcRawStages) & 1, kWaitLimitNs) ||
-            (i >= kTcLimbStages && !mbar_wait_warp(&sh.limb_empty[lb], ((i / kTcLimbStages) - 1) & 1, kWaitLimitNs))) {
+        const u32 b = i % kTcStages, jb = min(kTcJB, w.nJ - (st % sps) * kTcJB);
+        if (!mbar_wait_warp(&sh.full[b], (i / kTcStages) & 1, kWaitLimitNs)) {
           give_up();
           ok = false;
           break;
         }
-        const uint8_t* raw = raw0 + rb * kTcRawBytes;
-        uint8_t* At = At0 + lb * kTcABytes;
-        // weight digits: 16-byte chunk (row, plane p) -> 32 bytes of bf16 (chunks 2p, 2p + 1)
-        for (u32 t = e; t < kTcM * kTcPlanes; t += 32 * kTcConvWarps) {
-          const u32 row = t & (kTcM - 1), p = t >> 7;
-          if (row >= nw) continue;  // padding rows only feed outputs nobody stores
-          const uint4 x = *reinterpret_cast<const uint4*>(raw + (row >> 3) * kTcWGroupBytes + 128 * p + 16 * (row & 7));
-          const uint2 a = widen4(x.x), b = widen4(x.y), c = widen4(x.z), d = widen4(x.w);
-          uint8_t* dst = At + (row >> 3) * kTcGroupBytes + 256 * p + 16 * (row & 7);
-          *reinterpret_cast<uint4*>(dst) = make_uint4(a.x, a.y, b.x, b.y);
-          *reinterpret_cast<uint4*>(dst + 128) = make_uint4(c.x, c.y, d.x, d.y);
-        }
-        // input rows: (row, octet of 8 k-blocks) -> 7 digit planes, on the last warp (one weight
-        // chunk fewer than the first four)
-        if (e >= 32 * kTcConvWarps - 2 * kTcR) {
-          const u32 ei = e - (32 * kTcConvWarps - 2 * kTcR);
-          const u32 row = ei & (kTcR - 1), o = ei >> 4;
-          const u32 jb = min(kTcJB, w.nJ - (st % sps) * kTcJB);
-          if (row < nc) {
-            const uint8_t* src = raw + kTcWRawBytes + row * kTcRawRow;
-            u64 u[8];
+        uint8_t* stage = st0 + b * kTcStageBytes;
+        const u32 row = lane & (kTcR - 1), o = lane >> 4;  // (input row, octet of 8 k-blocks)
+        if (row < nc) {
+          const uint8_t* src = stage + kTcABytes + row * kTcRawRow;
+          u64 u[8];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {  // chunk 4 o + h of the row sits at position (4 o + h + row) mod 8
-              const uint4 x = *reinterpret_cast<const uint4*>(src + 16 * ((4 * o + h + row) & 7));
-              u[2 * h] = (u64)x.x | ((u64)x.y << 32);
-              u[2 * h + 1] = (u64)x.z | ((u64)x.w << 32);
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              if (8 * o + k >= jb) u[k] = 0;  // k-blocks past the product's last: zero digits
-              u[k] += 0x0080808080808080ull;
-            }
-            uint8_t* bt = Bt0 + lb * kTcBBytes;
-#pragma unroll
-            for (int p = 0; p < (int)kTcPlanes; ++p)
-              *reinterpret_cast<uint4*>(bt + tc::tile_offset(p * kTcR + row, 8 * o, kTcJB * 2, 2)) = digit_plane(u, p);
+          for (int h = 0; h < 4; ++h) {  // chunk 4 o + h of the row sits at position (4 o + h + row) mod 8
+            const uint4 x = *reinterpret_cast<const uint4*>(src + 16 * ((4 * o + h + row) & 7));
+            u[2 * h] = (u64)x.x | ((u64)x.y << 32);
+            u[2 * h + 1] = (u64)x.z | ((u64)x.w << 32);
           }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            if (8 * o + k >= jb) u[k] = 0;  // k-blocks past the product's last: zero digits
+            u[k] += 0x0080808080808080ull;
+          }
+          uint8_t* bt = stage + kTcABytes + kTcRawBytes;
+#pragma unroll
+          for (int p = 0; p < (int)kTcPlanes; ++p)
+            *reinterpret_cast<uint4*>(bt + tc::tile_offset(p * kTcR + row, 8 * o, kTcJB * 2, 2)) = digit_plane(u, p);
         }
         tc::fence_smem_to_async();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&sh.raw_empty[rb]);
-          mbar_arrive(&sh.limb_full[lb]);
-        }
+        if (lane == 0) mbar_arrive(&sh.conv[b]);
       }
     }
   } else {
     // ---------------------------------------------------------------- epilogue
     const u32 q = warp & 3;        // TMEM lane quadrant this warp may read
     const u32 I = 32 * q + lane;   // weight row (TMEM lane) of this thread's outputs
-    u64* const acc = accs + (threadIdx.x - 32 * (2 + kTcConvWarps));  // acc[r * 128]: this thread's row-r sum
+    u64* const acc = accs + (threadIdx.x - 96);  // acc[r * 128]: this thread's sum of output row r
     u32 round = 0;
     bool ok = true;
     for (u64 g = blockIdx.x; ok && g < total && !*abort_flag; g += gridDim.x) {
