@@ -575,14 +575,15 @@ def serving_leg(B, ctx, args):
            "policy": "up to 2 launches in flight, a second one only while the first is estimated to end within 2 "
                      "ms; each on a stream of lower CUDA priority than those running; a launch "
                      "takes the oldest admitted request plus, in arrival order, requests whose estimated device "
-                     "time fits 1.25 x the oldest's (at least 1 ms), up to 8; admission by a 32 GiB device "
-                     "budget for outputs + workspace; outputs released on completion", "rates": {}}
+                     "time fits 1.25 x the oldest's (at least 1 ms) and every request of the oldest's weight "
+                     "matrix (merged into one product sharing the weight stream), up to 16; admission by a 32 GiB "
+                     "device budget for outputs + workspace; outputs released on completion", "rates": {}}
     for rate in [float(x) for x in args.serving_rates.split(",") if x]:
         res = {}
         count = max(100, min(args.serving_requests, int(rate * 10)))  # at most ~10 s of arrivals per path
         for name, fn, kw in (("per_request", SV.run_per_request, {"keep_outputs": False}),
                              ("continuous_batching", SV.run_served,
-                              {"slots": 2, "max_batch": 8, "keep_outputs": False})):
+                              {"slots": 2, "max_batch": 16, "keep_outputs": False})):
             reqs = SV.make_requests(models, count, rate)
             st, _ = fn(ctx, models, reqs, **kw)
             res[name] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}

@@ -942,13 +942,20 @@ struct MultiPlan {
 };
 
 // Validates the products and lays out the table; workspace may be NULL (size query).
+// Compact products (HE_DROP_C0) at N >= 512 that share their encoded weights, k, n and
+// blocking become one merged item: their row-blocks back to back, so every weight stage
+// of the multiply-accumulate serves all of their rows (requests of one weight matrix in a
+// serving batch); each keeps its own inputs, outputs, mask seed and output indices, and
+// its result is bit-identical to its own he_matmul call.
 int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* workspace, MultiPlan* P) {
   if (count > (u32)he::kMaxMulti) return fail(HE_EINVAL, "at most 64 products per multi-product launch");
   if (count && !items) return fail(HE_EINVAL, "items is NULL");
   const u64 N = c->C.N, L = c->C.L;
   const u32 rows_t = he::mac_tile_rows(), cols_t = he::mac_tile_cols();
-  P->T.count = 0;
-  u64 off = 0;
+  auto same_blk = [](const he_blocking& a, const he_blocking& b) {
+    return a.m_b == b.m_b && a.k_b == b.k_b && a.n_b == b.n_b;
+  };
+  std::vector<std::vector<u32>> groups;  // products of each launch item, in first-appearance order
   for (u32 i = 0; i < count; ++i) {
     const he_product& x = items[i];
     if (int r = check_blk(c, &x.blk)) return r;
@@ -958,15 +965,58 @@ int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* w
     if (compact && !pow2(x.blk.k_b)) return fail(HE_EINVAL, "HE_DROP_C0 needs a power-of-two k_b");
     if (!x.m || !x.k || !x.n) continue;
     if (!x.ct_in || !x.pt || !x.ct_out) return fail(HE_EINVAL, "NULL buffer in a product");
+    if (shape_of(x.m, x.k, x.n, &x.blk).nJ > 4096) return fail(HE_EINVAL, "at most 4096 k-blocks per product");
+    bool placed = false;
+    if (compact && c->C.logN >= 9) {
+      for (auto& g : groups) {
+        const he_product& y = items[g[0]];
+        if ((y.flags & HE_DROP_C0) && y.pt == x.pt && y.k == x.k && y.n == x.n && same_blk(y.blk, x.blk)) {
+          g.push_back(i);
+          placed = true;
+          break;
+        }
+      }
+    }
+    if (!placed) groups.push_back({i});
+  }
+  P->T.count = 0;
+  P->T.nseg = 0;
+  u64 off = 0;
+  auto take = [&](u64 bytes) -> u64* {
+    off = (off + 255) & ~(u64)255;
+    u64* ptr = workspace ? (u64*)(workspace + off) : nullptr;
+    off += bytes;
+    return ptr;
+  };
+  for (const auto& g : groups) {
+    const he_product& x = items[g[0]];
+    const bool compact = x.flags & HE_DROP_C0;
     Shape s = shape_of(x.m, x.k, x.n, &x.blk);
-    if (s.nJ > 4096) return fail(HE_EINVAL, "at most 4096 k-blocks per product");
     he::MultiItem& it = P->T.it[P->T.count++];
     memset(&it, 0, sizeof(it));
-    it.ct_in = x.ct_in;
     it.pt = x.pt;
-    it.out = x.ct_out;
-    it.mask_seed = x.mask_seed;
-    it.seed_dev = (x.flags & HE_SEED_DEVICE) ? reinterpret_cast<const u64*>((uintptr_t)x.mask_seed) : nullptr;
+    if (g.size() == 1) {
+      it.ct_in = x.ct_in;
+      it.out = x.ct_out;
+      it.mask_seed = x.mask_seed;
+      it.seed_dev = (x.flags & HE_SEED_DEVICE) ? reinterpret_cast<const u64*>((uintptr_t)x.mask_seed) : nullptr;
+    } else {
+      it.seg0 = P->T.nseg;
+      it.nseg = (u32)g.size();
+      u32 lb = 0;
+      for (u32 i : g) {
+        const he_product& y = items[i];
+        he::MultiSeg& sg = P->T.seg[P->T.nseg++];
+        sg.ct_in = y.ct_in;
+        sg.out = y.ct_out;
+        sg.mask_seed = y.mask_seed;
+        sg.seed_dev = (y.flags & HE_SEED_DEVICE) ? reinterpret_cast<const u64*>((uintptr_t)y.mask_seed) : nullptr;
+        sg.lb0 = lb;
+        sg.pad = 0;
+        lb += shape_of(y.m, y.k, y.n, &y.blk).nLb;
+      }
+      s.nLb = lb;
+    }
     it.nI = s.nI;
     it.nJ = s.nJ;
     it.nLb = s.nLb;
@@ -975,16 +1025,13 @@ int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* w
     it.tilesR = (2 * s.nLb + rows_t - 1) / rows_t;
     it.tilesC = (s.nI + cols_t - 1) / cols_t;
     it.tc = use_tc(c, s.nJ);
-    const u64 in_words = operand_words(c, 2 * s.nLb, s.nJ), out_cts = (u64)s.nLb * s.nI;
-    off = (off + 255) & ~(u64)255;
-    it.ctN = workspace ? (u64*)(workspace + off) : nullptr;
-    off += in_words * 8;
+    const u64 out_cts = (u64)s.nLb * s.nI;
+    it.ctN = take(operand_words(c, 2 * s.nLb, s.nJ) * 8);
     if (compact) {
-      off = (off + 255) & ~(u64)255;
-      it.c0_ntt = workspace ? (u64*)(workspace + off) : nullptr;
-      off += out_cts * L * N * 8;
+      it.c0_ntt = take(out_cts * L * N * 8);
       P->max_nc = std::max<u32>(P->max_nc, he::c0_smem_words((u32)N, it.logkb));
     }
+    if (it.nseg) it.c1_ntt = take(out_cts * L * N * 8);
     it.fwd_begin = P->fwd;
     it.mac_begin = P->mac;
     it.inv_begin = P->inv;

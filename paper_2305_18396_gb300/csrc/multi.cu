@@ -34,6 +34,15 @@ __device__ __forceinline__ u32 find_item(const MultiTable& T, u64 b, F begin) {
 // The item's mask seed: its value, or the word it points to (a seed that a replayed CUDA
 // graph takes fresh on every replay).
 __device__ __forceinline__ u64 item_seed(const MultiItem& it) { return it.seed_dev ? *it.seed_dev : it.mask_seed; }
+__device__ __forceinline__ u64 seg_seed(const MultiSeg& sg) { return sg.seed_dev ? *sg.seed_dev : sg.mask_seed; }
+
+// The segment of a merged item that holds row-block Lb (the last with lb0 <= Lb).
+__device__ __forceinline__ const MultiSeg& find_seg(const MultiTable& T, const MultiItem& it, u32 Lb) {
+  u32 s = it.seg0;
+  for (u32 k = 1; k < it.nseg; ++k)
+    if (T.seg[it.seg0 + k].lb0 <= Lb) s = it.seg0 + k;
+  return T.seg[s];
+}
 
 template <int LOGN, int LOGR>
 __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>::kMinBlocks) k_fwd_multi_t(const __grid_constant__ MultiTable T,
@@ -46,7 +55,13 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
   const u32 l = local % C.L, c = (local / C.L) % 2;
   const u32 LbJ = (u32)(local / (2 * C.L));
   const u32 Lb = LbJ / it.nJ, J = LbJ % it.nJ;
-  const u64* sp = it.ct_in + local * S::N;
+  const u64* sp;
+  if (it.nseg) {  // merged: the request's own input ciphertexts, wire format
+    const MultiSeg& sg = find_seg(T, it, Lb);
+    sp = sg.ct_in + ((((u64)(Lb - sg.lb0) * it.nJ + J) * 2 + c) * C.L + l) * S::N;
+  } else {
+    sp = it.ct_in + local * S::N;
+  }
   const u64 row = (u64)Lb * 2 + c;
   if (it.tc) {
     const u32 nS = tc_stages(it.nJ), rows = 2 * it.nLb;
@@ -89,7 +104,11 @@ __global__ void __launch_bounds__(M::kThreads + 32, MINB) k_mac_multi_t(const __
   const u32 r0 = (tile % it.tilesR) * M::kRows, c0 = (tile / it.tilesR) * M::kCols;
   const u64 N = C.N, L = C.L;
   OutPlace out;
-  if (it.compact) {
+  if (it.nseg) {  // merged: both components to the workspace, NTT domain
+    out.base[0] = it.c0_ntt;
+    out.base[1] = it.c1_ntt;
+    out.ct_stride[0] = out.ct_stride[1] = L * N;
+  } else if (it.compact) {
     const u64 Nc = N >> it.logkb;
     out.base[0] = it.c0_ntt;
     out.ct_stride[0] = L * N;
@@ -121,7 +140,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc_multi(const __grid_con
     w.nI = it.nI;
     w.nJ = it.nJ;
     w.nLb = it.nLb;
-    if (it.compact) {
+    if (it.nseg) {  // merged: both components to the workspace, NTT domain
+      w.out.base[0] = it.c0_ntt;
+      w.out.base[1] = it.c1_ntt;
+      w.out.ct_stride[0] = w.out.ct_stride[1] = L * N;
+    } else if (it.compact) {
       const u64 Nc = N >> it.logkb;
       w.out.base[0] = it.c0_ntt;
       w.out.ct_stride[0] = L * N;
@@ -145,7 +168,13 @@ __device__ __forceinline__ void inv_block(const MultiTable& T, const Consts& C, 
   const u64 local = b - it.inv_begin;
   const u64 N = S::N, L = C.L;
   const u32 l = local % L;
-  if (it.compact) {
+  if (it.nseg) {  // merged: c1 from the workspace to the request's compact output
+    const u64 Nc = N >> it.logkb, o = local / L;
+    const MultiSeg& sg = find_seg(T, it, (u32)(o / it.nI));
+    const u64* src = it.c1_ntt + o * L * N + l * N;
+    u64* d = sg.out + (o - (u64)sg.lb0 * it.nI) * L * (Nc + N) + L * Nc + l * N;
+    ntt_inverse_block<S>(sm, C.p[l], [&](u32 e) { return src[e]; }, [&](u32 e, u64 v) { d[e] = v; });
+  } else if (it.compact) {
     const u64 Nc = N >> it.logkb;
     u64* d = it.out + (local / L) * L * (Nc + N) + L * Nc + l * N;
     ntt_inverse_block<S>(sm, C.p[l], [&](u32 e) { return d[e]; }, [&](u32 e, u64 v) { d[e] = v; });
@@ -174,6 +203,13 @@ __device__ __forceinline__ void c0_block(const MultiTable& T, const Consts& C, u
   const u64 N = C.N, L = C.L, Nc = N >> it.logkb;
   const u32 l = local % L;
   const u32 o = (u32)(local / L);
+  if (it.nseg) {  // merged: the request's output and seed, its own output index
+    const MultiSeg& sg = find_seg(T, it, o / it.nI);
+    const u32 ol = o - sg.lb0 * it.nI;
+    ntt_inverse_c0_targets(it.c0_ntt + local * N, sg.out + (u64)ol * L * (Nc + N) + l * Nc, it.logkb, seg_seed(sg), ol,
+                           l, C, sm);
+    return;
+  }
   ntt_inverse_c0_targets(it.c0_ntt + local * N, it.out + (u64)o * L * (Nc + N) + l * Nc, it.logkb, item_seed(it), o, l,
                          C, sm);
 }

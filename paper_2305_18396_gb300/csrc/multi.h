@@ -7,8 +7,22 @@ namespace he {
 
 constexpr int kMaxMulti = 64;  // products per multi-product launch
 
-// One product of a multi-product launch.  *_begin: first block of this product in each
-// kernel's grid (prefix sums in product order).
+// One request of a merged launch item (below): its own inputs, outputs and mask seed, and
+// the first row-block it occupies in the item.
+struct MultiSeg {
+  const u64* ct_in;     // input ciphertexts, wire format
+  u64* out;             // compact output ciphertexts
+  u64 mask_seed;
+  const u64* seed_dev;  // HE_SEED_DEVICE: the seed is read from here when the kernels run
+  u32 lb0, pad;
+};
+
+// One item of a multi-product launch: a product, or (nseg > 0) several products that share
+// their encoded weights, shape and blocking, merged into one whose row-blocks are the
+// requests' row-blocks back to back -- every weight stage then serves all their rows.  A
+// merged item's multiply-accumulate writes both components to the workspace (c0_ntt,
+// c1_ntt); the inverse transforms write each request's compact output with its own seed.
+// *_begin: first block of this item in each kernel's grid (prefix sums in item order).
 struct MultiItem {
   const u64* ct_in;  // input ciphertexts, wire format
   const u64* pt;     // encoded weights (slot-chunked)
@@ -20,11 +34,14 @@ struct MultiItem {
   u64 fwd_begin, mac_begin, inv_begin, c0_begin, tc_begin;
   u32 nI, nJ, nLb, logkb;
   u32 compact, tilesR, tilesC, tc;  // tc: operands in the stage-tiled layout, tensor-core MAC
+  u64* c1_ntt;                       // workspace (merged items): NTT-domain c1 of every output
+  u32 seg0, nseg;                    // merged items: segments seg0 .. seg0 + nseg - 1
 };
 
 struct MultiTable {
-  u32 count, pad;
+  u32 count, nseg;
   MultiItem it[kMaxMulti];
+  MultiSeg seg[kMaxMulti];
 };
 
 cudaError_t configure_multi_kernels();

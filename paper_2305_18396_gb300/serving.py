@@ -15,7 +15,9 @@ form; requests arrive over time and are
   multi-product launch (he_matmul_multi, up to 64 products of any shapes), so requests
   that arrive while others are on the GPU join the next launch and their work overlaps
   on the device with the running one.  The cap keeps a long request from being delayed
-  by the requests that arrived after it;
+  by the requests that arrived after it.  Requests of the oldest's weight matrix join
+  regardless of the cap: the launch merges them into one product whose weight stream
+  serves all their rows;
 * started only while the work still in flight is estimated to end within an overlap
   window (2 ms): short launches overlap the next one, a long launch runs without a
   second one taking SMs at its kernel boundaries (requests arriving meanwhile are
@@ -136,19 +138,23 @@ def priority_levels(n=4):
     return [p for p in range(greatest, least + 1)][:n] or [0]
 
 
-def take_batch(admitted, max_batch, work_factor, floor_s, fifo=False):
+def take_batch(admitted, max_batch, work_factor, floor_s, fifo=False, merge_same_model=False):
     """Batch formation: the oldest admitted request plus, in arrival order, the requests
     whose estimated device time keeps the batch within max(floor_s, (1 + work_factor) x
     the oldest's estimate) (no cap with work_factor None), at most max_batch in all.  With
-    fifo the batch ends at the first request that does not fit (none is overtaken), else
-    later requests that fit are still taken.  Returns (batch, the requests left admitted)."""
+    merge_same_model, requests of the oldest's weight matrix join regardless of the cap:
+    the multi-product launch merges them into one product whose weight stream serves all
+    their rows, so they add little to the launch.  With fifo the batch ends at the first
+    request that does not fit (none is overtaken), else later requests that fit are still
+    taken.  Returns (batch, the requests left admitted)."""
     first = admitted[0]
     cap = max(floor_s, first.est * (1.0 + work_factor)) if work_factor is not None else math.inf
     batch, rest, total = [first], [], first.est
     for i, r in enumerate(admitted[1:], 1):
-        if len(batch) < max_batch and total + r.est <= cap:
+        same = merge_same_model and r.model == first.model
+        if len(batch) < max_batch and (same or total + r.est <= cap):
             batch.append(r)
-            total += r.est
+            total += 0.0 if same else r.est
         elif fifo:
             rest = list(admitted[i:])
             break
@@ -183,13 +189,14 @@ def withdraw(queue, admitted, rid):
 class Server:
     def __init__(self, ctx, models, flags=B.HE_DROP_C0, hbm_budget=32 << 30, slots=2, max_batch=8,
                  batch_work_factor=0.25, batch_floor_ms=1.0, priorities=True, keep_outputs=True,
-                 overlap_ms=2.0, fifo=False):
+                 overlap_ms=2.0, fifo=False, merge_same_model=True):
         self.ctx, self.models, self.flags = ctx, {mm.name: mm for mm in models}, flags
         self.budget, self.max_batch = hbm_budget, min(max_batch, 64)
         self.slots = slots
         self.work_factor, self.floor_s = batch_work_factor, batch_floor_ms * 1e-3
         self.overlap_s = overlap_ms * 1e-3
         self.fifo = fifo
+        self.merge = merge_same_model and bool(flags & B.HE_DROP_C0)  # the launch merges compact products only
         self.keep = keep_outputs
         levels = priority_levels() if priorities else [0]
         # a fixed set of streams, `slots` per priority level; buffers are allocated on the
@@ -243,7 +250,8 @@ class Server:
             self.admitted.append(r)
 
     def _take_batch(self):
-        batch, self.admitted = take_batch(self.admitted, self.max_batch, self.work_factor, self.floor_s, self.fifo)
+        batch, self.admitted = take_batch(self.admitted, self.max_batch, self.work_factor, self.floor_s, self.fifo,
+                                          self.merge)
         return batch
 
     def _may_launch(self, now):

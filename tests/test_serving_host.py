@@ -168,3 +168,16 @@ def test_mark_failed_without_error_marks_nothing():
     assert not a.failed and not b.failed
     SV.mark_failed([a], [b], True)
     assert a.failed and b.failed
+
+
+def test_take_batch_merges_requests_of_the_oldest_matrix_past_the_cap():
+    admitted = reqs(1e-3, 5e-3, 4e-3, 0.1e-3)
+    admitted[1].model = admitted[2].model = "y"
+    admitted[0].model = admitted[3].model = "x"
+    batch, rest = SV.take_batch(admitted, 8, 0.25, 1e-3, merge_same_model=True)
+    assert [r.rid for r in batch] == [0, 3] and [r.rid for r in rest] == [1, 2]
+    big = reqs(1e-3, 9e-3, 9e-3, 9e-3)
+    batch, rest = SV.take_batch(big, 3, 0.25, 1e-3, merge_same_model=True)  # same matrix: past the cap, up to max_batch
+    assert [r.rid for r in batch] == [0, 1, 2] and [r.rid for r in rest] == [3]
+    batch, rest = SV.take_batch(big, 3, 0.25, 1e-3)  # without merging the cap holds
+    assert [r.rid for r in batch] == [0] and len(rest) == 3
