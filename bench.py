@@ -251,28 +251,33 @@ class Layer:
             self.multi_ws = ctx.empty(max(B.he_multi_workspace_bytes(ctx, arr) for arr in self.prod_chunks) // 8 + 1)
             # seed of item b of launch group c on step s: (s << 20) + idx_c + b
             self.seed_offs = np.array([c["idx"] + b for c in self.calls for b in range(c["cnt"])], dtype=np.int64)
-        # host-buffer steps of the whole-layer launch: `host_depth` streams, each with its own
-        # device workspace, per-step share encodings and pinned output buffers (inputs are
-        # shared, read-only); consecutive steps rotate over the streams so one step's uploads
-        # and downloads overlap the others' kernels
-        self.host_sets, self.host_k = [], 0
+        # host-buffer steps of the whole-layer launch through an he_pipe: uploads, kernels and
+        # downloads of consecutive steps overlap on the pipe's three streams over `host_depth`
+        # staging slots; inputs are shared (read-only), each slot's step downloads into its
+        # own pinned output buffers, and the server's per-step shares are encoded on the
+        # pipe's compute stream (in order with its launches) into one set of buffers
+        self.pipe, self.host_sets, self.host_k = None, [], 0
         if multi and want_host:
+            self.pipe = B.Pipe(ctx, depth=host_depth)
+            pt_bufs = {}
             for sidx in range(host_depth):
-                items, pt_bufs = [], {}
+                items = []
                 for c in self.calls:
                     p, si, cnt = c["p"], c["si"], c["cnt"]
                     pt_all = c.get("pt")
                     if pt_all is None:
-                        pt_all = pt_bufs[c["idx"]] = ctx.empty(cnt * si["pt_words"])
+                        if c["idx"] not in pt_bufs:
+                            pt_bufs[c["idx"]] = ctx.empty(cnt * si["pt_words"])
+                        pt_all = pt_bufs[c["idx"]]
                     out_h = torch.empty(cnt * si["out"], dtype=torch.int64).pin_memory()
                     for b in range(cnt):
                         items.append(dict(ct_in=c["in_host"][b * si["in_words"]:(b + 1) * si["in_words"]],
                                           pt=pt_all[b * si["pt_words"]:(b + 1) * si["pt_words"]],
                                           ct_out=out_h[b * si["out"]:(b + 1) * si["out"]], m=p.m, k=p.k, n=p.n,
                                           blk=c["blk"], flags=flags, mask_seed=0, keep=out_h))
-                chunks_h = [B.make_products(items[i:i + 64]) for i in range(0, len(items), 64)]
-                ws_h = ctx.empty(max(B.he_multi_host_workspace_bytes(ctx, arr) for arr in chunks_h) // 8 + 1)
-                self.host_sets.append((chunks_h, ws_h, pt_bufs, items))
+                self.host_sets.append((B.make_products(items), items))
+            self.pipe_pt = pt_bufs
+            self.pipe_ws = ctx.empty(self.pipe.workspace_bytes(self.host_sets[0][0]) // 8 + 1)
         self.graph, self.graph_kernels = None, 0
         if multi and graph:  # the replayed graph reads every product's mask seed from device memory
             self.seeds_dev = torch.zeros(len(self.prods), dtype=torch.int64, device=dev)
@@ -333,23 +338,20 @@ class Layer:
 
     def step(self, step_idx, host=False, eager=False):
         B, ctx = self.B, self.ctx
-        if self.multi and host:
+        if self.multi and host:  # enqueue only: the caller waits with self.pipe.wait()
             k = self.host_k
             self.host_k = (k + 1) % len(self.host_sets)
-            chunks_h, ws_h, pt_bufs, _ = self.host_sets[k]
-            st = self.host_streams[k]
+            arr, _ = self.host_sets[k]
+            st = self.pipe.compute_stream
             for c in self.calls:
-                if c["idx"] in pt_bufs:
+                if c["idx"] in self.pipe_pt:
                     p = c["p"]
-                    B.he_encode_weights_batch(ctx, c["W"], p.k, p.n, c["blk"], c["cnt"], pt=pt_bufs[c["idx"]],
+                    B.he_encode_weights_batch(ctx, c["W"], p.k, p.n, c["blk"], c["cnt"], pt=self.pipe_pt[c["idx"]],
                                               stream=st)
             seeds = (step_idx << 20) + self.seed_offs
-            i = 0
-            for arr in chunks_h:
-                for a in arr:
-                    a.mask_seed = int(seeds[i])
-                    i += 1
-                B.he_matmul_multi_host(ctx, arr, ws_h, flags=B.HE_ASYNC, stream=st)
+            for i, a in enumerate(arr):
+                a.mask_seed = int(seeds[i])
+            self.pipe.submit(arr, self.pipe_ws)
             return
         if self.multi and not host:
             seeds = (step_idx << 20) + self.seed_offs
@@ -883,14 +885,18 @@ def gpu_arm(args, world, rank, local):
     if want_host:
         h2d = sum(8 * c["cnt"] * c["si"]["in_words"] for c in layer.calls)
         d2h = sum(8 * c["cnt"] * c["si"]["out"] for c in layer.calls)
-        for w in range(max(2, len(layer.host_sets))):  # every stream's buffers once before timing
+        for w in range(max(2, len(layer.host_sets))):  # every slot's buffers once before timing
             layer.step(9000 + w, host=True)
+        if layer.pipe is not None:
+            layer.pipe.wait()
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ksteps = max(1, min(args.steps, 40))
         for k in range(ksteps):
             layer.step(9100 + k, host=True)
+        if layer.pipe is not None:
+            layer.pipe.wait()
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, world, device=f"cuda:{local}")
         e2e = {"value": world * layer.macs * ksteps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,

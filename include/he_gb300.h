@@ -333,6 +333,48 @@ HE_API int he_matmul_multi_host(he_ctx* ctx, uint32_t count, const he_product* i
                                 size_t workspace_bytes, void* stream);
 HE_API int he_multi_host_workspace_bytes(const he_ctx* ctx, uint32_t count, const he_product* items, size_t* bytes);
 
+/* Overlapped host-buffer execution of multi-product launches: a server's transfer
+ * pipeline (the paper has no counterpart; it moves the ciphertexts of Algorithm 1 steps 2
+ * and 4 between host and device).  A pipe owns three CUDA streams -- uploads, compute,
+ * downloads -- and cycles through `depth` staging slots of the caller's workspace.  Each
+ * he_pipe_submit enqueues
+ *   - on the upload stream, one host-to-device copy per product input into the next slot,
+ *     after the launch that last used that slot has finished reading it;
+ *   - on the compute stream, the multi-product launch (as he_matmul_multi), after those
+ *     copies and after the downloads that last read the slot's outputs;
+ *   - on the download stream, one device-to-host copy per product output, after the launch.
+ * Each queue runs in submission order, so consecutive submits overlap one's uploads with
+ * another's kernels and a third's downloads (an upload of a later submit never competes
+ * with the one the next launch waits for).  Nothing blocks but he_pipe_wait.
+ * The pipe's streams do not wait for other streams: what the launches read (encoded
+ * weights, seeds in device memory) must be complete, or enqueued on the compute stream,
+ * before the submit.
+ * Ownership: the pipe owns its streams and events (he_pipe_free); the caller owns the
+ * workspace and the host buffers and keeps them alive and unchanged (inputs) or unread
+ * (outputs) until he_pipe_wait returns.  Host buffers should be pinned (pageable copies
+ * are synchronous and serialize the pipeline).  Errors: HE_EINVAL for a NULL argument,
+ * depth 0 or > 16; HE_ENOMEM for a workspace below he_pipe_workspace_bytes(); HE_ECUDA for a
+ * failed enqueue; kernels' expired waits are reported by he_device_status. */
+typedef struct he_pipe he_pipe;
+HE_API int he_pipe_create(he_ctx* ctx, uint32_t depth, he_pipe** pipe);
+HE_API int he_pipe_free(he_pipe* pipe);
+/* The pipe's compute stream: work the caller enqueues there (e.g. encoding the server's
+ * per-request shares for the next submit) is ordered with the pipe's launches. */
+HE_API int he_pipe_compute_stream(he_pipe* pipe, void** stream);
+/* Device workspace for submits of these products: depth slots, each the largest
+ * multi-product workspace of the launches (64 products each) plus every staged input and
+ * output. */
+HE_API int he_pipe_workspace_bytes(const he_pipe* pipe, uint32_t count, const he_product* items, size_t* bytes);
+/* items: any number of products with HOST ct_in / ct_out (device pt; flags and mask seeds
+ * as in he_matmul_multi), run as consecutive multi-product launches of up to 64 products.
+ * workspace: device, the same on every submit of this pipe; slot i is
+ * [i * slot, (i + 1) * slot) with slot = workspace_bytes / depth rounded down to 256 bytes,
+ * and depth * slot must be >= he_pipe_workspace_bytes(pipe, count, items). */
+HE_API int he_pipe_submit(he_pipe* pipe, uint32_t count, const he_product* items, void* workspace,
+                          size_t workspace_bytes);
+/* Blocks until every submitted product's outputs are in host memory. */
+HE_API int he_pipe_wait(he_pipe* pipe);
+
 /* he_matmul for callers that cannot allocate device memory.  Some callers have no
  * way to obtain a workspace: a serving process whose device memory is already
  * reserved by another allocator (where cudaMalloc would fail, or would stall the

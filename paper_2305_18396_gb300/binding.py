@@ -105,6 +105,12 @@ def _load():
         "he_share_matmul": (ctypes.c_int, [P, P, P, P, P, u32, u32, u32, P, P]),
         "he_share_matmul_batch": (ctypes.c_int, [P, P, P, P, P, u32, u32, u32, u32, P, P]),
         "he_matmul_multi_host": (ctypes.c_int, [P, u32, ctypes.POINTER(Product), u32, P, sz, P]),
+        "he_pipe_create": (ctypes.c_int, [P, u32, ctypes.POINTER(P)]),
+        "he_pipe_free": (ctypes.c_int, [P]),
+        "he_pipe_compute_stream": (ctypes.c_int, [P, ctypes.POINTER(P)]),
+        "he_pipe_submit": (ctypes.c_int, [P, u32, ctypes.POINTER(Product), P, sz]),
+        "he_pipe_workspace_bytes": (ctypes.c_int, [P, u32, ctypes.POINTER(Product), ctypes.POINTER(sz)]),
+        "he_pipe_wait": (ctypes.c_int, [P]),
         "he_multi_host_workspace_bytes": (ctypes.c_int, [P, u32, ctypes.POINTER(Product), ctypes.POINTER(sz)]),
         "he_expand_compact": (ctypes.c_int, [P, P, u32, u32, P, P]),
         "he_ct_export": (ctypes.c_int, [P, P, u32, u32, P, P]),
@@ -356,8 +362,11 @@ def he_matmul_batch(ctx, ct_in, pt, m, k, n, blk, batch, mask_seed, ct_out=None,
 
 
 def make_products(items):
-    """items: dicts with ct_in, pt, ct_out (device tensors), m, k, n, blk, flags, mask_seed."""
+    """items: dicts with ct_in, pt, ct_out (device tensors), m, k, n, blk, flags, mask_seed.
+    The returned descriptor array holds references to the tensors, so buffers made only for
+    the call stay allocated while the array is alive."""
     arr = (Product * len(items))()
+    arr._tensors = [(x["ct_in"], x["pt"], x["ct_out"]) for x in items]
     for a, x in zip(arr, items):
         a.ct_in, a.pt, a.ct_out = x["ct_in"].data_ptr(), x["pt"].data_ptr(), x["ct_out"].data_ptr()
         a.m, a.k, a.n = x["m"], x["k"], x["n"]
@@ -388,6 +397,45 @@ def he_matmul_multi_host(ctx, products, workspace, flags=HE_FLAGS_NONE, stream=N
     """products: from make_products with HOST (preferably pinned) ct_in / ct_out tensors."""
     _check(lib.he_matmul_multi_host(ctx.h, len(products), products, flags, _ptr(workspace), workspace.numel() * 8,
                                     _stream(stream)))
+
+
+class Pipe:
+    """Owns an he_pipe: multi-product launches from host buffers with uploads, kernels and
+    downloads of consecutive submits overlapped on three streams, over `depth` slots of
+    one device workspace."""
+
+    def __init__(self, ctx, depth=3):
+        h = ctypes.c_void_p()
+        _check(lib.he_pipe_create(ctx.h, depth, ctypes.byref(h)))
+        self.h, self.ctx, self.depth = h, ctx, depth
+        st = ctypes.c_void_p()
+        _check(lib.he_pipe_compute_stream(h, ctypes.byref(st)))
+        self.compute_stream = torch.cuda.ExternalStream(st.value, device=ctx.device)
+
+    def workspace_bytes(self, products):
+        """Device workspace for submits of these products (depth slots)."""
+        out = ctypes.c_size_t()
+        _check(lib.he_pipe_workspace_bytes(self.h, len(products), products, ctypes.byref(out)))
+        return out.value
+
+    def submit(self, products, workspace):
+        """products: from make_products with HOST (pinned) ct_in / ct_out tensors; keep them
+        alive until wait()."""
+        _check(lib.he_pipe_submit(self.h, len(products), products, _ptr(workspace), workspace.numel() * 8))
+
+    def wait(self):
+        _check(lib.he_pipe_wait(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.he_pipe_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def he_matmul(ctx, ct_in, pt, m, k, n, blk, mask_seed, ct_out=None, workspace=None, flags=HE_FLAGS_NONE,

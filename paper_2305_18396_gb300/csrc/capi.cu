@@ -291,6 +291,14 @@ int he_params_init(he_ctx** out, uint32_t N, uint32_t L, const uint64_t* q, uint
     P.r50_sh = shoup(P.r50, ql);
     P.r64 = (u64)(((u128)1 << 64) % ql);
     P.r64_sh = shoup(P.r64, ql);
+    u64 pw = 1, pw_sum = 0;
+    for (u32 d = 0; d < 13; ++d) {  // 256^d mod q < 2^50: high halves below 2^18
+      P.pw256_lo[d] = (uint32_t)pw;
+      P.pw256_hi[d] = (uint32_t)(pw >> 32);
+      pw_sum = (pw_sum + pw) % ql;
+      pw = mulm(pw, 256, ql);
+    }
+    P.pw256_bias = mulm((1ull << 24) % ql, pw_sum, ql);
     u64 Ml = 1;
     for (u32 j = 0; j < L; ++j)
       if (j != l) Ml = mulm(Ml, q[j] % ql, ql);
@@ -1158,6 +1166,163 @@ int he_matmul_multi_host(he_ctx* c, uint32_t count, const he_product* items, uin
     if (e != cudaSuccess) return cuda_fail(e, "matmul_multi_host: synchronize");
   }
   return HE_OK;
+}
+
+}  // extern "C"
+
+struct he_pipe {
+  he_ctx* c = nullptr;
+  uint32_t depth = 0;
+  uint64_t submits = 0;
+  cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
+  std::vector<cudaEvent_t> uploaded, computed, downloaded;  // per slot
+};
+
+extern "C" {
+
+int he_pipe_create(he_ctx* c, uint32_t depth, he_pipe** out) {
+  if (!c || !out) return fail(HE_EINVAL, "NULL argument");
+  if (!depth || depth > 16) return fail(HE_EINVAL, "pipe depth must be 1 .. 16");
+  if (int r = set_device(c)) return r;
+  he_pipe* p = new he_pipe;
+  p->c = c;
+  p->depth = depth;
+  cudaError_t e = cudaSuccess;
+  for (cudaStream_t* s : {&p->up, &p->comp, &p->down})
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+  for (auto* v : {&p->uploaded, &p->computed, &p->downloaded})
+    for (uint32_t i = 0; i < depth && e == cudaSuccess; ++i) {
+      cudaEvent_t ev = nullptr;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) v->push_back(ev);
+    }
+  if (e != cudaSuccess) {
+    he_pipe_free(p);
+    return cuda_fail(e, "pipe_create");
+  }
+  *out = p;
+  return HE_OK;
+}
+
+int he_pipe_free(he_pipe* p) {
+  if (!p) return HE_OK;
+  set_device(p->c);
+  for (cudaStream_t s : {p->up, p->comp, p->down})
+    if (s) cudaStreamSynchronize(s);
+  for (auto* v : {&p->uploaded, &p->computed, &p->downloaded})
+    for (cudaEvent_t ev : *v) cudaEventDestroy(ev);
+  for (cudaStream_t s : {p->up, p->comp, p->down})
+    if (s) cudaStreamDestroy(s);
+  delete p;
+  return HE_OK;
+}
+
+int he_pipe_compute_stream(he_pipe* p, void** stream) {
+  if (!p || !stream) return fail(HE_EINVAL, "NULL argument");
+  *stream = (void*)p->comp;
+  return HE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+constexpr uint32_t kPipeChunk = 64;  // products per multi-product launch
+
+// Bytes of one pipe slot: the largest chunk's multi-product workspace, then every
+// product's staged input and output.
+int pipe_slot_bytes(he_ctx* c, uint32_t count, const he_product* items, u64* bytes) {
+  u64 ws = 0, io = 0;
+  for (uint32_t i0 = 0; i0 < count; i0 += kPipeChunk) {
+    MultiPlan P;
+    if (int r = plan_multi(c, std::min(kPipeChunk, count - i0), items + i0, nullptr, &P)) return r;
+    ws = std::max(ws, (u64)P.ws_bytes);
+  }
+  for (uint32_t i = 0; i < count; ++i) {
+    u64 in_w, out_w;
+    product_io_words(c, items[i], &in_w, &out_w);
+    io += up256(8 * in_w) + up256(8 * out_w);
+  }
+  *bytes = up256(ws) + io;
+  return HE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int he_pipe_workspace_bytes(const he_pipe* p, uint32_t count, const he_product* items, size_t* bytes) {
+  if (!p || !bytes || (count && !items)) return fail(HE_EINVAL, "NULL argument");
+  u64 slot = 0;
+  if (int r = pipe_slot_bytes(p->c, count, items, &slot)) return r;
+  *bytes = (size_t)p->depth * slot;
+  return HE_OK;
+}
+
+int he_pipe_submit(he_pipe* p, uint32_t count, const he_product* items, void* workspace, size_t workspace_bytes) {
+  if (!p) return fail(HE_EINVAL, "pipe is NULL");
+  if (!count) return HE_OK;
+  if (!items) return fail(HE_EINVAL, "items is NULL");
+  he_ctx* c = p->c;
+  u64 need = 0;
+  if (int r = pipe_slot_bytes(c, count, items, &need)) return r;
+  if (!workspace) return fail(HE_EINVAL, "workspace is NULL");
+  const u64 slot_bytes = (workspace_bytes / p->depth) & ~(u64)255;
+  if (slot_bytes < need) return fail(HE_ENOMEM, "workspace smaller than he_pipe_workspace_bytes()");
+  if (int r = set_device(c)) return r;
+  const uint32_t slot = (uint32_t)(p->submits % p->depth);
+  const bool reuse = p->submits >= p->depth;
+  char* base = (char*)workspace + slot * slot_bytes;
+  u64 ws = 0;
+  for (uint32_t i0 = 0; i0 < count; i0 += kPipeChunk) {
+    MultiPlan P;
+    if (int r = plan_multi(c, std::min(kPipeChunk, count - i0), items + i0, nullptr, &P)) return r;
+    ws = std::max(ws, (u64)P.ws_bytes);
+  }
+  std::vector<he_product> dev(items, items + count);
+  std::vector<u64> in_words(count), out_words(count);
+  u64 off = up256(ws);
+  for (u32 i = 0; i < count; ++i) {
+    product_io_words(c, items[i], &in_words[i], &out_words[i]);
+    if (in_words[i] && (!items[i].ct_in || !items[i].ct_out)) return fail(HE_EINVAL, "NULL host buffer");
+    dev[i].ct_in = (const uint64_t*)(base + off);
+    off += up256(8 * in_words[i]);
+    dev[i].ct_out = (uint64_t*)(base + off);
+    off += up256(8 * out_words[i]);
+  }
+  cudaError_t e = cudaSuccess;
+  // uploads: after the launches that last read this slot
+  if (reuse) e = cudaStreamWaitEvent(p->up, p->computed[slot], 0);
+  for (u32 i = 0; i < count && e == cudaSuccess; ++i)
+    if (in_words[i])
+      e = cudaMemcpyAsync((void*)dev[i].ct_in, items[i].ct_in, 8 * in_words[i], cudaMemcpyHostToDevice, p->up);
+  if (e == cudaSuccess) e = cudaEventRecord(p->uploaded[slot], p->up);
+  // launches: after the uploads and after the downloads that last read this slot's outputs
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->comp, p->uploaded[slot], 0);
+  if (e == cudaSuccess && reuse) e = cudaStreamWaitEvent(p->comp, p->downloaded[slot], 0);
+  if (e != cudaSuccess) return cuda_fail(e, "pipe_submit: upload");
+  for (uint32_t i0 = 0; i0 < count; i0 += kPipeChunk)
+    if (int r = he_matmul_multi(c, std::min(kPipeChunk, count - i0), dev.data() + i0, base, ws, (void*)p->comp))
+      return r;
+  e = cudaEventRecord(p->computed[slot], p->comp);
+  // downloads: after the launches
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->down, p->computed[slot], 0);
+  for (u32 i = 0; i < count && e == cudaSuccess; ++i)
+    if (out_words[i])
+      e = cudaMemcpyAsync(items[i].ct_out, dev[i].ct_out, 8 * out_words[i], cudaMemcpyDeviceToHost, p->down);
+  if (e == cudaSuccess) e = cudaEventRecord(p->downloaded[slot], p->down);
+  if (e != cudaSuccess) return cuda_fail(e, "pipe_submit: download");
+  ++p->submits;
+  return HE_OK;
+}
+
+int he_pipe_wait(he_pipe* p) {
+  if (!p) return fail(HE_EINVAL, "pipe is NULL");
+  if (int r = set_device(p->c)) return r;
+  cudaError_t e = cudaStreamSynchronize(p->down);  // the downloads wait on every other queue
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->comp);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->up);
+  return e == cudaSuccess ? HE_OK : cuda_fail(e, "pipe_wait");
 }
 
 int he_expand_compact(he_ctx* c, const uint64_t* ct_compact, uint32_t cnt, uint32_t k_b, uint64_t* ct_full,

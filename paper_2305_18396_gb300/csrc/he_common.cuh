@@ -34,6 +34,8 @@ struct PrimeConsts {
   u64 r64, r64_sh;     // 2^64 mod q
   u64 crt, crt_sh;     // ((Q / q)^{-1} mod q), for decryption
   u64 theta_hi, theta_lo;  // floor(t 2^128 / q) as two words (decryption)
+  u32 pw256_lo[13], pw256_hi[13];  // 256^d mod q (d < 13) as 32-bit halves (tensor-core MAC epilogue)
+  u64 pw256_bias;                  // 2^24 sum_d 256^d mod q
   const u64* psi;      // psi^{brev(k)}, k < N       (forward twiddles)
   const u64* psi_sh;
   const u64* ipsi;     // psi^{-brev(k)}, k < N      (inverse twiddles)

@@ -170,15 +170,21 @@ __device__ __forceinline__ void fwd_store_smem(const u64 (&x)[S::R], u64* sm) {
 }
 
 // Remaining forward passes, recursively (S0 = first stage of the pass).
+// Passes that start below `start` are skipped (their stages already ran, or were copies,
+// with the values left in shared memory in natural order); the last pass always leaves
+// its values in x.  `start` is the same for every thread of the block.
 template <class S, int S0>
-__device__ __forceinline__ void fwd_rest(u64 (&x)[S::R], u64* sm, const PrimeConsts& P) {
+__device__ __forceinline__ void fwd_rest(u64 (&x)[S::R], u64* sm, const PrimeConsts& P, u32 start = 0) {
   if constexpr (S0 < S::kLogN) {
-    fwd_load_smem<S, S0, S::LOGR>(x, sm);
-    fwd_pass_regs<S, S0, S::LOGR>(x, P);
+    const bool run = (u32)S0 >= start;
+    if (run || S0 + S::LOGR == S::kLogN) fwd_load_smem<S, S0, S::LOGR>(x, sm);
+    if (run) fwd_pass_regs<S, S0, S::LOGR>(x, P);
     if constexpr (S0 + S::LOGR < S::kLogN) {
-      fwd_store_smem<S, S0, S::LOGR>(x, sm);
-      __syncthreads();
-      fwd_rest<S, S0 + S::LOGR>(x, sm, P);
+      if (run) {
+        fwd_store_smem<S, S0, S::LOGR>(x, sm);
+        __syncthreads();
+      }
+      fwd_rest<S, S0 + S::LOGR>(x, sm, P, start);
     }
   }
 }
@@ -190,33 +196,76 @@ __device__ __forceinline__ void fwd_rest(u64 (&x)[S::R], u64* sm, const PrimeCon
 //                   thread stride, coalesced);
 //   prefix       -- the coefficients at and above `prefix` are zero (default: none);
 //   sm: S::kSmemWords words of shared memory.  Synchronizes internally.
-// The first pass pairs element e with e + N/2, e + N/4, ..., i.e. each thread's group is
-// e = g + j N / 2^RS0 (j < 2^RS0).  With prefix <= N / 2^RS0 only j = 0 can be nonzero,
-// every butterfly of the pass has V = 0 and passes U through, so the pass reduces to
-// copying that element to the whole group (the skipped "+ 4q" offsets change nothing mod
-// q, and the final reduction is exact): a weight block of Algorithm 1's encoding pi_A
-// fills only its lowest n_b k_b = N / m_b coefficients.
+// Sparse input (a weight block of Algorithm 1's encoding pi_A fills only its lowest
+// n_b k_b = N / m_b coefficients).  Stage s pairs e with e + N / 2^(s+1).  With
+// prefix <= N / 2^s0 every butterfly of stages 0 .. s0 - 1 has V = 0 and passes U through,
+// so after them element e holds coefficient e mod N / 2^s0: those stages are copies (the
+// skipped "+ 4q" offsets change nothing mod q, and the final reduction is exact).
+//   s0 == RS0: the first pass is replaced by copying each group's one nonzero element in
+//              registers;
+//   s0 >  RS0: the replicated input is written to shared memory, the stages from s0 up to
+//              the next pass boundary run there one by one, and the register passes resume
+//              at that boundary (fwd_rest's `start`): log2 N - s0 stages instead of log2 N.
+template <class S>
+__device__ __forceinline__ void fwd_stage_smem(u64* sm, u32 s, const PrimeConsts& P) {
+  const u32 tlog = S::kLogN - 1 - s, span = 1u << tlog;
+  const u64 four_q = 2 * P.two_q;
+  for (u32 b = threadIdx.x; b < (u32)(S::N / 2); b += S::T) {
+    const u32 g = b >> tlog;
+    const u32 j = (g << (tlog + 1)) + (b & (span - 1));
+    const u32 widx = (1u << s) + g;
+    const u64 w = __ldg(P.psi + widx), wsh = __ldg(P.psi_sh + widx);
+    const u64 U = sm[S::pad(j)];
+    const u64 V = mul_shoup_lazy(sm[S::pad(j + span)], w, wsh, P.q);
+    sm[S::pad(j)] = U + V;
+    sm[S::pad(j + span)] = U - V + four_q;
+  }
+}
+
 template <class S, class Load, class Store>
 __device__ __forceinline__ void ntt_forward_block(u64* sm, const PrimeConsts& P, Load&& load, Store&& store,
                                                   u32 prefix = S::N) {
   u64 x[S::R];
-  if (prefix <= (u32)(S::N >> S::RS0)) {
+  const u32 s0 = prefix <= 1 ? (u32)S::kLogN : (u32)S::kLogN - (32 - __clz(prefix - 1));  // prefix <= N >> s0
+  u32 start = 0;  // first register pass to run
+  if (s0 > (u32)S::RS0) {
+    const u32 mask = (S::N >> s0) - 1;
+    if ((S::N >> s0) <= S::T) {  // every element of this thread maps to the same coefficient
+      const u64 v = load(threadIdx.x & mask);
 #pragma unroll
-    for (int h = 0; h < (S::R >> S::RS0); ++h) {
-      const u64 v = load(fwd_elem<S, 0, S::RS0>(h, 0));
+      for (int i = 0; i < S::R; ++i) sm[S::pad(threadIdx.x + S::T * i)] = v;
+    } else {
 #pragma unroll
-      for (int j = 0; j < (1 << S::RS0); ++j) x[h * (1 << S::RS0) + j] = v;
+      for (int i = 0; i < S::R; ++i) {
+        const u32 e = threadIdx.x + S::T * i;
+        sm[S::pad(e)] = load(e & mask);
+      }
+    }
+    __syncthreads();
+    start = min((u32)S::RS0 + ((s0 - S::RS0 + S::LOGR - 1) / S::LOGR) * S::LOGR, (u32)S::kLogN);
+    for (u32 s = s0; s < start; ++s) {
+      fwd_stage_smem<S>(sm, s, P);
+      __syncthreads();
     }
   } else {
+    if (s0 == (u32)S::RS0) {
 #pragma unroll
-    for (int h = 0; h < (S::R >> S::RS0); ++h)
+      for (int h = 0; h < (S::R >> S::RS0); ++h) {
+        const u64 v = load(fwd_elem<S, 0, S::RS0>(h, 0));
 #pragma unroll
-      for (int j = 0; j < (1 << S::RS0); ++j) x[h * (1 << S::RS0) + j] = load(fwd_elem<S, 0, S::RS0>(h, j));
-    fwd_pass_regs<S, 0, S::RS0>(x, P);
+        for (int j = 0; j < (1 << S::RS0); ++j) x[h * (1 << S::RS0) + j] = v;
+      }
+    } else {
+#pragma unroll
+      for (int h = 0; h < (S::R >> S::RS0); ++h)
+#pragma unroll
+        for (int j = 0; j < (1 << S::RS0); ++j) x[h * (1 << S::RS0) + j] = load(fwd_elem<S, 0, S::RS0>(h, j));
+      fwd_pass_regs<S, 0, S::RS0>(x, P);
+    }
+    fwd_store_smem<S, 0, S::RS0>(x, sm);
+    __syncthreads();
   }
-  fwd_store_smem<S, 0, S::RS0>(x, sm);
-  __syncthreads();
-  fwd_rest<S, S::RS0>(x, sm, P);
+  fwd_rest<S, S::RS0>(x, sm, P, start);
   // last pass ended with contiguous groups in registers: reduce, stage, copy out coalesced
   constexpr int S0L = S::kLogN - S::LOGR;
 #pragma unroll

@@ -24,7 +24,7 @@ import sys
 import numpy as np
 
 
-def run_case(m, k, n, repeat=3, compact=True, logN=12, L=2, multi=False, engine=0):
+def run_case(m, k, n, repeat=3, compact=True, logN=12, L=2, multi=False, engine=0, blk=None, encodes=1):
     import torch
 
     from . import binding as B
@@ -32,12 +32,13 @@ def run_case(m, k, n, repeat=3, compact=True, logN=12, L=2, multi=False, engine=
 
     ctx = B.Context(1 << logN, L)
     ctx.set_mac_engine(engine)
-    blk = ctx.default_blocking(m, k, n)
+    blk = tuple(blk) if blk else ctx.default_blocking(m, k, n)
     X = torch.from_numpy(S.uniform_share((m, k), 1).view(np.int64).reshape(-1)).to(ctx.device)
     W = torch.from_numpy(S.fixed_point_weights((k, n), 2).view(np.int64).reshape(-1)).to(ctx.device)
     sk = B.he_keygen(ctx, 3)
     ct = B.he_encrypt(ctx, sk, B.he_pack_input(ctx, X, m, k, blk), 4)
-    pt = B.he_encode_weights(ctx, W, k, n, blk)
+    for _ in range(encodes):  # encodes > 1: the weight encoding's own kernel, launched again
+        pt = B.he_encode_weights(ctx, W, k, n, blk)
     flags = B.HE_DROP_C0 if compact else 0
     out = None
     if multi:  # through the multi-product launch (one product): the kernels of a whole-layer step
@@ -130,6 +131,8 @@ def main(argv=None):
     c.add_argument("--L", type=int, default=2, help="number of primes")
     c.add_argument("--multi", action="store_true", help="run through he_matmul_multi")
     c.add_argument("--engine", type=int, default=0, help="0 auto, 1 integer, 2 tensor (he_set_mac_engine)")
+    c.add_argument("--blocking", help="m_b,k_b,n_b (default: the context's default blocking)")
+    c.add_argument("--encodes", type=int, default=1, help="weight encodings before the products")
     sh = sub.add_parser("share")
     sh.add_argument("m", type=int)
     sh.add_argument("k", type=int)
@@ -145,7 +148,8 @@ def main(argv=None):
     s.add_argument("--last", help="window ends at the last launch whose name contains this")
     a = ap.parse_args(argv)
     if a.cmd == "case":
-        blk, si = run_case(a.m, a.k, a.n, a.repeat, not a.full_c0, a.logn, a.L, a.multi, a.engine)
+        blk = [int(v) for v in a.blocking.split(",")] if a.blocking else None
+        blk, si = run_case(a.m, a.k, a.n, a.repeat, not a.full_c0, a.logn, a.L, a.multi, a.engine, blk, a.encodes)
         print("ok", blk, si)
     elif a.cmd == "share":
         run_share_case(a.m, a.k, a.n, a.repeat)

@@ -109,3 +109,18 @@ def test_wire_format_calls_reject_a_null_context_without_gpu(B):
     for fn in (B.lib.he_ct_export, B.lib.he_ct_import):
         assert fn(None, buf, 1, 0, buf, None) == B.HE_EINVAL
         assert "ctx" in B.lib.he_last_error().decode()
+
+
+def test_pipe_calls_reject_null_arguments_without_gpu(B):
+    import ctypes
+
+    h = ctypes.c_void_p()
+    assert B.lib.he_pipe_create(None, 3, ctypes.byref(h)) == B.HE_EINVAL
+    assert B.lib.he_pipe_submit(None, 1, None, None, 0) == B.HE_EINVAL
+    assert "pipe" in B.lib.he_last_error().decode()
+    assert B.lib.he_pipe_wait(None) == B.HE_EINVAL
+    out = ctypes.c_void_p()
+    assert B.lib.he_pipe_compute_stream(None, ctypes.byref(out)) == B.HE_EINVAL
+    sz = ctypes.c_size_t()
+    assert B.lib.he_pipe_workspace_bytes(None, 0, None, ctypes.byref(sz)) == B.HE_EINVAL
+    assert B.lib.he_pipe_free(None) == B.HE_OK
