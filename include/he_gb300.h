@@ -98,7 +98,8 @@ HE_API const char* he_last_error(void);
 
 /* Parameters {N, t, q} of Sec. 2.2 with q = q_0 ... q_{L-1} (RNS), t = 2^log2_t.
  * N: power of two in [32, 8192].  L in [1, 3] (L * N <= 3 * 8192).
- * q: L distinct primes, each = 1 mod 2N and 2^log2_t < q_l < 2^50 (host array).
+ * q: L distinct primes, each = 1 mod 2N and = 1 mod 2^32 (q_l = c 2^32 + 1, whose products
+ *    the kernels reduce with one 32-bit multiply), 2^log2_t < q_l < 2^50 (host array).
  * log2_t in [2, 48].  device: CUDA ordinal the context (and all buffers passed
  * with it) lives on.  Allocates the NTT twiddle tables on that device.
  * Returns HE_EINVAL on any invalid parameter (no GPU call made), HE_ECUDA or

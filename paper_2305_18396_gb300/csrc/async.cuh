@@ -37,6 +37,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
+// try_wait that may keep the thread suspended for up to `hint_ns` while the phase is
+// incomplete (it resumes as soon as the phase completes): a waiting warp then issues a few
+// instructions per wait instead of spinning on the issue slots its SM sub-partition shares
+// with the working warps.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return done != 0;
+}
+
+constexpr uint32_t kSuspendHintNs = 10000;  // well below every wait limit
+
 __device__ __forceinline__ uint64_t global_timer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -48,7 +66,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_suspend(bar, parity, kSuspendHintNs)) return true;
     if (global_timer_ns() - t0 > limit_ns) return false;
   }
 }
@@ -65,7 +83,7 @@ __device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, u
   if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;  // already complete: no clock read
   const uint64_t t0 = global_timer_ns();
   while (true) {
-    const bool ok = mbar_try_wait(bar, parity);
+    const bool ok = mbar_try_wait_suspend(bar, parity, kSuspendHintNs);
     if (__all_sync(0xffffffffu, ok)) return true;
     const bool late = global_timer_ns() - t0 > limit_ns;
     if (__any_sync(0xffffffffu, late)) return false;

@@ -237,6 +237,7 @@ int he_params_init(he_ctx** out, uint32_t N, uint32_t L, const uint64_t* q, uint
   for (u32 l = 0; l < L; ++l) {
     if (q[l] >= (1ull << 50) || q[l] <= (1ull << log2_t)) return fail(HE_EINVAL, "need 2^log2_t < q_l < 2^50");
     if ((q[l] - 1) % (2ull * N)) return fail(HE_EINVAL, "q_l must be 1 mod 2N");
+    if ((q[l] & 0xffffffffull) != 1) return fail(HE_EINVAL, "q_l must be 1 mod 2^32 (q_l = c 2^32 + 1)");
     if (!prime64(q[l])) return fail(HE_EINVAL, "q_l must be prime");
     for (u32 j = 0; j < l; ++j)
       if (q[j] == q[l]) return fail(HE_EINVAL, "primes must be distinct");
@@ -1229,6 +1230,37 @@ namespace {
 
 constexpr uint32_t kPipeChunk = 64;  // products per multi-product launch
 
+// One copy per run of consecutive products whose source buffers and destination buffers
+// are both adjacent (8 * words[i] bytes each, empty products skipped): the host link moves
+// a few large copies much faster than one per product.  Adjacent host buffers may still
+// belong to different allocations (two pinned arrays side by side), which one copy may
+// not span: the runtime then rejects the copy at enqueue time (nothing is queued), the
+// error is cleared and the run goes product by product.
+template <class Dst, class Src>
+cudaError_t copy_runs(uint32_t count, const u64* words, Dst dst, Src src, cudaMemcpyKind kind, cudaStream_t st) {
+  uint32_t i = 0;
+  while (i < count) {
+    if (!words[i]) {
+      ++i;
+      continue;
+    }
+    char* d0 = dst(i);
+    const char* s0 = src(i);
+    u64 bytes = 8 * words[i];
+    uint32_t j = i + 1;
+    for (; j < count && words[j] && dst(j) == d0 + bytes && src(j) == s0 + bytes; ++j) bytes += 8 * words[j];
+    cudaError_t e = cudaMemcpyAsync(d0, s0, bytes, kind, st);
+    if (e == cudaErrorInvalidValue && j > i + 1) {
+      cudaGetLastError();  // not sticky: clear it so later checks do not see it
+      e = cudaSuccess;
+      for (uint32_t k = i; k < j && e == cudaSuccess; ++k) e = cudaMemcpyAsync(dst(k), src(k), 8 * words[k], kind, st);
+    }
+    if (e != cudaSuccess) return e;
+    i = j;
+  }
+  return cudaSuccess;
+}
+
 // Bytes of one pipe slot: the largest chunk's multi-product workspace, then every
 // product's staged input and output.
 int pipe_slot_bytes(he_ctx* c, uint32_t count, const he_product* items, u64* bytes) {
@@ -1279,6 +1311,8 @@ int he_pipe_submit(he_pipe* p, uint32_t count, const he_product* items, void* wo
     if (int r = plan_multi(c, std::min(kPipeChunk, count - i0), items + i0, nullptr, &P)) return r;
     ws = std::max(ws, (u64)P.ws_bytes);
   }
+  // slot: [multi-product workspace][every input][every output], so that products whose
+  // host buffers are adjacent (e.g. slices of one array) move in one copy
   std::vector<he_product> dev(items, items + count);
   std::vector<u64> in_words(count), out_words(count);
   u64 off = up256(ws);
@@ -1287,15 +1321,17 @@ int he_pipe_submit(he_pipe* p, uint32_t count, const he_product* items, void* wo
     if (in_words[i] && (!items[i].ct_in || !items[i].ct_out)) return fail(HE_EINVAL, "NULL host buffer");
     dev[i].ct_in = (const uint64_t*)(base + off);
     off += up256(8 * in_words[i]);
+  }
+  for (u32 i = 0; i < count; ++i) {
     dev[i].ct_out = (uint64_t*)(base + off);
     off += up256(8 * out_words[i]);
   }
   cudaError_t e = cudaSuccess;
   // uploads: after the launches that last read this slot
   if (reuse) e = cudaStreamWaitEvent(p->up, p->computed[slot], 0);
-  for (u32 i = 0; i < count && e == cudaSuccess; ++i)
-    if (in_words[i])
-      e = cudaMemcpyAsync((void*)dev[i].ct_in, items[i].ct_in, 8 * in_words[i], cudaMemcpyHostToDevice, p->up);
+  if (e == cudaSuccess)
+    e = copy_runs(count, in_words.data(), [&](u32 i) { return (char*)dev[i].ct_in; },
+                  [&](u32 i) { return (char*)items[i].ct_in; }, cudaMemcpyHostToDevice, p->up);
   if (e == cudaSuccess) e = cudaEventRecord(p->uploaded[slot], p->up);
   // launches: after the uploads and after the downloads that last read this slot's outputs
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->comp, p->uploaded[slot], 0);
@@ -1307,9 +1343,9 @@ int he_pipe_submit(he_pipe* p, uint32_t count, const he_product* items, void* wo
   e = cudaEventRecord(p->computed[slot], p->comp);
   // downloads: after the launches
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->down, p->computed[slot], 0);
-  for (u32 i = 0; i < count && e == cudaSuccess; ++i)
-    if (out_words[i])
-      e = cudaMemcpyAsync(items[i].ct_out, dev[i].ct_out, 8 * out_words[i], cudaMemcpyDeviceToHost, p->down);
+  if (e == cudaSuccess)
+    e = copy_runs(count, out_words.data(), [&](u32 i) { return (char*)items[i].ct_out; },
+                  [&](u32 i) { return (char*)dev[i].ct_out; }, cudaMemcpyDeviceToHost, p->down);
   if (e == cudaSuccess) e = cudaEventRecord(p->downloaded[slot], p->down);
   if (e != cudaSuccess) return cuda_fail(e, "pipe_submit: download");
   ++p->submits;

@@ -52,10 +52,16 @@ struct Consts {
 
 // ---------------------------------------------------------------- arithmetic
 
+// x w - qh q mod 2^64 for the library's primes q = q1 2^32 + 1 (he_params_init accepts only
+// q = 1 mod 2^32): the low 64 bits of qh q are qh + 2^32 ((qh mod 2^32) q1 mod 2^32), one
+// 32-bit multiply instead of the three of a 64-bit product.
+__device__ __forceinline__ u64 sub_qh_q(u64 xw, u64 qh, u64 q) {
+  return xw - qh - ((u64)((u32)qh * (u32)(q >> 32)) << 32);
+}
+
 // x * w mod q up to one extra q: result in [0, 2q) for any x < 2^64, w < q < 2^63.
 __device__ __forceinline__ u64 mul_shoup(u64 x, u64 w, u64 w_sh, u64 q) {
-  u64 qh = __umul64hi(x, w_sh);
-  return x * w - qh * q;
+  return sub_qh_q(x * w, __umul64hi(x, w_sh), q);
 }
 
 // Shoup product with an estimated quotient, for the lazily reduced forward transforms:
@@ -67,7 +73,7 @@ __device__ __forceinline__ u64 mul_shoup(u64 x, u64 w, u64 w_sh, u64 q) {
 __device__ __forceinline__ u64 mul_shoup_lazy(u64 x, u64 w, u64 w_sh, u64 q) {
   const u32 x0 = (u32)x, x1 = (u32)(x >> 32), s0 = (u32)w_sh, s1 = (u32)(w_sh >> 32);
   const u64 qh = (u64)x1 * s1 + __umulhi(x1, s0) + __umulhi(x0, s1);
-  return x * w - qh * q;
+  return sub_qh_q(x * w, qh, q);
 }
 
 __device__ __forceinline__ u64 csub(u64 x, u64 b) { return x >= b ? x - b : x; }

@@ -47,6 +47,7 @@ def test_params_init_rejects_bad_parameters_without_gpu(B):
         (4096, 2, (q_ok[0], q_ok[0] + 2 * 4096 * 2), 37, "composite"),
         (4096, 2, q_ok, 60, "t too large"),
         (4096, 1, (65537,), 37, "q below t"),
+        (4096, 1, (562949953216513,), 37, "prime 1 mod 2N but not 1 mod 2^32"),
     ]
     for N, L, q, lt, why in cases:
         if why == "ok-shape":

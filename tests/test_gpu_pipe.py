@@ -129,3 +129,33 @@ def test_pipe_rejects_a_small_workspace_and_a_bad_depth(env):
     with pytest.raises(B.HEError):
         pipe.submit(arr, ctx.empty(need // 8 - 64))
     pipe.close()
+
+
+def test_pipe_moves_slices_of_one_host_array_in_one_copy_and_still_matches(env):
+    """Inputs and outputs as adjacent slices of one pinned array each (the copies merge
+    into one per direction), next to products with buffers of their own."""
+    B, ctx, P, s = env
+    m, k, n, blk = 12, 96, 40, (4, 8, 16)
+    prods = _case(B, ctx, P, s, [(m, k, n, blk, B.HE_DROP_C0)] * 5, 800)
+    iw = prods[0]["in_h"].numel()
+    big_in = torch.empty(5 * iw, dtype=torch.int64).pin_memory()
+    for i, p in enumerate(prods):
+        big_in[i * iw:(i + 1) * iw].copy_(p["in_h"])
+        p["in_h"] = big_in[i * iw:(i + 1) * iw]
+    ow = prods[0]["ow"]
+    big_out = torch.empty(5 * ow, dtype=torch.int64).pin_memory()
+    outs = [big_out[i * ow:(i + 1) * ow] for i in range(5)]
+    pipe = B.Pipe(ctx, depth=2)
+    arr = B.make_products(_items(prods, outs, [40 + i for i in range(5)], True))
+    ws = ctx.empty(pipe.workspace_bytes(arr) // 8 + 1)
+    pipe.submit(arr, ws)
+    pipe.wait()
+    B.he_device_status(ctx)
+    kb, Nc, L, N = blk[1], P.N // blk[1], P.L, P.N
+    for i in (0, 4):
+        p = prods[i]
+        want = O.matmul(P, p["ct"], p["W"], m, k, n, blk, 40 + i)
+        got = outs[i].numpy().view(np.uint64).reshape(want.shape[0], L * (Nc + N))
+        assert np.array_equal(got[:, L * Nc:].reshape(-1, L, N), want[:, 1]), i
+        assert np.array_equal(got[:, :L * Nc].reshape(-1, L, Nc), want[:, 0, :, kb - 1::kb]), i
+    pipe.close()
