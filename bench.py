@@ -86,8 +86,9 @@ def parse():
                     help="tuned: he_autotune_blocking per product at set-up; model: the cost model's choice")
     ap.add_argument("--ntt-radix", default="tuned", choices=["tuned", "3", "4", "5"],
                     help="log2 of the values per thread of the transforms: tuned = he_autotune_ntt_radix at set-up")
-    ap.add_argument("--mac-engine", default="auto", choices=["auto", "integer", "tensor"],
-                    help="multiply-accumulate engine (he_set_mac_engine): auto = tensor cores from 32 k-blocks on")
+    ap.add_argument("--mac-engine", default="auto", choices=["auto", "integer", "tensor", "coset"],
+                    help="multiply-accumulate engine (he_set_mac_engine): auto = the coset form where n_b k_b <= N/2, "
+                         "else the tensor cores from 32 k-blocks on")
     ap.add_argument("--full-c0", action="store_true",
                     help="return all of c0 instead of only the decoded coefficients (Sec. 3.1.3)")
     return ap.parse_args()
@@ -215,7 +216,7 @@ class Layer:
                                 polys=polys[b * si["packed_words"]:(b + 1) * si["packed_words"]])
             ct_in = B.he_encrypt(ctx, self.sk, polys, seed + 900_000)
             call = dict(p=p, blk=blk, si=si, cnt=cnt, ct_in=ct_in, out=ctx.empty(cnt * si["out"]), idx=idx,
-                        tc=ctx.uses_tensor_cores(p.k, blk))
+                        tc=ctx.uses_tensor_cores(p.k, blk), coset=ctx.uses_cosets(blk))
             if p.share_weights:
                 call["W"] = Wd  # the server's shares, encoded on every step
                 max_pt = max(max_pt, cnt * si["pt_words"])
@@ -396,12 +397,20 @@ class Layer:
 
     def algorithmic_bytes(self):
         """Per kernel family: algorithmic HBM bytes of one step (reads + writes, 8-byte words)."""
-        tot = {"mac": 0, "mac_tc": 0, "ntt_forward": 0, "intt_mask": 0, "encode_weights": 0}
+        tot = {"mac": 0, "mac_tc": 0, "ntt_forward": 0, "intt_mask": 0, "encode_weights": 0, "coset_forward": 0,
+               "coset_inverse": 0, "coset_encode": 0}
         for c in self.calls:
             si, p, cnt = c["si"], c["p"], c["cnt"]
             pt_b, in_b = 8 * si["pt_words"], 8 * si["in_words"]
             full_b = 8 * si["out_words"]  # the multiply-accumulate writes both components in full (NTT domain)
             c1_b = full_b // 2
+            if c["coset"]:  # 2N words per input and output component in the transform domain
+                tot["coset_forward"] += cnt * 3 * in_b
+                tot["mac_tc"] += cnt * (pt_b + 2 * in_b + 2 * full_b)
+                tot["coset_inverse"] += cnt * (2 * full_b + 8 * si["out"])
+                if p.share_weights:
+                    tot["coset_encode"] += cnt * (8 * p.k * p.n + pt_b)
+                continue
             tot["mac_tc" if c["tc"] else "mac"] += cnt * (pt_b + in_b + full_b)
             tot["ntt_forward"] += cnt * 2 * in_b
             if self.flags:  # c1: read + write; c0: read in full, write the kept coefficients
@@ -416,10 +425,11 @@ class Layer:
 
     def slot_macs(self, tc=None):
         """Slot-wise modular multiply-accumulates of one step (tc: only the products on the tensor
-        cores (True) or on the integer pipe (False))."""
+        cores (True) or on the integer pipe (False)); a coset product performs 2N per pair of
+        input and weight blocks and component, twice the N of the NTT domain."""
         L, N = self.ctx.L, self.ctx.N
-        return sum(c["cnt"] * c["si"]["nI"] * c["si"]["nJ"] * c["si"]["nLb"] * 2 * L * N for c in self.calls
-                   if tc is None or c["tc"] == tc)
+        return sum(c["cnt"] * c["si"]["nI"] * c["si"]["nJ"] * c["si"]["nLb"] * 2 * L * N * (2 if c["coset"] else 1)
+                   for c in self.calls if tc is None or c["tc"] == tc)
 
 
 def kernel_source_hash():
@@ -734,7 +744,7 @@ def bert_base_leg(B, args, local, flags, steps=20):
     from paper_2305_18396_gb300 import workloads
 
     ctx = B.Context(4096, 2, device=local)
-    ctx.set_mac_engine({"auto": B.HE_MAC_AUTO, "integer": B.HE_MAC_INTEGER, "tensor": B.HE_MAC_TENSOR}[args.mac_engine])
+    ctx.set_mac_engine({"auto": B.HE_MAC_AUTO, "integer": B.HE_MAC_INTEGER, "tensor": B.HE_MAC_TENSOR, "coset": B.HE_MAC_COSET}[args.mac_engine])
     if args.ntt_radix == "tuned":
         ctx.autotune_ntt_radix()
     else:
@@ -775,7 +785,7 @@ def gpu_arm(args, world, rank, local):
     torch.cuda.set_device(local)
     wl = WORKLOADS[args.workload]
     ctx = B.Context(wl["N"], wl["L"], device=local)
-    engine = {"auto": B.HE_MAC_AUTO, "integer": B.HE_MAC_INTEGER, "tensor": B.HE_MAC_TENSOR}[args.mac_engine]
+    engine = {"auto": B.HE_MAC_AUTO, "integer": B.HE_MAC_INTEGER, "tensor": B.HE_MAC_TENSOR, "coset": B.HE_MAC_COSET}[args.mac_engine]
     ctx.set_mac_engine(engine)  # before any weights are encoded: it fixes their layout
     if args.ntt_radix == "tuned":  # before the blocking tuner, which times whole products at this radix
         radix_ms = {str(r): round(v, 4) for r, v in ctx.autotune_ntt_radix()[1].items()}

@@ -185,8 +185,19 @@ HE_API int he_autotune_ntt_radix(he_ctx* ctx, uint32_t cnt, void* scratch, size_
  *   HE_MAC_TENSOR: residues split into seven balanced 8-bit digits, exact in bf16; the
  *     digit products summed on the tcgen05 tensor cores with f32 accumulation (every sum
  *     stays an exact integer below 2^24) and recombined mod q_l.  Needs N >= 512.
- *   HE_MAC_AUTO (the default): the tensor cores for products of at least 32 k-blocks
- *     (k / k_b) when N >= 512, the integer path otherwise.
+ *   HE_MAC_COSET: the tensor-core multiply-accumulate through the ring's cosets where
+ *     n_b k_b <= N/2 (else as HE_MAC_TENSOR).  A weight block of pi_A has at most n_b k_b
+ *     nonzero coefficients; with D = max(8, n_b k_b rounded up to a power of two) and
+ *     G = N / D, x^N + 1 splits into the G factors x^D - zeta_g.  The inputs get the first
+ *     log2 G NTT stages (their residues mod each factor) and then a zero-padded length-2D
+ *     transform per coset; the weights get only that length-2D transform, which is the
+ *     same for every coset.  The weights then cost 2D residues per block instead of N, the
+ *     workspace twice the inputs' and outputs' NTT size, and the multiply-accumulate twice
+ *     the slot products; an inverse per coset, a fold by zeta_g and the inverse of the first
+ *     stages give the same output ciphertexts bit for bit.
+ *   HE_MAC_AUTO (the default): the coset form wherever it applies (N >= 512); else the
+ *     tensor cores for products of at least 32 k-blocks (k / k_b), the integer path
+ *     otherwise.
  * The choice fixes the layout of he_encode_weights' output and of the workspace (he_sizes
  * reports both for the engine in force), so set it before encoding weights and keep it
  * while those weights are in use.  Must not change while another thread uses the
@@ -194,11 +205,16 @@ HE_API int he_autotune_ntt_radix(he_ctx* ctx, uint32_t cnt, void* scratch, size_
 #define HE_MAC_AUTO 0u
 #define HE_MAC_INTEGER 1u
 #define HE_MAC_TENSOR 2u
+#define HE_MAC_COSET 3u
 HE_API int he_set_mac_engine(he_ctx* ctx, uint32_t engine);
 HE_API int he_get_mac_engine(const he_ctx* ctx, uint32_t* engine);
 /* Host-side: *yes = 1 if products of inner dimension k under blk use the tensor cores on
  * this context (engine and N as above), else 0. */
 HE_API int he_mac_uses_tensor_cores(const he_ctx* ctx, uint32_t k, const he_blocking* blk, uint32_t* yes);
+/* Host-side: *yes = 1 if products under blk take the coset form on this context
+ * (HE_MAC_COSET above: HE_MAC_AUTO or HE_MAC_COSET, N >= 512, n_b k_b <= N/2), else 0.
+ * Errors: HE_EINVAL (NULL argument, invalid blocking). */
+HE_API int he_mac_uses_cosets(const he_ctx* ctx, const he_blocking* blk, uint32_t* yes);
 
 /* ---- test client (Sec. 2.2 BFV; encrypt/decrypt are the client's side) -- */
 

@@ -20,7 +20,7 @@ HE_OK, HE_EINVAL, HE_ENOMEM, HE_ECUDA, HE_ETIMEOUT, HE_ENOISE = range(6)
 HE_FLAGS_NONE = 0
 HE_DROP_C0 = 1
 HE_ASYNC = 2
-HE_MAC_AUTO, HE_MAC_INTEGER, HE_MAC_TENSOR = 0, 1, 2
+HE_MAC_AUTO, HE_MAC_INTEGER, HE_MAC_TENSOR, HE_MAC_COSET = 0, 1, 2, 3
 _NAMES = {1: "HE_EINVAL", 2: "HE_ENOMEM", 3: "HE_ECUDA", 4: "HE_ETIMEOUT", 5: "HE_ENOISE"}
 
 
@@ -99,6 +99,7 @@ def _load():
         "he_set_mac_engine": (ctypes.c_int, [P, u32]),
         "he_get_mac_engine": (ctypes.c_int, [P, pu32]),
         "he_mac_uses_tensor_cores": (ctypes.c_int, [P, u32, pB, pu32]),
+        "he_mac_uses_cosets": (ctypes.c_int, [P, pB, pu32]),
         "he_get_ntt_radix": (ctypes.c_int, [P, pu32]),
         "he_autotune_ntt_radix": (ctypes.c_int, [P, u32, P, sz, ctypes.POINTER(sz), ctypes.POINTER(ctypes.c_float),
                                                  pu32, P]),
@@ -227,7 +228,7 @@ class Context:
 
     @property
     def mac_engine(self):
-        """HE_MAC_AUTO, HE_MAC_INTEGER or HE_MAC_TENSOR (he_get_mac_engine)."""
+        """HE_MAC_AUTO, HE_MAC_INTEGER, HE_MAC_TENSOR or HE_MAC_COSET (he_get_mac_engine)."""
         v = ctypes.c_uint32(0)
         _check(lib.he_get_mac_engine(self.h, ctypes.byref(v)))
         return v.value
@@ -239,6 +240,11 @@ class Context:
     def uses_tensor_cores(self, k, blk):
         v = ctypes.c_uint32(0)
         _check(lib.he_mac_uses_tensor_cores(self.h, k, _blk(blk), ctypes.byref(v)))
+        return bool(v.value)
+
+    def uses_cosets(self, blk):
+        v = ctypes.c_uint32(0)
+        _check(lib.he_mac_uses_cosets(self.h, _blk(blk), ctypes.byref(v)))
         return bool(v.value)
 
     def autotune_ntt_radix(self, cnt=0, stream=None):

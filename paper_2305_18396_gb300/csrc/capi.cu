@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/he_gb300.h"
+#include "coset.cuh"
 #include "kernels.h"
 #include "mac_tc.cuh"
 #include "multi.h"
@@ -123,12 +124,13 @@ struct ProfRec {
 
 enum Kind {
   KNttFwd, KNttInv, KPolyMul, KKeygen, KEncrypt, KDecrypt, KPack, KUnpack, KUnmask, KEncode, KMac, KInttMask, KInttC0,
-  KExpand, KProbe, KShare, KInvC0, KCheck, KMacTc, KCount
+  KExpand, KProbe, KShare, KInvC0, KCheck, KMacTc, KCosetFwd, KCosetInv, KCosetEnc, KCount
 };
 static const char* kKindNames[KCount] = {"ntt_forward", "ntt_inverse", "poly_mul", "keygen", "encrypt",
                                          "decrypt", "pack", "unpack", "unmask", "encode_weights",
                                          "mac", "intt_mask", "intt_c0_targets", "expand_compact", "probe",
-                                         "share_matmul", "intt_c1_c0", "check_residues", "mac_tc"};
+                                         "share_matmul", "intt_c1_c0", "check_residues", "mac_tc",
+                                         "coset_forward", "coset_inverse", "coset_encode"};
 
 struct he_ctx {
   int device = 0;
@@ -205,19 +207,48 @@ he::Blk to_blk(const he_blocking* b) { return {b->m_b, b->k_b, b->n_b}; }
 // kTcMinKBlocks k-blocks on, where the exact limb split amortises its digit split and
 // epilogue; HE_MAC_TENSOR for every product; HE_MAC_INTEGER never.
 constexpr u32 kTcMinKBlocks = 32;
-bool use_tc(const he_ctx* c, u32 nJ) {
-  if (c->C.logN < 9 || c->mac_engine == HE_MAC_INTEGER) return false;
-  return c->mac_engine == HE_MAC_TENSOR || nJ >= kTcMinKBlocks;
+
+// Whether a product under blocking b runs through the ring's cosets (coset.cuh): weight
+// blocks of 2D residues instead of N, D = max(8, next power of two of n_b k_b) <= N/2, on the
+// tensor-core multiply-accumulate.  HE_MAC_AUTO and HE_MAC_COSET take it wherever it applies
+// (N >= 512).
+bool use_coset(const he_ctx* c, const he_blocking* b) {
+  if (c->C.logN < 9 || (c->mac_engine != HE_MAC_AUTO && c->mac_engine != HE_MAC_COSET)) return false;
+  return he::coset_logD(b->n_b * b->k_b) < c->C.logN;
 }
+bool use_tc(const he_ctx* c, const he_blocking* b, u32 nJ) {
+  if (c->C.logN < 9 || c->mac_engine == HE_MAC_INTEGER) return false;
+  if (use_coset(c, b)) return true;
+  return c->mac_engine == HE_MAC_TENSOR || c->mac_engine == HE_MAC_COSET || nJ >= kTcMinKBlocks;
+}
+
+// Geometry of a coset product: 2D slots per prime, rows (2 Lb + c) G + g.
+struct CosetGeom {
+  u32 logD, S, R;
+  u64 ctn_words, acc_words;
+};
+CosetGeom coset_geom(const he_ctx* c, const he_blocking* b, u32 nI, u32 nJ, u32 nLb) {
+  CosetGeom g;
+  g.logD = he::coset_logD(b->n_b * b->k_b);
+  g.S = 2u << g.logD;
+  g.R = (2 * nLb) << (c->C.logN - g.logD);
+  g.ctn_words = he::tc_words(g.R, nJ, c->C.L, g.S);
+  g.acc_words = (u64)nLb * nI * 2 * c->C.L * 2 * c->C.N;
+  return g;
+}
+u64 up256(u64 b) { return (b + 255) & ~(u64)255; }
 
 // Words of the NTT of a product's inputs (2 nLb rows) and of its encoded weights (nI rows) in
 // the layout of its multiply-accumulate: the tensor-core one pads k-blocks to stages of 16 and
-// stores the weights as bf16 digit tiles.
-u64 operand_words(const he_ctx* c, u32 rows, u32 nJ) {
-  return use_tc(c, nJ) ? he::tc_words(rows, nJ, c->C.L, c->C.N) : (u64)rows * nJ * c->C.L * c->C.N;
+// stores the weights as bf16 digit tiles; coset products have 2D slots per prime (and G times
+// the input rows).
+u64 operand_words(const he_ctx* c, const he_blocking* b, u32 rows, u32 nJ) {
+  if (use_coset(c, b)) return coset_geom(c, b, 0, nJ, rows / 2).ctn_words;
+  return use_tc(c, b, nJ) ? he::tc_words(rows, nJ, c->C.L, c->C.N) : (u64)rows * nJ * c->C.L * c->C.N;
 }
-u64 weight_words(const he_ctx* c, u32 nI, u32 nJ) {
-  return use_tc(c, nJ) ? he::tc_weight_words(nI, nJ, c->C.L, c->C.N) : (u64)nI * nJ * c->C.L * c->C.N;
+u64 weight_words(const he_ctx* c, const he_blocking* b, u32 nI, u32 nJ) {
+  if (use_coset(c, b)) return he::tc_weight_words(nI, nJ, c->C.L, 2u << he::coset_logD(b->n_b * b->k_b));
+  return use_tc(c, b, nJ) ? he::tc_weight_words(nI, nJ, c->C.L, c->C.N) : (u64)nI * nJ * c->C.L * c->C.N;
 }
 
 }  // namespace
@@ -258,7 +289,8 @@ int he_params_init(he_ctx** out, uint32_t N, uint32_t L, const uint64_t* q, uint
   for (u32 l = 0; l < L; ++l) qmt = (u64)(((u128)qmt * (q[l] & C.tmask)) & C.tmask);
   C.q_mod_t = qmt;
 
-  std::vector<u64> host((size_t)4 * L * N);
+  constexpr u32 kTableWords = 6;  // per prime: 4N twiddle words, then 2N words of coset fold factors
+  std::vector<u64> host((size_t)kTableWords * L * N);
   for (u32 l = 0; l < L; ++l) {
     const u64 ql = q[l];
     he::PrimeConsts& P = C.p[l];
@@ -269,13 +301,23 @@ int he_params_init(he_ctx** out, uint32_t N, uint32_t L, const uint64_t* q, uint
     }
     c->psi[l] = psi;
     u64 ipsi = invm(psi, ql);
-    u64* tw = host.data() + (size_t)4 * l * N;
+    u64* tw = host.data() + (size_t)kTableWords * l * N;
     for (u32 kk = 0; kk < N; ++kk) {
       u32 e = brev(kk, C.logN);
       tw[kk] = powm(psi, e, ql);
       tw[N + kk] = shoup(tw[kk], ql);
       tw[2 * N + kk] = powm(ipsi, e, ql);
       tw[3 * N + kk] = shoup(tw[2 * N + kk], ql);
+    }
+    // coset fold factors (1 +- psi^{brev(k)} psi^{-N/2}) / (2N), k < N/2 (coset.cuh)
+    const u64 inv2n = invm((2ull * N) % ql, ql), w_half = tw[2 * N + 1];
+    for (u32 kk = 0; kk < N / 2; ++kk) {
+      const u64 zw = mulm(tw[kk], w_half, ql);
+      u64* f = tw + 4 * N + 4 * kk;
+      f[0] = mulm((1 + zw) % ql, inv2n, ql);
+      f[1] = shoup(f[0], ql);
+      f[2] = mulm((1 + ql - zw) % ql, inv2n, ql);
+      f[3] = shoup(f[2], ql);
     }
     P.q = ql;
     P.two_q = 2 * ql;
@@ -336,11 +378,12 @@ int he_params_init(he_ctx** out, uint32_t N, uint32_t L, const uint64_t* q, uint
     return cuda_fail(e, "table upload / kernel configuration");
   }
   for (u32 l = 0; l < L; ++l) {
-    u64* tw = c->d_tables + (size_t)4 * l * N;
+    u64* tw = c->d_tables + (size_t)kTableWords * l * N;
     C.p[l].psi = tw;
     C.p[l].psi_sh = tw + N;
     C.p[l].ipsi = tw + 2 * N;
     C.p[l].ipsi_sh = tw + 3 * N;
+    C.p[l].fold = tw + 4 * N;
   }
   *out = c;
   return HE_OK;
@@ -387,12 +430,17 @@ int he_sizes(const he_ctx* c, uint32_t m, uint32_t k, uint32_t n, const he_block
   out->pts = (u64)s.nI * s.nJ;
   out->in_words = out->in_cts * 2 * L * N;
   out->out_words = out->out_cts * 2 * L * N;
-  out->pt_words = weight_words(c, s.nI, s.nJ);
+  out->pt_words = weight_words(c, blk, s.nI, s.nJ);
   out->packed_words = out->in_cts * N;
-  const u64 ntt_words = operand_words(c, 2 * s.nLb, s.nJ);  // NTT of the input ciphertexts (MAC layout)
-  out->workspace_bytes = ntt_words * sizeof(u64);
   const u64 Nc = pow2(blk->k_b) ? N / blk->k_b : 0;
   out->out_words_compact = Nc ? out->out_cts * L * (Nc + N) : 0;
+  if (use_coset(c, blk)) {  // the inputs' coset transforms, then the sums of both components
+    const CosetGeom g = coset_geom(c, blk, s.nI, s.nJ, s.nLb);
+    out->workspace_bytes = out->workspace_bytes_compact = up256(g.ctn_words * 8) + up256(g.acc_words * 8);
+    return HE_OK;
+  }
+  const u64 ntt_words = operand_words(c, blk, 2 * s.nLb, s.nJ);  // NTT of the input ciphertexts (MAC layout)
+  out->workspace_bytes = ntt_words * sizeof(u64);
   out->workspace_bytes_compact = (ntt_words + out->out_cts * L * N) * sizeof(u64);
   return HE_OK;
 }
@@ -416,7 +464,13 @@ struct Candidate {
 //     ps per slot product divided by the fill of its 128-weight-row x 16-row work units,
 //     plus the weights' digit form (14 instead of 8 bytes per residue; when encoded per
 //     call also cleared and written in that form);
-//   memory: algorithmic bytes at 6.75 TB/s.
+//   memory: algorithmic bytes at 6.75 TB/s;
+//   coset products (where the engine puts the product there, coset.cuh): 2N slot products per
+//     input block, weight block and component; transforms of the inputs and the outputs
+//     scaled by their stages, (log2 G + 2 log2 D) / log2 N, with 2N words each in the
+//     transform domain; weights of 2D slots in digit form; the multiply-accumulate's
+//     epilogue (3 ps per output word and accumulation round of 128 k-blocks) overlapping its
+//     MMAs.
 // Ties go to the larger m_b, then the larger k_b.
 std::vector<Candidate> blocking_candidates(u32 Nw, u32 Lw, u32 m, u32 k, u32 n, u32 weights_per_call,
                                            u32 engine = HE_MAC_AUTO) {
@@ -439,7 +493,23 @@ std::vector<Candidate> blocking_candidates(u32 Nw, u32 Lw, u32 m, u32 k, u32 n, 
         const double pts = nI * nJ, in = nLb * nJ, outc = nLb * nI;
         const double polys = 2 * L * in + 2 * L * outc + (weights_per_call ? L * pts : 0);
         const double rows = 2 * nLb, slots = nI * nJ * nLb * 2 * L * N;
-        const bool tc = Nw >= 512 && engine != HE_MAC_INTEGER && (engine == HE_MAC_TENSOR || nJ >= 32);
+        const u32 logD = he::coset_logD((u32)(kb * nb));
+        if (Nw >= 512 && (engine == HE_MAC_AUTO || engine == HE_MAC_COSET) && (1u << logD) <= Nw / 2) {
+          const double D = (double)(1u << logD), G = N / D, S = 2 * D, R = rows * G;
+          const double nS = std::ceil(nJ / 16.0);
+          const double fill = (R / (16 * std::ceil(R / 16))) * (nI / (128 * std::ceil(nI / 128)));
+          const double mma = 2 * slots * (16 * nS / nJ) * t_slot_tc / fill;
+          const double epi = 3e-12 * R * nI * S * L * std::ceil(nS / 8);
+          const double xf = t_poly * (std::log2(G) + 2 * std::log2(D)) / std::log2(N) * 1.5;
+          const double cbytes = 8 * N * L * (10 * in + 10 * outc) + 14 * S * L * pts * (weights_per_call ? 2 : 1) +
+                                (weights_per_call ? 8.0 * k * n : 0);
+          out.push_back({{(u32)mb, (u32)kb, (u32)nb},
+                         (2 * L * in + 2 * L * outc + (weights_per_call ? L * pts * S / N : 0)) * xf +
+                             std::max(mma, epi) + cbytes / hbm});
+          continue;
+        }
+        const bool tc = Nw >= 512 && engine != HE_MAC_INTEGER &&
+                        (engine == HE_MAC_TENSOR || engine == HE_MAC_COSET || nJ >= 32);
         double bytes = 8 * N * L * (pts * (weights_per_call ? 3 : 1) + 6 * in + 4 * outc), mac;
         if (tc) {
           const double fill = (rows / (16 * std::ceil(rows / 16))) * (nI / (128 * std::ceil(nI / 128)));
@@ -603,8 +673,12 @@ int he_encode_weights_batch(he_ctx* c, const uint64_t* W, uint32_t k, uint32_t n
   if (!W || !pt) return fail(HE_EINVAL, "NULL buffer");
   if (int r = set_device(c)) return r;
   Shape s = shape_of(1, k, n, blk);
+  if (use_coset(c, blk))
+    return launch(c, KCosetEnc, (cudaStream_t)stream, "encode_weights (cosets)", [&] {
+      return he::launch_coset_encode_weights(c->C, W, k, n, to_blk(blk), s.nI, s.nJ, batch, pt, (cudaStream_t)stream);
+    });
   return launch(c, KEncode, (cudaStream_t)stream, "encode_weights", [&] {
-    return he::launch_encode_weights(c->C, W, k, n, to_blk(blk), s.nI, s.nJ, batch, use_tc(c, s.nJ), pt,
+    return he::launch_encode_weights(c->C, W, k, n, to_blk(blk), s.nI, s.nJ, batch, use_tc(c, blk, s.nJ), pt,
                                      (cudaStream_t)stream);
   });
 }
@@ -620,14 +694,88 @@ static u32 log2u(u32 x) {
   return r;
 }
 
+namespace {
+
+// A coset product's entry in a multi-product table (coset.cuh); the begins are the running
+// block counts of the three coset grids, advanced past this item.
+void coset_item(const he_ctx* c, he::MultiItem& it, const he_blocking* blk, Shape s, bool compact, u64* ws,
+                u64* cfwd, u64* tc, u64* cinv) {
+  const CosetGeom g = coset_geom(c, blk, s.nI, s.nJ, s.nLb);
+  const u64 L = c->C.L;
+  it.nI = s.nI;
+  it.nJ = s.nJ;
+  it.nLb = s.nLb;
+  it.compact = compact;
+  it.logkb = compact ? log2u(blk->k_b) : 0;
+  it.tc = 1;
+  it.coset = 1;
+  it.logD = g.logD;
+  it.ctN = ws;
+  it.acc = ws ? (u64*)((char*)ws + up256(g.ctn_words * 8)) : nullptr;
+  it.cfwd_begin = *cfwd;
+  it.tc_begin = *tc;
+  it.cinv_begin = *cinv;
+  *cfwd += (u64)s.nLb * s.nJ * 2 * L;
+  *tc += he::tc_units(g.S, (u32)L, s.nI, g.R);
+  *cinv += (u64)s.nLb * s.nI * 2 * L;
+}
+
+int launch_coset_grids(he_ctx* c, const he::MultiTable& T, u64 cfwd, u64 tc, u64 cinv, bool compact, cudaStream_t st) {
+  int r = HE_OK;
+  if (cfwd)
+    r = launch(c, KCosetFwd, st, "coset forward transforms",
+               [&] { return he::launch_coset_fwd_multi(c->C, T, cfwd, st); });
+  if (!r && tc)
+    r = launch(c, KMacTc, st, "tensor-core multiply-accumulate (cosets)",
+               [&] { return he::launch_mac_tc_multi(c->C, T, tc, c->d_err, st); });
+  if (!r && cinv)
+    r = launch(c, KCosetInv, st, compact ? "coset inverse transforms + mask (compact)" : "coset inverse transforms + mask",
+               [&] { return he::launch_coset_inv_multi(c->C, T, cinv, st); });
+  return r;
+}
+
+// he_matmul / he_matmul_batch of a coset product: the batch in tables of up to 64 items;
+// item b reads its inputs and weights, writes its outputs and uses its workspace at b times
+// the per-item sizes, and masks with mask_seed + b.
+int coset_matmul(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
+                 const he_blocking* blk, uint32_t batch, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out,
+                 void* ws, cudaStream_t st) {
+  he_size_info si;
+  he_sizes(c, m, k, n, blk, &si);
+  const bool compact = flags & HE_DROP_C0;
+  const Shape s = shape_of(m, k, n, blk);
+  const u64 out_w = compact ? si.out_words_compact : si.out_words;
+  static thread_local he::MultiTable T;
+  for (u32 b0 = 0; b0 < batch; b0 += he::kMaxMulti) {
+    const u32 cnt = std::min<u32>(he::kMaxMulti, batch - b0);
+    memset(&T, 0, sizeof(T));
+    T.count = cnt;
+    u64 cfwd = 0, tc = 0, cinv = 0;
+    for (u32 i = 0; i < cnt; ++i) {
+      const u64 b = b0 + i;
+      he::MultiItem& it = T.it[i];
+      it.ct_in = ct_in + b * si.in_words;
+      it.pt = pt + b * si.pt_words;
+      it.out = ct_out + b * out_w;
+      it.mask_seed = mask_seed + b;
+      coset_item(c, it, blk, s, compact, (u64*)((char*)ws + b * si.workspace_bytes), &cfwd, &tc, &cinv);
+    }
+    if (int r = launch_coset_grids(c, T, cfwd, tc, cinv, compact, st)) return r;
+  }
+  return HE_OK;
+}
+
+}  // namespace
+
 static int matmul_device(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t m, uint32_t k, uint32_t n,
                          const he_blocking* blk, uint32_t batch, uint64_t mask_seed, uint32_t flags, uint64_t* ct_out,
                          void* ws, cudaStream_t st) {
+  if (use_coset(c, blk)) return coset_matmul(c, ct_in, pt, m, k, n, blk, batch, mask_seed, flags, ct_out, ws, st);
   Shape s = shape_of(m, k, n, blk);
   const u64 N = c->C.N, L = c->C.L;
   const u64 out_cts = (u64)s.nLb * s.nI;
   u64* ctN = (u64*)ws;
-  const bool tc = use_tc(c, s.nJ);
+  const bool tc = use_tc(c, blk, s.nJ);
   auto mac = [&](u64* o0, u64 st0, u64* o1, u64 st1) {
     return tc ? he::launch_mac_tc(c->C, ctN, pt, o0, st0, o1, st1, s.nI, s.nJ, s.nLb, batch, c->d_err, st)
               : he::launch_mac(c->C, ctN, pt, o0, st0, o1, st1, s.nI, s.nJ, s.nLb, batch, c->d_err, st);
@@ -645,7 +793,7 @@ static int matmul_device(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, u
   // compact output: per ciphertext [c0 at the decoded coefficients: L x N/k_b][c1: L x N]
   const u32 logkb = log2u(blk->k_b);
   const u64 Nc = N >> logkb, ct_stride = L * (Nc + N);
-  u64* c0_ntt = ctN + (u64)batch * operand_words(c, 2 * s.nLb, s.nJ);  // after the inputs' NTT
+  u64* c0_ntt = ctN + (u64)batch * operand_words(c, blk, 2 * s.nLb, s.nJ);  // after the inputs' NTT
   r = launch(c, tc ? KMacTc : KMac, st, "matmul: multiply-accumulate",
              [&] { return mac(c0_ntt, L * N, ct_out + L * Nc, ct_stride); });
   if (r) return r;
@@ -752,8 +900,12 @@ int he_autotune_blocking(he_ctx* c, uint32_t m, uint32_t k, uint32_t n, uint32_t
     void* ws = base + p.w + p.pt + p.in + p.out;
     Shape s = shape_of(m, k, n, &b);
     auto encode = [&] {
+      if (use_coset(c, &b))
+        return launch(c, KCosetEnc, st, "autotune: encode (cosets)", [&] {
+          return he::launch_coset_encode_weights(c->C, W, k, n, to_blk(&b), s.nI, s.nJ, batch, pt, st);
+        });
       return launch(c, KEncode, st, "autotune: encode", [&] {
-        return he::launch_encode_weights(c->C, W, k, n, to_blk(&b), s.nI, s.nJ, batch, use_tc(c, s.nJ), pt, st);
+        return he::launch_encode_weights(c->C, W, k, n, to_blk(&b), s.nI, s.nJ, batch, use_tc(c, &b, s.nJ), pt, st);
       });
     };
     if ((rc = launch(c, KProbe, st, "autotune: fill", [&] {
@@ -788,7 +940,8 @@ int he_autotune_blocking(he_ctx* c, uint32_t m, uint32_t k, uint32_t n, uint32_t
 
 int he_set_mac_engine(he_ctx* c, uint32_t engine) {
   if (!c) return fail(HE_EINVAL, "ctx is NULL");
-  if (engine > HE_MAC_TENSOR) return fail(HE_EINVAL, "engine must be HE_MAC_AUTO, HE_MAC_INTEGER or HE_MAC_TENSOR");
+  if (engine > HE_MAC_COSET)
+    return fail(HE_EINVAL, "engine must be HE_MAC_AUTO, HE_MAC_INTEGER, HE_MAC_TENSOR or HE_MAC_COSET");
   c->mac_engine = engine;
   return HE_OK;
 }
@@ -802,7 +955,14 @@ int he_get_mac_engine(const he_ctx* c, uint32_t* engine) {
 int he_mac_uses_tensor_cores(const he_ctx* c, uint32_t k, const he_blocking* blk, uint32_t* yes) {
   if (!c || !yes) return fail(HE_EINVAL, "NULL argument");
   if (int r = check_blk(c, blk)) return r;
-  *yes = use_tc(c, shape_of(1, k, 1, blk).nJ) ? 1 : 0;
+  *yes = use_tc(c, blk, shape_of(1, k, 1, blk).nJ) ? 1 : 0;
+  return HE_OK;
+}
+
+int he_mac_uses_cosets(const he_ctx* c, const he_blocking* blk, uint32_t* yes) {
+  if (!c || !yes) return fail(HE_EINVAL, "NULL argument");
+  if (int r = check_blk(c, blk)) return r;
+  *yes = use_coset(c, blk) ? 1 : 0;
   return HE_OK;
 }
 
@@ -947,6 +1107,7 @@ namespace {
 struct MultiPlan {
   he::MultiTable T;
   u64 fwd = 0, mac = 0, tc = 0, inv = 0, c0 = 0, ws_bytes = 0;
+  u64 cfwd = 0, cinv = 0;  // blocks of the coset grids (coset products)
   u32 max_nc = 0;  // shared-memory words of the largest c0 transform
 };
 
@@ -1026,6 +1187,18 @@ int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* w
       }
       s.nLb = lb;
     }
+    it.fwd_begin = P->fwd;
+    it.mac_begin = P->mac;
+    it.inv_begin = P->inv;
+    it.c0_begin = P->c0;
+    if (use_coset(c, &x.blk)) {  // forward, multiply-accumulate and inverse in the coset grids
+      const CosetGeom cg = coset_geom(c, &x.blk, s.nI, s.nJ, s.nLb);
+      u64* ws = take(up256(cg.ctn_words * 8) + cg.acc_words * 8);
+      coset_item(c, it, &x.blk, s, compact, ws, &P->cfwd, &P->tc, &P->cinv);
+      continue;
+    }
+    it.cfwd_begin = P->cfwd;
+    it.cinv_begin = P->cinv;
     it.nI = s.nI;
     it.nJ = s.nJ;
     it.nLb = s.nLb;
@@ -1033,9 +1206,9 @@ int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* w
     it.logkb = compact ? log2u(x.blk.k_b) : 0;
     it.tilesR = (2 * s.nLb + rows_t - 1) / rows_t;
     it.tilesC = (s.nI + cols_t - 1) / cols_t;
-    it.tc = use_tc(c, s.nJ);
+    it.tc = use_tc(c, &x.blk, s.nJ);
     const u64 out_cts = (u64)s.nLb * s.nI;
-    it.ctN = take(operand_words(c, 2 * s.nLb, s.nJ) * 8);
+    it.ctN = take(operand_words(c, &x.blk, 2 * s.nLb, s.nJ) * 8);
     if (compact) {
       it.c0_ntt = take(out_cts * L * N * 8);
       P->max_nc = std::max<u32>(P->max_nc, he::c0_smem_words((u32)N, it.logkb));
@@ -1047,13 +1220,14 @@ int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* w
     it.c0_begin = P->c0;
     it.tc_begin = P->tc;
     P->fwd += (u64)s.nLb * s.nJ * 2 * L;
-    if (it.tc) P->tc += he::tc_units((u32)N, (u32)L, s.nI, s.nLb);
+    if (it.tc) P->tc += he::tc_units((u32)N, (u32)L, s.nI, 2 * s.nLb);
     else P->mac += (N >> 5) * it.tilesR * it.tilesC * L;
     P->inv += out_cts * (compact ? 1 : 2) * L;
     P->c0 += compact ? out_cts * L : 0;
   }
   P->ws_bytes = off;
-  if (P->fwd >= (1ull << 31) || P->mac >= (1ull << 31) || P->tc >= (1ull << 31) || P->inv >= (1ull << 31))
+  if (P->fwd >= (1ull << 31) || P->mac >= (1ull << 31) || P->tc >= (1ull << 31) || P->inv >= (1ull << 31) ||
+      P->cfwd >= (1ull << 31) || P->cinv >= (1ull << 31))
     return fail(HE_EINVAL, "multi-product launch too large");
   return HE_OK;
 }
@@ -1078,7 +1252,12 @@ int he_matmul_multi(he_ctx* c, uint32_t count, const he_product* items, void* wo
   if (workspace_bytes < P.ws_bytes) return fail(HE_ENOMEM, "workspace smaller than he_multi_workspace_bytes()");
   if (int r = set_device(c)) return r;
   cudaStream_t st = (cudaStream_t)stream;
-  int r = launch(c, KNttFwd, st, "multi: forward NTT", [&] { return he::launch_fwd_multi(c->C, P.T, P.fwd, st); });
+  int r = HE_OK;
+  if (P.fwd)
+    r = launch(c, KNttFwd, st, "multi: forward NTT", [&] { return he::launch_fwd_multi(c->C, P.T, P.fwd, st); });
+  if (!r && P.cfwd)
+    r = launch(c, KCosetFwd, st, "multi: coset forward transforms",
+               [&] { return he::launch_coset_fwd_multi(c->C, P.T, P.cfwd, st); });
   if (!r && P.mac)
     r = launch(c, KMac, st, "multi: multiply-accumulate",
                [&] { return he::launch_mac_multi(c->C, P.T, P.mac, c->d_err, st); });
@@ -1089,9 +1268,12 @@ int he_matmul_multi(he_ctx* c, uint32_t count, const he_product* items, void* wo
     r = launch(c, KInvC0, st, "multi: inverse NTT of c1 + pruned inverse NTT of c0",
                [&] { return he::launch_inv_c0_multi(c->C, P.T, P.inv, P.c0, P.max_nc, st); });
     if (!r && !he::inv_c0_fused(c->C)) c->launches.fetch_add(1, std::memory_order_relaxed);  // two grids there
-  } else if (!r) {
+  } else if (!r && P.inv) {
     r = launch(c, KInttMask, st, "multi: inverse NTT", [&] { return he::launch_inv_multi(c->C, P.T, P.inv, st); });
   }
+  if (!r && P.cinv)
+    r = launch(c, KCosetInv, st, "multi: coset inverse transforms + mask",
+               [&] { return he::launch_coset_inv_multi(c->C, P.T, P.cinv, st); });
   return r;
 }
 
@@ -1105,8 +1287,6 @@ void product_io_words(const he_ctx* c, const he_product& x, u64* in_w, u64* out_
   *in_w = empty ? 0 : si.in_words;
   *out_w = empty ? 0 : ((x.flags & HE_DROP_C0) ? si.out_words_compact : si.out_words);
 }
-
-u64 up256(u64 b) { return (b + 255) & ~(u64)255; }
 
 }  // namespace
 

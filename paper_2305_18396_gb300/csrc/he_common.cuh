@@ -40,6 +40,9 @@ struct PrimeConsts {
   const u64* psi_sh;
   const u64* ipsi;     // psi^{-brev(k)}, k < N      (inverse twiddles)
   const u64* ipsi_sh;
+  // coset products (coset.cuh): for k < N/2 the four words (1 + psi^{brev(k)} w) / (2N),
+  // its Shoup companion, (1 - psi^{brev(k)} w) / (2N), its companion; w = psi^{-N/2}
+  const u64* fold;
 };
 
 struct Consts {

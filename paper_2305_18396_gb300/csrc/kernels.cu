@@ -446,7 +446,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc(const u64* __restrict_
   const u64 per_in = tc_words(2 * nLb, nJ, C.L, C.N), per_pt = tc_weight_words(nI, nJ, C.L, C.N);
   auto get = [&](u64 g, TcWork& w) {
     const u64 item = g / units;
-    tc_unit(g % units, C.N, nI, nLb, w);
+    tc_unit(g % units, C.N, nI, 2 * nLb, w);
+    w.acc = nullptr;
+    w.logG = 0;
     w.ctN = ctN + item * per_in;
     w.ptd = reinterpret_cast<const uint8_t*>(pt + item * per_pt);
     w.out = out;
@@ -732,7 +734,7 @@ cudaError_t launch_mac_tc(const Consts& C, const u64* ctN, const u64* pt, u64* o
   o.base[1] = out1;
   o.ct_stride[0] = stride0;
   o.ct_stride[1] = stride1;
-  const u64 units = tc_units(C.N, C.L, nI, nLb);
+  const u64 units = tc_units(C.N, C.L, nI, 2 * nLb);
   if (!units || !nJ || !batch) return cudaGetLastError();
   if (C.logN < 9) return cudaErrorInvalidValue;
   const u64 total = units * batch, grid = std::min<u64>(total, (u64)device_sms());

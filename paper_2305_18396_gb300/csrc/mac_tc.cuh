@@ -62,8 +62,10 @@ constexpr u32 kTcJB = 16;          // k-blocks per stage (one MMA K step)
 constexpr u32 kTcRound = 8;        // stages per exact accumulation round (128 k-blocks)
 constexpr u32 kTcSlots = 8;        // consecutive slots per work unit
 constexpr u32 kTcStages = 4;       // stages in flight (measured: 6 stages, 225 KB of shared memory, ran 4% slower)
-constexpr u32 kTcEpiWarps = 4;     // epilogue: one per TMEM lane quadrant
-constexpr u32 kTcThreads = 32 * (3 + kTcEpiWarps);  // producer, MMA, digit split, epilogue: 224
+constexpr u32 kTcSplitWarps = 2;   // digit split of the input rows: planes 0-3 and 4-6
+constexpr u32 kTcEpi0 = 2 + kTcSplitWarps;  // first epilogue warp
+constexpr u32 kTcEpiWarps = 8;     // epilogue: two per TMEM lane quadrant (warp w reads quadrant w mod 4), 8 rows each
+constexpr u32 kTcThreads = 32 * (kTcEpi0 + kTcEpiWarps);  // producer, MMA, digit split, epilogue: 384
 constexpr u32 kTcCols = 512;       // TMEM: two accumulator sets of 13 x 16 columns, at 0 and 256
 constexpr u32 kTcSetCols = 256;
 constexpr u32 kTcRawRow = kTcJB * 8;                          // bytes per staged input row
@@ -73,7 +75,7 @@ constexpr u32 kTcGroupBytes = 8 * kTcAKBytes;                 // one 8-row group
 constexpr u32 kTcABytes = kTcM * kTcAKBytes;                  // weight digit tile of a unit
 constexpr u32 kTcBBytes = kTcPlanes * kTcR * kTcJB * 2;       // input digit tile (112 rows)
 constexpr u32 kTcZBytes = (kTcDiag - kTcPlanes) * kTcR * kTcJB * 2;  // zero tile (96 rows)
-constexpr u32 kTcAccBytes = kTcR * 32 * kTcEpiWarps * 8;     // the epilogue's running sums mod q
+constexpr u32 kTcAccBytes = kTcR * kTcM * 8;                // the epilogue's running sums mod q
 constexpr u32 kTcStageBytes = kTcABytes + kTcRawBytes + kTcBBytes;
 constexpr u32 kTcSmem = kTcStages * kTcStageBytes + kTcZBytes + kTcAccBytes + 128;
 static_assert(kTcSmem <= 227 * 1024, "tensor-core MAC shared memory above the per-block limit");
@@ -131,31 +133,41 @@ struct TcShared {
 // One work unit: slots s0 .. s0 + kTcSlots - 1 of prime l, weight rows I0 .. I0 + 127 and output
 // rows r0 .. r0 + 15 of one product (input NTT ctN, weight digit tiles ptd; outputs `out`, the
 // product's first output ciphertext at index ct0).
+//
+// Coset products (coset.cuh): each prime has S = 2D slots instead of N and the operand rows
+// are (Lb, component, coset g), row = (2 Lb + c) G + g (R = 2 nLb G rows); acc != nullptr
+// then receives the sums, output ciphertext o, component c, prime l at
+// acc + ((o 2 + c) L + l) 2N + g S + s.
 struct TcWork {
   const u64* ctN;
   const uint8_t* ptd;
   OutPlace out;
+  u64* acc;
   u64 ct0;
   u32 nI, nJ, nLb, I0, r0, s0, l;
+  u32 S, R, logG;  // slots per prime, operand rows, log2 of the cosets (coset products)
 };
 
 // Work units of one product: ciphertext-row tiles fastest, then weight-row tiles, then groups
 // of kTcSlots slots, then primes -- the units that share a slot's operands run together and
 // re-read them from L2.
+// S slots per prime, R operand rows (2 nLb, or 2 nLb G for coset products).
 __host__ __device__ inline u32 tc_tiles_I(u32 nI) { return (nI + kTcM - 1) / kTcM; }
-__host__ __device__ inline u32 tc_tiles_R(u32 nLb) { return (2 * nLb + kTcR - 1) / kTcR; }
-__host__ __device__ inline u64 tc_units(u32 N, u32 L, u32 nI, u32 nLb) {
-  return (u64)L * (N / kTcSlots) * tc_tiles_I(nI) * tc_tiles_R(nLb);
+__host__ __device__ inline u32 tc_tiles_R(u32 R) { return (R + kTcR - 1) / kTcR; }
+__host__ __device__ inline u64 tc_units(u32 S, u32 L, u32 nI, u32 R) {
+  return (u64)L * (S / kTcSlots) * tc_tiles_I(nI) * tc_tiles_R(R);
 }
 
-__device__ __forceinline__ void tc_unit(u64 u, u32 N, u32 nI, u32 nLb, TcWork& w) {
-  const u32 nRt = tc_tiles_R(nLb), nIt = tc_tiles_I(nI);
+__device__ __forceinline__ void tc_unit(u64 u, u32 S, u32 nI, u32 R, TcWork& w) {
+  const u32 nRt = tc_tiles_R(R), nIt = tc_tiles_I(nI);
   w.r0 = (u32)(u % nRt) * kTcR;
   u /= nRt;
   w.I0 = (u32)(u % nIt) * kTcM;
   u /= nIt;
-  w.s0 = (u32)(u % (N / kTcSlots)) * kTcSlots;
-  w.l = (u32)(u / (N / kTcSlots));
+  w.s0 = (u32)(u % (S / kTcSlots)) * kTcSlots;
+  w.l = (u32)(u / (S / kTcSlots));
+  w.S = S;
+  w.R = R;
 }
 
 // One block per SM: work units blockIdx.x, blockIdx.x + gridDim.x, ... < total, each unit
@@ -175,7 +187,7 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
   if (threadIdx.x == 0) {
     for (u32 b = 0; b < kTcStages; ++b) {
       mbar_init(&sh.full[b], 1);
-      mbar_init(&sh.conv[b], 1);
+      mbar_init(&sh.conv[b], kTcSplitWarps);
       mbar_init(&sh.empty[b], 1);
     }
     for (u32 b = 0; b < 2; ++b) {
@@ -208,7 +220,7 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
     for (u64 g = blockIdx.x; ok && g < total && !*abort_flag; g += gridDim.x) {
       TcWork w;
       get(g, w);
-      const u32 sps = tc_stages(w.nJ), R = 2 * w.nLb;
+      const u32 sps = tc_stages(w.nJ), R = w.R;
       const u32 nw = min(kTcM, w.nI - w.I0), nc = min(kTcR, R - w.r0);
       for (u32 st = 0; st < kTcSlots * sps; ++st, ++i) {
         const u32 b = i % kTcStages;
@@ -223,8 +235,8 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
           const u32 abytes = ((nw + 7) / 8) * kTcGroupBytes;
           fence_proxy_async_smem();
           mbar_arrive_expect_tx(&sh.full[b], abytes + nc * kTcRawRow);
-          bulk_copy_g2s(dst, w.ptd + tc_weight_offset(w.I0, w.l, s, js, w.nI, sps, N), abytes, &sh.full[b]);
-          bulk_copy_g2s(dst + kTcABytes, w.ctN + tc_index(w.r0, js * kTcJB, w.l, s, R, sps, N), nc * kTcRawRow,
+          bulk_copy_g2s(dst, w.ptd + tc_weight_offset(w.I0, w.l, s, js, w.nI, sps, w.S), abytes, &sh.full[b]);
+          bulk_copy_g2s(dst + kTcABytes, w.ctN + tc_index(w.r0, js * kTcJB, w.l, s, R, sps, w.S), nc * kTcRawRow,
                         &sh.full[b]);
         }
         __syncwarp();
@@ -274,14 +286,15 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
     if (lane == 0) tc::commit(&sh.done);  // every MMA issued has completed once this arrives
     __syncwarp();
     mbar_wait_warp(&sh.done, 0, kWaitLimitNs);
-  } else if (warp == 2) {
+  } else if (warp < kTcEpi0) {
     // ---------------------------------------------------------------- input digit planes
+    const int p0 = warp == 2 ? 0 : 4, p1 = warp == 2 ? 4 : (int)kTcPlanes;  // this warp's planes
     u32 i = 0;
     bool ok = true;
     for (u64 g = blockIdx.x; ok && g < total && !*abort_flag; g += gridDim.x) {
       TcWork w;
       get(g, w);
-      const u32 sps = tc_stages(w.nJ), nc = min(kTcR, 2 * w.nLb - w.r0);
+      const u32 sps = tc_stages(w.nJ), nc = min(kTcR, w.R - w.r0);
       for (u32 st = 0; st < kTcSlots * sps; ++st, ++i) {
         const u32 b = i % kTcStages, jb = min(kTcJB, w.nJ - (st % sps) * kTcJB);
         if (!mbar_wait_warp(&sh.full[b], (i / kTcStages) & 1, kWaitLimitNs)) {
@@ -308,7 +321,8 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
           uint8_t* bt = stage + kTcABytes + kTcRawBytes;
 #pragma unroll
           for (int p = 0; p < (int)kTcPlanes; ++p)
-            *reinterpret_cast<uint4*>(bt + tc::tile_offset(p * kTcR + row, 8 * o, kTcJB * 2, 2)) = digit_plane(u, p);
+            if (p >= p0 && p < p1)
+              *reinterpret_cast<uint4*>(bt + tc::tile_offset(p * kTcR + row, 8 * o, kTcJB * 2, 2)) = digit_plane(u, p);
         }
         tc::fence_smem_to_async();
         __syncwarp();
@@ -319,13 +333,14 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
     // ---------------------------------------------------------------- epilogue
     const u32 q = warp & 3;        // TMEM lane quadrant this warp may read
     const u32 I = 32 * q + lane;   // weight row (TMEM lane) of this thread's outputs
-    u64* const acc = accs + (threadIdx.x - 96);  // acc[r * 128]: this thread's sum of output row r
+    const u32 rh = (warp - kTcEpi0) >> 2;  // output rows 8 rh .. 8 rh + 7
+    u64* const acc = accs + I;     // acc[r * 128]: this thread's sum of output row r
     u32 round = 0;
     bool ok = true;
     for (u64 g = blockIdx.x; ok && g < total && !*abort_flag; g += gridDim.x) {
       TcWork w;
       get(g, w);
-      const u32 sps = tc_stages(w.nJ), R = 2 * w.nLb, rounds = (sps + kTcRound - 1) / kTcRound;
+      const u32 sps = tc_stages(w.nJ), R = w.R, rounds = (sps + kTcRound - 1) / kTcRound;
       const PrimeConsts& P = C.p[w.l];
       u32 clo[kTcDiag], chi[kTcDiag];  // 256^d mod q_l in 32-bit halves
 #pragma unroll
@@ -348,7 +363,8 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
           // A = sum (D_d + 2^24) lo_d < 2^61 and B = sum (D_d + 2^24) hi_d < 2^47 take one
           // mad.wide each per diagonal; A + 2^32 B, less 2^24 sum_d 256^d, is reduced once.
 #pragma unroll
-          for (u32 hh = 0; hh < kTcR / 4; ++hh) {
+          for (u32 h4 = 0; h4 < kTcR / 8; ++h4) {
+            const u32 hh = 2 * rh + h4;  // rows 4 hh .. 4 hh + 3
             u64 A[4] = {0, 0, 0, 0}, Bh[4] = {0, 0, 0, 0};
 #pragma unroll
             for (u32 gg = 0; gg < 3; ++gg) {  // diagonals 0-3, 4-7, 8-12 (bounded registers)
@@ -363,14 +379,14 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
                 for (u32 dd = 0; dd < nd; ++dd) {
                   const uint32_t D = (uint32_t)(f32_to_s32(v[dd][r]) + (1 << 24));
                   mad_wide(A[r], D, clo[d0 + dd]);
-                  mad_wide(Bh[r], D, chi[d0 + dd]);
+                  if (d0 + dd >= 4) mad_wide(Bh[r], D, chi[d0 + dd]);  // 256^d < 2^32 below d = 4
                 }
             }
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
               u64 x = reduce_word(A[r], P) + csub(mul_shoup(Bh[r], P.r32, P.r32_sh, P.q), P.q);  // [0, 2q)
               x = sub_mod(csub(x, P.q), P.pw256_bias, P.q);
-              u64& a = acc[(4 * hh + r) * 32 * kTcEpiWarps];
+              u64& a = acc[(4 * hh + r) * kTcM];
               a = rd ? add_mod(a, x, P.q) : x;
             }
           }
@@ -381,13 +397,26 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
         if (!ok) break;
         const u32 s = w.s0 + slot;  // the slot is complete: store its outputs
         if (w.I0 + I < w.nI) {
+          if (w.acc) {  // coset product: row (2 Lb + c) G + g
+            const u32 G = 1u << w.logG;
 #pragma unroll
-          for (u32 r = 0; r < kTcR; ++r) {
-            const u32 row = w.r0 + r;
-            if (row < R) {
-              const u32 c = row & 1;
-              w.out.base[c][(w.ct0 + (u64)(row >> 1) * w.nI + w.I0 + I) * w.out.ct_stride[c] + (u64)w.l * N + s] =
-                  acc[r * 32 * kTcEpiWarps];
+            for (u32 r = 8 * rh; r < 8 * rh + 8; ++r) {
+              const u32 row = w.r0 + r;
+              if (row < R) {
+                const u32 rc = row >> w.logG, g = row & (G - 1);
+                w.acc[(((w.ct0 + (u64)(rc >> 1) * w.nI + w.I0 + I) * 2 + (rc & 1)) * C.L + w.l) * (2ull * N) +
+                      (u64)g * w.S + s] = acc[r * kTcM];
+              }
+            }
+          } else {
+#pragma unroll
+            for (u32 r = 8 * rh; r < 8 * rh + 8; ++r) {
+              const u32 row = w.r0 + r;
+              if (row < R) {
+                const u32 c = row & 1;
+                w.out.base[c][(w.ct0 + (u64)(row >> 1) * w.nI + w.I0 + I) * w.out.ct_stride[c] + (u64)w.l * N + s] =
+                    acc[r * kTcM];
+              }
             }
           }
         }

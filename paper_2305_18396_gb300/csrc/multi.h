@@ -2,6 +2,7 @@
 #pragma once
 
 #include "he_common.cuh"
+#include "kernels.h"
 
 namespace he {
 
@@ -36,6 +37,12 @@ struct MultiItem {
   u32 compact, tilesR, tilesC, tc;  // tc: operands in the stage-tiled layout, tensor-core MAC
   u64* c1_ntt;                       // workspace (merged items): NTT-domain c1 of every output
   u32 seg0, nseg;                    // merged items: segments seg0 .. seg0 + nseg - 1
+  // coset products (coset.cuh; tc is set too): the inputs' coset transforms in ctN (rows
+  // (2 Lb + c) G + g, 2D slots per prime), the multiply-accumulate's sums in acc
+  // ([out ct][2][L][2N]); cfwd_begin / cinv_begin: first block in the coset grids
+  u64* acc;
+  u64 cfwd_begin, cinv_begin;
+  u32 coset, logD;
 };
 
 struct MultiTable {
@@ -54,6 +61,15 @@ cudaError_t launch_mac_multi(const Consts& C, const MultiTable& T, u64 blocks, i
 cudaError_t launch_mac_tc_multi(const Consts& C, const MultiTable& T, u64 blocks, int* err, cudaStream_t st);
 cudaError_t launch_inv_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
 cudaError_t launch_c0_multi(const Consts& C, const MultiTable& T, u64 blocks, u32 c0_words, cudaStream_t st);
+// Coset products: the forward transforms of their inputs (one block per input polynomial)
+// and the inverse transforms, fold and mask of their outputs (one block per output
+// component), each as one grid over the coset items of the table.
+cudaError_t launch_coset_fwd_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
+cudaError_t launch_coset_inv_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
+// Encoded weights of coset products: per weight block the zero-padded length-2D transform
+// of its pi_A block, as bf16 digit tiles over 2D slots; `batch` same-shape matrices.
+cudaError_t launch_coset_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u32 batch,
+                                        u64* pt, cudaStream_t st);
 // The inverse-NTT grid and the c0 grid as one launch where inv_c0_fused(C), else two.
 bool inv_c0_fused(const Consts& C);
 cudaError_t launch_inv_c0_multi(const Consts& C, const MultiTable& T, u64 inv_blocks, u64 c0_blocks, u32 c0_words,

@@ -4,7 +4,7 @@ Compact products (Sec. 3.1.3) with the same encoded weights, shape and blocking 
 one product whose row-blocks are the requests' row-blocks back to back (each weight stage
 of Algorithm 1 step 3 then serves every request's rows); each request keeps its own input
 ciphertexts, output buffer, mask seed and output indices.  Every merged result must equal
-the request's own he_matmul call bit for bit, on both multiply-accumulate engines, with a
+the request's own he_matmul call bit for bit, on every multiply-accumulate engine, with a
 mask seed read from device memory among them; sampled outputs are also compared with the
 oracle's Pi_MatMul of the oracle's own encryptions.
 """
@@ -27,11 +27,11 @@ def B():
     return binding
 
 
-@pytest.mark.parametrize("engine", ["tensor", "integer"])
+@pytest.mark.parametrize("engine", ["coset", "tensor", "integer"])
 def test_merged_requests_equal_their_own_calls_and_the_oracle(B, engine):
     N, L = 4096, 2
     ctx = B.Context(N, L)
-    ctx.set_mac_engine(B.HE_MAC_TENSOR if engine == "tensor" else B.HE_MAC_INTEGER)
+    ctx.set_mac_engine({"coset": B.HE_MAC_COSET, "tensor": B.HE_MAC_TENSOR, "integer": B.HE_MAC_INTEGER}[engine])
     P = O.Params(N, L)
     s = O.keygen(P, S.SEED_KEY)
     mats = {"a": (384, 96, (4, 8, 16)), "b": (160, 200, (8, 4, 16))}  # k, n, blocking

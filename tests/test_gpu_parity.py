@@ -233,7 +233,10 @@ def test_launch_count_and_profile(B):
     stats = B.he_profile_read(ctx)
     B.he_profile_enable(ctx, False)
     assert B.he_launch_count(ctx) - before == 3
-    assert set(stats) == {"ntt_forward", "mac", "intt_mask"}
+    if ctx.uses_cosets(blk):  # n_b k_b = 512 <= N/2: the default engine's coset form
+        assert set(stats) == {"coset_forward", "mac_tc", "coset_inverse"}
+    else:
+        assert set(stats) == {"ntt_forward", "mac", "intt_mask"}
     assert all(v["launches"] == 1 and v["total_ms"] > 0 for v in stats.values())
 
 

@@ -83,12 +83,13 @@ def test_tensor_mac_equals_integer_mac_and_oracle(B, N, L, m, k, n, blk):
 
 
 def test_tensor_mac_batch_and_mixed_multi_launch(B):
-    """Same-shape batch on the tensor cores; a multi-product launch with one tensor-core
-    product (nJ 48) and one integer product (nJ 8) under the default engine."""
+    """Same-shape batch on the tensor cores (through the cosets, n_b k_b = 128); a
+    multi-product launch with that product and one on the integer pipe (n_b k_b = N: no
+    coset form; nJ 4) under the default engine."""
     N, L = 4096, 2
     P = O.Params(N, L)
     ctx = ctx_for(B, N, L, B.HE_MAC_AUTO)
-    blk_t, blk_i = (8, 8, 16), (8, 32, 16)
+    blk_t, blk_i = (8, 8, 16), (1, 64, 64)
     m, k, n = 24, 384, 96
     assert ctx.uses_tensor_cores(k, blk_t) and not ctx.uses_tensor_cores(256, blk_i)
     s, X, W, ct = _inputs(P, blk_t, m, k, n, 90)
