@@ -231,11 +231,12 @@ __host__ __device__ constexpr int coset_inv_last_s0() {
   else return S0;
 }
 
-// Inverse coset transform of one output component: load(g, slot) -> the sum at slot `slot`
-// of coset g, in [0, q); store(e, v) <- coefficient e in [0, q) (each e once).  sm:
-// S::kSmemWords words.  blockDim.x == S::T.
-template <class S, int LOGD, class Load, class Store>
-__device__ __forceinline__ void coset_inverse_fast(u64* sm, const PrimeConsts& P, Load&& load, Store&& store) {
+// Inverse coset transform of one output component: src[g 2D + slot] is the sum at slot
+// `slot` of coset g, in [0, q) (src 16-byte aligned); store(e, v) <- coefficient e in
+// [0, q) (each e once).  sm: S::kSmemWords words.  blockDim.x == S::T.
+template <class S, int LOGD, class Store>
+__device__ __forceinline__ void coset_inverse_fast(u64* sm, const PrimeConsts& P, const u64* __restrict__ src,
+                                                   Store&& store) {
   constexpr int D = 1 << LOGD;
   constexpr u32 G = S::N >> LOGD;
   const u64 q = P.q, two_q = P.two_q;
@@ -246,8 +247,13 @@ __device__ __forceinline__ void coset_inverse_fast(u64* sm, const PrimeConsts& P
 #pragma unroll
     for (u32 h = 0; h < 2; ++h) {
       u64 v[D];
+      const ulonglong2* sv = reinterpret_cast<const ulonglong2*>(src + ((u64)g << (LOGD + 1)) + (h << LOGD));
 #pragma unroll
-      for (int j = 0; j < D; ++j) v[j] = load(g, (h << LOGD) + j);
+      for (int j = 0; j < D; j += 2) {
+        const ulonglong2 t = sv[j >> 1];
+        v[j] = t.x;
+        v[j + 1] = t.y;
+      }
 #pragma unroll
       for (int s = LOGD; s >= 1; --s) {
         const int t = D >> s;

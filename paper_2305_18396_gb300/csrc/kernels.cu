@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_forward(const u64* src, u64
                                                              const __grid_constant__ Consts C) {
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
-  const PrimeConsts& P = C.p[poly % C.L];
+  const PrimeConsts P = C.p[poly % C.L];
   const u64* s = src + poly * C.N;
   for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) sm[i] = s[i];
   __syncthreads();
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_inverse(const u64* src, u64
                                                              const __grid_constant__ Consts C) {
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
-  const PrimeConsts& P = C.p[poly % C.L];
+  const PrimeConsts P = C.p[poly % C.L];
   const u64* s = src + poly * C.N;
   for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) sm[i] = s[i];
   __syncthreads();
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kNttThreads) k_poly_mul(const u64* a, const u6
   u64* sa = sm;
   u64* sb = sm + C.N;
   const u64 poly = blockIdx.x;
-  const PrimeConsts& P = C.p[poly % C.L];
+  const PrimeConsts P = C.p[poly % C.L];
   for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) {
     sa[i] = a[poly * C.N + i];
     sb[i] = b[poly * C.N + i];
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt_forward_mm_small(const u64*
   const u32 c = (local / C.L) % 2;
   const u32 LbJ = (u32)(local / (2 * C.L));
   const u32 Lb = LbJ / nJ, J = LbJ % nJ;
-  const PrimeConsts& P = C.p[l];
+  const PrimeConsts P = C.p[l];
   u64* dst = ctN + item * item_polys * C.N;
   for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) sm[i] = src[poly * C.N + i];
   __syncthreads();
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
   using S = NttShape<LOGN, LOGR>;
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
-  const PrimeConsts& P = C.p[poly % C.L];
+  const PrimeConsts P = C.p[poly % C.L];
   const u64* s = src + poly * S::N;
   u64* d = dst + poly * S::N;
   ntt_forward_block<S>(sm, P, [&](u32 e) { return s[e]; }, [&](u32 e, u64 v) { d[e] = v; });
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
   using S = NttShape<LOGN, LOGR>;
   extern __shared__ u64 sm[];
   const u64 poly = blockIdx.x;
-  const PrimeConsts& P = C.p[poly % C.L];
+  const PrimeConsts P = C.p[poly % C.L];
   const u64* s = src + poly * S::N;
   u64* d = dst + poly * S::N;
   ntt_inverse_block<S>(sm, P, [&](u32 e) { return s[e]; }, [&](u32 e, u64 v) { d[e] = v; });
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
 __global__ void __launch_bounds__(kNttThreads) k_keygen(u64 seed, u64* sk, const __grid_constant__ Consts C) {
   extern __shared__ u64 sm[];
   const u32 l = blockIdx.x;
-  const PrimeConsts& P = C.p[l];
+  const PrimeConsts P = C.p[l];
   for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) {
     long long v = (long long)(lo64(draw(seed, i, 0, kDomainSecret, 0)) % 3ull) - 1;
     sm[i] = signed_to_residue(v, P.q);
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kNttThreads) k_encrypt(const u64* sk, const u6
                                                          const __grid_constant__ Consts C) {
   extern __shared__ u64 sm[];
   const u32 j = blockIdx.x / C.L, l = blockIdx.x % C.L;
-  const PrimeConsts& P = C.p[l];
+  const PrimeConsts P = C.p[l];
   const u64 N = C.N;
   u64* c0 = ct + ((u64)j * 2 * C.L + l) * N;
   u64* c1 = ct + ((u64)j * 2 * C.L + C.L + l) * N;
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kNttThreads) k_decrypt(const u64* sk, const u6
   const u32 j = blockIdx.x;
   const u64 N = C.N;
   for (u32 l = 0; l < C.L; ++l) {
-    const PrimeConsts& P = C.p[l];
+    const PrimeConsts P = C.p[l];
     u64* x = sm + (u64)l * N;
     const u64* c0 = ct + ((u64)j * 2 * C.L + l) * N;
     const u64* c1 = ct + ((u64)j * 2 * C.L + C.L + l) * N;
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kNttThreads) k_decrypt(const u64* sk, const u6
   for (u32 i = threadIdx.x; i < N; i += blockDim.x) {
     u64 ip = 0, fh = 0, fl = 0;  // integer part, fraction (2^-64 and 2^-128 words)
     for (u32 l = 0; l < C.L; ++l) {
-      const PrimeConsts& P = C.p[l];
+      const PrimeConsts P = C.p[l];
       u64 y = csub(mul_shoup(sm[(u64)l * N + i], P.crt, P.crt_sh, P.q), P.q);
       u64 l1 = y * P.theta_lo, h1 = __umul64hi(y, P.theta_lo);
       u64 l2 = y * P.theta_hi, h2 = __umul64hi(y, P.theta_hi);
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kNttThreads) k_encode_weights(const u64* W, u3
   const u32 l = poly % C.L;
   const u32 IJ = (u32)(poly / C.L);
   const u32 I = IJ / nJ, J = IJ % nJ;
-  const PrimeConsts& P = C.p[l];
+  const PrimeConsts P = C.p[l];
   const u32 nk = b.n_b * b.k_b;
   const u64 half_t = (C.tmask >> 1) + 1;
   for (u32 p = threadIdx.x; p < C.N; p += blockDim.x) {
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
   const u32 l = poly % C.L;
   const u32 IJ = (u32)(poly / C.L);
   const u32 I = IJ / nJ, J = IJ % nJ;
-  const PrimeConsts& P = C.p[l];
+  const PrimeConsts P = C.p[l];
   const u32 nk = b.n_b * b.k_b;
   const u64 half_t = (C.tmask >> 1) + 1;
   auto load = [&](u32 p) -> u64 {
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
   const u32 l = poly % C.L;
   const u32 c = (poly / C.L) % 2;
   const u32 o = (u32)((poly / (2 * C.L)) % out_cts);
-  const PrimeConsts& P = C.p[l];
+  const PrimeConsts P = C.p[l];
   u64* d = out + poly * S::N;
   ntt_inverse_block<S>(sm, P, [&](u32 e) { return d[e]; }, [&](u32 e, u64 v) {
     if (c == 0) {
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, LOGR>::T, NttShape<LOGN, LOGR>:
   const u32 c = (local / C.L) % 2;
   const u32 LbJ = (u32)(local / (2 * C.L));
   const u32 Lb = LbJ / nJ, J = LbJ % nJ;
-  const PrimeConsts& P = C.p[l];
+  const PrimeConsts P = C.p[l];
   const u64* sp = src + poly * S::N;
   const u32 nS = tc_stages(nJ);
   u64* dst = ctN + item * (tc ? tc_words(2 * nLb, nJ, C.L, S::N) : (u64)nLb * nJ * 2 * C.L * S::N);
@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(kNttThreads) k_intt_mask(u64* out, u64 out_cts
   const u32 l = poly % C.L;
   const u32 c = (poly / C.L) % 2;
   const u32 o = (u32)((poly / (2 * C.L)) % out_cts);
-  const PrimeConsts& P = C.p[l];
+  const PrimeConsts P = C.p[l];
   u64* d = out + poly * C.N;
   for (u32 i = threadIdx.x; i < C.N; i += blockDim.x) sm[i] = d[i];
   __syncthreads();

@@ -79,7 +79,7 @@ __device__ __forceinline__ void mac_tile_ws(const u64* __restrict__ ctN, const u
   constexpr u32 kConsumers = M::kWR * M::kWC;
 
   const u32 N = C.N, L = C.L;
-  const PrimeConsts& P = C.p[l];
+  const PrimeConsts P = C.p[l];
   const u32 rows = 2 * nLb;
   const u32 nrows = min((u32)M::kRows, rows - r0), ncols = min((u32)M::kCols, nI - c0);
   const u32 nstages = (nJ + JB - 1) / JB;

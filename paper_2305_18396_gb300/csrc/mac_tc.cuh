@@ -61,7 +61,7 @@ constexpr u32 kTcDiag = 13;        // diagonals a + b
 constexpr u32 kTcJB = 16;          // k-blocks per stage (one MMA K step)
 constexpr u32 kTcRound = 8;        // stages per exact accumulation round (128 k-blocks)
 constexpr u32 kTcSlots = 8;        // consecutive slots per work unit
-constexpr u32 kTcStages = 4;       // stages in flight (measured: 6 stages, 225 KB of shared memory, ran 4% slower)
+constexpr u32 kTcStages = 6;       // stages in flight: 225 KB of shared memory (coset products, operands from L2: 2.4% faster than 4)
 constexpr u32 kTcSplitWarps = 2;   // digit split of the input rows: planes 0-3 and 4-6
 constexpr u32 kTcEpi0 = 2 + kTcSplitWarps;  // first epilogue warp
 constexpr u32 kTcEpiWarps = 8;     // epilogue: two per TMEM lane quadrant (warp w reads quadrant w mod 4), 8 rows each
@@ -105,6 +105,35 @@ __device__ __forceinline__ int f32_to_s32(uint32_t bits) {
   int r;
   asm("cvt.rni.s32.f32 %0, %1;" : "=r"(r) : "f"(__uint_as_float(bits)));
   return r;
+}
+
+// The same for an exact integer of magnitude at most 2^22, on the add pipes instead of the
+// conversion unit: x + 1.5 2^23 lies in [2^23, 2^24], where floats are the integers, so its
+// bits are 0x4B400000 + x.
+__device__ __forceinline__ int f32_small_to_s32(uint32_t bits) {
+  return (int)(__float_as_uint(__fadd_rn(__uint_as_float(bits), 12582912.0f)) - 0x4B400000u);
+}
+
+// sum_d D_d 256^d mod q, less 2^24 sum_d 256^d, for four outputs (TMEM words v[d][r], exact
+// f32 integers, |D_d| < 2^24; SMALL: |D_d| <= 2^22).  With D_d + 2^24 in [0, 2^25) and
+// 256^d mod q = lo_d + 2^32 hi_d (hi_d = 0 below d = 4), A = sum (D_d + 2^24) lo_d < 2^61 and
+// B = sum (D_d + 2^24) hi_d < 2^47 take one mad.wide each per diagonal, in two chains each
+// (even and odd d) for instruction-level parallelism; A + 2^32 B is reduced once.
+template <bool SMALL>
+__device__ __forceinline__ void tc_combine4(const uint32_t (&v)[13][4], const u32 (&clo)[13], const u32 (&chi)[13],
+                                            const PrimeConsts& P, u64 (&x)[4]) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    u64 A0 = 0, A1 = 0, B0 = 0, B1 = 0;
+#pragma unroll
+    for (int d = 0; d < 13; ++d) {
+      const uint32_t D = (uint32_t)((SMALL ? f32_small_to_s32(v[d][r]) : f32_to_s32(v[d][r])) + (1 << 24));
+      mad_wide(d & 1 ? A1 : A0, D, clo[d]);
+      if (d >= 4) mad_wide(d & 1 ? B1 : B0, D, chi[d]);
+    }
+    const u64 y = reduce_word(A0 + A1, P) + csub(mul_shoup(B0 + B1, P.r32, P.r32_sh, P.q), P.q);  // [0, 2q)
+    x[r] = sub_mod(csub(y, P.q), P.pw256_bias, P.q);
+  }
 }
 
 // Digit p of u = v + 0x0080808080808080 (v < 2^50) as the bits of an exact f32: byte p of u
@@ -341,7 +370,7 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
       TcWork w;
       get(g, w);
       const u32 sps = tc_stages(w.nJ), R = w.R, rounds = (sps + kTcRound - 1) / kTcRound;
-      const PrimeConsts& P = C.p[w.l];
+      const PrimeConsts P = C.p[w.l];
       u32 clo[kTcDiag], chi[kTcDiag];  // 256^d mod q_l in 32-bit halves
 #pragma unroll
       for (u32 d = 0; d < kTcDiag; ++d) {
@@ -358,36 +387,27 @@ __device__ __forceinline__ void mac_tc_run(const GetWork& get, u64 total, int* e
           }
           tc::fence_after_sync();
           const uint32_t tbase = tmem + set * kTcSetCols + ((32 * q) << 16);
-          // 13 diagonal sums D_d per output (exact integers, |D_d| < 2^24) -> sum_d D_d 256^d
-          // mod q: with D_d + 2^24 in [0, 2^25) and 256^d mod q = lo + 2^32 hi, the sums
-          // A = sum (D_d + 2^24) lo_d < 2^61 and B = sum (D_d + 2^24) hi_d < 2^47 take one
-          // mad.wide each per diagonal; A + 2^32 B, less 2^24 sum_d 256^d, is reduced once.
+          // 13 diagonal sums per output -> sum_d D_d 256^d mod q (tc_combine4); a round of at
+          // most 32 k-blocks keeps |D_d| <= 7 * 32 * 2^14 < 2^22
+          const bool small_round = w.nJ - rd * kTcRound * kTcJB <= 2 * kTcJB;
+          // a warp whose 32 weight rows or 8 output rows all lie past the product's skips
+          // the work (it still waits and arrives, keeping the rounds in step)
+          const bool live = w.I0 + 32 * q < w.nI && w.r0 + 8 * rh < R;
 #pragma unroll
           for (u32 h4 = 0; h4 < kTcR / 8; ++h4) {
+            if (!live) break;
             const u32 hh = 2 * rh + h4;  // rows 4 hh .. 4 hh + 3
-            u64 A[4] = {0, 0, 0, 0}, Bh[4] = {0, 0, 0, 0};
+            uint32_t v[13][4];
 #pragma unroll
-            for (u32 gg = 0; gg < 3; ++gg) {  // diagonals 0-3, 4-7, 8-12 (bounded registers)
-              const u32 d0 = 4 * gg, nd = gg == 2 ? 5 : 4;
-              uint32_t v[5][4];
-#pragma unroll
-              for (u32 dd = 0; dd < nd; ++dd) tc::ld_32x32b_x4(tbase + (d0 + dd) * kTcR + 4 * hh, v[dd]);
-              tc::wait_ld();
-#pragma unroll
-              for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (u32 dd = 0; dd < nd; ++dd) {
-                  const uint32_t D = (uint32_t)(f32_to_s32(v[dd][r]) + (1 << 24));
-                  mad_wide(A[r], D, clo[d0 + dd]);
-                  if (d0 + dd >= 4) mad_wide(Bh[r], D, chi[d0 + dd]);  // 256^d < 2^32 below d = 4
-                }
-            }
+            for (u32 d = 0; d < kTcDiag; ++d) tc::ld_32x32b_x4(tbase + d * kTcR + 4 * hh, v[d]);
+            tc::wait_ld();
+            u64 x[4];
+            if (small_round) tc_combine4<true>(v, clo, chi, P, x);
+            else tc_combine4<false>(v, clo, chi, P, x);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-              u64 x = reduce_word(A[r], P) + csub(mul_shoup(Bh[r], P.r32, P.r32_sh, P.q), P.q);  // [0, 2q)
-              x = sub_mod(csub(x, P.q), P.pw256_bias, P.q);
               u64& a = acc[(4 * hh + r) * kTcM];
-              a = rd ? add_mod(a, x, P.q) : x;
+              a = rd ? add_mod(a, x[r], P.q) : x[r];
             }
           }
           tc::fence_before_sync();

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_fwd_multi_t(cons
   } else {
     sp = it.ct_in + local * N;
   }
-  const PrimeConsts& P = C.p[l];
+  const PrimeConsts P = C.p[l];
   const u32 logD = it.logD, logG = LOGN - logD;
   const u32 S2 = 2u << logD, R = (2 * it.nLb) << logG, nS = tc_stages(it.nJ), row0 = (Lb * 2 + c) << logG;
   u64* dst = it.ctN;
@@ -232,8 +232,8 @@ __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_inv_multi_t(cons
   const u64 local = blockIdx.x - it.cinv_begin;
   const u32 N = S::N, L = C.L, l = local % L, c = (local / L) % 2;
   const u64 o = local / (2 * L);
-  const PrimeConsts& P = C.p[l];
-  const u32 logD = it.logD, D = 1u << logD, S2 = 2u << logD;
+  const PrimeConsts P = C.p[l];
+  const u32 logD = it.logD, D = 1u << logD;
   const u64* src = it.acc + local * 2 * (u64)N;
   u64* base;
   u64 seed, oo = o;
@@ -260,11 +260,10 @@ __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_inv_multi_t(cons
       base[(compact ? (u64)L * Nc : (u64)L * N) + (u64)l * N + e] = v;
     }
   };
-  auto load = [&](u32 g, u32 slot) { return src[(u64)g * S2 + slot]; };
   switch (logD) {
-    case 3: coset_inverse_fast<S, 3>(sm, P, load, emit); break;
-    case 4: coset_inverse_fast<S, 4>(sm, P, load, emit); break;
-    case 5: coset_inverse_fast<S, 5>(sm, P, load, emit); break;
+    case 3: coset_inverse_fast<S, 3>(sm, P, src, emit); break;
+    case 4: coset_inverse_fast<S, 4>(sm, P, src, emit); break;
+    case 5: coset_inverse_fast<S, 5>(sm, P, src, emit); break;
     default: {
       u64* A = sm;
       u64* B = sm + N;
@@ -292,7 +291,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_encode_t(const u
   const u32 per = nI * nJ, bpl = (per + G - 1) / G;  // weight blocks and blocks of the grid per (item, prime)
   const u32 il = blockIdx.x / bpl, first = (blockIdx.x % bpl) * G;
   const u32 item = il / C.L, l = il % C.L;
-  const PrimeConsts& P = C.p[l];
+  const PrimeConsts P = C.p[l];
   W += (u64)item * k * n;
   uint8_t* const ptd = reinterpret_cast<uint8_t*>(pt + (u64)item * tc_weight_words(nI, nJ, C.L, S2));
   const u32 nk = b.n_b * b.k_b, nS = tc_stages(nJ);
@@ -365,7 +364,7 @@ __device__ __forceinline__ void inv_block(const MultiTable& T, const Consts& C, 
   } else {
     const u32 c = (local / L) % 2;
     const u32 o = (u32)(local / (2 * L));
-    const PrimeConsts& P = C.p[l];
+    const PrimeConsts P = C.p[l];
     u64* d = it.out + local * N;
     const u64 seed = item_seed(it);
     ntt_inverse_block<S>(sm, P, [&](u32 e) { return d[e]; }, [&](u32 e, u64 v) {
@@ -423,7 +422,7 @@ __global__ void __launch_bounds__(kThreadsSmall) k_inv_multi_small(const __grid_
   const u64 local = blockIdx.x - it.inv_begin;
   const u64 N = C.N, L = C.L;
   const u32 l = local % L;
-  const PrimeConsts& P = C.p[l];
+  const PrimeConsts P = C.p[l];
   u64* d;
   u32 c = 1, o = 0;
   if (it.compact) {

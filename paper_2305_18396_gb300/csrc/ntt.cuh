@@ -416,7 +416,7 @@ __device__ __forceinline__ u64 c0_pruned_group(const u64* __restrict__ src, u32 
 
 __device__ __forceinline__ void ntt_inverse_c0_targets(const u64* src, u64* dst, u32 logkb, u64 seed, u32 o, u32 l,
                                                        const Consts& C, u64* sm) {
-  const PrimeConsts& P = C.p[l];
+  const PrimeConsts P = C.p[l];
   const u32 N = C.N, logN = C.logN, Nc = N >> logkb;
   const u64 q = P.q, two_q = P.two_q;
   u64* z;  // compact values
