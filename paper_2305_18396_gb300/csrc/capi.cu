@@ -14,6 +14,7 @@
 #include "coset.cuh"
 #include "kernels.h"
 #include "mac_tc.cuh"
+#include "mac_tcr.cuh"
 #include "multi.h"
 #include "ntt.cuh"
 
@@ -216,6 +217,11 @@ bool use_coset(const he_ctx* c, const he_blocking* b) {
   if (c->C.logN < 9 || (c->mac_engine != HE_MAC_AUTO && c->mac_engine != HE_MAC_COSET)) return false;
   return he::coset_logD(b->n_b * b->k_b) < c->C.logN;
 }
+// Coset products of at most 64 k-blocks run the row-major tensor-core MAC (mac_tcr.cuh):
+// inputs on the MMA's M, every weight tile streamed past them.
+bool use_tcr(const he_ctx* c, const he_blocking* b, u32 nJ) {
+  return use_coset(c, b) && nJ <= he::kTcrMaxStages * he::kTcJB;
+}
 bool use_tc(const he_ctx* c, const he_blocking* b, u32 nJ) {
   if (c->C.logN < 9 || c->mac_engine == HE_MAC_INTEGER) return false;
   if (use_coset(c, b)) return true;
@@ -247,7 +253,10 @@ u64 operand_words(const he_ctx* c, const he_blocking* b, u32 rows, u32 nJ) {
   return use_tc(c, b, nJ) ? he::tc_words(rows, nJ, c->C.L, c->C.N) : (u64)rows * nJ * c->C.L * c->C.N;
 }
 u64 weight_words(const he_ctx* c, const he_blocking* b, u32 nI, u32 nJ) {
-  if (use_coset(c, b)) return he::tc_weight_words(nI, nJ, c->C.L, 2u << he::coset_logD(b->n_b * b->k_b));
+  if (use_coset(c, b)) {
+    const u32 S = 2u << he::coset_logD(b->n_b * b->k_b);
+    return use_tcr(c, b, nJ) ? he::tcr_weight_words(nI, nJ, c->C.L, S) : he::tc_weight_words(nI, nJ, c->C.L, S);
+  }
   return use_tc(c, b, nJ) ? he::tc_weight_words(nI, nJ, c->C.L, c->C.N) : (u64)nI * nJ * c->C.L * c->C.N;
 }
 
@@ -675,7 +684,8 @@ int he_encode_weights_batch(he_ctx* c, const uint64_t* W, uint32_t k, uint32_t n
   Shape s = shape_of(1, k, n, blk);
   if (use_coset(c, blk))
     return launch(c, KCosetEnc, (cudaStream_t)stream, "encode_weights (cosets)", [&] {
-      return he::launch_coset_encode_weights(c->C, W, k, n, to_blk(blk), s.nI, s.nJ, batch, pt, (cudaStream_t)stream);
+      return he::launch_coset_encode_weights(c->C, W, k, n, to_blk(blk), s.nI, s.nJ, batch, use_tcr(c, blk, s.nJ), pt,
+                                             (cudaStream_t)stream);
     });
   return launch(c, KEncode, (cudaStream_t)stream, "encode_weights", [&] {
     return he::launch_encode_weights(c->C, W, k, n, to_blk(blk), s.nI, s.nJ, batch, use_tc(c, blk, s.nJ), pt,
@@ -699,7 +709,7 @@ namespace {
 // A coset product's entry in a multi-product table (coset.cuh); the begins are the running
 // block counts of the three coset grids, advanced past this item.
 void coset_item(const he_ctx* c, he::MultiItem& it, const he_blocking* blk, Shape s, bool compact, u64* ws,
-                u64* cfwd, u64* tc, u64* cinv) {
+                u64* cfwd, u64* tc, u64* tcr, u64* cinv) {
   const CosetGeom g = coset_geom(c, blk, s.nI, s.nJ, s.nLb);
   const u64 L = c->C.L;
   it.nI = s.nI;
@@ -714,13 +724,17 @@ void coset_item(const he_ctx* c, he::MultiItem& it, const he_blocking* blk, Shap
   it.acc = ws ? (u64*)((char*)ws + up256(g.ctn_words * 8)) : nullptr;
   it.cfwd_begin = *cfwd;
   it.tc_begin = *tc;
+  it.tcr_begin = *tcr;
   it.cinv_begin = *cinv;
+  it.tcr = use_tcr(c, blk, s.nJ);
   *cfwd += (u64)s.nLb * s.nJ * 2 * L;
-  *tc += he::tc_units(g.S, (u32)L, s.nI, g.R);
+  if (it.tcr) *tcr += he::tcr_units(g.S, (u32)L, g.R);
+  else *tc += he::tc_units(g.S, (u32)L, s.nI, g.R);
   *cinv += (u64)s.nLb * s.nI * 2 * L;
 }
 
-int launch_coset_grids(he_ctx* c, const he::MultiTable& T, u64 cfwd, u64 tc, u64 cinv, bool compact, cudaStream_t st) {
+int launch_coset_grids(he_ctx* c, const he::MultiTable& T, u64 cfwd, u64 tc, u64 tcr, u64 cinv, bool compact,
+                       cudaStream_t st) {
   int r = HE_OK;
   if (cfwd)
     r = launch(c, KCosetFwd, st, "coset forward transforms",
@@ -728,6 +742,9 @@ int launch_coset_grids(he_ctx* c, const he::MultiTable& T, u64 cfwd, u64 tc, u64
   if (!r && tc)
     r = launch(c, KMacTc, st, "tensor-core multiply-accumulate (cosets)",
                [&] { return he::launch_mac_tc_multi(c->C, T, tc, c->d_err, st); });
+  if (!r && tcr)
+    r = launch(c, KMacTc, st, "row-major tensor-core multiply-accumulate (cosets)",
+               [&] { return he::launch_mac_tcr_multi(c->C, T, tcr, c->d_err, st); });
   if (!r && cinv)
     r = launch(c, KCosetInv, st, compact ? "coset inverse transforms + mask (compact)" : "coset inverse transforms + mask",
                [&] { return he::launch_coset_inv_multi(c->C, T, cinv, st); });
@@ -750,7 +767,7 @@ int coset_matmul(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t 
     const u32 cnt = std::min<u32>(he::kMaxMulti, batch - b0);
     memset(&T, 0, sizeof(T));
     T.count = cnt;
-    u64 cfwd = 0, tc = 0, cinv = 0;
+    u64 cfwd = 0, tc = 0, tcr = 0, cinv = 0;
     for (u32 i = 0; i < cnt; ++i) {
       const u64 b = b0 + i;
       he::MultiItem& it = T.it[i];
@@ -758,9 +775,9 @@ int coset_matmul(he_ctx* c, const uint64_t* ct_in, const uint64_t* pt, uint32_t 
       it.pt = pt + b * si.pt_words;
       it.out = ct_out + b * out_w;
       it.mask_seed = mask_seed + b;
-      coset_item(c, it, blk, s, compact, (u64*)((char*)ws + b * si.workspace_bytes), &cfwd, &tc, &cinv);
+      coset_item(c, it, blk, s, compact, (u64*)((char*)ws + b * si.workspace_bytes), &cfwd, &tc, &tcr, &cinv);
     }
-    if (int r = launch_coset_grids(c, T, cfwd, tc, cinv, compact, st)) return r;
+    if (int r = launch_coset_grids(c, T, cfwd, tc, tcr, cinv, compact, st)) return r;
   }
   return HE_OK;
 }
@@ -902,7 +919,8 @@ int he_autotune_blocking(he_ctx* c, uint32_t m, uint32_t k, uint32_t n, uint32_t
     auto encode = [&] {
       if (use_coset(c, &b))
         return launch(c, KCosetEnc, st, "autotune: encode (cosets)", [&] {
-          return he::launch_coset_encode_weights(c->C, W, k, n, to_blk(&b), s.nI, s.nJ, batch, pt, st);
+          return he::launch_coset_encode_weights(c->C, W, k, n, to_blk(&b), s.nI, s.nJ, batch, use_tcr(c, &b, s.nJ), pt,
+                                                 st);
         });
       return launch(c, KEncode, st, "autotune: encode", [&] {
         return he::launch_encode_weights(c->C, W, k, n, to_blk(&b), s.nI, s.nJ, batch, use_tc(c, &b, s.nJ), pt, st);
@@ -1107,7 +1125,7 @@ namespace {
 struct MultiPlan {
   he::MultiTable T;
   u64 fwd = 0, mac = 0, tc = 0, inv = 0, c0 = 0, ws_bytes = 0;
-  u64 cfwd = 0, cinv = 0;  // blocks of the coset grids (coset products)
+  u64 cfwd = 0, cinv = 0, tcr = 0;  // blocks of the coset grids, units of the row-major MAC (coset products)
   u32 max_nc = 0;  // shared-memory words of the largest c0 transform
 };
 
@@ -1194,11 +1212,12 @@ int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* w
     if (use_coset(c, &x.blk)) {  // forward, multiply-accumulate and inverse in the coset grids
       const CosetGeom cg = coset_geom(c, &x.blk, s.nI, s.nJ, s.nLb);
       u64* ws = take(up256(cg.ctn_words * 8) + cg.acc_words * 8);
-      coset_item(c, it, &x.blk, s, compact, ws, &P->cfwd, &P->tc, &P->cinv);
+      coset_item(c, it, &x.blk, s, compact, ws, &P->cfwd, &P->tc, &P->tcr, &P->cinv);
       continue;
     }
     it.cfwd_begin = P->cfwd;
     it.cinv_begin = P->cinv;
+    it.tcr_begin = P->tcr;
     it.nI = s.nI;
     it.nJ = s.nJ;
     it.nLb = s.nLb;
@@ -1227,7 +1246,7 @@ int plan_multi(const he_ctx* c, uint32_t count, const he_product* items, char* w
   }
   P->ws_bytes = off;
   if (P->fwd >= (1ull << 31) || P->mac >= (1ull << 31) || P->tc >= (1ull << 31) || P->inv >= (1ull << 31) ||
-      P->cfwd >= (1ull << 31) || P->cinv >= (1ull << 31))
+      P->cfwd >= (1ull << 31) || P->cinv >= (1ull << 31) || P->tcr >= (1ull << 31))
     return fail(HE_EINVAL, "multi-product launch too large");
   return HE_OK;
 }
@@ -1264,6 +1283,9 @@ int he_matmul_multi(he_ctx* c, uint32_t count, const he_product* items, void* wo
   if (!r && P.tc)
     r = launch(c, KMacTc, st, "multi: tensor-core multiply-accumulate",
                [&] { return he::launch_mac_tc_multi(c->C, P.T, P.tc, c->d_err, st); });
+  if (!r && P.tcr)
+    r = launch(c, KMacTc, st, "multi: row-major tensor-core multiply-accumulate",
+               [&] { return he::launch_mac_tcr_multi(c->C, P.T, P.tcr, c->d_err, st); });
   if (!r && P.c0) {  // compact products: c1 inverse NTTs and pruned c0 transforms in one grid
     r = launch(c, KInvC0, st, "multi: inverse NTT of c1 + pruned inverse NTT of c0",
                [&] { return he::launch_inv_c0_multi(c->C, P.T, P.inv, P.c0, P.max_nc, st); });

@@ -11,6 +11,7 @@
 #include "kernels.h"
 #include "mac.cuh"
 #include "mac_tc.cuh"
+#include "mac_tcr.cuh"
 #include "multi.h"
 #include "ntt.cuh"
 
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_inv_multi_t(cons
 // weight blocks here -- and writes each one's 2D slots as bf16 digit tiles (mac_tc.cuh).
 template <int LOGN>
 __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_encode_t(const u64* W, u32 k, u32 n, Blk b, u32 nI,
-                                                                       u32 nJ, u32 logD, u64* pt,
+                                                                       u32 nJ, u32 logD, u32 tcr, u64* pt,
                                                                        const __grid_constant__ Consts C) {
   using S = NttShape<LOGN, 4>;
   extern __shared__ u64 sm[];
@@ -293,7 +294,8 @@ __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_encode_t(const u
   const u32 item = il / C.L, l = il % C.L;
   const PrimeConsts P = C.p[l];
   W += (u64)item * k * n;
-  uint8_t* const ptd = reinterpret_cast<uint8_t*>(pt + (u64)item * tc_weight_words(nI, nJ, C.L, S2));
+  uint8_t* const ptd =
+      reinterpret_cast<uint8_t*>(pt + (u64)item * (tcr ? tcr_weight_words(nI, nJ, C.L, S2) : tc_weight_words(nI, nJ, C.L, S2)));
   const u32 nk = b.n_b * b.k_b, nS = tc_stages(nJ);
   const u64 half_t = (C.tmask >> 1) + 1;
   const bool fast = logD <= (u32)kCosetFastMaxLogD;
@@ -317,6 +319,14 @@ __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_encode_t(const u
     if (wb >= per) return;
     const u32 I = wb / nJ, J = wb % nJ;
     const u64 u = v + 0x0080808080808080ull;
+    if (tcr) {  // row-major digit tile (mac_tcr.cuh): row 16 b + i of weight tile I / 16
+      uint8_t* tile = ptd + tcr_weight_offset(I >> 4, l, slot, J >> 4, tcr_tiles_I(nI), nS, S2);
+#pragma unroll
+      for (int q = 0; q < (int)kTcPlanes; ++q)
+        *reinterpret_cast<uint16_t*>(tile + tc::tile_offset(kTcrI * q + (I & 15), J & 15, kTcJB * 2, 2)) =
+            (uint16_t)(digit_f32_bits(u, q) >> 16);
+      return;
+    }
     uint8_t* grp = ptd + tc_weight_offset(I & ~7u, l, slot, J >> 4, nI, nS, S2);
 #pragma unroll
     for (int q = 0; q < (int)kTcPlanes; ++q)
@@ -340,6 +350,28 @@ size_t coset_smem(const Consts& C, const MultiTable& T) {
   for (u32 i = 0; i < T.count; ++i)
     if (T.it[i].coset && T.it[i].logD > (u32)kCosetFastMaxLogD) fast = false;
   return (fast ? (size_t)C.N + (C.N >> 4) : 2 * (size_t)C.N) * sizeof(u64);
+}
+
+// The row-major tensor-core multiply-accumulate (mac_tcr.cuh) over the items flagged tcr:
+// one block per SM works through their units (product, prime, slot, 128 input rows).
+__global__ void __launch_bounds__(kTcrThreads, 1) k_mac_tcr_multi(const __grid_constant__ MultiTable T, u64 total,
+                                                                 int* err, const __grid_constant__ Consts C) {
+  extern __shared__ __align__(128) uint8_t smem_tcr[];
+  __shared__ TcrShared sh;
+  auto get = [&](u64 g, TcrWork& w) {
+    const u32 i = find_item(T, g, [](const MultiItem& x) { return x.tcr_begin; });
+    const MultiItem& it = T.it[i];
+    const u32 logG = C.logN - it.logD;
+    tcr_unit(g - it.tcr_begin, 2u << it.logD, (2 * it.nLb) << logG, w);
+    w.ctN = it.ctN;
+    w.ptd = reinterpret_cast<const uint8_t*>(it.pt);
+    w.acc = it.acc;
+    w.ct0 = 0;
+    w.nI = it.nI;
+    w.nJ = it.nJ;
+    w.logG = logG;
+  };
+  mac_tcr_run(get, total, err, C, smem_tcr, sh);
 }
 
 // Inverse NTT of block b of the inverse grid: compact products transform their c1
@@ -478,6 +510,7 @@ cudaError_t configure_multi_kernels() {
   set((const void*)k_c0_multi, 2 * one);
   set((const void*)k_mac_multi_t<MacProd, kMacMinBlocks>, (int)MacProd::kSmemBytes);
   set((const void*)k_mac_tc_multi, (int)kTcSmem);
+  set((const void*)k_mac_tcr_multi, (int)kTcrSmem);
 #define HE_SET_COSET(LN)                                                                      \
   set((const void*)k_coset_fwd_multi_t<LN>, 2 * (1 << LN) * (int)sizeof(u64));               \
   set((const void*)k_coset_inv_multi_t<LN>, 2 * (1 << LN) * (int)sizeof(u64));               \
@@ -519,6 +552,14 @@ cudaError_t launch_mac_tc_multi(const Consts& C, const MultiTable& T, u64 units,
   if (units) {
     const u64 grid = std::min<u64>(units, (u64)device_sms());
     k_mac_tc_multi<<<(unsigned)grid, kTcThreads, kTcSmem, st>>>(T, units, err, C);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mac_tcr_multi(const Consts& C, const MultiTable& T, u64 units, int* err, cudaStream_t st) {
+  if (units) {
+    const u64 grid = std::min<u64>(units, (u64)device_sms());
+    k_mac_tcr_multi<<<(unsigned)grid, kTcrThreads, kTcrSmem, st>>>(T, units, err, C);
   }
   return cudaGetLastError();
 }
@@ -590,17 +631,18 @@ cudaError_t launch_coset_inv_multi(const Consts& C, const MultiTable& T, u64 blo
 }
 
 cudaError_t launch_coset_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u32 batch,
-                                        u64* pt, cudaStream_t st) {
+                                        u32 tcr, u64* pt, cudaStream_t st) {
   const u32 logD = coset_logD(b.n_b * b.k_b);
   if (!nI || !nJ || !batch) return cudaGetLastError();
   if (C.logN < 9 || logD >= C.logN) return cudaErrorInvalidValue;
   const u32 S2 = 2u << logD, G = C.N >> logD;
   // digit tiles: k-blocks past the last and rows past nI must read as zero digits
-  cudaError_t e = cudaMemsetAsync(pt, 0, 8ull * batch * tc_weight_words(nI, nJ, C.L, S2), st);
+  cudaError_t e = cudaMemsetAsync(
+      pt, 0, 8ull * batch * (tcr ? tcr_weight_words(nI, nJ, C.L, S2) : tc_weight_words(nI, nJ, C.L, S2)), st);
   if (e != cudaSuccess) return e;
   const u64 blocks = (u64)batch * C.L * (((u64)nI * nJ + G - 1) / G);
   const size_t smem = (logD <= (u32)kCosetFastMaxLogD ? (size_t)C.N + (C.N >> 4) : 2 * (size_t)C.N) * sizeof(u64);
-  HE_COSET_DISPATCH(k_coset_encode_t, (unsigned)blocks, smem, st, W, k, n, b, nI, nJ, logD, pt, C)
+  HE_COSET_DISPATCH(k_coset_encode_t, (unsigned)blocks, smem, st, W, k, n, b, nI, nJ, logD, tcr, pt, C)
   return cudaGetLastError();
 }
 

@@ -43,6 +43,10 @@ struct MultiItem {
   u64* acc;
   u64 cfwd_begin, cinv_begin;
   u32 coset, logD;
+  // coset products of at most 64 k-blocks: the row-major tensor-core MAC (mac_tcr.cuh), weights
+  // as row-major digit tiles; tcr_begin: first unit in its grid
+  u64 tcr_begin;
+  u32 tcr, pad2;
 };
 
 struct MultiTable {
@@ -65,11 +69,14 @@ cudaError_t launch_c0_multi(const Consts& C, const MultiTable& T, u64 blocks, u3
 // and the inverse transforms, fold and mask of their outputs (one block per output
 // component), each as one grid over the coset items of the table.
 cudaError_t launch_coset_fwd_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
+// The row-major tensor-core multiply-accumulate of the items flagged tcr (units: theirs).
+cudaError_t launch_mac_tcr_multi(const Consts& C, const MultiTable& T, u64 units, int* err, cudaStream_t st);
 cudaError_t launch_coset_inv_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
 // Encoded weights of coset products: per weight block the zero-padded length-2D transform
-// of its pi_A block, as bf16 digit tiles over 2D slots; `batch` same-shape matrices.
+// of its pi_A block, as bf16 digit tiles over 2D slots (row-major digit tiles when tcr);
+// `batch` same-shape matrices.
 cudaError_t launch_coset_encode_weights(const Consts& C, const u64* W, u32 k, u32 n, Blk b, u32 nI, u32 nJ, u32 batch,
-                                        u64* pt, cudaStream_t st);
+                                        u32 tcr, u64* pt, cudaStream_t st);
 // The inverse-NTT grid and the c0 grid as one launch where inv_c0_fused(C), else two.
 bool inv_c0_fused(const Consts& C);
 cudaError_t launch_inv_c0_multi(const Consts& C, const MultiTable& T, u64 inv_blocks, u64 c0_blocks, u32 c0_words,
