@@ -44,9 +44,9 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "bert-large-n8192"
 
-# Blockings (m_b, k_b, n_b) of the products the CPU oracle legs sample, keyed by (N, m, k, n):
-# the library cost model's choice for these shapes, written out so that the oracle legs
-# load no part of the CUDA library.
+# Blockings (m_b, k_b, n_b) of the products the CPU oracle legs sample, keyed by (N, m, k, n),
+# written out so that the oracle legs load no part of the CUDA library (the blocking fixes
+# the ciphertexts, not the plain MACs a product computes).
 ORACLE_BLOCKINGS = {
     (4096, 128, 64, 128): (32, 8, 16), (4096, 128, 128, 64): (32, 16, 8), (4096, 64, 128, 128): (16, 16, 16),
     (8192, 512, 64, 512): (64, 4, 32), (8192, 512, 512, 64): (64, 32, 4), (8192, 64, 512, 512): (8, 32, 32),
@@ -439,7 +439,8 @@ def kernel_source_hash():
     figure recorded for an older fingerprint is stale."""
     csrc = ROOT / "paper_2305_18396_gb300" / "csrc"
     h = hashlib.sha256((csrc / "mac.cuh").read_bytes())
-    for f in ("async.cuh", "he_common.cuh", "multi.cu", "capi.cu"):
+    for f in ("mac_tc.cuh", "mac_tcr.cuh", "coset.cuh", "tcgen05.cuh", "async.cuh", "he_common.cuh", "multi.cu",
+              "capi.cu"):
         h.update((csrc / f).read_bytes())
     h.update((ROOT / "paper_2305_18396_gb300" / "workloads.py").read_bytes())
     return h.hexdigest()[:16]

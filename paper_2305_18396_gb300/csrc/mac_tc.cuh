@@ -35,14 +35,16 @@
 // (Lb, c) are 128 contiguous bytes, rows back to back,
 //   word ((((l N + s) nS + js) rows + row) 16 + chunk 2 + (J & 1),
 //   chunk = ((J & 15) / 2 + row) mod 8   (the 16-byte chunks rotated by the row),
-// nS = ceil(nJ / 16), rows = 2 nLb; one warp splits a unit's 16 input rows into digit
-// planes per stage (the rotation keeps its shared-memory reads free of bank conflicts).
+// nS = ceil(nJ / 16), rows = 2 nLb (2 nLb G rows and 2D slots per prime for coset products,
+// coset.cuh); two warps split a unit's 16 input rows into digit planes per stage (planes
+// 0-3 and 4-6; the rotation keeps their shared-memory reads free of bank conflicts).
 // A work unit is kTcSlots consecutive slots of one prime, one tile of 128 weight rows and
-// one tile of 16 input rows; per stage a producer warp issues the two bulk copies, one
-// warp splits the input rows, one thread issues the MMAs, and four warps read the
-// accumulators back after each round while the MMAs of the next round fill the other of
-// two accumulator sets.  One block per SM works through its share of the launch's work
-// units back to back, so the pipeline never drains between units.
+// one tile of 16 input rows; per stage a producer warp issues the two bulk copies, the two
+// split warps convert the input rows, one thread issues the MMAs, and eight warps (two per
+// TMEM lane quadrant, 8 output rows each) read the accumulators back after each round while
+// the MMAs of the next round fill the other of two accumulator sets.  One block per SM
+// works through its share of the launch's work units back to back, so the pipeline never
+// drains between units.  Coset products of at most 64 k-blocks take mac_tcr.cuh instead.
 #pragma once
 
 #include <cuda_bf16.h>
