@@ -35,6 +35,7 @@ constexpr u32 kTcrM = 128;                 // input rows per unit (MMA M)
 constexpr u32 kTcrI = 16;                  // weight rows per tile
 constexpr u32 kTcrMaxStages = 4;           // k-blocks per product at most 64
 constexpr u32 kTcrBStages = 8;             // weight tiles in flight
+constexpr u32 kTcrRawStages = 4;           // raw input stages in flight (a unit's at most 4 load together)
 constexpr u32 kTcrSplitWarps = 4;
 constexpr u32 kTcrEpiWarps = 8;            // two per TMEM lane quadrant, 8 weight rows each
 constexpr u32 kTcrEpi0 = 2 + kTcrSplitWarps;
@@ -43,7 +44,8 @@ constexpr u32 kTcrPlaneBytes = kTcrM * kTcJB * 2;           // one digit plane o
 constexpr u32 kTcrABytes = kTcPlanes * kTcrPlaneBytes;      // a stage's 7 planes: 28 KB
 constexpr u32 kTcrRawBytes = kTcrM * kTcRawRow;             // a stage's raw words: 16 KB
 constexpr u32 kTcrBBytes = kTcPlanes * kTcrI * kTcJB * 2;   // one weight tile: 3584 bytes
-constexpr u32 kTcrSmem = kTcrMaxStages * kTcrABytes + 2 * kTcrRawBytes + kTcrBBytes * kTcrBStages + kTcZBytes + 128;
+constexpr u32 kTcrSmem =
+    kTcrMaxStages * kTcrABytes + kTcrRawStages * kTcrRawBytes + kTcrBBytes * kTcrBStages + kTcZBytes + 128;
 static_assert(kTcrSmem <= 227 * 1024, "row-major tensor-core MAC shared memory above the per-block limit");
 
 __host__ __device__ inline u32 tcr_tiles_I(u32 nI) { return (nI + kTcrI - 1) / kTcrI; }
@@ -77,7 +79,7 @@ __device__ __forceinline__ void tcr_unit(u64 u, u32 S, u32 R, TcrWork& w) {
 }
 
 struct TcrShared {
-  uint64_t raw_full[2], raw_empty[2], a_full[kTcrMaxStages], a_free;
+  uint64_t raw_full[kTcrRawStages], raw_empty[kTcrRawStages], a_full[kTcrMaxStages], a_free;
   uint64_t b_full[kTcrBStages], b_empty[kTcrBStages];
   uint64_t acc_full[2], acc_empty[2], done;
   uint32_t tmem;
@@ -90,16 +92,18 @@ template <class GetWork>
 __device__ __forceinline__ void mac_tcr_run(const GetWork& get, u64 total, int* err, const Consts& C, uint8_t* smem,
                                             TcrShared& sh) {
   uint8_t* const Ad = smem;                                         // [stage][plane][128 x 16] digits
-  uint8_t* const Raw = Ad + kTcrMaxStages * kTcrABytes;             // [2][128 rows x 128 bytes]
-  uint8_t* const Bt = Raw + 2 * kTcrRawBytes;                       // [kTcrBStages][3584]
+  uint8_t* const Raw = Ad + kTcrMaxStages * kTcrABytes;             // [kTcrRawStages][128 rows x 128 bytes]
+  uint8_t* const Bt = Raw + kTcrRawStages * kTcrRawBytes;           // [kTcrBStages][3584]
   uint8_t* const Zt = Bt + kTcrBBytes * kTcrBStages;                // 96 zero rows
   const u32 warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const u32 N = C.N;
 
   if (threadIdx.x == 0) {
-    for (u32 b = 0; b < 2; ++b) {
+    for (u32 b = 0; b < kTcrRawStages; ++b) {
       mbar_init(&sh.raw_full[b], 1);
       mbar_init(&sh.raw_empty[b], kTcrSplitWarps);
+    }
+    for (u32 b = 0; b < 2; ++b) {
       mbar_init(&sh.acc_full[b], 1);
       mbar_init(&sh.acc_empty[b], kTcrEpiWarps);
     }
@@ -137,8 +141,9 @@ __device__ __forceinline__ void mac_tcr_run(const GetWork& get, u64 total, int* 
       get(g, w);
       const u32 nS = tc_stages(w.nJ), nIt = tcr_tiles_I(w.nI), nc = min(kTcrM, w.R - w.r0);
       for (u32 js = 0; ok && js < nS; ++js, ++rc) {
-        const u32 b = rc & 1;
-        if (rc >= 2 && !mbar_wait_warp(&sh.raw_empty[b], ((rc >> 1) - 1) & 1, kWaitLimitNs)) {
+        const u32 b = rc % kTcrRawStages;
+        if (rc >= kTcrRawStages &&
+            !mbar_wait_warp(&sh.raw_empty[b], ((rc / kTcrRawStages) - 1) & 1, kWaitLimitNs)) {
           give_up();
           ok = false;
           break;
@@ -170,7 +175,8 @@ __device__ __forceinline__ void mac_tcr_run(const GetWork& get, u64 total, int* 
         }
     }
     // copies still in flight must land before the block's shared memory is released
-    for (u32 k = rc > 2 ? rc - 2 : 0; k < rc; ++k) mbar_wait_warp(&sh.raw_full[k & 1], (k >> 1) & 1, kWaitLimitNs);
+    for (u32 k = rc > kTcrRawStages ? rc - kTcrRawStages : 0; k < rc; ++k)
+      mbar_wait_warp(&sh.raw_full[k % kTcrRawStages], (k / kTcrRawStages) & 1, kWaitLimitNs);
     for (u32 k = bc > kTcrBStages ? bc - kTcrBStages : 0; k < bc; ++k)
       mbar_wait_warp(&sh.b_full[k % kTcrBStages], (k / kTcrBStages) & 1, kWaitLimitNs);
   } else if (warp == 1) {
@@ -241,8 +247,8 @@ __device__ __forceinline__ void mac_tcr_run(const GetWork& get, u64 total, int* 
         break;
       }
       for (u32 js = 0; js < nS; ++js, ++rc) {
-        const u32 b = rc & 1, jb = min(kTcJB, w.nJ - js * kTcJB);
-        if (!mbar_wait_warp(&sh.raw_full[b], (rc >> 1) & 1, kWaitLimitNs)) {
+        const u32 b = rc % kTcrRawStages, jb = min(kTcJB, w.nJ - js * kTcJB);
+        if (!mbar_wait_warp(&sh.raw_full[b], (rc / kTcrRawStages) & 1, kWaitLimitNs)) {
           give_up();
           ok = false;
           break;
