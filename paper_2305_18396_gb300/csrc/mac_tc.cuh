@@ -62,7 +62,7 @@ constexpr u32 kTcPlanes = 7;       // balanced base-256 digits of a 50-bit resid
 constexpr u32 kTcDiag = 13;        // diagonals a + b
 constexpr u32 kTcJB = 16;          // k-blocks per stage (one MMA K step)
 constexpr u32 kTcRound = 8;        // stages per exact accumulation round (128 k-blocks)
-constexpr u32 kTcSlots = 8;        // consecutive slots per work unit
+constexpr u32 kTcSlots = 4;        // consecutive slots per work unit (measured: 2.5% faster than 8 on the coset FC products, 16 slower)
 constexpr u32 kTcStages = 6;       // stages in flight: 225 KB of shared memory (coset products, operands from L2: 2.4% faster than 4)
 constexpr u32 kTcSplitWarps = 2;   // digit split of the input rows: planes 0-3 and 4-6
 constexpr u32 kTcEpi0 = 2 + kTcSplitWarps;  // first epilogue warp
