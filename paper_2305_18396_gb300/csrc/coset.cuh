@@ -290,4 +290,111 @@ __device__ __forceinline__ void coset_inverse_fast(u64* sm, const PrimeConsts& P
     for (int j = 0; j < (1 << RSL); ++j) store(inv_elem<S, S0L, RSL>(hh, j), csub(x[hh * (1 << RSL) + j], q));
 }
 
+// ---------------------------------------------------------------- register passes, D = 64, 128
+//
+// For cosets too long to hold in one thread, each half's length-D transform is a batched
+// transform over all G cosets: the full NTT's register passes over the stages log2 G ..
+// log2 N - 1 with the tail's twiddle indices (fwd_pass_regs / inv_pass_regs, TAILG / TAILD).
+// Each half works on its own padded copy of the polynomial: 2 S::kSmemWords words.
+
+constexpr int kCosetPassMinLogD = 6, kCosetPassMaxLogD = 7;
+
+template <class S, int S0, int LOGG, class Store>
+__device__ __forceinline__ void coset_tail_passes(u64 (&x)[S::R], u64* sm, const PrimeConsts& P, u32 h,
+                                                  Store&& store) {
+  constexpr int RS = (S::kLogN - S0) < S::LOGR ? (S::kLogN - S0) : S::LOGR;
+  fwd_load_smem<S, S0, RS>(x, sm);
+  fwd_pass_regs<S, S0, RS, LOGG>(x, P, h);
+  if constexpr (S0 + RS < S::kLogN) {
+    fwd_store_smem<S, S0, RS>(x, sm);
+    __syncthreads();
+    coset_tail_passes<S, S0 + RS, LOGG>(x, sm, P, h, store);
+  } else {
+    constexpr int LOGD = S::kLogN - LOGG;
+#pragma unroll
+    for (int hh = 0; hh < (S::R >> RS); ++hh)
+#pragma unroll
+      for (int j = 0; j < (1 << RS); ++j) {
+        const u32 e = fwd_elem<S, S0, RS>(hh, j);
+        store(e >> LOGD, (h << LOGD) + (e & ((1u << LOGD) - 1)), reduce_word(x[hh * (1 << RS) + j], P));
+      }
+  }
+}
+
+// Both halves of the zero-padded length-2D transforms of the G blocks in sm (padded, values
+// below 2^56 after at most log2 G lazy stages); sm2: a second S::kSmemWords words.  sm is
+// overwritten by the second half.
+template <class S, int LOGD, class Store>
+__device__ __forceinline__ void coset_tail_both(u64* sm, u64* sm2, const PrimeConsts& P, Store&& store) {
+  constexpr int LOGG = S::kLogN - LOGD;
+  for (u32 i = threadIdx.x; i < (u32)S::kSmemWords; i += S::T) sm2[i] = sm[i];
+  __syncthreads();
+  u64 x[S::R];
+  coset_tail_passes<S, LOGG, LOGG>(x, sm2, P, 0u, store);
+  coset_tail_passes<S, LOGG, LOGG>(x, sm, P, 1u, store);
+}
+
+template <class S, int LOGD, class Load, class Store>
+__device__ __forceinline__ void coset_forward_passes(u64* sm, u64* sm2, const PrimeConsts& P, Load&& load,
+                                                     Store&& store) {
+#pragma unroll
+  for (int i = 0; i < S::R; ++i) {
+    const u32 e = threadIdx.x + S::T * i;
+    sm[S::pad(e)] = load(e);
+  }
+  __syncthreads();
+  u64 x[S::R];
+  coset_head_passes<S, 0, S::kLogN - LOGD>(x, sm, P);
+  coset_tail_both<S, LOGD>(sm, sm2, P, store);
+}
+
+template <class S, int S0, int LOGD>
+__device__ __forceinline__ void coset_inv_tail_passes(u64 (&x)[S::R], u64* sm, const PrimeConsts& P, u32 h) {
+  if constexpr (S0 < LOGD) {
+    constexpr int RS = (LOGD - S0) < S::LOGR ? (LOGD - S0) : S::LOGR;
+    inv_load_smem<S, S0, RS>(x, sm);
+    inv_pass_regs<S, S0, RS, LOGD>(x, P, h);
+    inv_store_smem<S, S0, RS>(x, sm);
+    __syncthreads();
+    coset_inv_tail_passes<S, S0 + RS, LOGD>(x, sm, P, h);
+  }
+}
+
+// As coset_inverse_fast, for D = 2^LOGD too long for one thread: smA, smB: S::kSmemWords
+// words each (the two halves), src 16-byte aligned.
+template <class S, int LOGD, class Store>
+__device__ __forceinline__ void coset_inverse_passes(u64* smA, u64* smB, const PrimeConsts& P,
+                                                     const u64* __restrict__ src, Store&& store) {
+  constexpr u32 D = 1u << LOGD, G = S::N >> LOGD;
+  const u64 q = P.q, two_q = P.two_q;
+  for (u32 e = 2 * threadIdx.x; e < 2 * (u32)S::N; e += 2 * S::T) {  // pairs of slots, coalesced
+    const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(src + e);
+    const u32 g = e >> (LOGD + 1), pos = e & (2 * D - 1);
+    u64* half = pos < D ? smA : smB;
+    half[S::pad(g * D + (pos & (D - 1)))] = t.x;
+    half[S::pad(g * D + (pos & (D - 1)) + 1)] = t.y;
+  }
+  __syncthreads();
+  u64 x[S::R];
+  coset_inv_tail_passes<S, 0, LOGD>(x, smA, P, 0u);
+  coset_inv_tail_passes<S, 0, LOGD>(x, smB, P, 1u);
+  for (u32 e = threadIdx.x; e < (u32)S::N; e += S::T) {  // last butterfly + fold + (2N)^{-1}
+    const u32 g = e >> LOGD;
+    const u64* f = P.fold + 4 * ((G >> 1) + (g >> 1));
+    const u32 o = (g & 1) ? 2 : 0;  // odd g: zeta_g = -psi^{brev(k)}, the factors swap
+    u64& y = smA[S::pad(e)];
+    y = csub(mul_shoup(y, __ldg(f + o), __ldg(f + o + 1), q) + mul_shoup(smB[S::pad(e)], __ldg(f + 2 - o), __ldg(f + 3 - o), q),
+             two_q);
+  }
+  __syncthreads();
+  coset_inv_head_passes<S, LOGD>(x, smA, P);
+  constexpr int S0L = coset_inv_last_s0<S, LOGD>();
+  constexpr int RSL = S::kLogN - S0L;
+#pragma unroll
+  for (int hh = 0; hh < (S::R >> RSL); ++hh)
+#pragma unroll
+    for (int j = 0; j < (1 << RSL); ++j) store(inv_elem<S, S0L, RSL>(hh, j), csub(x[hh * (1 << RSL) + j], q));
+}
+
 }  // namespace he
+

@@ -172,6 +172,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc_multi(const __grid_con
 
 // ---------------------------------------------------------------- coset products
 //
+// Resident blocks per SM asked of the compiler: two for blocks of at most 256 threads (128
+// registers each), else one.
+template <int LOGN>
+constexpr int kCosetMinBlocks = NttShape<LOGN, 4>::T <= 256 ? 2 : 1;
+//
 // One block of S::T = N / 16 threads per polynomial (S = NttShape<log2 N, 4>); products with
 // D <= 32 take the register-blocked transforms of coset.cuh (S::kSmemWords words of shared
 // memory), larger D the shared-memory forms (2N words).
@@ -181,7 +186,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc_multi(const __grid_con
 // stage-tiled operand layout of the tensor-core multiply-accumulate (rows (2 Lb + c) G + g,
 // 2D slots per prime).
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_fwd_multi_t(const __grid_constant__ MultiTable T,
+__global__ void __launch_bounds__(NttShape<LOGN, 4>::T, kCosetMinBlocks<LOGN>) k_coset_fwd_multi_t(const __grid_constant__ MultiTable T,
                                                                           const __grid_constant__ Consts C) {
   using S = NttShape<LOGN, 4>;
   extern __shared__ u64 sm[];
@@ -208,6 +213,8 @@ __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_fwd_multi_t(cons
     case 3: coset_forward_fast<S, 3>(sm, P, load, store); break;
     case 4: coset_forward_fast<S, 4>(sm, P, load, store); break;
     case 5: coset_forward_fast<S, 5>(sm, P, load, store); break;
+    case 6: coset_forward_passes<S, 6>(sm, sm + S::kSmemWords, P, load, store); break;
+    case 7: coset_forward_passes<S, 7>(sm, sm + S::kSmemWords, P, load, store); break;
     default: {
       u64* A = sm;
       u64* B = sm + N;
@@ -224,7 +231,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_fwd_multi_t(cons
 // stages; c0 is re-masked (Algorithm 1 step 3) and, for compact products, kept only at the
 // decoded coefficients (Sec. 3.1.3).
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_inv_multi_t(const __grid_constant__ MultiTable T,
+__global__ void __launch_bounds__(NttShape<LOGN, 4>::T, kCosetMinBlocks<LOGN>) k_coset_inv_multi_t(const __grid_constant__ MultiTable T,
                                                                           const __grid_constant__ Consts C) {
   using S = NttShape<LOGN, 4>;
   extern __shared__ u64 sm[];
@@ -265,6 +272,8 @@ __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_inv_multi_t(cons
     case 3: coset_inverse_fast<S, 3>(sm, P, src, emit); break;
     case 4: coset_inverse_fast<S, 4>(sm, P, src, emit); break;
     case 5: coset_inverse_fast<S, 5>(sm, P, src, emit); break;
+    case 6: coset_inverse_passes<S, 6>(sm, sm + S::kSmemWords, P, src, emit); break;
+    case 7: coset_inverse_passes<S, 7>(sm, sm + S::kSmemWords, P, src, emit); break;
     default: {
       u64* A = sm;
       u64* B = sm + N;
@@ -283,7 +292,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_inv_multi_t(cons
 // prime) at once -- the G blocks of D coefficients of the tail transform are G different
 // weight blocks here -- and writes each one's 2D slots as bf16 digit tiles (mac_tc.cuh).
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_encode_t(const u64* W, u32 k, u32 n, Blk b, u32 nI,
+__global__ void __launch_bounds__(NttShape<LOGN, 4>::T, kCosetMinBlocks<LOGN>) k_coset_encode_t(const u64* W, u32 k, u32 n, Blk b, u32 nI,
                                                                        u32 nJ, u32 logD, u32 tcr, u64* pt,
                                                                        const __grid_constant__ Consts C) {
   using S = NttShape<LOGN, 4>;
@@ -298,7 +307,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_encode_t(const u
       reinterpret_cast<uint8_t*>(pt + (u64)item * (tcr ? tcr_weight_words(nI, nJ, C.L, S2) : tc_weight_words(nI, nJ, C.L, S2)));
   const u32 nk = b.n_b * b.k_b, nS = tc_stages(nJ);
   const u64 half_t = (C.tmask >> 1) + 1;
-  const bool fast = logD <= (u32)kCosetFastMaxLogD;
+  const bool fast = logD <= (u32)kCosetPassMaxLogD;  // the padded layout of the register forms
   for (u32 e = threadIdx.x; e < N; e += blockDim.x) {
     const u32 wb = first + (e >> logD), p = e & (D - 1);
     u64 v = 0;
@@ -337,19 +346,26 @@ __global__ void __launch_bounds__(NttShape<LOGN, 4>::T) k_coset_encode_t(const u
     case 3: coset_tail_regs<S, 3>(sm, P, store); break;
     case 4: coset_tail_regs<S, 4>(sm, P, store); break;
     case 5: coset_tail_regs<S, 5>(sm, P, store); break;
+    case 6: coset_tail_both<S, 6>(sm, sm + S::kSmemWords, P, store); break;
+    case 7: coset_tail_both<S, 7>(sm, sm + S::kSmemWords, P, store); break;
     default: coset_tail_fwd(sm, sm + N, LOGN, logD, P, store);
   }
 }
 
 #define HE_COSET_LOGNS(X) X(9) X(10) X(11) X(12) X(13)
 
-// Shared-memory bytes of the coset grids: the register-blocked forms' padded array where
-// every coset item of the table has D <= 32, else 2N words.
+// Shared-memory bytes of the coset grids: the most any coset item of the table needs.
+// Shared-memory words of a coset transform of one polynomial with cosets of 2^logD.
+__host__ __device__ inline u32 coset_words(u32 N, u32 logD) {
+  const u32 padded = N + (N >> 4);
+  return logD <= (u32)kCosetFastMaxLogD ? padded : logD <= (u32)kCosetPassMaxLogD ? 2 * padded : 2 * N;
+}
+
 size_t coset_smem(const Consts& C, const MultiTable& T) {
-  bool fast = true;
+  u32 words = 0;
   for (u32 i = 0; i < T.count; ++i)
-    if (T.it[i].coset && T.it[i].logD > (u32)kCosetFastMaxLogD) fast = false;
-  return (fast ? (size_t)C.N + (C.N >> 4) : 2 * (size_t)C.N) * sizeof(u64);
+    if (T.it[i].coset) words = max(words, coset_words(C.N, T.it[i].logD));
+  return (size_t)words * sizeof(u64);
 }
 
 // The row-major tensor-core multiply-accumulate (mac_tcr.cuh) over the items flagged tcr:
@@ -512,9 +528,9 @@ cudaError_t configure_multi_kernels() {
   set((const void*)k_mac_tc_multi, (int)kTcSmem);
   set((const void*)k_mac_tcr_multi, (int)kTcrSmem);
 #define HE_SET_COSET(LN)                                                                      \
-  set((const void*)k_coset_fwd_multi_t<LN>, 2 * (1 << LN) * (int)sizeof(u64));               \
-  set((const void*)k_coset_inv_multi_t<LN>, 2 * (1 << LN) * (int)sizeof(u64));               \
-  set((const void*)k_coset_encode_t<LN>, 2 * (1 << LN) * (int)sizeof(u64));
+  set((const void*)k_coset_fwd_multi_t<LN>, 2 * ((1 << LN) + (1 << LN) / 16) * (int)sizeof(u64)); \
+  set((const void*)k_coset_inv_multi_t<LN>, 2 * ((1 << LN) + (1 << LN) / 16) * (int)sizeof(u64)); \
+  set((const void*)k_coset_encode_t<LN>, 2 * ((1 << LN) + (1 << LN) / 16) * (int)sizeof(u64));
   HE_COSET_LOGNS(HE_SET_COSET)
 #undef HE_SET_COSET
   if (e == cudaSuccess)  // two blocks per SM need the largest shared-memory carveout
@@ -641,7 +657,7 @@ cudaError_t launch_coset_encode_weights(const Consts& C, const u64* W, u32 k, u3
       pt, 0, 8ull * batch * (tcr ? tcr_weight_words(nI, nJ, C.L, S2) : tc_weight_words(nI, nJ, C.L, S2)), st);
   if (e != cudaSuccess) return e;
   const u64 blocks = (u64)batch * C.L * (((u64)nI * nJ + G - 1) / G);
-  const size_t smem = (logD <= (u32)kCosetFastMaxLogD ? (size_t)C.N + (C.N >> 4) : 2 * (size_t)C.N) * sizeof(u64);
+  const size_t smem = (size_t)coset_words(C.N, logD) * sizeof(u64);
   HE_COSET_DISPATCH(k_coset_encode_t, (unsigned)blocks, smem, st, W, k, n, b, nI, nJ, logD, tcr, pt, C)
   return cudaGetLastError();
 }

@@ -118,8 +118,12 @@ struct NttShape {
 // One forward (Cooley-Tukey) pass over stages [S0, S0 + RS) on the R values in x:
 // x[h * 2^RS + j] is element e = blk * 2^(LOGN - S0) + off + j * t_last of group
 // g = tid + T * h, with t_last = 2^(LOGN - S0 - RS), blk = g / t_last, off = g % t_last.
-template <class S, int S0, int RS>
-__device__ __forceinline__ void fwd_pass_regs(u64 (&x)[S::R], const PrimeConsts& P) {
+// TAILG >= 0: the stages are those of the zero-padded length-2D transforms of G = 2^TAILG
+// cosets of length D (coset.cuh), half th: stage S0 + u is the transform's stage
+// sp = S0 + u - TAILG + 1, whose twiddle index is 2^sp + th 2^(sp - 1) + (the group's
+// index within its coset half) instead of the full transform's 2^(S0 + u) + (group index).
+template <class S, int S0, int RS, int TAILG = -1>
+__device__ __forceinline__ void fwd_pass_regs(u64 (&x)[S::R], const PrimeConsts& P, u32 th = 0) {
   constexpr int G = S::R >> RS;
   constexpr int TLAST_LOG = S::kLogN - S0 - RS;
   const u64 four_q = 2 * P.two_q, q = P.q;
@@ -133,7 +137,11 @@ __device__ __forceinline__ void fwd_pass_regs(u64 (&x)[S::R], const PrimeConsts&
 #pragma unroll
       for (int j = 0; j < (1 << RS); ++j) {
         if (j & span) continue;
-        const u32 widx = (1u << (S0 + u)) + (blk << u) + (j >> (RS - u));
+        u32 widx = (1u << (S0 + u)) + (blk << u) + (j >> (RS - u));
+        if constexpr (TAILG >= 0) {
+          const int sp = S0 + u - TAILG + 1;
+          widx = (1u << sp) + (th << (sp - 1)) + (widx & ((1u << (sp - 1)) - 1));
+        }
         const u64 w = __ldg(P.psi + widx), wsh = __ldg(P.psi_sh + widx);
         u64& A = x[h * (1 << RS) + j];
         u64& Bv = x[h * (1 << RS) + j + span];
@@ -289,8 +297,12 @@ __device__ __forceinline__ u32 inv_elem(int h, int j) {
   return ((g >> S0) << (S0 + RS)) + (g & ((1u << S0) - 1)) + ((u32)j << S0);
 }
 
-template <class S, int S0, int RS>
-__device__ __forceinline__ void inv_pass_regs(u64 (&x)[S::R], const PrimeConsts& P) {
+// TAILD >= 0: inverse stages (span 2^(S0 + u) < 2^TAILD) of the zero-padded length-2D
+// transforms of cosets of length D = 2^TAILD, half th: the transform's stage
+// sp = TAILD - (S0 + u), twiddle index 2^sp + th 2^(sp - 1) + (the group's index within its
+// coset half) instead of N / 2^(S0 + u + 1) + (group index).
+template <class S, int S0, int RS, int TAILD = -1>
+__device__ __forceinline__ void inv_pass_regs(u64 (&x)[S::R], const PrimeConsts& P, u32 th = 0) {
   constexpr int G = S::R >> RS;
   const u64 two_q = P.two_q, q = P.q;
 #pragma unroll
@@ -303,7 +315,12 @@ __device__ __forceinline__ void inv_pass_regs(u64 (&x)[S::R], const PrimeConsts&
 #pragma unroll
       for (int j = 0; j < (1 << RS); ++j) {
         if (j & span) continue;
-        const u32 widx = (u32)(S::N >> (S0 + u + 1)) + (blk << (RS - u - 1)) + (j >> (u + 1));
+        u32 widx = (u32)(S::N >> (S0 + u + 1)) + (blk << (RS - u - 1)) + (j >> (u + 1));
+        if constexpr (TAILD >= 0) {
+          const int sp = TAILD - (S0 + u);
+          const u32 gi = (blk << (RS - u - 1)) + (j >> (u + 1));
+          widx = (1u << sp) + (th << (sp - 1)) + (gi & ((1u << (sp - 1)) - 1));
+        }
         const u64 w = __ldg(P.ipsi + widx), wsh = __ldg(P.ipsi_sh + widx);
         u64& A = x[h * (1 << RS) + j];
         u64& Bv = x[h * (1 << RS) + j + span];
