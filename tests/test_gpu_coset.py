@@ -6,7 +6,8 @@ and q_l; the coset form reaches the same polynomials by the first log2 G NTT sta
 zero-padded length-2D transform per coset, the multiply-accumulate over 2D slots, the
 inverse and a fold by each coset's root.  Every output must equal the oracle's Pi_MatMul
 (and the integer engine's output) bit for bit.  The shapes cover the geometry's edges: the
-smallest D (8) and the largest (N/2, two cosets), ragged blocks, an odd number of k-blocks,
+smallest D (8) and the largest (N/2, two cosets), each transform form (D <= 32 per thread,
+64 and 128 as register passes, larger in shared memory), ragged blocks, an odd number of k-blocks,
 more than one exact accumulation round (> 128 k-blocks), many operand-row tiles, N = 4096
 and 8192, full and compact (Sec. 3.1.3) outputs, and same-shape batches.
 """
@@ -45,6 +46,8 @@ CASES = [  # (N, L, m, k, n, blocking); D = max(8, n_b k_b rounded up), G = N / 
     (4096, 2, 20, 264, 200, (4, 8, 16)),      # D 128, nJ 33 (odd), 13 weight blocks
     (4096, 2, 18, 520, 1040, (2, 4, 8)),      # D 32, nJ 130 (two rounds), 130 weight blocks, 2304 rows
     (4096, 2, 40, 96, 300, (2, 16, 128)),     # D 2048 = N/2: two cosets
+    (4096, 2, 24, 100, 160, (8, 8, 8)),       # D 64: register passes per coset half
+    (8192, 3, 30, 200, 90, (16, 16, 16)),     # D 256: shared-memory transforms
     (8192, 3, 24, 300, 100, (8, 4, 32)),      # D 128, nJ 75, N = 8192, three primes
     (8192, 3, 512, 64, 512, (512, 4, 4)),     # a BERT-large attention product: D 16, G 512, 1024 rows
 ]
