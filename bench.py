@@ -440,7 +440,7 @@ def kernel_source_hash():
     csrc = ROOT / "paper_2305_18396_gb300" / "csrc"
     h = hashlib.sha256((csrc / "mac.cuh").read_bytes())
     for f in ("mac_tc.cuh", "mac_tcr.cuh", "coset.cuh", "tcgen05.cuh", "async.cuh", "he_common.cuh", "multi.cu",
-              "capi.cu"):
+              "multi_items.cuh", "coset.cu", "capi.cu"):
         h.update((csrc / f).read_bytes())
     h.update((ROOT / "paper_2305_18396_gb300" / "workloads.py").read_bytes())
     return h.hexdigest()[:16]

@@ -15,7 +15,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 OUT = PKG / "_lib"
 LIB = OUT / "libhe_gb300.so"
-SOURCES = ["kernels.cu", "multi.cu", "share.cu", "tc_probe.cu", "capi.cu"]
+SOURCES = ["kernels.cu", "multi.cu", "coset.cu", "share.cu", "tc_probe.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", str(ROOT / "include")]

@@ -56,6 +56,7 @@ struct MultiTable {
 };
 
 cudaError_t configure_multi_kernels();
+cudaError_t configure_coset_kernels();  // coset.cu (called by configure_multi_kernels)
 u32 mac_tile_rows();
 u32 mac_tile_cols();
 cudaError_t launch_fwd_multi(const Consts& C, const MultiTable& T, u64 blocks, cudaStream_t st);
