@@ -125,3 +125,17 @@ def test_pipe_calls_reject_null_arguments_without_gpu(B):
     sz = ctypes.c_size_t()
     assert B.lib.he_pipe_workspace_bytes(None, 0, None, ctypes.byref(sz)) == B.HE_EINVAL
     assert B.lib.he_pipe_free(None) == B.HE_OK
+
+
+def test_cost_model_fills_ciphertexts_with_rows_in_the_coset_form(B):
+    """Coset products store 2D residues per weight block whatever m_b is, so the cost model
+    packs a whole sequence into each ciphertext (m_b = m) for the BERT-large products at
+    N = 8192 and keeps n_b k_b = N / m_b (every coefficient used)."""
+    from paper_2305_18396_gb300 import workloads
+
+    for p in workloads.bert_layer_products(distinct_heads=1, **workloads.BERT_LARGE):
+        mb, kb, nb = B.he_choose_blocking(8192, 3, p.m, p.k, p.n)
+        if p.m == 512:
+            assert mb == 512, (p.name, mb, kb, nb)
+        assert mb * kb * nb == 8192, (p.name, mb, kb, nb)
+        assert kb * nb <= 4096  # n_b k_b <= N/2: the coset form applies
