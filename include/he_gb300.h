@@ -29,7 +29,9 @@
  *   ciphertexts      [cnt][2][L][N]      (c0, c1), residues in [0, q_l), coefficient form
  *   input ciphertext  index Lb * nJ + J   (encrypts pi_B of block (J, Lb) of X^T)
  *   output ciphertext index Lb * nI + I   (share of block (Lb, I) of X W)
- *   encoded weights  opaque, he_sizes().pt_words words (NTT form, resident)
+ *   encoded weights  opaque, he_sizes().pt_words words (transform form, resident: the
+ *                    2D-slot coset transforms of the blocks under the default engine,
+ *                    N-slot NTTs under HE_MAC_TENSOR / HE_MAC_INTEGER)
  *   secret key       opaque, L * N words (NTT form)
  *   X, W, shares     [rows][cols] values in Z_t (only the low log2_t bits are read)
  */
@@ -86,7 +88,8 @@ typedef struct {
   uint64_t pts;             /* nI * nJ encoded weight plaintexts             */
   uint64_t in_words;        /* in_cts * 2 * L * N                            */
   uint64_t out_words;       /* out_cts * 2 * L * N                           */
-  uint64_t pt_words;        /* words of the opaque encoded-weight buffer     */
+  uint64_t pt_words;        /* words of the opaque encoded-weight buffer (its layout
+                               depends on the engine and, for coset products, on D)   */
   uint64_t packed_words;    /* in_cts * N: he_pack_input output              */
   uint64_t workspace_bytes; /* device workspace he_matmul needs              */
   uint64_t out_words_compact;       /* output words with HE_DROP_C0 (0 if k_b is not a power of two) */
